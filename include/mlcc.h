@@ -1,0 +1,207 @@
+/*
+ * libmlcc -- multilevel CC2 / CCSD ground state and Jacobian transformation on one GPU.
+ *
+ * Method: arXiv 2006.05226 (Folkestad, Kjonstad, Goletto, Koch), Sec. 2.1 and Appendix A.
+ * Given MO Cholesky vectors L^J_pq (Sec. 2.4, g_pqrs = sum_J L^J_pq L^J_rs), the Fock
+ * matrix F_pq of the reduced space (Sec. 2.3, Eq. eff_fock) and a partition of the
+ * orbitals into CCS-, CC2- and CCSD-active levels (Sec. 2.1), the library solves the
+ * MLCC ground-state equations Omega = 0 and finds the lowest eigenvalues of the Jacobian
+ * A = dOmega/dx with a Davidson solver built on sigma = A c.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All floating point is IEEE binary64 unless an entry point says otherwise.
+ *  - Matrices are row-major. Cholesky vectors are [n_chol][n_mo][n_mo], symmetric in pq.
+ *  - The caller's orbital order must list the n_occ occupied orbitals first.
+ *  - Inside a system the orbitals are re-ordered by level: occupied orbitals as
+ *    [CCSD, CC2-only, CCS-only], then virtual orbitals in the same level order, each
+ *    group in ascending caller index. mlcc_orbital_order() returns that permutation.
+ *    Every amplitude, residual and trial vector that crosses the ABI uses this internal
+ *    order:
+ *        singles  [n_vir][n_occ]                     (A, I): all virtuals x all occupied
+ *        doubles  [s_vir][s_occ][s_vir][s_occ]       (a, i, b, j): CC2-active orbitals,
+ *                 symmetric under (ai) <-> (bj); the CCSD-active orbitals are the
+ *                 leading t_occ / t_vir of each range.
+ *    A "vector" is singles followed by doubles, vector_len = n_vir n_occ + (s_vir s_occ)^2.
+ *    Doubles amplitudes x parameterise X2 = 1/2 sum x_aibj E_ai E_bj; doubles residuals
+ *    and sigma doubles are the coefficients in the same expansion (biorthonormal
+ *    projection), so sigma = d Omega / dh along (x + h c) in this storage.
+ *  - Three-level model: doubles with all four indices CCSD-active (P_T) obey the CCSD
+ *    equation built from P_T amplitudes only; every other CC2-active doubles element
+ *    obeys the CC2 equation g~ + eps x = 0 (Appendix A, Eq. mlcc2_omega2); singles and
+ *    energy use all doubles. No CCSD level gives MLCC2, CCSD = CC2 gives CCS/CCSD.
+ *  - F must be diagonal inside the occupied-occupied and virtual-virtual blocks of the
+ *    CC2-active orbitals (semicanonical basis, Sec. 2.1); otherwise MLCC_E_ARG.
+ *
+ * Memory and errors
+ * -----------------
+ *  - "_dev" pointers are device pointers on the context's device; "_host" pointers are
+ *    host pointers. The caller owns every buffer it passes; the library never frees
+ *    caller memory. A system allocates its own device workspace (its size is reported
+ *    by mlcc_system_info) and frees it in mlcc_system_destroy.
+ *  - Entry points return mlcc_status. No exception, abort or device trap crosses the
+ *    ABI. On error mlcc_last_error() returns a thread-local message.
+ *  - Work is issued on the context's stream (mlcc_ctx_stream); entry points that return
+ *    results to host memory synchronise that stream, device-output entry points do not.
+ */
+#ifndef MLCC_H
+#define MLCC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MLCC_OK = 0,
+  MLCC_E_ARG = -1,          /* invalid argument, size or partition               */
+  MLCC_E_OOM = -2,          /* device allocation failed                          */
+  MLCC_E_GS_NOCONV = -3,    /* ground state not converged in max_gs_iter         */
+  MLCC_E_ES_NOCONV = -4,    /* excited states not converged in max_es_iter       */
+  MLCC_E_COMPLEX_ROOT = -5, /* a wanted Ritz value has a non-zero imaginary part */
+  MLCC_E_NAN = -6,          /* NaN or Inf met in a residual or sigma             */
+  MLCC_E_CUDA = -8,         /* a CUDA runtime call failed                        */
+  MLCC_E_STATE = -9         /* call order violated (e.g. sigma before prepare)   */
+} mlcc_status;
+
+typedef enum {
+  MLCC_FP64 = 0,  /* every contraction in binary64                                  */
+  MLCC_BF16 = 1   /* Cholesky-rank doubles contractions on tcgen05 tensor cores with
+                     bfloat16 operands and fp32 accumulation; the rest in binary64   */
+} mlcc_precision;
+
+typedef enum { MLCC_LEVEL_CCS = 0, MLCC_LEVEL_CC2 = 1, MLCC_LEVEL_CCSD = 2 } mlcc_level;
+
+typedef struct mlcc_ctx mlcc_ctx;
+typedef struct mlcc_system mlcc_system;
+
+typedef struct {
+  int32_t n_mo;          /* orbitals in the reduced space (occupied first)            */
+  int32_t n_occ;         /* doubly occupied orbitals                                  */
+  int32_t n_chol;        /* Cholesky vectors N_J                                      */
+  const int8_t* level;   /* host [n_mo], mlcc_level per orbital; CCSD must be a
+                            subset of CC2 (nested active spaces, Sec. 2.1)            */
+} mlcc_problem;
+
+typedef struct {
+  int32_t n_occ, n_vir;      /* N_o, N_v                                  */
+  int32_t s_occ, s_vir;      /* CC2-active (includes the CCSD-active)     */
+  int32_t t_occ, t_vir;      /* CCSD-active                               */
+  int64_t n_singles;         /* n_vir * n_occ                             */
+  int64_t n_doubles;         /* (s_vir * s_occ)^2                         */
+  int64_t vector_len;        /* n_singles + n_doubles                     */
+  int64_t workspace_bytes;   /* device memory held by the system          */
+} mlcc_dims;
+
+typedef struct {
+  int32_t n_roots;        /* excitation energies wanted                               */
+  int32_t max_gs_iter;    /* ground-state iterations                                  */
+  int32_t max_es_iter;    /* Davidson iterations                                      */
+  int32_t diis_dim;       /* DIIS history length                                      */
+  int32_t max_subspace;   /* Davidson basis size before collapse (0: 8 n_roots)       */
+  int32_t precision;      /* mlcc_precision of sigma inside the Davidson loop          */
+  int32_t refine_fp64;    /* with MLCC_BF16: continue the Davidson loop with binary64
+                             sigma from the converged low-precision vectors            */
+  int32_t _pad;
+  double gs_tol;          /* |Omega|_2 threshold                                      */
+  double gs_energy_tol;   /* |dE| threshold between iterations                        */
+  double es_res_tol;      /* |A R - w R|_2 threshold per root                          */
+  double es_omega_tol;    /* |dw| threshold per root                                   */
+  double lowp_res_tol;    /* residual threshold of the low-precision phase            */
+} mlcc_options;
+
+typedef struct {
+  double e_hf;            /* sum_I (h_II + F_II), reduced-space reference energy      */
+  double e_corr;          /* Eq. mlcc_energy at convergence                           */
+  double omega_norm;      /* final |Omega|_2 (singles and CCSD doubles)               */
+  int32_t iterations;
+  int32_t converged;
+} mlcc_gs_info;
+
+typedef struct {
+  int32_t iterations;     /* Davidson iterations (both phases)                         */
+  int32_t n_sigma;        /* sigma-vectors evaluated                                  */
+  int32_t n_sigma_lowp;   /* of which in low precision                                */
+  int32_t converged;
+  int32_t complex_pair;
+  int32_t _pad;
+} mlcc_es_info;
+
+/* ---- context ------------------------------------------------------------------ */
+/* Defaults: 3 roots, 200 GS / 200 ES iterations, DIIS 8, FP64, gs_tol 1e-11,
+   gs_energy_tol 1e-12, es_res_tol 1e-8, es_omega_tol 1e-11, lowp_res_tol 1e-4. */
+void mlcc_default_options(mlcc_options* opt);
+/* Creates a context on CUDA device `device` with its own non-blocking stream. */
+mlcc_status mlcc_ctx_create(int device, mlcc_ctx** out);
+void mlcc_ctx_destroy(mlcc_ctx* ctx);
+/* The cudaStream_t (as void*) that every entry point of this context launches on. */
+void* mlcc_ctx_stream(mlcc_ctx* ctx);
+const char* mlcc_last_error(void);
+/* Kernel timing: when enabled, the library records CUDA events around each launch of
+   the named kernel family ("rank_gemm": the Cholesky-rank doubles GEMMs) on the
+   context stream; mlcc_kernel_time returns launches, summed milliseconds and summed
+   algorithmic flops since the last reset (it synchronises the stream). */
+void mlcc_kernel_timing(mlcc_ctx* ctx, int enable);
+mlcc_status mlcc_kernel_time(mlcc_ctx* ctx, const char* family, int64_t* launches,
+                             double* total_ms, double* total_flop);
+
+/* ---- system -------------------------------------------------------------------- */
+/* Takes device copies of chol (Sec. 2.4 MO Cholesky vectors) and fock (Eq. eff_fock),
+   re-orders orbitals by level, recovers the one-electron matrix
+   h = F - sum_i (2 g_pqii - g_piiq) (Eq. eff_fock, environment absorbed in h) and
+   allocates the workspace. chol_dev / fock_dev may be freed after the call returns. */
+mlcc_status mlcc_system_create(mlcc_ctx* ctx, const mlcc_problem* prob,
+                               const double* chol_dev, const double* fock_dev,
+                               mlcc_system** out);
+void mlcc_system_destroy(mlcc_system* sys);
+mlcc_status mlcc_system_info(const mlcc_system* sys, mlcc_dims* dims);
+/* perm_host[k] = caller index of internal orbital k, k < n_mo. */
+mlcc_status mlcc_orbital_order(const mlcc_system* sys, int32_t* perm_host);
+
+/* ---- steps of the hot path (device buffers, internal order, no host sync) ------- */
+/* T1-dressing (Sec. 2.1 "Cholesky vectors in the X1 basis", Appendix A):
+   Lt^J = (1 - t1) L^J (1 + t1) for every J. t1_dev [n_vir][n_occ];
+   lt_dev [n_chol][n_mo][n_mo] (not symmetric). */
+mlcc_status mlcc_t1_transform(mlcc_system* sys, const double* t1_dev, double* lt_dev);
+/* Fock matrix in the X1 basis (Appendix A, with the one-electron term h~):
+   F~ = h~ + sum_J [2 Lt^J (sum_I Lt^J_II) - Lt^J_{:,occ} Lt^J_{occ,:}]; f_dev [n_mo][n_mo]. */
+mlcc_status mlcc_fock_t1(mlcc_system* sys, const double* t1_dev, double* f_dev);
+/* Ground-state residual with t1 and all doubles as independent inputs (Appendix A:
+   Eq. mlcc2_omega_codable for the singles, the analytic CC2 equation on P_S, the MLCCSD
+   doubles residual on P_T) and the correlation energy of Eq. mlcc_energy.
+   om1_dev [n_singles], om2_dev [n_doubles]; energy_dev: one double (device). */
+mlcc_status mlcc_omega(mlcc_system* sys, const double* t1_dev, const double* x2_dev,
+                       double* om1_dev, double* om2_dev, double* energy_dev);
+/* DIIS-accelerated quasi-Newton solve of Omega = 0 (Sec. 2.1). Outputs the converged
+   amplitudes (device) and fills info (host). Keeps them as the Jacobian ground state. */
+mlcc_status mlcc_ground_state(mlcc_system* sys, const mlcc_options* opt,
+                              double* t1_dev, double* x2_dev, mlcc_gs_info* info);
+/* Builds everything sigma needs at the ground state (t1, x2): dressed vectors, F~,
+   the MLCC2 intermediates X_Ji and Y_aB (Appendix A) and the CCSD-block value tensors.
+   Must precede mlcc_sigma; mlcc_ground_state calls it on success. */
+mlcc_status mlcc_jacobian_prepare(mlcc_system* sys, const double* t1_dev,
+                                  const double* x2_dev);
+/* sigma = A c for n_vec trial vectors (Appendix A, Jacobian transformation):
+   c_dev, sigma_dev [n_vec][vector_len]. precision: mlcc_precision. */
+mlcc_status mlcc_sigma(mlcc_system* sys, int32_t n_vec, const double* c_dev,
+                       double* sigma_dev, int32_t precision);
+/* Davidson solve for the lowest opt->n_roots eigenpairs of A at the prepared ground
+   state. omega_host [n_roots] (Hartree, ascending); r_dev [n_roots][vector_len]
+   (unit 2-norm, largest-magnitude element positive) or NULL; info (host). */
+mlcc_status mlcc_excited_states(mlcc_system* sys, const mlcc_options* opt,
+                                double* omega_host, double* r_dev, mlcc_es_info* info);
+
+/* ---- whole solve from host memory ------------------------------------------------ */
+/* Copies chol_host / fock_host to the device, runs ground state and excited states and
+   returns energies (host). t1_host [n_vir][n_occ] may be NULL. */
+mlcc_status mlcc_solve(mlcc_ctx* ctx, const mlcc_problem* prob, const double* chol_host,
+                       const double* fock_host, const mlcc_options* opt,
+                       mlcc_gs_info* gs, double* omega_host, mlcc_es_info* es,
+                       double* t1_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLCC_H */

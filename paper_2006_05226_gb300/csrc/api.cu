@@ -1,0 +1,444 @@
+// C ABI of libmlcc (declared in include/mlcc.h): argument validation, system set-up
+// (orbital re-ordering, recovery of the one-electron matrix of Sec. 2.3) and the
+// exception-to-status boundary.
+#include "system.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+namespace mlcc {
+const char* last_error_cstr();
+mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out, double* x2_out,
+                         mlcc_gs_info* info);
+mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omega_host,
+                           double* r_out, mlcc_es_info* info);
+
+namespace {
+__global__ void k_reorder(const double* src, const int* perm, int n, int64_t batch, double* dst) {
+  const int64_t nn = int64_t(n) * n, total = nn * batch;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t J = t / nn, r = t - J * nn;
+    const int p = int(r / n), q = int(r - int64_t(p) * n);
+    dst[t] = src[J * nn + int64_t(perm[p]) * n + perm[q]];
+  }
+}
+// max_J,p,q |X[J][p][q] - X[J][q][p]| as an order-preserving integer (values >= 0)
+__global__ void k_asym(const double* X, int n, int64_t batch, unsigned long long* out) {
+  const int64_t nn = int64_t(n) * n, total = nn * batch;
+  double m = 0.0;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t J = t / nn, r = t - J * nn;
+    const int p = int(r / n), q = int(r - int64_t(p) * n);
+    const double d = fabs(X[t] - X[J * nn + int64_t(q) * n + p]);
+    m = (d > m || d != d) ? (d != d ? 1e308 : d) : m;
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+__global__ void k_diag(const double* F, int n, double* eps) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) eps[p] = F[int64_t(p) * n + p];
+}
+}  // namespace
+
+template <class F>
+static mlcc_status guard(F&& f) {
+  try {
+    return f();
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.status;
+  } catch (const std::exception& e) {
+    set_last_error(e.what());
+    return MLCC_E_CUDA;
+  } catch (...) {
+    set_last_error("unknown error");
+    return MLCC_E_CUDA;
+  }
+}
+
+static void setup_system(mlcc_system* S, const mlcc_problem* P, const double* chol, const double* fock) {
+  cudaStream_t s = S->ctx->stream;
+  const int n = P->n_mo, no = P->n_occ, nj = P->n_chol;
+  S->n = n;
+  S->no = no;
+  S->nv = n - no;
+  S->nj = nj;
+  // level-ordered permutation: occupied [CCSD, CC2-only, CCS], then virtual likewise
+  S->perm.clear();
+  int cnt[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  for (int part = 0; part < 2; ++part) {
+    const int lo = part == 0 ? 0 : no, hi = part == 0 ? no : n;
+    for (int lev = 2; lev >= 0; --lev)
+      for (int p = lo; p < hi; ++p)
+        if (P->level[p] == lev) {
+          S->perm.push_back(p);
+          ++cnt[part][lev];
+        }
+  }
+  S->to = cnt[0][2];
+  S->tv = cnt[1][2];
+  S->so = cnt[0][2] + cnt[0][1];
+  S->sv = cnt[1][2] + cnt[1][1];
+  S->dS = int64_t(S->sv) * S->so;
+  S->nd = S->dS * S->dS;
+  const int64_t nn = int64_t(n) * n, dS = S->dS;
+  // persistent buffers
+  const size_t per = size_t(nj) * nn * 2 + 3 * size_t(nn) + size_t(n) + 3 * size_t(nj) * dS +
+                     size_t(S->nd) * 2 + size_t(dS) + size_t(S->nv) * no;
+  S->persist.reserve(per * 8 + 64 * 256);
+  S->L = S->persist.get<double>(size_t(nj) * nn);
+  S->Lt = S->persist.get<double>(size_t(nj) * nn);
+  S->h = S->persist.get<double>(nn);
+  S->ht = S->persist.get<double>(nn);
+  S->Ft = S->persist.get<double>(nn);
+  S->eps = S->persist.get<double>(n);
+  S->Lai = S->persist.get<double>(size_t(nj) * dS);
+  S->Lov = S->persist.get<double>(size_t(nj) * dS);
+  S->Z = S->persist.get<double>(size_t(nj) * dS);
+  S->u = S->persist.get<double>(size_t(S->nd));
+  S->x2gs = S->persist.get<double>(size_t(S->nd));
+  S->Fov = S->persist.get<double>(size_t(dS));
+  S->t1gs = S->persist.get<double>(size_t(S->nv) * no);
+  // scratch: enough for sigma (dLt, three doubles-sized arrays, two [nj][dS]) plus GEMM
+  // partials and the einsum engine's permuted operands
+  const int64_t tl = int64_t(S->tv) * S->to * S->tv * S->to;
+  const size_t ws = size_t(nj) * nn + 4 * size_t(nn) + 3 * size_t(S->nd) + 4 * size_t(nj) * dS +
+                    4 * size_t(dS) + size_t(nj) * (no * no + 2) + 64 * size_t(std::max<int64_t>(tl, 1)) +
+                    size_t(S->tv) * S->tv * S->tv * S->tv * 4 +
+                    size_t(nj) * (size_t(S->tv + S->to) * (S->tv + S->to)) * 4 +
+                    (size_t(1) << 27);
+  S->ws.reserve(ws * 8);
+  S->workspace_bytes = int64_t(S->persist.capacity() + S->ws.capacity());
+  // re-ordered copies of L and F
+  int* dperm = S->ws.get<int>(size_t(n));
+  MLCC_CUDA(cudaMemcpyAsync(dperm, S->perm.data(), size_t(n) * 4, cudaMemcpyHostToDevice, s));
+  {
+    const int64_t total = nn * nj;
+    const int blocks = int(std::min<int64_t>((total + 255) / 256, 16384));
+    k_reorder<<<blocks, 256, 0, s>>>(chol, dperm, n, nj, S->L);
+    MLCC_CHECK_LAUNCH();
+    k_reorder<<<int(std::min<int64_t>((nn + 255) / 256, 16384)), 256, 0, s>>>(fock, dperm, n, 1, S->ht);
+    MLCC_CHECK_LAUNCH();
+  }
+  // checks: symmetric L and F, semicanonical CC2-active blocks
+  unsigned long long* asym = S->ws.get<unsigned long long>(1);
+  MLCC_CUDA(cudaMemsetAsync(asym, 0, 8, s));
+  k_asym<<<1024, 256, 0, s>>>(S->L, n, nj, asym);
+  MLCC_CHECK_LAUNCH();
+  unsigned long long ah = 0;
+  MLCC_CUDA(cudaMemcpyAsync(&ah, asym, 8, cudaMemcpyDeviceToHost, s));
+  std::vector<double> Fh(static_cast<size_t>(nn));
+  MLCC_CUDA(cudaMemcpyAsync(Fh.data(), S->ht, size_t(nn) * 8, cudaMemcpyDeviceToHost, s));
+  MLCC_CUDA(cudaStreamSynchronize(s));
+  double amax;
+  std::memcpy(&amax, &ah, 8);
+  if (!(amax <= 1e-10)) throw Error(MLCC_E_ARG, "Cholesky vectors are not symmetric in pq (max asymmetry " + std::to_string(amax) + ")");
+  double fmax = 0.0;
+  for (int p = 0; p < n; ++p) fmax = std::max(fmax, std::fabs(Fh[size_t(p) * n + p]));
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < n; ++q) {
+      const double a = Fh[size_t(p) * n + q], b = Fh[size_t(q) * n + p];
+      if (!std::isfinite(a)) throw Error(MLCC_E_NAN, "Fock matrix has NaN or Inf");
+      if (std::fabs(a - b) > 1e-10 * std::max(1.0, fmax)) throw Error(MLCC_E_ARG, "Fock matrix is not symmetric");
+    }
+  auto check_block = [&](int lo, int hi) {
+    for (int p = lo; p < hi; ++p)
+      for (int q = lo; q < hi; ++q)
+        if (p != q && std::fabs(Fh[size_t(p) * n + q]) > 1e-10 * std::max(1.0, fmax))
+          throw Error(MLCC_E_ARG, "Fock matrix is not diagonal in the CC2-active occupied-occupied or "
+                                  "virtual-virtual block (semicanonical basis required, Sec. 2.1)");
+  };
+  if (S->nd > 0 && S->nd != int64_t(S->tv) * S->to * S->tv * S->to) {
+    check_block(0, S->so);
+    check_block(no, no + S->sv);
+  }
+  S->eps_host.resize(n);
+  for (int p = 0; p < n; ++p) S->eps_host[p] = Fh[size_t(p) * n + p];
+  k_diag<<<(n + 255) / 256, 256, 0, s>>>(S->ht, n, S->eps);
+  MLCC_CHECK_LAUNCH();
+  // h = F - sum_J [2 L^J (sum_i L^J_ii) - L^J[:, i] L^J[i, :]]   (Eq. eff_fock)
+  MLCC_CUDA(cudaMemcpyAsync(S->h, S->ht, size_t(nn) * 8, cudaMemcpyDeviceToDevice, s));
+  {
+    // reuse build_fock with the sign flipped: F(h=0) then h = F - F(h=0)
+    Scope sc(S->ws);
+    double* zero = S->ws.get<double>(size_t(nn));
+    double* G = S->ws.get<double>(size_t(nn));
+    fill(zero, nn, 0.0, s);
+    build_fock(S, zero, S->L, G);
+    axpby(S->h, G, nn, -1.0, 1.0, s);
+  }
+  MLCC_CUDA(cudaStreamSynchronize(s));
+  S->prepared = false;
+}
+
+}  // namespace mlcc
+
+using namespace mlcc;
+
+extern "C" {
+
+void mlcc_default_options(mlcc_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->n_roots = 3;
+  o->max_gs_iter = 200;
+  o->max_es_iter = 200;
+  o->diis_dim = 8;
+  o->max_subspace = 0;
+  o->precision = MLCC_FP64;
+  o->refine_fp64 = 1;
+  o->gs_tol = 1e-11;
+  o->gs_energy_tol = 1e-12;
+  o->es_res_tol = 1e-8;
+  o->es_omega_tol = 1e-11;
+  o->lowp_res_tol = 1e-4;
+}
+
+const char* mlcc_last_error(void) { return last_error_cstr(); }
+
+mlcc_status mlcc_ctx_create(int device, mlcc_ctx** out) {
+  return guard([&] {
+    MLCC_REQUIRE(out != nullptr, "mlcc_ctx_create: out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    MLCC_CUDA(cudaGetDeviceCount(&ndev));
+    MLCC_REQUIRE(device >= 0 && device < ndev, "mlcc_ctx_create: no such CUDA device");
+    MLCC_CUDA(cudaSetDevice(device));
+    auto* c = new mlcc_ctx();
+    c->device = device;
+    MLCC_CUDA(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device));
+    MLCC_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    *out = c;
+    return MLCC_OK;
+  });
+}
+
+void mlcc_ctx_destroy(mlcc_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  ctx->timer.reset();
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+void* mlcc_ctx_stream(mlcc_ctx* ctx) { return ctx ? static_cast<void*>(ctx->stream) : nullptr; }
+
+void mlcc_kernel_timing(mlcc_ctx* ctx, int enable) {
+  if (!ctx) return;
+  ctx->timer.reset();
+  ctx->timer.enabled = enable != 0;
+}
+
+mlcc_status mlcc_kernel_time(mlcc_ctx* ctx, const char* family, int64_t* launches,
+                             double* total_ms, double* total_flop) {
+  return guard([&] {
+    MLCC_REQUIRE(ctx && family, "mlcc_kernel_time: NULL argument");
+    MLCC_CUDA(cudaStreamSynchronize(ctx->stream));
+    int64_t n = 0;
+    double ms = 0.0, fl = 0.0;
+    auto it = ctx->timer.recs.find(family);
+    if (it != ctx->timer.recs.end()) {
+      for (auto& r : it->second) {
+        float t = 0.f;
+        MLCC_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+        ms += t;
+        fl += r.flop;
+        ++n;
+      }
+    }
+    if (launches) *launches = n;
+    if (total_ms) *total_ms = ms;
+    if (total_flop) *total_flop = fl;
+    return MLCC_OK;
+  });
+}
+
+mlcc_status mlcc_system_create(mlcc_ctx* ctx, const mlcc_problem* prob, const double* chol_dev,
+                               const double* fock_dev, mlcc_system** out) {
+  return guard([&] {
+    MLCC_REQUIRE(ctx && prob && out && chol_dev && fock_dev, "mlcc_system_create: NULL argument");
+    *out = nullptr;
+    MLCC_REQUIRE(prob->level != nullptr, "mlcc_system_create: level is NULL");
+    MLCC_REQUIRE(prob->n_mo > 0 && prob->n_occ > 0 && prob->n_occ < prob->n_mo,
+                 "mlcc_system_create: need 0 < n_occ < n_mo");
+    MLCC_REQUIRE(prob->n_chol > 0, "mlcc_system_create: n_chol must be positive");
+    for (int p = 0; p < prob->n_mo; ++p)
+      MLCC_REQUIRE(prob->level[p] >= 0 && prob->level[p] <= 2, "mlcc_system_create: level must be 0, 1 or 2");
+    MLCC_CUDA(cudaSetDevice(ctx->device));
+    auto* S = new mlcc_system();
+    S->ctx = ctx;
+    try {
+      setup_system(S, prob, chol_dev, fock_dev);
+    } catch (...) {
+      delete S;
+      throw;
+    }
+    *out = S;
+    return MLCC_OK;
+  });
+}
+
+void mlcc_system_destroy(mlcc_system* sys) {
+  if (!sys) return;
+  cudaSetDevice(sys->ctx->device);
+  cudaStreamSynchronize(sys->ctx->stream);
+  ccsd_cache_free(sys);
+  delete sys;
+}
+
+mlcc_status mlcc_system_info(const mlcc_system* S, mlcc_dims* d) {
+  return guard([&] {
+    MLCC_REQUIRE(S && d, "mlcc_system_info: NULL argument");
+    d->n_occ = S->no;
+    d->n_vir = S->nv;
+    d->s_occ = S->so;
+    d->s_vir = S->sv;
+    d->t_occ = S->to;
+    d->t_vir = S->tv;
+    d->n_singles = int64_t(S->nv) * S->no;
+    d->n_doubles = S->nd;
+    d->vector_len = d->n_singles + d->n_doubles;
+    d->workspace_bytes = S->workspace_bytes;
+    return MLCC_OK;
+  });
+}
+
+mlcc_status mlcc_orbital_order(const mlcc_system* S, int32_t* perm) {
+  return guard([&] {
+    MLCC_REQUIRE(S && perm, "mlcc_orbital_order: NULL argument");
+    std::copy(S->perm.begin(), S->perm.end(), perm);
+    return MLCC_OK;
+  });
+}
+
+mlcc_status mlcc_t1_transform(mlcc_system* S, const double* t1, double* lt) {
+  return guard([&] {
+    MLCC_REQUIRE(S && t1 && lt, "mlcc_t1_transform: NULL argument");
+    MLCC_CUDA(cudaSetDevice(S->ctx->device));
+    S->prepared = false;
+    dress(S, t1, lt, nullptr);
+    return MLCC_OK;
+  });
+}
+
+mlcc_status mlcc_fock_t1(mlcc_system* S, const double* t1, double* f) {
+  return guard([&] {
+    MLCC_REQUIRE(S && t1 && f, "mlcc_fock_t1: NULL argument");
+    MLCC_CUDA(cudaSetDevice(S->ctx->device));
+    S->prepared = false;
+    dress(S, t1, S->Lt, S->ht);
+    build_fock(S, S->ht, S->Lt, f);
+    return MLCC_OK;
+  });
+}
+
+mlcc_status mlcc_omega(mlcc_system* S, const double* t1, const double* x2, double* om1,
+                       double* om2, double* energy) {
+  return guard([&] {
+    MLCC_REQUIRE(S && t1 && om1, "mlcc_omega: NULL argument");
+    MLCC_REQUIRE(S->nd == 0 || (x2 && om2), "mlcc_omega: doubles buffers required");
+    MLCC_CUDA(cudaSetDevice(S->ctx->device));
+    omega_eval(S, t1, x2, false, nullptr, nullptr, om1, om2, energy);
+    return MLCC_OK;
+  });
+}
+
+mlcc_status mlcc_ground_state(mlcc_system* S, const mlcc_options* opt, double* t1, double* x2,
+                              mlcc_gs_info* info) {
+  return guard([&] {
+    MLCC_REQUIRE(S && opt && t1, "mlcc_ground_state: NULL argument");
+    MLCC_REQUIRE(S->nd == 0 || x2, "mlcc_ground_state: x2 buffer required");
+    MLCC_REQUIRE(opt->max_gs_iter >= 1 && opt->diis_dim >= 1, "mlcc_ground_state: bad options");
+    MLCC_CUDA(cudaSetDevice(S->ctx->device));
+    mlcc_gs_info local{};
+    mlcc_status st = ground_state(S, opt, t1, x2, info ? info : &local);
+    if (info) {
+      double e_hf = 0.0;
+      std::vector<double> h(static_cast<size_t>(S->n) * S->n);
+      copy_d2h(h.data(), S->h, int64_t(S->n) * S->n, S->ctx->stream);
+      for (int i = 0; i < S->no; ++i) e_hf += h[size_t(i) * S->n + i] + S->eps_host[i];
+      info->e_hf = e_hf;
+    }
+    if (st == MLCC_E_GS_NOCONV) set_last_error("ground state did not converge");
+    return st;
+  });
+}
+
+mlcc_status mlcc_jacobian_prepare(mlcc_system* S, const double* t1, const double* x2) {
+  return guard([&] {
+    MLCC_REQUIRE(S && t1 && (S->nd == 0 || x2), "mlcc_jacobian_prepare: NULL argument");
+    MLCC_CUDA(cudaSetDevice(S->ctx->device));
+    jacobian_prepare(S, t1, x2);
+    return MLCC_OK;
+  });
+}
+
+mlcc_status mlcc_sigma(mlcc_system* S, int32_t n_vec, const double* c, double* sigma,
+                       int32_t precision) {
+  return guard([&] {
+    MLCC_REQUIRE(S && c && sigma, "mlcc_sigma: NULL argument");
+    MLCC_REQUIRE(n_vec >= 0, "mlcc_sigma: n_vec < 0");
+    MLCC_REQUIRE(precision == MLCC_FP64 || precision == MLCC_BF16, "mlcc_sigma: unknown precision");
+    MLCC_CUDA(cudaSetDevice(S->ctx->device));
+    const int64_t len = int64_t(S->nv) * S->no + S->nd;
+    for (int k = 0; k < n_vec; ++k) sigma_eval(S, c + k * len, sigma + k * len, precision);
+    return MLCC_OK;
+  });
+}
+
+mlcc_status mlcc_excited_states(mlcc_system* S, const mlcc_options* opt, double* omega,
+                                double* r, mlcc_es_info* info) {
+  return guard([&] {
+    MLCC_REQUIRE(S && opt && omega, "mlcc_excited_states: NULL argument");
+    MLCC_CUDA(cudaSetDevice(S->ctx->device));
+    mlcc_status st = excited_states(S, opt, omega, r, info);
+    if (st == MLCC_E_ES_NOCONV) set_last_error("excited states did not converge");
+    if (st == MLCC_E_COMPLEX_ROOT) set_last_error("a wanted Ritz value is complex");
+    return st;
+  });
+}
+
+mlcc_status mlcc_solve(mlcc_ctx* ctx, const mlcc_problem* prob, const double* chol_host,
+                       const double* fock_host, const mlcc_options* opt, mlcc_gs_info* gs,
+                       double* omega, mlcc_es_info* es, double* t1_host) {
+  return guard([&] {
+    MLCC_REQUIRE(ctx && prob && chol_host && fock_host && opt && omega, "mlcc_solve: NULL argument");
+    MLCC_CUDA(cudaSetDevice(ctx->device));
+    const int64_t nn = int64_t(prob->n_mo) * prob->n_mo;
+    double *dL = nullptr, *dF = nullptr;
+    MLCC_CUDA(cudaMalloc(&dL, size_t(nn) * prob->n_chol * 8));
+    struct Free {
+      double** a; double** b;
+      ~Free() { if (*a) cudaFree(*a); if (*b) cudaFree(*b); }
+    } fr{&dL, &dF};
+    MLCC_CUDA(cudaMalloc(&dF, size_t(nn) * 8));
+    MLCC_CUDA(cudaMemcpyAsync(dL, chol_host, size_t(nn) * prob->n_chol * 8, cudaMemcpyHostToDevice, ctx->stream));
+    MLCC_CUDA(cudaMemcpyAsync(dF, fock_host, size_t(nn) * 8, cudaMemcpyHostToDevice, ctx->stream));
+    mlcc_system* S = nullptr;
+    mlcc_status st = mlcc_system_create(ctx, prob, dL, dF, &S);
+    if (st != MLCC_OK) return st;
+    struct Sys { mlcc_system* s; ~Sys() { mlcc_system_destroy(s); } } sg{S};
+    cudaFree(dL); dL = nullptr;
+    cudaFree(dF); dF = nullptr;
+    double *t1 = nullptr, *x2 = nullptr;
+    MLCC_CUDA(cudaMalloc(&t1, size_t(S->nv) * S->no * 8 + 8));
+    MLCC_CUDA(cudaMalloc(&x2, size_t(S->nd) * 8 + 8));
+    struct Free2 { double* a; double* b; ~Free2() { cudaFree(a); cudaFree(b); } } f2{t1, x2};
+    mlcc_gs_info gi{};
+    st = mlcc_ground_state(S, opt, t1, x2, &gi);
+    if (gs) *gs = gi;
+    if (st != MLCC_OK) return st;
+    if (t1_host) copy_d2h(t1_host, t1, int64_t(S->nv) * S->no, ctx->stream);
+    mlcc_es_info ei{};
+    st = mlcc_excited_states(S, opt, omega, nullptr, &ei);
+    if (es) *es = ei;
+    return st;
+  });
+}
+
+}  // extern "C"

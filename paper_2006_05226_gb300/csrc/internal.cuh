@@ -1,0 +1,136 @@
+// Internal declarations shared by the libmlcc translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+#include <map>
+#include <stdexcept>
+
+#include "../../include/mlcc.h"
+
+namespace mlcc {
+
+// ---------------------------------------------------------------------------------
+// Errors: every failure becomes an mlcc::Error caught at the ABI boundary.
+struct Error : std::runtime_error {
+  mlcc_status status;
+  Error(mlcc_status s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+void set_last_error(const std::string& msg);
+
+#define MLCC_CUDA(call)                                                              \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      throw ::mlcc::Error(e_ == cudaErrorMemoryAllocation ? MLCC_E_OOM : MLCC_E_CUDA, \
+                          std::string(#call) + ": " + cudaGetErrorString(e_));       \
+    }                                                                                \
+  } while (0)
+#define MLCC_CHECK_LAUNCH() MLCC_CUDA(cudaGetLastError())
+#define MLCC_REQUIRE(cond, msg)                                      \
+  do {                                                               \
+    if (!(cond)) throw ::mlcc::Error(MLCC_E_ARG, std::string(msg));  \
+  } while (0)
+
+// ---------------------------------------------------------------------------------
+// Device arena: one cudaMalloc, bump allocation with marks. Allocations are 256-byte
+// aligned so every TMA / vector access starts on an aligned boundary.
+class Arena {
+ public:
+  Arena() = default;
+  ~Arena();
+  void reserve(size_t bytes);
+  void* alloc(size_t bytes);
+  template <class T> T* get(size_t n) { return static_cast<T*>(alloc(n * sizeof(T))); }
+  size_t mark() const { return top_; }
+  void release(size_t m) { top_ = m; }
+  size_t capacity() const { return cap_; }
+  size_t high_water() const { return hw_; }
+ private:
+  char* base_ = nullptr;
+  size_t cap_ = 0, top_ = 0, hw_ = 0;
+};
+
+// RAII scratch scope on an arena.
+struct Scope {
+  Arena& a;
+  size_t m;
+  explicit Scope(Arena& ar) : a(ar), m(ar.mark()) {}
+  ~Scope() { a.release(m); }
+};
+
+// ---------------------------------------------------------------------------------
+// Per-context kernel timing (CUDA events around launches of one kernel family).
+struct KernelTimer {
+  bool enabled = false;
+  struct Rec { cudaEvent_t a, b; double flop; };
+  std::map<std::string, std::vector<Rec>> recs;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get_event();
+  void begin(const char* fam, cudaStream_t s, double flop, cudaEvent_t* a, cudaEvent_t* b);
+  void reset();
+  ~KernelTimer();
+};
+
+}  // namespace mlcc
+
+struct mlcc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  mlcc::KernelTimer timer;
+  int sm_count = 0;
+};
+
+namespace mlcc {
+
+// ---------------------------------------------------------------------------------
+// Dense binary64 GEMM on the CUDA cores (row-major):
+//   C[b] = alpha * op(A[b]) op(B[b]) + beta * C[b]             (batch mode)
+//   C    = alpha * sum_b op(A[b]) op(B[b]) + beta * C          (reduce mode)
+// op(A) is M x K (A[m*lda+k], or A[k*lda+m] when ta), op(B) is K x N.
+struct Gemm {
+  bool ta = false, tb = false;
+  int64_t M = 0, N = 0, K = 0;
+  double alpha = 1.0, beta = 0.0;
+  const double* A = nullptr; int64_t lda = 0, sA = 0;
+  const double* B = nullptr; int64_t ldb = 0, sB = 0;
+  double* C = nullptr; int64_t ldc = 0, sC = 0;
+  int64_t batch = 1;
+  bool reduce = false;
+};
+void gemm_f64(const Gemm& g, Arena& ws, cudaStream_t s, int sm_count);
+
+// Strided permute-accumulate: dst = alpha * src (re-indexed) + beta * dst, both given by
+// dims and element strides in the order of the destination's loop nest (<= 8 dims).
+void permute_f64(int nd, const int64_t* dims, const double* src, const int64_t* src_strides,
+                 double* dst, const int64_t* dst_strides, double alpha, double beta,
+                 cudaStream_t s);
+
+// Contiguous row-major device tensor (binary64).
+struct DT {
+  double* p = nullptr;
+  std::vector<int64_t> d;
+  int64_t size() const { int64_t n = 1; for (auto x : d) n *= x; return n; }
+};
+
+// Pairwise tensor contraction C = alpha * contract(A, B) + beta * C following an einsum
+// specification "ab,bc->ac". Indices shared by A, B and C are batch indices, indices in
+// A and C (B and C) are rows (columns), indices in A and B only are summed. Operands are
+// brought to GEMM layout by permute kernels when their order requires it.
+void einsum(const char* spec, double alpha, const DT& A, const DT& B, double beta, const DT& C,
+            Arena& ws, cudaStream_t s, int sm_count);
+// C = alpha * permute(A) + beta * C with a spec "abcd->cdab".
+void eperm(const char* spec, double alpha, const DT& A, double beta, const DT& C, cudaStream_t s);
+
+// Elementwise / reduction helpers (binary64).
+void fill(double* p, int64_t n, double v, cudaStream_t s);
+void axpby(double* y, const double* x, int64_t n, double a, double b, cudaStream_t s);  // y = a x + b y
+// Deterministic dot products: out_dev[k] = sum_i x_k[i] y[i] for k < nx (x_k at x + k*ldx).
+void dots(const double* x, int64_t ldx, int nx, const double* y, int64_t n, double* out_dev,
+          Arena& ws, cudaStream_t s);
+void copy_d2h(double* h, const double* d, int64_t n, cudaStream_t s);
+void copy_h2d(double* d, const double* h, int64_t n, cudaStream_t s);
+
+}  // namespace mlcc

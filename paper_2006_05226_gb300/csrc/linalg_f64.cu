@@ -1,0 +1,554 @@
+// Binary64 building blocks of libmlcc: device arena, kernel timers, a tiled DGEMM on the
+// CUDA cores (batched and batch-reduced), strided permutations, a pairwise einsum engine
+// built from those two, and deterministic reductions.
+#include "internal.cuh"
+
+#include <algorithm>
+#include <cstring>
+#include <thread>
+
+namespace mlcc {
+
+static thread_local std::string g_last_error;
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+const char* last_error_cstr() { return g_last_error.c_str(); }
+
+// ---------------------------------------------------------------------------------
+Arena::~Arena() {
+  if (base_) cudaFree(base_);
+}
+void Arena::reserve(size_t bytes) {
+  if (base_) cudaFree(base_);
+  base_ = nullptr;
+  cap_ = top_ = hw_ = 0;
+  if (bytes == 0) return;
+  MLCC_CUDA(cudaMalloc(&base_, bytes));
+  cap_ = bytes;
+}
+void* Arena::alloc(size_t bytes) {
+  size_t off = (top_ + 255) & ~size_t(255);
+  size_t need = off + ((bytes + 255) & ~size_t(255));
+  if (need > cap_)
+    throw Error(MLCC_E_OOM, "workspace arena exhausted: need " + std::to_string(need) +
+                                " of " + std::to_string(cap_) + " bytes");
+  top_ = need;
+  hw_ = std::max(hw_, top_);
+  return base_ + off;
+}
+
+// ---------------------------------------------------------------------------------
+cudaEvent_t KernelTimer::get_event() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  MLCC_CUDA(cudaEventCreate(&e));
+  return e;
+}
+void KernelTimer::begin(const char* fam, cudaStream_t s, double flop, cudaEvent_t* a,
+                        cudaEvent_t* b) {
+  *a = get_event();
+  *b = get_event();
+  MLCC_CUDA(cudaEventRecord(*a, s));
+  recs[fam].push_back({*a, *b, flop});
+}
+void KernelTimer::reset() {
+  for (auto& kv : recs)
+    for (auto& r : kv.second) {
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+  recs.clear();
+}
+KernelTimer::~KernelTimer() {
+  reset();
+  for (auto e : pool) cudaEventDestroy(e);
+}
+
+// ---------------------------------------------------------------------------------
+// DGEMM: 64 x 64 output tile per CTA, 256 threads, each thread a 4 x 4 register block,
+// K stepped by 16 through double-buffered shared memory.
+namespace {
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+struct GP {
+  int64_t M, N, K;
+  const double* A; int64_t lda, sA;
+  const double* B; int64_t ldb, sB;
+  double* C; int64_t ldc, sC;
+  double alpha, beta;
+  int64_t batch;
+  int reduce;       // 1: sum over batches inside the CTA's share
+  double* partial;  // reduce with several splits: [split][M][N]
+};
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(NT) k_dgemm(GP p) {
+  __shared__ double As[2][BK][BM];
+  __shared__ double Bs[2][BK][BN];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int64_t m0 = int64_t(blockIdx.y) * BM, n0 = int64_t(blockIdx.x) * BN;
+  double acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+
+  int64_t b_begin, b_end, b_step;
+  if (p.reduce) {
+    b_begin = blockIdx.z;
+    b_end = p.batch;
+    b_step = gridDim.z;
+  } else {
+    b_begin = blockIdx.z;
+    b_end = blockIdx.z + 1;
+    b_step = 1;
+  }
+  const int64_t nk = (p.K + BK - 1) / BK;
+  for (int64_t b = b_begin; b < b_end; b += b_step) {
+    const double* A = p.A + b * p.sA;
+    const double* B = p.B + b * p.sB;
+    double ra[4], rb[4];
+    auto load = [&](int64_t kt) {
+      const int64_t k0 = kt * BK;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int e = tid + NT * r;
+        int mm, kk;
+        if (!TA) { mm = e >> 4; kk = e & 15; } else { kk = e >> 6; mm = e & 63; }
+        const int64_t gm = m0 + mm, gk = k0 + kk;
+        ra[r] = (gm < p.M && gk < p.K) ? (TA ? A[gk * p.lda + gm] : A[gm * p.lda + gk]) : 0.0;
+        int nn, kb;
+        if (!TB) { kb = e >> 6; nn = e & 63; } else { nn = e >> 4; kb = e & 15; }
+        const int64_t gn = n0 + nn, gkb = k0 + kb;
+        rb[r] = (gn < p.N && gkb < p.K) ? (TB ? B[gn * p.ldb + gkb] : B[gkb * p.ldb + gn]) : 0.0;
+      }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int e = tid + NT * r;
+        int mm, kk;
+        if (!TA) { mm = e >> 4; kk = e & 15; } else { kk = e >> 6; mm = e & 63; }
+        As[buf][kk][mm] = ra[r];
+        int nn, kb;
+        if (!TB) { kb = e >> 6; nn = e & 63; } else { nn = e >> 4; kb = e & 15; }
+        Bs[buf][kb][nn] = rb[r];
+      }
+    };
+    load(0);
+    store(0);
+    __syncthreads();
+    for (int64_t kt = 0; kt < nk; ++kt) {
+      const int buf = kt & 1;
+      if (kt + 1 < nk) load(kt + 1);
+#pragma unroll
+      for (int k = 0; k < BK; ++k) {
+        double a[4], bb[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) a[r] = As[buf][k][ty * 4 + r];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) bb[c] = Bs[buf][k][tx * 4 + c];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], bb[c], acc[r][c]);
+      }
+      if (kt + 1 < nk) store(buf ^ 1);
+      __syncthreads();
+    }
+  }
+  if (p.reduce && gridDim.z > 1) {
+    double* P = p.partial + int64_t(blockIdx.z) * p.M * p.N;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int64_t gm = m0 + ty * 4 + r;
+      if (gm >= p.M) continue;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int64_t gn = n0 + tx * 4 + c;
+        if (gn < p.N) P[gm * p.N + gn] = acc[r][c];
+      }
+    }
+    return;
+  }
+  double* C = p.C + (p.reduce ? 0 : int64_t(blockIdx.z) * p.sC);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int64_t gm = m0 + ty * 4 + r;
+    if (gm >= p.M) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int64_t gn = n0 + tx * 4 + c;
+      if (gn >= p.N) continue;
+      double* cp = C + gm * p.ldc + gn;
+      const double v = p.alpha * acc[r][c];
+      *cp = (p.beta == 0.0) ? v : v + p.beta * (*cp);
+    }
+  }
+}
+
+// C = alpha * sum_s partial[s] + beta * C, summed in split order (deterministic).
+__global__ void k_reduce_partials(const double* partial, int nsplit, int64_t M, int64_t N,
+                                  double* C, int64_t ldc, double alpha, double beta) {
+  const int64_t total = M * N;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < nsplit; ++k) s += partial[int64_t(k) * total + i];
+    const int64_t m = i / N, n = i - m * N;
+    double* cp = C + m * ldc + n;
+    *cp = (beta == 0.0) ? alpha * s : alpha * s + beta * (*cp);
+  }
+}
+}  // namespace
+
+void gemm_f64(const Gemm& g, Arena& ws, cudaStream_t s, int sm_count) {
+  if (g.M <= 0 || g.N <= 0) return;
+  if (g.K <= 0 || g.batch <= 0) {
+    // empty contraction: C = beta * C for each output matrix
+    const int64_t nb = g.reduce ? 1 : std::max<int64_t>(g.batch, 1);
+    for (int64_t b = 0; b < nb; ++b) {
+      int64_t dims[2] = {g.M, g.N};
+      int64_t st[2] = {g.ldc, 1};
+      permute_f64(2, dims, g.C + b * g.sC, st, g.C + b * g.sC, st, 0.0, g.beta, s);
+    }
+    return;
+  }
+  GP p;
+  p.M = g.M; p.N = g.N; p.K = g.K;
+  p.A = g.A; p.lda = g.lda; p.sA = g.sA;
+  p.B = g.B; p.ldb = g.ldb; p.sB = g.sB;
+  p.C = g.C; p.ldc = g.ldc; p.sC = g.sC;
+  p.alpha = g.alpha; p.beta = g.beta;
+  p.batch = g.batch;
+  p.reduce = g.reduce ? 1 : 0;
+  p.partial = nullptr;
+  const int64_t tm = (g.M + BM - 1) / BM, tn = (g.N + BN - 1) / BN;
+  MLCC_REQUIRE(tm < 65536, "gemm_f64: M too large for the grid");
+  int64_t gz = 1;
+  size_t mk = ws.mark();
+  if (g.reduce) {
+    const int64_t tiles = tm * tn;
+    const int64_t want = (4LL * std::max(sm_count, 1) + tiles - 1) / tiles;
+    gz = std::max<int64_t>(1, std::min<int64_t>({g.batch, want, 4096}));
+    // cap the partial buffer at 1 GiB
+    while (gz > 1 && gz * g.M * g.N * 8 > (int64_t(1) << 30)) gz /= 2;
+    if (gz > 1) p.partial = ws.get<double>(size_t(gz) * g.M * g.N);
+  } else {
+    gz = g.batch;
+    MLCC_REQUIRE(gz < 65536, "gemm_f64: batch too large for the grid");
+  }
+  dim3 grid{unsigned(tn), unsigned(tm), unsigned(gz)};
+  if (!g.ta && !g.tb) k_dgemm<false, false><<<grid, NT, 0, s>>>(p);
+  else if (g.ta && !g.tb) k_dgemm<true, false><<<grid, NT, 0, s>>>(p);
+  else if (!g.ta && g.tb) k_dgemm<false, true><<<grid, NT, 0, s>>>(p);
+  else k_dgemm<true, true><<<grid, NT, 0, s>>>(p);
+  MLCC_CHECK_LAUNCH();
+  if (g.reduce && gz > 1) {
+    const int64_t total = g.M * g.N;
+    const int blocks = int(std::min<int64_t>((total + 255) / 256, 4096));
+    k_reduce_partials<<<blocks, 256, 0, s>>>(p.partial, int(gz), g.M, g.N, g.C, g.ldc,
+                                              g.alpha, g.beta);
+    MLCC_CHECK_LAUNCH();
+  }
+  ws.release(mk);
+}
+
+// ---------------------------------------------------------------------------------
+namespace {
+constexpr int MAXD = 8;
+struct PP {
+  int nd;
+  int64_t dims[MAXD];
+  int64_t ss[MAXD];
+  int64_t ds[MAXD];
+  int64_t total;
+  double alpha, beta;
+  const double* src;
+  double* dst;
+};
+__global__ void k_permute(PP p) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < p.total;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    int64_t rem = i, so = 0, dof = 0;
+    for (int d = p.nd - 1; d >= 0; --d) {
+      const int64_t q = rem / p.dims[d];
+      const int64_t x = rem - q * p.dims[d];
+      rem = q;
+      so += x * p.ss[d];
+      dof += x * p.ds[d];
+    }
+    const double v = (p.alpha == 0.0) ? 0.0 : p.alpha * p.src[so];
+    p.dst[dof] = (p.beta == 0.0) ? v : v + p.beta * p.dst[dof];
+  }
+}
+}  // namespace
+
+void permute_f64(int nd, const int64_t* dims, const double* src, const int64_t* src_strides,
+                 double* dst, const int64_t* dst_strides, double alpha, double beta,
+                 cudaStream_t s) {
+  MLCC_REQUIRE(nd >= 0 && nd <= MAXD, "permute_f64: too many dimensions");
+  PP p;
+  p.nd = nd;
+  p.total = 1;
+  for (int d = 0; d < nd; ++d) {
+    p.dims[d] = dims[d];
+    p.ss[d] = src_strides[d];
+    p.ds[d] = dst_strides[d];
+    p.total *= dims[d];
+  }
+  if (p.total == 0) return;
+  p.alpha = alpha;
+  p.beta = beta;
+  p.src = src;
+  p.dst = dst;
+  const int blocks = int(std::min<int64_t>((p.total + 255) / 256, 8192));
+  k_permute<<<blocks, 256, 0, s>>>(p);
+  MLCC_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------------
+// einsum engine
+namespace {
+struct Spec {
+  std::string a, b, c;
+};
+Spec parse(const char* spec) {
+  std::string s(spec);
+  const size_t comma = s.find(','), arrow = s.find("->");
+  Spec r;
+  if (comma == std::string::npos) {
+    MLCC_REQUIRE(arrow != std::string::npos, std::string("bad einsum spec ") + spec);
+    r.a = s.substr(0, arrow);
+    r.c = s.substr(arrow + 2);
+    return r;
+  }
+  MLCC_REQUIRE(arrow != std::string::npos && comma < arrow, std::string("bad einsum spec ") + spec);
+  r.a = s.substr(0, comma);
+  r.b = s.substr(comma + 1, arrow - comma - 1);
+  r.c = s.substr(arrow + 2);
+  return r;
+}
+std::vector<int64_t> strides_of(const std::vector<int64_t>& d) {
+  std::vector<int64_t> st(d.size());
+  int64_t acc = 1;
+  for (int i = int(d.size()) - 1; i >= 0; --i) {
+    st[i] = acc;
+    acc *= d[i];
+  }
+  return st;
+}
+bool has(const std::string& s, char c) { return s.find(c) != std::string::npos; }
+}  // namespace
+
+void eperm(const char* spec, double alpha, const DT& A, double beta, const DT& C, cudaStream_t s) {
+  Spec sp = parse(spec);
+  MLCC_REQUIRE(sp.a.size() == A.d.size() && sp.c.size() == C.d.size() && sp.a.size() == sp.c.size(),
+               std::string("eperm rank mismatch: ") + spec);
+  auto sa = strides_of(A.d), sc = strides_of(C.d);
+  std::vector<int64_t> dims(sp.c.size()), ss(sp.c.size()), ds(sp.c.size());
+  for (size_t i = 0; i < sp.c.size(); ++i) {
+    const size_t j = sp.a.find(sp.c[i]);
+    MLCC_REQUIRE(j != std::string::npos, std::string("eperm index missing: ") + spec);
+    MLCC_REQUIRE(A.d[j] == C.d[i], std::string("eperm size mismatch: ") + spec);
+    dims[i] = C.d[i];
+    ss[i] = sa[j];
+    ds[i] = sc[i];
+  }
+  permute_f64(int(dims.size()), dims.data(), A.p, ss.data(), C.p, ds.data(), alpha, beta, s);
+}
+
+void einsum(const char* spec, double alpha, const DT& A, const DT& B, double beta, const DT& C,
+            Arena& ws, cudaStream_t s, int sm_count) {
+  Spec sp = parse(spec);
+  MLCC_REQUIRE(sp.a.size() == A.d.size() && sp.b.size() == B.d.size() && sp.c.size() == C.d.size(),
+               std::string("einsum rank mismatch: ") + spec);
+  std::map<char, int64_t> size;
+  auto reg = [&](const std::string& str, const std::vector<int64_t>& d) {
+    for (size_t i = 0; i < str.size(); ++i) {
+      auto it = size.find(str[i]);
+      if (it == size.end()) size[str[i]] = d[i];
+      else MLCC_REQUIRE(it->second == d[i], std::string("einsum size mismatch: ") + spec);
+    }
+  };
+  reg(sp.a, A.d);
+  reg(sp.b, B.d);
+  reg(sp.c, C.d);
+  std::string bat, mi, ni, ka, kb;
+  for (char ch : sp.c) {
+    const bool ia = has(sp.a, ch), ib = has(sp.b, ch);
+    MLCC_REQUIRE(ia || ib, std::string("einsum output index not in inputs: ") + spec);
+    if (ia && ib) bat += ch;
+    else if (ia) mi += ch;
+    else ni += ch;
+  }
+  for (char ch : sp.a) {
+    if (!has(sp.c, ch)) {
+      MLCC_REQUIRE(has(sp.b, ch), std::string("einsum index summed in one operand only: ") + spec);
+      ka += ch;
+    }
+  }
+  for (char ch : sp.b) {
+    if (!has(sp.c, ch)) {
+      MLCC_REQUIRE(has(sp.a, ch), std::string("einsum index summed in one operand only: ") + spec);
+      kb += ch;
+    }
+  }
+  auto prod = [&](const std::string& str) {
+    int64_t p = 1;
+    for (char ch : str) p *= size[ch];
+    return p;
+  };
+  const int64_t nb = prod(bat), M = prod(mi), N = prod(ni), K = prod(ka);
+  // choose the K order (that of A or of B) that needs fewer operand permutations
+  auto cost = [&](const std::string& korder) {
+    int c = 0;
+    if (!(sp.a == bat + mi + korder || sp.a == bat + korder + mi)) c += 1;
+    if (!(sp.b == bat + korder + ni || sp.b == bat + ni + korder)) c += 1;
+    return c;
+  };
+  std::string kord = cost(ka) <= cost(kb) ? ka : kb;
+  Scope scope(ws);
+  Gemm g;
+  g.M = M; g.N = N; g.K = K;
+  g.batch = nb;
+  // A operand
+  const double* Ap = A.p;
+  if (sp.a == bat + mi + kord) { g.ta = false; g.lda = K; }
+  else if (sp.a == bat + kord + mi) { g.ta = true; g.lda = M; }
+  else {
+    DT t;
+    t.p = ws.get<double>(size_t(nb * M * K));
+    for (char ch : bat + mi + kord) t.d.push_back(size[ch]);
+    const std::string sps = sp.a + "->" + bat + mi + kord;
+    eperm(sps.c_str(), 1.0, A, 0.0, t, s);
+    Ap = t.p;
+    g.ta = false;
+    g.lda = K;
+  }
+  g.A = Ap;
+  g.sA = M * K;
+  const double* Bp = B.p;
+  if (sp.b == bat + kord + ni) { g.tb = false; g.ldb = N; }
+  else if (sp.b == bat + ni + kord) { g.tb = true; g.ldb = K; }
+  else {
+    DT t;
+    t.p = ws.get<double>(size_t(nb * K * N));
+    for (char ch : bat + kord + ni) t.d.push_back(size[ch]);
+    const std::string sps = sp.b + "->" + bat + kord + ni;
+    eperm(sps.c_str(), 1.0, B, 0.0, t, s);
+    Bp = t.p;
+    g.tb = false;
+    g.ldb = N;
+  }
+  g.B = Bp;
+  g.sB = K * N;
+  if (sp.c == bat + mi + ni) {
+    g.C = C.p;
+    g.ldc = N;
+    g.sC = M * N;
+    g.alpha = alpha;
+    g.beta = beta;
+    gemm_f64(g, ws, s, sm_count);
+  } else {
+    DT t;
+    t.p = ws.get<double>(size_t(nb * M * N));
+    for (char ch : bat + mi + ni) t.d.push_back(size[ch]);
+    g.C = t.p;
+    g.ldc = N;
+    g.sC = M * N;
+    g.alpha = alpha;
+    g.beta = 0.0;
+    gemm_f64(g, ws, s, sm_count);
+    const std::string sps = bat + mi + ni + "->" + sp.c;
+    eperm(sps.c_str(), 1.0, t, beta, C, s);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+namespace {
+__global__ void k_fill(double* p, int64_t n, double v) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x)
+    p[i] = v;
+}
+__global__ void k_axpby(double* y, const double* x, int64_t n, double a, double b) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x)
+    y[i] = (b == 0.0) ? a * x[i] : a * x[i] + b * y[i];
+}
+constexpr int DOT_BLOCKS = 512;
+// partial[k][blk] = sum over the block's grid-stride share of x_k * y
+__global__ void k_dots_stage1(const double* x, int64_t ldx, int nx, const double* y, int64_t n,
+                              double* partial) {
+  __shared__ double red[256];
+  for (int k = 0; k < nx; ++k) {
+    const double* xk = x + int64_t(k) * ldx;
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x)
+      s = fma(xk[i], y[i], s);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[int64_t(k) * gridDim.x + blockIdx.x] = red[0];
+    __syncthreads();
+  }
+}
+__global__ void k_dots_stage2(const double* partial, int nblk, double* out) {
+  __shared__ double red[256];
+  const int k = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += partial[int64_t(k) * nblk + i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[k] = red[0];
+}
+}  // namespace
+
+void fill(double* p, int64_t n, double v, cudaStream_t s) {
+  if (n <= 0) return;
+  const int blocks = int(std::min<int64_t>((n + 255) / 256, 8192));
+  k_fill<<<blocks, 256, 0, s>>>(p, n, v);
+  MLCC_CHECK_LAUNCH();
+}
+void axpby(double* y, const double* x, int64_t n, double a, double b, cudaStream_t s) {
+  if (n <= 0) return;
+  const int blocks = int(std::min<int64_t>((n + 255) / 256, 8192));
+  k_axpby<<<blocks, 256, 0, s>>>(y, x, n, a, b);
+  MLCC_CHECK_LAUNCH();
+}
+void dots(const double* x, int64_t ldx, int nx, const double* y, int64_t n, double* out_dev,
+          Arena& ws, cudaStream_t s) {
+  if (nx <= 0) return;
+  Scope sc(ws);
+  int blocks = int(std::min<int64_t>((n + 255) / 256, DOT_BLOCKS));
+  blocks = std::max(blocks, 1);
+  double* partial = ws.get<double>(size_t(nx) * blocks);
+  k_dots_stage1<<<blocks, 256, 0, s>>>(x, ldx, nx, y, n, partial);
+  MLCC_CHECK_LAUNCH();
+  k_dots_stage2<<<nx, 256, 0, s>>>(partial, blocks, out_dev);
+  MLCC_CHECK_LAUNCH();
+}
+void copy_d2h(double* h, const double* d, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  MLCC_CUDA(cudaMemcpyAsync(h, d, size_t(n) * 8, cudaMemcpyDeviceToHost, s));
+  MLCC_CUDA(cudaStreamSynchronize(s));
+}
+void copy_h2d(double* d, const double* h, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  MLCC_CUDA(cudaMemcpyAsync(d, h, size_t(n) * 8, cudaMemcpyHostToDevice, s));
+}
+
+}  // namespace mlcc

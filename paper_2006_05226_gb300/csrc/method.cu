@@ -1,0 +1,602 @@
+// The MLCC residual and Jacobian transformation on the device (arXiv 2006.05226,
+// Sec. 2.1 and Appendix A). The residual pipeline is written once; the Jacobian
+// transformation sigma = A c is its forward-mode derivative along c, evaluated by the
+// product rule contraction by contraction around the cached ground-state values.
+#include "system.cuh"
+
+#include <algorithm>
+
+namespace mlcc {
+
+static inline cudaStream_t stm(mlcc_system* S) { return S->ctx->stream; }
+static inline int smc(mlcc_system* S) { return S->ctx->sm_count; }
+static inline int nblk(int64_t n) { return int(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 16384))); }
+
+// ---------------------------------------------------------------------------------
+// kernels
+namespace {
+// D[J] = sum_{I < no} X[J][I][I]
+__global__ void k_trace_occ(const double* X, int nj, int n, int no, double* D) {
+  const int J = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (J >= nj) return;
+  const double* x = X + int64_t(J) * n * n;
+  double s = 0.0;
+  for (int I = lane; I < no; I += 32) s += x[int64_t(I) * n + I];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) D[J] = s;
+}
+// out[J][a*so + i] = X[J][no + a][i]   (virtual-occupied block, CC2-active)
+__global__ void k_gather_vo(const double* X, int nj, int n, int no, int sv, int so, double* out) {
+  const int64_t dS = int64_t(sv) * so, total = dS * nj;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t J = t / dS, r = t - J * dS;
+    const int a = int(r / so), i = int(r - int64_t(a) * so);
+    out[t] = X[J * n * n + int64_t(no + a) * n + i];
+  }
+}
+// out[J][c*so + j] = X[J][j][no + c]   (occupied-virtual block, CC2-active)
+__global__ void k_gather_ov(const double* X, int nj, int n, int no, int sv, int so, double* out) {
+  const int64_t dS = int64_t(sv) * so, total = dS * nj;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t J = t / dS, r = t - J * dS;
+    const int c = int(r / so), j = int(r - int64_t(c) * so);
+    out[t] = X[J * n * n + int64_t(j) * n + no + c];
+  }
+}
+__device__ __forceinline__ void split4(int64_t t, int sv, int so, int& a, int& i, int& b, int& j) {
+  j = int(t % so);
+  t /= so;
+  b = int(t % sv);
+  t /= sv;
+  i = int(t % so);
+  a = int(t / so);
+}
+// u[a,i,b,j] = 2 x[a,i,b,j] - x[a,j,b,i]
+__global__ void k_make_u(const double* x, int sv, int so, double* u) {
+  const int64_t total = int64_t(sv) * so * sv * so;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    int a, i, b, j;
+    split4(t, sv, so, a, i, b, j);
+    const int64_t tx = ((int64_t(a) * so + j) * sv + b) * so + i;
+    u[t] = 2.0 * x[t] - x[tx];
+  }
+}
+__device__ __forceinline__ bool in_T(int a, int i, int b, int j, int tv, int to) {
+  return a < tv && i < to && b < tv && j < to;
+}
+__device__ __forceinline__ double eps4(const double* eps, int no, int a, int i, int b, int j) {
+  return eps[no + a] - eps[i] + eps[no + b] - eps[j];
+}
+// GS: CC2 doubles s = -g~/eps on P_S (Appendix A), P_T amplitudes from tT (or 0)
+__global__ void k_cc2_amp(const double* g, const double* eps, int no, int sv, int so, int tv,
+                          int to, const double* tT, double* x2) {
+  const int64_t total = int64_t(sv) * so * sv * so;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    int a, i, b, j;
+    split4(t, sv, so, a, i, b, j);
+    if (in_T(a, i, b, j, tv, to)) {
+      x2[t] = tT ? tT[((int64_t(a) * to + i) * tv + b) * to + j] : 0.0;
+    } else {
+      x2[t] = -g[t] / eps4(eps, no, a, i, b, j);
+    }
+  }
+}
+// Omega on P_S: g~ + eps x (Eq. mlcc2_omega2 in the semicanonical basis); P_T rows 0
+__global__ void k_omega2_cc2(const double* g, const double* x2, const double* eps, int no, int sv,
+                             int so, int tv, int to, double* om2) {
+  const int64_t total = int64_t(sv) * so * sv * so;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    int a, i, b, j;
+    split4(t, sv, so, a, i, b, j);
+    om2[t] = in_T(a, i, b, j, tv, to) ? 0.0 : g[t] + eps4(eps, no, a, i, b, j) * x2[t];
+  }
+}
+// sigma on P_S: W_(ai)(bj) + W_(bj)(ai) + eps c; P_T rows 0. 32 x 32 tiles through shared
+// memory so that both the direct and the transposed read are coalesced.
+__global__ void k_sigma2_cc2(const double* W, const double* c, const double* eps, int no, int sv,
+                             int so, int tv, int to, double* s2) {
+  __shared__ double tile[32][33];
+  const int64_t dS = int64_t(sv) * so;
+  const int64_t r0 = int64_t(blockIdx.y) * 32, c0 = int64_t(blockIdx.x) * 32;
+  // transposed block W[c0.., r0..] -> tile[col][row]
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int64_t rr = c0 + y, cc = r0 + threadIdx.x;
+    tile[y][threadIdx.x] = (rr < dS && cc < dS) ? W[rr * dS + cc] : 0.0;
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int64_t row = r0 + y, col = c0 + threadIdx.x;
+    if (row >= dS || col >= dS) continue;
+    const int a = int(row / so), i = int(row - int64_t(a) * so);
+    const int b = int(col / so), j = int(col - int64_t(b) * so);
+    const int64_t t = row * dS + col;
+    s2[t] = in_T(a, i, b, j, tv, to)
+                ? 0.0
+                : W[t] + tile[threadIdx.x][y] + eps4(eps, no, a, i, b, j) * c[t];
+  }
+}
+// om1[a*no + i] += alpha * tmp[a*so + i]
+__global__ void k_scatter_add_ai(const double* tmp, int sv, int so, int no, double alpha,
+                                 double* om1) {
+  const int64_t total = int64_t(sv) * so;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int a = int(t / so), i = int(t - int64_t(a) * so);
+    om1[int64_t(a) * no + i] += alpha * tmp[t];
+  }
+}
+// fv[b*so + j] = F[j][no + b]
+__global__ void k_fov(const double* F, int n, int no, int sv, int so, double* fv) {
+  const int64_t total = int64_t(sv) * so;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int b = int(t / so), j = int(t - int64_t(b) * so);
+    fv[t] = F[int64_t(j) * n + no + b];
+  }
+}
+// part[J] = 2 tr(M_J)^2 - sum_IK M_J[I][K] M_J[K][I]   (Eq. mlcc_energy, singles term)
+__global__ void k_energy1(const double* M, int no, double* part) {
+  __shared__ double r1[256], r2[256];
+  const double* m = M + int64_t(blockIdx.x) * no * no;
+  double tr = 0.0, q = 0.0;
+  for (int t = threadIdx.x; t < no * no; t += blockDim.x) {
+    const int I = t / no, K = t - I * no;
+    if (I == K) tr += m[t];
+    q += m[t] * m[int64_t(K) * no + I];
+  }
+  r1[threadIdx.x] = tr;
+  r2[threadIdx.x] = q;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      r1[threadIdx.x] += r1[threadIdx.x + w];
+      r2[threadIdx.x] += r2[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = 2.0 * r1[0] * r1[0] - r2[0];
+}
+// out = sum_k part[k] + extra[0]  (one block, fixed order)
+__global__ void k_sum_plus(const double* part, int n, const double* extra, double* out) {
+  __shared__ double r[256];
+  double s = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) s += part[k];
+  r[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) r[threadIdx.x] += r[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = r[0] + (extra ? extra[0] : 0.0);
+}
+}  // namespace
+
+// ---------------------------------------------------------------------------------
+// strided 2-D block copy / accumulate: dst[r*ldd + c] = alpha src[r*lds + c] + beta dst
+static void block2d(mlcc_system* S, int64_t rows, int64_t cols, const double* src, int64_t lds,
+                    double* dst, int64_t ldd, double alpha, double beta) {
+  int64_t dims[2] = {rows, cols}, ss[2] = {lds, 1}, ds[2] = {ldd, 1};
+  permute_f64(2, dims, src, ss, dst, ds, alpha, beta, stm(S));
+}
+
+void gather_vo(mlcc_system* S, const double* X, double* out) {
+  if (S->dS == 0) return;
+  k_gather_vo<<<nblk(S->dS * S->nj), 256, 0, stm(S)>>>(X, S->nj, S->n, S->no, S->sv, S->so, out);
+  MLCC_CHECK_LAUNCH();
+}
+void gather_ov(mlcc_system* S, const double* X, double* out) {
+  if (S->dS == 0) return;
+  k_gather_ov<<<nblk(S->dS * S->nj), 256, 0, stm(S)>>>(X, S->nj, S->n, S->no, S->sv, S->so, out);
+  MLCC_CHECK_LAUNCH();
+}
+void make_u(mlcc_system* S, const double* x2, double* u) {
+  if (S->nd == 0) return;
+  k_make_u<<<nblk(S->nd), 256, 0, stm(S)>>>(x2, S->sv, S->so, u);
+  MLCC_CHECK_LAUNCH();
+}
+
+// T1-dressing (Sec. 2.1, Appendix A): Lt = (1 - t) L (1 + t), t in the vir-occ block.
+// (1 - t) L changes the virtual rows: Lt[v,:] = L[v,:] - t L[o,:]; the right factor
+// changes the occupied columns: Lt[:,o] += Lt[:,v] t.
+void dress(mlcc_system* S, const double* t1, double* Lt, double* ht) {
+  const int n = S->n, no = S->no, nv = S->nv, nj = S->nj;
+  const int64_t nn = int64_t(n) * n;
+  cudaStream_t s = stm(S);
+  auto one = [&](const double* X, double* Y, int64_t batch) {
+    MLCC_CUDA(cudaMemcpyAsync(Y, X, size_t(batch * nn) * 8, cudaMemcpyDeviceToDevice, s));
+    if (no == 0 || nv == 0) return;
+    Gemm g1;
+    g1.M = nv; g1.N = n; g1.K = no;
+    g1.A = t1; g1.lda = no; g1.sA = 0;
+    g1.B = X; g1.ldb = n; g1.sB = nn;
+    g1.C = Y + int64_t(no) * n; g1.ldc = n; g1.sC = nn;
+    g1.alpha = -1.0; g1.beta = 1.0; g1.batch = batch;
+    gemm_f64(g1, S->ws, s, smc(S));
+    Gemm g2;
+    g2.M = n; g2.N = no; g2.K = nv;
+    g2.A = Y + no; g2.lda = n; g2.sA = nn;
+    g2.B = t1; g2.ldb = no; g2.sB = 0;
+    g2.C = Y; g2.ldc = n; g2.sC = nn;
+    g2.alpha = 1.0; g2.beta = 1.0; g2.batch = batch;
+    gemm_f64(g2, S->ws, s, smc(S));
+  };
+  one(S->L, Lt, nj);
+  if (ht) one(S->h, ht, 1);
+}
+
+// Tangent of the dressing along c1: d Lt = Lt C - C Lt with C the vir-occ matrix of c1
+// (exp(-T) M exp(T) differentiated; C T = T C = 0).
+void dress_tangent(mlcc_system* S, const double* c1, double* dLt, double* dht) {
+  const int n = S->n, no = S->no, nv = S->nv, nj = S->nj;
+  const int64_t nn = int64_t(n) * n;
+  cudaStream_t s = stm(S);
+  auto one = [&](const double* X, double* Y, int64_t batch) {
+    MLCC_CUDA(cudaMemsetAsync(Y, 0, size_t(batch * nn) * 8, s));
+    if (no == 0 || nv == 0) return;
+    Gemm g1;  // Y[:, o] = X[:, v] c1
+    g1.M = n; g1.N = no; g1.K = nv;
+    g1.A = X + no; g1.lda = n; g1.sA = nn;
+    g1.B = c1; g1.ldb = no; g1.sB = 0;
+    g1.C = Y; g1.ldc = n; g1.sC = nn;
+    g1.alpha = 1.0; g1.beta = 0.0; g1.batch = batch;
+    gemm_f64(g1, S->ws, s, smc(S));
+    Gemm g2;  // Y[v, :] -= c1 X[o, :]
+    g2.M = nv; g2.N = n; g2.K = no;
+    g2.A = c1; g2.lda = no; g2.sA = 0;
+    g2.B = X; g2.ldb = n; g2.sB = nn;
+    g2.C = Y + int64_t(no) * n; g2.ldc = n; g2.sC = nn;
+    g2.alpha = -1.0; g2.beta = 1.0; g2.batch = batch;
+    gemm_f64(g2, S->ws, s, smc(S));
+  };
+  one(S->Lt, dLt, nj);
+  one(S->ht, dht, 1);
+}
+
+static void trace_occ(mlcc_system* S, const double* X, double* D) {
+  const int warps = 8;
+  k_trace_occ<<<(S->nj + warps - 1) / warps, 32 * warps, 0, stm(S)>>>(X, S->nj, S->n, S->no, D);
+  MLCC_CHECK_LAUNCH();
+}
+
+// F += alpha_c * 2 sum_J D_J X^J  and  F -= alpha_x * sum_J X^J[:, o] Y^J[o, :]
+static void fock_terms(mlcc_system* S, const double* D, const double* X, const double* XL,
+                       const double* YR, double* F, double sgn) {
+  const int n = S->n, no = S->no, nj = S->nj;
+  const int64_t nn = int64_t(n) * n;
+  cudaStream_t s = stm(S);
+  if (D) {
+    Gemm c;
+    c.M = 1; c.N = nn; c.K = nj;
+    c.A = D; c.lda = nj; c.B = X; c.ldb = nn; c.C = F; c.ldc = nn;
+    c.alpha = 2.0 * sgn; c.beta = 1.0;
+    gemm_f64(c, S->ws, s, smc(S));
+  }
+  if (XL && no > 0) {
+    Gemm x;
+    x.M = n; x.N = n; x.K = no;
+    x.A = XL; x.lda = n; x.sA = nn;
+    x.B = YR; x.ldb = n; x.sB = nn;
+    x.C = F; x.ldc = n;
+    x.alpha = -sgn; x.beta = 1.0; x.batch = nj; x.reduce = true;
+    gemm_f64(x, S->ws, s, smc(S));
+  }
+}
+
+// F~ = h~ + sum_J [2 Lt^J (sum_I Lt^J_II) - Lt^J[:, I] Lt^J[I, :]]   (Appendix A, F~_PQ)
+void build_fock(mlcc_system* S, const double* ht, const double* Lt, double* Ft) {
+  Scope sc(S->ws);
+  const int64_t nn = int64_t(S->n) * S->n;
+  double* D = S->ws.get<double>(S->nj);
+  trace_occ(S, Lt, D);
+  MLCC_CUDA(cudaMemcpyAsync(Ft, ht, size_t(nn) * 8, cudaMemcpyDeviceToDevice, stm(S)));
+  fock_terms(S, D, Lt, Lt, Lt, Ft, 1.0);
+}
+
+void build_fock_tangent(mlcc_system* S, const double* dht, const double* dLt, double* dFt) {
+  Scope sc(S->ws);
+  const int64_t nn = int64_t(S->n) * S->n;
+  double* D = S->ws.get<double>(S->nj);
+  double* dD = S->ws.get<double>(S->nj);
+  trace_occ(S, S->Lt, D);
+  trace_occ(S, dLt, dD);
+  MLCC_CUDA(cudaMemcpyAsync(dFt, dht, size_t(nn) * 8, cudaMemcpyDeviceToDevice, stm(S)));
+  fock_terms(S, D, dLt, dLt, S->Lt, dFt, 1.0);
+  fock_terms(S, dD, S->Lt, S->Lt, dLt, dFt, 1.0);
+}
+
+// ---------------------------------------------------------------------------------
+// The Cholesky-rank doubles GEMMs (the dominant work): C[dS x dS] = A^T B with A, B
+// [nj][dS], or C[nj x dS] = A[nj x dS] B[dS x dS]. Binary64 here; the tensor-core path
+// replaces them when precision is MLCC_BF16.
+void rank_gemm_f64(mlcc_system* S, bool outer, const double* A, const double* B, double* C,
+                   double alpha, double beta);
+void rank_gemm_lowp(mlcc_system* S, bool outer, const double* A, const double* B, double* C,
+                    double alpha, double beta);
+
+void rank_gemm_f64(mlcc_system* S, bool outer, const double* A, const double* B, double* C,
+                   double alpha, double beta) {
+  const int64_t dS = S->dS, nj = S->nj;
+  Gemm g;
+  if (outer) {  // C[dS][dS] = A^T B, K = nj
+    g.ta = true; g.M = dS; g.N = dS; g.K = nj;
+    g.A = A; g.lda = dS; g.B = B; g.ldb = dS; g.C = C; g.ldc = dS;
+  } else {      // C[nj][dS] = A[nj][dS] B[dS][dS]
+    g.M = nj; g.N = dS; g.K = dS;
+    g.A = A; g.lda = dS; g.B = B; g.ldb = dS; g.C = C; g.ldc = dS;
+  }
+  g.alpha = alpha;
+  g.beta = beta;
+  timed(S, "rank_gemm", 2.0 * double(g.M) * double(g.N) * double(g.K),
+        [&] { gemm_f64(g, S->ws, stm(S), smc(S)); });
+}
+
+static void rank_gemm(mlcc_system* S, int precision, bool outer, const double* A, const double* B,
+                      double* C, double alpha, double beta) {
+  if (precision == MLCC_BF16) rank_gemm_lowp(S, outer, A, B, C, alpha, beta);
+  else rank_gemm_f64(S, outer, A, B, C, alpha, beta);
+}
+
+// ---------------------------------------------------------------------------------
+// CCSD-active block extraction helpers (the CCSD orbitals lead each range)
+struct Box {
+  Dual Lai, Lac, Lki, Lkc, Fvv, Foo, t;
+};
+
+static DT box_view(mlcc_system* S, int64_t a, int64_t b, int64_t c) {
+  DT x;
+  x.d = {a, b, c};
+  x.p = S->ws.get<double>(size_t(a * b * c));
+  return x;
+}
+
+// copy the [nj] x rows x cols sub-block at (r0, c0) of X[nj][n][n]
+static void take_block(mlcc_system* S, const double* X, int64_t batch, int r0, int rows, int c0,
+                       int cols, DT& out) {
+  const int64_t n = S->n, nn = n * n;
+  int64_t dims[3] = {batch, rows, cols}, ss[3] = {nn, n, 1}, ds[3] = {int64_t(rows) * cols, cols, 1};
+  permute_f64(3, dims, X + r0 * n + c0, ss, out.p, ds, 1.0, 0.0, stm(S));
+}
+
+static void take_tbox(mlcc_system* S, const double* x2, DT& out) {
+  const int so = S->so, sv = S->sv, to = S->to, tv = S->tv;
+  int64_t dims[4] = {tv, to, tv, to};
+  int64_t ss[4] = {int64_t(so) * sv * so, int64_t(sv) * so, so, 1};
+  int64_t ds[4] = {int64_t(to) * tv * to, int64_t(tv) * to, to, 1};
+  permute_f64(4, dims, x2, ss, out.p, ds, 1.0, 0.0, stm(S));
+}
+static void put_tbox(mlcc_system* S, const double* om, double* x2) {
+  const int so = S->so, sv = S->sv, to = S->to, tv = S->tv;
+  int64_t dims[4] = {tv, to, tv, to};
+  int64_t ss[4] = {int64_t(to) * tv * to, int64_t(tv) * to, to, 1};
+  int64_t ds[4] = {int64_t(so) * sv * so, int64_t(sv) * so, so, 1};
+  permute_f64(4, dims, om, ss, x2, ds, 1.0, 0.0, stm(S));
+}
+
+// Values (or tangents) of the CCSD-block inputs from full Lt / Ft-like buffers.
+static void extract_box(mlcc_system* S, const double* Lt, const double* Ft, const double* x2,
+                        DT& Lai, DT& Lac, DT& Lki, DT& Lkc, DT& Fvv, DT& Foo, DT& t) {
+  const int no = S->no, to = S->to, tv = S->tv, nj = S->nj;
+  Lai = box_view(S, nj, tv, to);
+  Lac = box_view(S, nj, tv, tv);
+  Lki = box_view(S, nj, to, to);
+  Lkc = box_view(S, nj, to, tv);
+  take_block(S, Lt, nj, no, tv, 0, to, Lai);
+  take_block(S, Lt, nj, no, tv, no, tv, Lac);
+  take_block(S, Lt, nj, 0, to, 0, to, Lki);
+  take_block(S, Lt, nj, 0, to, no, tv, Lkc);
+  Fvv.d = {tv, tv};
+  Fvv.p = S->ws.get<double>(size_t(tv) * tv);
+  Foo.d = {to, to};
+  Foo.p = S->ws.get<double>(size_t(to) * to);
+  take_block(S, Ft, 1, no, tv, no, tv, Fvv);
+  take_block(S, Ft, 1, 0, to, 0, to, Foo);
+  t.d = {tv, to, tv, to};
+  t.p = S->ws.get<double>(size_t(tv) * to * tv * to);
+  take_tbox(S, x2, t);
+}
+
+// ---------------------------------------------------------------------------------
+// Residual. gs_mode: the P_S doubles are the analytic CC2 amplitudes of the current t1
+// (written to x2_out, with the P_T part from tT); otherwise x2 is an independent input.
+// om2 (full doubles, may be NULL) receives the P_S rows and, if om2 != NULL, the P_T rows;
+// in gs_mode the compact P_T residual is written to om2 as [tv][to][tv][to] instead.
+void omega_eval(mlcc_system* S, const double* t1, const double* x2, bool gs_mode,
+                const double* tT, double* x2_out, double* om1, double* om2, double* energy) {
+  cudaStream_t s = stm(S);
+  const int n = S->n, no = S->no, nv = S->nv, nj = S->nj, so = S->so, sv = S->sv;
+  const int64_t nn = int64_t(n) * n, dS = S->dS;
+  S->prepared = false;
+  Scope sc(S->ws);
+  dress(S, t1, S->Lt, S->ht);
+  build_fock(S, S->ht, S->Lt, S->Ft);
+  gather_vo(S, S->Lt, S->Lai);
+  gather_ov(S, S->Lt, S->Lov);
+  const double* xuse = x2;
+  if (dS > 0) {
+    double* g = S->ws.get<double>(size_t(S->nd));
+    rank_gemm_f64(S, true, S->Lai, S->Lai, g, 1.0, 0.0);   // g~_aibj = Lt_ai Lt_bj
+    if (gs_mode) {
+      k_cc2_amp<<<nblk(S->nd), 256, 0, s>>>(g, S->eps, no, sv, so, S->tv, S->to, tT, x2_out);
+      MLCC_CHECK_LAUNCH();
+      xuse = x2_out;
+    } else if (om2) {
+      k_omega2_cc2<<<nblk(S->nd), 256, 0, s>>>(g, x2, S->eps, no, sv, so, S->tv, S->to, om2);
+      MLCC_CHECK_LAUNCH();
+    }
+  }
+  // CCSD doubles residual on P_T
+  if (S->to > 0 && S->tv > 0 && om2) {
+    Scope sb(S->ws);
+    Dual Lai, Lac, Lki, Lkc, Fvv, Foo, t;
+    extract_box(S, S->Lt, S->Ft, xuse, Lai.v, Lac.v, Lki.v, Lkc.v, Fvv.v, Foo.v, t.v);
+    const int64_t tl = int64_t(S->tv) * S->to * S->tv * S->to;
+    double* omT = gs_mode ? om2 : S->ws.get<double>(size_t(tl));
+    ccsd_block(S, Mode::Value, Lai, Lac, Lki, Lkc, Fvv, Foo, t, omT, false);
+    if (!gs_mode) put_tbox(S, omT, om2);
+  }
+  // singles (Eq. mlcc2_omega_codable) with u from all doubles
+  block2d(S, nv, no, S->Ft + int64_t(no) * n, n, om1, no, 1.0, 0.0);
+  if (dS > 0) {
+    make_u(S, xuse, S->u);
+    rank_gemm_f64(S, false, S->Lov, S->u, S->Z, 1.0, 0.0);  // Z^J_(bi) = Lov^J_(cj) u_(cj)(bi)
+    Gemm a;  // om1[A][i] += sum_J Lt^J[A][b] Z^J[b][i]
+    a.M = nv; a.N = so; a.K = sv;
+    a.A = S->Lt + int64_t(no) * n + no; a.lda = n; a.sA = nn;
+    a.B = S->Z; a.ldb = so; a.sB = dS;
+    a.C = om1; a.ldc = no; a.alpha = 1.0; a.beta = 1.0; a.batch = nj; a.reduce = true;
+    gemm_f64(a, S->ws, s, smc(S));
+    Gemm b;  // om1[a][I] -= sum_J Z^J[a][j] Lt^J[j][I]
+    b.M = sv; b.N = no; b.K = so;
+    b.A = S->Z; b.lda = so; b.sA = dS;
+    b.B = S->Lt; b.ldb = n; b.sB = nn;
+    b.C = om1; b.ldc = no; b.alpha = -1.0; b.beta = 1.0; b.batch = nj; b.reduce = true;
+    gemm_f64(b, S->ws, s, smc(S));
+    k_fov<<<nblk(dS), 256, 0, s>>>(S->Ft, n, no, sv, so, S->Fov);
+    MLCC_CHECK_LAUNCH();
+    double* tmp = S->ws.get<double>(size_t(dS));
+    Gemm c;  // tmp_(ai) = u_(ai)(bj) F~_jb
+    c.M = dS; c.N = 1; c.K = dS;
+    c.A = S->u; c.lda = dS; c.B = S->Fov; c.ldb = 1; c.C = tmp; c.ldc = 1;
+    gemm_f64(c, S->ws, s, smc(S));
+    k_scatter_add_ai<<<nblk(dS), 256, 0, s>>>(tmp, sv, so, no, 1.0, om1);
+    MLCC_CHECK_LAUNCH();
+  }
+  // energy (Eq. mlcc_energy)
+  if (energy) {
+    double* M = S->ws.get<double>(size_t(nj) * no * no);
+    double* part = S->ws.get<double>(size_t(nj));
+    double* e2 = S->ws.get<double>(1);
+    Gemm m;  // M^J[I][K] = sum_B L^J_IB t_BK  (L~_ov = L_ov)
+    m.M = no; m.N = no; m.K = nv;
+    m.A = S->Lt + no; m.lda = n; m.sA = nn;
+    m.B = t1; m.ldb = no; m.sB = 0;
+    m.C = M; m.ldc = no; m.sC = int64_t(no) * no; m.batch = nj;
+    gemm_f64(m, S->ws, s, smc(S));
+    k_energy1<<<nj, 256, 0, s>>>(M, no, part);
+    MLCC_CHECK_LAUNCH();
+    if (dS > 0) {
+      // sum_aibj u_aibj g_iajb = sum_J sum_(ai) Lov^J_(ai) Z^J_(ai)
+      dots(S->Lov, 0, 1, S->Z, int64_t(nj) * dS, e2, S->ws, s);
+    } else {
+      fill(e2, 1, 0.0, s);
+    }
+    k_sum_plus<<<1, 256, 0, s>>>(part, nj, e2, energy);
+    MLCC_CHECK_LAUNCH();
+  }
+}
+
+// ---------------------------------------------------------------------------------
+void jacobian_prepare(mlcc_system* S, const double* t1, const double* x2) {
+  cudaStream_t s = stm(S);
+  const int n = S->n, no = S->no, nv = S->nv, so = S->so, sv = S->sv;
+  const int64_t dS = S->dS;
+  S->prepared = false;
+  ccsd_cache_free(S);
+  Scope sc(S->ws);
+  MLCC_CUDA(cudaMemcpyAsync(S->t1gs, t1, size_t(nv) * no * 8, cudaMemcpyDeviceToDevice, s));
+  if (S->nd)
+    MLCC_CUDA(cudaMemcpyAsync(S->x2gs, x2, size_t(S->nd) * 8, cudaMemcpyDeviceToDevice, s));
+  dress(S, S->t1gs, S->Lt, S->ht);
+  build_fock(S, S->ht, S->Lt, S->Ft);
+  gather_vo(S, S->Lt, S->Lai);
+  gather_ov(S, S->Lt, S->Lov);
+  if (dS > 0) {
+    make_u(S, S->x2gs, S->u);
+    rank_gemm_f64(S, false, S->Lov, S->u, S->Z, 1.0, 0.0);
+    k_fov<<<nblk(dS), 256, 0, s>>>(S->Ft, n, no, sv, so, S->Fov);
+    MLCC_CHECK_LAUNCH();
+  }
+  if (S->to > 0 && S->tv > 0) {
+    Scope sb(S->ws);
+    Dual Lai, Lac, Lki, Lkc, Fvv, Foo, t;
+    extract_box(S, S->Lt, S->Ft, S->x2gs, Lai.v, Lac.v, Lki.v, Lkc.v, Fvv.v, Foo.v, t.v);
+    const int64_t tl = int64_t(S->tv) * S->to * S->tv * S->to;
+    double* omT = S->ws.get<double>(size_t(tl));
+    ccsd_block(S, Mode::Value, Lai, Lac, Lki, Lkc, Fvv, Foo, t, omT, true);
+  }
+  S->prepared = true;
+}
+
+// sigma = dOmega/dh (x_gs + h c) for one trial vector c = (c1, c2).
+void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision) {
+  if (!S->prepared) throw Error(MLCC_E_STATE, "mlcc_sigma: call mlcc_jacobian_prepare first");
+  cudaStream_t s = stm(S);
+  const int n = S->n, no = S->no, nv = S->nv, nj = S->nj, so = S->so, sv = S->sv;
+  const int64_t nn = int64_t(n) * n, dS = S->dS;
+  const double* c1 = c;
+  const double* c2 = c + int64_t(nv) * no;
+  double* s1 = sigma;
+  double* s2 = sigma + int64_t(nv) * no;
+  Scope sc(S->ws);
+  double* dLt = S->ws.get<double>(size_t(nj) * nn);
+  double* dht = S->ws.get<double>(size_t(nn));
+  double* dFt = S->ws.get<double>(size_t(nn));
+  dress_tangent(S, c1, dLt, dht);
+  build_fock_tangent(S, dht, dLt, dFt);
+  // singles: tangent of F~_AI
+  block2d(S, nv, no, dFt + int64_t(no) * n, n, s1, no, 1.0, 0.0);
+  if (dS > 0) {
+    // doubles on P_S: d g~_aibj = dLt_ai Lt_bj + Lt_ai dLt_bj, plus eps c
+    {
+      Scope sd(S->ws);
+      double* V = S->ws.get<double>(size_t(nj) * dS);
+      gather_vo(S, dLt, V);
+      double* W = S->ws.get<double>(size_t(S->nd));
+      rank_gemm(S, precision, true, S->Lai, V, W, 1.0, 0.0);
+      dim3 blk(32, 8), grd(unsigned((dS + 31) / 32), unsigned((dS + 31) / 32));
+      k_sigma2_cc2<<<grd, blk, 0, s>>>(W, c2, S->eps, no, sv, so, S->tv, S->to, s2);
+      MLCC_CHECK_LAUNCH();
+    }
+    // singles from the u-terms of Eq. mlcc2_omega_codable, by the product rule
+    double* uc = S->ws.get<double>(size_t(S->nd));
+    make_u(S, c2, uc);
+    double* Zc = S->ws.get<double>(size_t(nj) * dS);
+    rank_gemm(S, precision, false, S->Lov, uc, Zc, 1.0, 0.0);
+    Gemm a;
+    a.M = nv; a.N = so; a.K = sv;
+    a.ldb = so; a.sB = dS; a.lda = n; a.sA = nn;
+    a.C = s1; a.ldc = no; a.alpha = 1.0; a.beta = 1.0; a.batch = nj; a.reduce = true;
+    a.A = dLt + int64_t(no) * n + no; a.B = S->Z;
+    gemm_f64(a, S->ws, s, smc(S));
+    a.A = S->Lt + int64_t(no) * n + no; a.B = Zc;
+    gemm_f64(a, S->ws, s, smc(S));
+    Gemm b;
+    b.M = sv; b.N = no; b.K = so;
+    b.lda = so; b.sA = dS; b.ldb = n; b.sB = nn;
+    b.C = s1; b.ldc = no; b.alpha = -1.0; b.beta = 1.0; b.batch = nj; b.reduce = true;
+    b.A = Zc; b.B = S->Lt;
+    gemm_f64(b, S->ws, s, smc(S));
+    b.A = S->Z; b.B = dLt;
+    gemm_f64(b, S->ws, s, smc(S));
+    double* dfv = S->ws.get<double>(size_t(dS));
+    k_fov<<<nblk(dS), 256, 0, s>>>(dFt, n, no, sv, so, dfv);
+    MLCC_CHECK_LAUNCH();
+    double* tmp = S->ws.get<double>(size_t(dS));
+    Gemm cc;
+    cc.M = dS; cc.N = 1; cc.K = dS; cc.lda = dS; cc.ldb = 1; cc.C = tmp; cc.ldc = 1;
+    cc.A = uc; cc.B = S->Fov; cc.beta = 0.0;
+    gemm_f64(cc, S->ws, s, smc(S));
+    cc.A = S->u; cc.B = dfv; cc.beta = 1.0;
+    gemm_f64(cc, S->ws, s, smc(S));
+    k_scatter_add_ai<<<nblk(dS), 256, 0, s>>>(tmp, sv, so, no, 1.0, s1);
+    MLCC_CHECK_LAUNCH();
+  }
+  // CCSD rows: tangent of the CCSD residual around the cached values
+  if (S->to > 0 && S->tv > 0) {
+    Scope sb(S->ws);
+    Dual Lai, Lac, Lki, Lkc, Fvv, Foo, t;
+    extract_box(S, dLt, dFt, c2, Lai.d, Lac.d, Lki.d, Lkc.d, Fvv.d, Foo.d, t.d);
+    const int64_t tl = int64_t(S->tv) * S->to * S->tv * S->to;
+    double* omT = S->ws.get<double>(size_t(tl));
+    ccsd_block(S, Mode::Tangent, Lai, Lac, Lki, Lkc, Fvv, Foo, t, omT, false);
+    put_tbox(S, omT, s2);
+  }
+}
+
+}  // namespace mlcc

@@ -1,0 +1,541 @@
+// Control loops on the host, arithmetic on the device: the DIIS-accelerated quasi-Newton
+// ground-state solver (Sec. 2.1) and the Davidson solver for the lowest right
+// eigenpairs of the non-symmetric Jacobian (Sec. 2.1, excitation energies).
+#include "system.cuh"
+#include "small_eig.h"
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <numeric>
+
+namespace mlcc {
+
+namespace {
+inline int nblk(int64_t n) { return int(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 16384))); }
+
+// quasi-Newton step on (t1, tT): p = x - Omega / eps, e = Omega / eps
+__global__ void k_qn(const double* t1, const double* tT, const double* om1, const double* omT,
+                     const double* eps, int no, int nv, int tv, int to, double* p, double* e) {
+  const int64_t n1 = int64_t(nv) * no, nt = int64_t(tv) * to * tv * to, total = n1 + nt;
+  for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < total;
+       k += int64_t(gridDim.x) * blockDim.x) {
+    double x, om, den;
+    if (k < n1) {
+      const int a = int(k / no), i = int(k - int64_t(a) * no);
+      x = t1[k];
+      om = om1[k];
+      den = eps[no + a] - eps[i];
+    } else {
+      int64_t t = k - n1;
+      const int j = int(t % to); t /= to;
+      const int b = int(t % tv); t /= tv;
+      const int i = int(t % to);
+      const int a = int(t / to);
+      x = tT[k - n1];
+      om = omT[k - n1];
+      den = eps[no + a] - eps[i] + eps[no + b] - eps[j];
+    }
+    e[k] = om / den;
+    p[k] = x - om / den;
+  }
+}
+
+// Davidson preconditioner: d = (w - eps_mu)^-1 r, doubles symmetrised over (ai) <-> (bj)
+__global__ void k_precond_singles(const double* r, const double* eps, int no, int nv, double w,
+                                  double* d) {
+  const int64_t n1 = int64_t(nv) * no;
+  for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < n1;
+       k += int64_t(gridDim.x) * blockDim.x) {
+    const int a = int(k / no), i = int(k - int64_t(a) * no);
+    double den = w - (eps[no + a] - eps[i]);
+    if (fabs(den) < 1e-8) den = den < 0 ? -1e-8 : 1e-8;
+    d[k] = r[k] / den;
+  }
+}
+__global__ void k_precond_doubles(const double* r, const double* eps, int no, int sv, int so,
+                                  double w, double* d) {
+  __shared__ double tile[32][33];
+  const int64_t dS = int64_t(sv) * so;
+  const int64_t r0 = int64_t(blockIdx.y) * 32, c0 = int64_t(blockIdx.x) * 32;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int64_t rr = c0 + y, cc = r0 + threadIdx.x;
+    tile[y][threadIdx.x] = (rr < dS && cc < dS) ? r[rr * dS + cc] : 0.0;
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int64_t row = r0 + y, col = c0 + threadIdx.x;
+    if (row >= dS || col >= dS) continue;
+    const int a = int(row / so), i = int(row - int64_t(a) * so);
+    const int b = int(col / so), j = int(col - int64_t(b) * so);
+    double den = w - (eps[no + a] - eps[i] + eps[no + b] - eps[j]);
+    if (fabs(den) < 1e-8) den = den < 0 ? -1e-8 : 1e-8;
+    d[row * dS + col] = 0.5 * (r[row * dS + col] + tile[threadIdx.x][y]) / den;
+  }
+}
+// R_k -= w_k X_k
+__global__ void k_resid(double* R, const double* X, int64_t dim, double w) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < dim;
+       i += int64_t(gridDim.x) * blockDim.x)
+    R[i] -= w * X[i];
+}
+__global__ void k_scale(double* x, int64_t n, double a) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x)
+    x[i] *= a;
+}
+__global__ void k_set(double* x, int64_t i, double v) { x[i] = v; }
+// index of the largest |x| (first on ties), deterministic two-level reduction in one block
+__global__ void k_argmax_abs(const double* x, int64_t n, double* out_val) {
+  __shared__ double bv[256];
+  __shared__ long long bi[256];
+  double best = -1.0;
+  long long bidx = 0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double a = fabs(x[i]);
+    if (a > best) { best = a; bidx = i; }
+  }
+  bv[threadIdx.x] = best;
+  bi[threadIdx.x] = bidx;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      const double o = bv[threadIdx.x + w];
+      const long long oi = bi[threadIdx.x + w];
+      if (o > bv[threadIdx.x] || (o == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
+        bv[threadIdx.x] = o;
+        bi[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out_val[0] = x[bi[0]];
+}
+}  // namespace
+
+static double host_scalar(mlcc_system* S, const double* d) {
+  double h;
+  copy_d2h(&h, d, 1, S->ctx->stream);
+  return h;
+}
+
+// =================================================================================
+// Ground state
+mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out,
+                         double* x2_out, mlcc_gs_info* info) {
+  cudaStream_t s = S->ctx->stream;
+  const int no = S->no, nv = S->nv, to = S->to, tv = S->tv;
+  const int64_t n1 = int64_t(nv) * no;
+  const int64_t tl = (to > 0 && tv > 0) ? int64_t(tv) * to * tv * to : 0;
+  const int64_t len = n1 + tl;
+  const int dd = std::max(1, opt->diis_dim);
+  Scope sc(S->ws);
+  double* t1 = S->ws.get<double>(n1);
+  double* tT = S->ws.get<double>(std::max<int64_t>(tl, 1));
+  double* om1 = S->ws.get<double>(n1);
+  double* omT = S->ws.get<double>(std::max<int64_t>(tl, 1));
+  double* x2 = S->nd ? x2_out : nullptr;
+  double* energy = S->ws.get<double>(1);
+  double* nrm = S->ws.get<double>(2);
+  double* P = S->ws.get<double>(size_t(dd) * len);
+  double* Er = S->ws.get<double>(size_t(dd) * len);
+  double* pn = S->ws.get<double>(len);
+  double* en = S->ws.get<double>(len);
+  double* dv = S->ws.get<double>(dd);
+  double* cdev = S->ws.get<double>(dd);
+  fill(t1, n1, 0.0, s);
+  if (tl) fill(tT, tl, 0.0, s);
+  std::vector<double> Bm(size_t(dd) * dd, 0.0);
+  std::vector<int> order;   // ring slots, oldest first
+  double e_old = 0.0, e = 0.0, norm = 0.0;
+  int it = 0;
+  bool conv = false;
+  for (it = 1; it <= opt->max_gs_iter; ++it) {
+    omega_eval(S, t1, nullptr, true, tl ? tT : nullptr, x2, om1, tl ? omT : nullptr, energy);
+    dots(om1, 0, 1, om1, n1, nrm, S->ws, s);
+    if (tl) dots(omT, 0, 1, omT, tl, nrm + 1, S->ws, s);
+    else fill(nrm + 1, 1, 0.0, s);
+    double h[3];
+    copy_d2h(h, energy, 1, s);
+    copy_d2h(h + 1, nrm, 2, s);
+    e = h[0];
+    norm = std::sqrt(h[1] + h[2]);
+    if (!std::isfinite(e) || !std::isfinite(norm))
+      throw Error(MLCC_E_NAN, "ground state: NaN or Inf in the residual at iteration " + std::to_string(it));
+    if (norm < opt->gs_tol && std::fabs(e - e_old) < opt->gs_energy_tol) {
+      conv = true;
+      break;
+    }
+    e_old = e;
+    k_qn<<<nblk(len), 256, 0, s>>>(t1, tT, om1, omT, S->eps, no, nv, tv, to, pn, en);
+    MLCC_CHECK_LAUNCH();
+    // ring buffer of (p, e)
+    int slot;
+    if (int(order.size()) < dd) {
+      slot = int(order.size());
+    } else {
+      slot = order.front();
+      order.erase(order.begin());
+    }
+    order.push_back(slot);
+    MLCC_CUDA(cudaMemcpyAsync(P + int64_t(slot) * len, pn, size_t(len) * 8, cudaMemcpyDeviceToDevice, s));
+    MLCC_CUDA(cudaMemcpyAsync(Er + int64_t(slot) * len, en, size_t(len) * 8, cudaMemcpyDeviceToDevice, s));
+    dots(Er, len, dd, en, len, dv, S->ws, s);
+    std::vector<double> dh(dd);
+    copy_d2h(dh.data(), dv, dd, s);
+    for (int k : order) {
+      Bm[size_t(slot) * dd + k] = dh[k];
+      Bm[size_t(k) * dd + slot] = dh[k];
+    }
+    const int m = int(order.size());
+    std::vector<double> coef(dd, 0.0);
+    bool ok = false;
+    if (m > 1) {
+      double scale = 0.0;
+      for (int k : order) scale = std::max(scale, std::fabs(Bm[size_t(k) * dd + k]));
+      if (scale <= 0.0) scale = 1.0;
+      std::vector<double> A(size_t(m + 1) * (m + 1), 0.0), b(m + 1, 0.0), x;
+      for (int r = 0; r < m; ++r) {
+        for (int c = 0; c < m; ++c) A[r * (m + 1) + c] = Bm[size_t(order[r]) * dd + order[c]] / scale;
+        A[r * (m + 1) + m] = -1.0;
+        A[m * (m + 1) + r] = -1.0;
+      }
+      b[m] = -1.0;
+      if (solve_linear(m + 1, A, b, x)) {
+        for (int r = 0; r < m; ++r) coef[order[r]] = x[r];
+        ok = true;
+      }
+    }
+    if (!ok) {
+      std::fill(coef.begin(), coef.end(), 0.0);
+      coef[slot] = 1.0;
+    }
+    copy_h2d(cdev, coef.data(), dd, s);
+    Gemm g;  // pn = sum_k coef_k P_k
+    g.M = 1; g.N = len; g.K = dd;
+    g.A = cdev; g.lda = dd; g.B = P; g.ldb = len; g.C = pn; g.ldc = len;
+    gemm_f64(g, S->ws, s, S->ctx->sm_count);
+    MLCC_CUDA(cudaMemcpyAsync(t1, pn, size_t(n1) * 8, cudaMemcpyDeviceToDevice, s));
+    if (tl) MLCC_CUDA(cudaMemcpyAsync(tT, pn + n1, size_t(tl) * 8, cudaMemcpyDeviceToDevice, s));
+  }
+  if (!conv) it = opt->max_gs_iter;
+  MLCC_CUDA(cudaMemcpyAsync(t1_out, t1, size_t(n1) * 8, cudaMemcpyDeviceToDevice, s));
+  if (info) {
+    info->e_corr = e;
+    info->omega_norm = norm;
+    info->iterations = it;
+    info->converged = conv ? 1 : 0;
+  }
+  // the Jacobian is taken at the returned amplitudes
+  jacobian_prepare(S, t1_out, x2_out);
+  MLCC_CUDA(cudaStreamSynchronize(s));
+  return conv ? MLCC_OK : MLCC_E_GS_NOCONV;
+}
+
+// =================================================================================
+// Davidson
+namespace {
+struct DavState {
+  mlcc_system* S;
+  int64_t dim;
+  int maxsub;
+  double* B;   // [maxsub][dim]
+  double* Sg;  // [maxsub][dim]
+  int m = 0;
+  std::vector<double> G;  // [maxsub][maxsub] host, G[i][j] = B_i . S_j
+};
+}  // namespace
+
+static void sigma_batch(mlcc_system* S, const double* C, double* Sg, int nvec, int64_t dim, int prec) {
+  for (int k = 0; k < nvec; ++k) sigma_eval(S, C + int64_t(k) * dim, Sg + int64_t(k) * dim, prec);
+}
+
+// add the new columns [m0, m) to G
+static void update_G(DavState& D, int m0) {
+  mlcc_system* S = D.S;
+  cudaStream_t s = S->ctx->stream;
+  Scope sc(S->ws);
+  double* out = S->ws.get<double>(D.maxsub);
+  std::vector<double> h(D.maxsub);
+  for (int k = m0; k < D.m; ++k) {
+    // G[i][k] = B_i . S_k for i < m
+    dots(D.B, D.dim, D.m, D.Sg + int64_t(k) * D.dim, D.dim, out, S->ws, s);
+    copy_d2h(h.data(), out, D.m, s);
+    for (int i = 0; i < D.m; ++i) D.G[size_t(i) * D.maxsub + k] = h[i];
+    // G[k][j] = B_k . S_j for j < m0
+    if (m0 > 0) {
+      dots(D.Sg, D.dim, m0, D.B + int64_t(k) * D.dim, D.dim, out, S->ws, s);
+      copy_d2h(h.data(), out, m0, s);
+      for (int j = 0; j < m0; ++j) D.G[size_t(k) * D.maxsub + j] = h[j];
+    }
+  }
+}
+
+// orthonormalise v against B[0..m) (two passes); returns false if v collapses
+static bool orthonormalise(DavState& D, double* v) {
+  mlcc_system* S = D.S;
+  cudaStream_t s = S->ctx->stream;
+  Scope sc(S->ws);
+  double* coef = S->ws.get<double>(std::max(D.m, 1));
+  double* nr = S->ws.get<double>(1);
+  dots(v, 0, 1, v, D.dim, nr, S->ws, s);
+  const double n0 = std::sqrt(host_scalar(S, nr));
+  if (!(n0 > 0.0) || !std::isfinite(n0)) return false;
+  for (int pass = 0; pass < 2 && D.m > 0; ++pass) {
+    dots(D.B, D.dim, D.m, v, D.dim, coef, S->ws, s);
+    Gemm g;
+    g.M = 1; g.N = D.dim; g.K = D.m;
+    g.A = coef; g.lda = D.m; g.B = D.B; g.ldb = D.dim; g.C = v; g.ldc = D.dim;
+    g.alpha = -1.0; g.beta = 1.0;
+    gemm_f64(g, S->ws, s, S->ctx->sm_count);
+  }
+  dots(v, 0, 1, v, D.dim, nr, S->ws, s);
+  const double n1 = std::sqrt(host_scalar(S, nr));
+  if (!(n1 > 1e-10 * n0)) return false;
+  k_scale<<<nblk(D.dim), 256, 0, s>>>(v, D.dim, 1.0 / n1);
+  MLCC_CHECK_LAUNCH();
+  return true;
+}
+
+// X = Y^T B, R = Y^T S - w X for the wanted Ritz pairs
+static void ritz(DavState& D, const std::vector<double>& Yt, int nr, const std::vector<double>& w,
+                 double* X, double* R) {
+  mlcc_system* S = D.S;
+  cudaStream_t s = S->ctx->stream;
+  Scope sc(S->ws);
+  double* y = S->ws.get<double>(size_t(nr) * D.m);
+  copy_h2d(y, Yt.data(), int64_t(nr) * D.m, s);
+  Gemm g;
+  g.M = nr; g.N = D.dim; g.K = D.m;
+  g.A = y; g.lda = D.m; g.B = D.B; g.ldb = D.dim; g.C = X; g.ldc = D.dim;
+  gemm_f64(g, S->ws, s, S->ctx->sm_count);
+  g.B = D.Sg; g.C = R;
+  gemm_f64(g, S->ws, s, S->ctx->sm_count);
+  for (int k = 0; k < nr; ++k) {
+    k_resid<<<nblk(D.dim), 256, 0, s>>>(R + int64_t(k) * D.dim, X + int64_t(k) * D.dim, D.dim, w[k]);
+    MLCC_CHECK_LAUNCH();
+  }
+}
+
+mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omega_host,
+                           double* r_out, mlcc_es_info* info) {
+  if (!S->prepared) throw Error(MLCC_E_STATE, "mlcc_excited_states: no prepared ground state");
+  cudaStream_t s = S->ctx->stream;
+  const int no = S->no, nv = S->nv, nr = opt->n_roots;
+  const int64_t n1 = int64_t(nv) * no, dim = n1 + S->nd;
+  MLCC_REQUIRE(nr >= 1 && nr <= n1, "n_roots must be in [1, n_vir * n_occ]");
+  int maxsub = opt->max_subspace > 0 ? opt->max_subspace : 8 * nr;
+  maxsub = std::max(maxsub, 3 * nr);
+  const int collapse = 2 * nr;
+  // Davidson memory: basis and sigma vectors, Ritz vectors, residuals, collapse scratch
+  Arena dav;
+  const size_t need = size_t(dim) * 8 * size_t(2 * maxsub + 2 * nr + 2 * collapse + 2) + (1 << 20);
+  dav.reserve(need);
+  DavState D{S, dim, maxsub, dav.get<double>(size_t(maxsub) * dim), dav.get<double>(size_t(maxsub) * dim)};
+  D.G.assign(size_t(maxsub) * maxsub, 0.0);
+  double* X = dav.get<double>(size_t(nr) * dim);
+  double* R = dav.get<double>(size_t(nr) * dim);
+  double* CB = dav.get<double>(size_t(collapse) * dim);
+  double* CS = dav.get<double>(size_t(collapse) * dim);
+  double* tmpv = dav.get<double>(size_t(dim));
+
+  // start vectors: 2 n_roots unit singles with the lowest eps_a - eps_i
+  std::vector<double> eh(S->n);
+  copy_d2h(eh.data(), S->eps, S->n, s);
+  std::vector<int64_t> idx(n1);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) {
+    const double ex = eh[no + x / no] - eh[x % no], ey = eh[no + y / no] - eh[y % no];
+    return ex < ey;
+  });
+  const int nguess = int(std::min<int64_t>(2 * nr, n1));
+  MLCC_CUDA(cudaMemsetAsync(D.B, 0, size_t(nguess) * dim * 8, s));
+  for (int k = 0; k < nguess; ++k) k_set<<<1, 1, 0, s>>>(D.B + int64_t(k) * dim, idx[k], 1.0);
+  MLCC_CHECK_LAUNCH();
+  D.m = nguess;
+
+  int prec = opt->precision;
+  const bool two_phase = (prec == MLCC_BF16) && opt->refine_fp64;
+  int n_sigma = 0, n_sigma_lowp = 0;
+  auto count_sigma = [&](int k) {
+    n_sigma += k;
+    if (prec == MLCC_BF16) n_sigma_lowp += k;
+  };
+  sigma_batch(S, D.B, D.Sg, D.m, dim, prec);
+  count_sigma(D.m);
+  update_G(D, 0);
+
+  std::vector<double> w_old(nr, 1e300), w(nr), rn(nr);
+  bool conv = false, complex_pair = false;
+  int it = 0;
+  const int max_it = std::max(1, opt->max_es_iter);
+  for (it = 1; it <= max_it; ++it) {
+    // subspace eigenproblem (host, binary64)
+    std::vector<double> Gm(size_t(D.m) * D.m);
+    for (int i = 0; i < D.m; ++i)
+      for (int j = 0; j < D.m; ++j) Gm[size_t(i) * D.m + j] = D.G[size_t(i) * maxsub + j];
+    std::vector<std::complex<double>> ev;
+    std::vector<std::vector<std::complex<double>>> vecs;
+    const int nwant = std::min(std::max(nr, collapse), D.m);
+    if (!eig_nonsym(D.m, Gm, ev, &vecs, nwant))
+      throw Error(MLCC_E_ES_NOCONV, "Davidson: subspace eigenproblem failed");
+    complex_pair = false;
+    for (int k = 0; k < nr; ++k) {
+      w[k] = ev[k].real();
+      if (std::fabs(ev[k].imag()) > 1e-10 * std::max(1.0, std::fabs(ev[k].real()))) complex_pair = true;
+    }
+    std::vector<double> Yt(size_t(nr) * D.m);
+    for (int k = 0; k < nr; ++k)
+      for (int i = 0; i < D.m; ++i) Yt[size_t(k) * D.m + i] = vecs[k][i].real();
+    ritz(D, Yt, nr, w, X, R);
+    // normalise X_k (and R_k with it), residual norms
+    {
+      Scope sc2(S->ws);
+      double* nx = S->ws.get<double>(1);
+      double* nrr = S->ws.get<double>(1);
+      for (int k = 0; k < nr; ++k) {
+        dots(X + int64_t(k) * dim, 0, 1, X + int64_t(k) * dim, dim, nx, S->ws, s);
+        const double xn = std::sqrt(host_scalar(S, nx));
+        k_scale<<<nblk(dim), 256, 0, s>>>(X + int64_t(k) * dim, dim, 1.0 / xn);
+        k_scale<<<nblk(dim), 256, 0, s>>>(R + int64_t(k) * dim, dim, 1.0 / xn);
+        MLCC_CHECK_LAUNCH();
+        dots(R + int64_t(k) * dim, 0, 1, R + int64_t(k) * dim, dim, nrr, S->ws, s);
+        rn[k] = std::sqrt(host_scalar(S, nrr));
+        if (!std::isfinite(rn[k])) throw Error(MLCC_E_NAN, "Davidson: NaN in a residual");
+      }
+    }
+    const double rtol = (two_phase && prec == MLCC_BF16) ? opt->lowp_res_tol : opt->es_res_tol;
+    std::vector<int> todo;
+    for (int k = 0; k < nr; ++k) {
+      const bool ok = (rn[k] < rtol) && (two_phase && prec == MLCC_BF16 ? true
+                                                                       : std::fabs(w[k] - w_old[k]) < opt->es_omega_tol);
+      if (!ok) todo.push_back(k);
+    }
+    w_old = w;
+    if (todo.empty()) {
+      if (two_phase && prec == MLCC_BF16) {
+        // refinement: restart from the low-precision Ritz vectors with binary64 sigma
+        prec = MLCC_FP64;
+        const int keep = std::min(nr, D.m);
+        MLCC_CUDA(cudaMemcpyAsync(CB, X, size_t(keep) * dim * 8, cudaMemcpyDeviceToDevice, s));
+        D.m = 0;
+        int added = 0;
+        for (int k = 0; k < keep; ++k) {
+          MLCC_CUDA(cudaMemcpyAsync(D.B + int64_t(D.m) * dim, CB + int64_t(k) * dim, size_t(dim) * 8,
+                                    cudaMemcpyDeviceToDevice, s));
+          if (orthonormalise(D, D.B + int64_t(D.m) * dim)) {
+            ++D.m;
+            ++added;
+          }
+        }
+        sigma_batch(S, D.B, D.Sg, D.m, dim, prec);
+        count_sigma(D.m);
+        std::fill(D.G.begin(), D.G.end(), 0.0);
+        update_G(D, 0);
+        std::fill(w_old.begin(), w_old.end(), 1e300);
+        continue;
+      }
+      conv = true;
+      break;
+    }
+    // new directions
+    std::vector<int> newk;
+    if (D.m + int(todo.size()) > maxsub) {
+      // collapse onto the lowest `collapse` Ritz vectors
+      const int c = std::min(collapse, D.m);
+      std::vector<double> Yc(size_t(c) * D.m);
+      for (int k = 0; k < c; ++k)
+        for (int i = 0; i < D.m; ++i) Yc[size_t(k) * D.m + i] = vecs[k][i].real();
+      {
+        Scope sc3(S->ws);
+        double* y = S->ws.get<double>(size_t(c) * D.m);
+        copy_h2d(y, Yc.data(), int64_t(c) * D.m, s);
+        Gemm g;
+        g.M = c; g.N = dim; g.K = D.m;
+        g.A = y; g.lda = D.m; g.B = D.B; g.ldb = dim; g.C = CB; g.ldc = dim;
+        gemm_f64(g, S->ws, s, S->ctx->sm_count);
+        g.B = D.Sg; g.C = CS;
+        gemm_f64(g, S->ws, s, S->ctx->sm_count);
+        // Gram-Schmidt on CB with the same combinations on CS
+        double* coef = S->ws.get<double>(size_t(c));
+        double* nx = S->ws.get<double>(1);
+        for (int k = 0; k < c; ++k) {
+          double* bk = CB + int64_t(k) * dim;
+          double* sk = CS + int64_t(k) * dim;
+          for (int pass = 0; pass < 2 && k > 0; ++pass) {
+            dots(CB, dim, k, bk, dim, coef, S->ws, s);
+            Gemm h;
+            h.M = 1; h.N = dim; h.K = k;
+            h.A = coef; h.lda = k; h.B = CB; h.ldb = dim; h.C = bk; h.ldc = dim;
+            h.alpha = -1.0; h.beta = 1.0;
+            gemm_f64(h, S->ws, s, S->ctx->sm_count);
+            h.B = CS; h.C = sk;
+            gemm_f64(h, S->ws, s, S->ctx->sm_count);
+          }
+          dots(bk, 0, 1, bk, dim, nx, S->ws, s);
+          const double nk = std::sqrt(host_scalar(S, nx));
+          k_scale<<<nblk(dim), 256, 0, s>>>(bk, dim, 1.0 / nk);
+          k_scale<<<nblk(dim), 256, 0, s>>>(sk, dim, 1.0 / nk);
+          MLCC_CHECK_LAUNCH();
+        }
+      }
+      MLCC_CUDA(cudaMemcpyAsync(D.B, CB, size_t(c) * dim * 8, cudaMemcpyDeviceToDevice, s));
+      MLCC_CUDA(cudaMemcpyAsync(D.Sg, CS, size_t(c) * dim * 8, cudaMemcpyDeviceToDevice, s));
+      D.m = c;
+      std::fill(D.G.begin(), D.G.end(), 0.0);
+      update_G(D, 0);
+    }
+    const int m0 = D.m;
+    for (int k : todo) {
+      if (D.m >= maxsub) break;
+      double* v = D.B + int64_t(D.m) * dim;
+      k_precond_singles<<<nblk(n1), 256, 0, s>>>(R + int64_t(k) * dim, S->eps, no, nv, w[k], v);
+      MLCC_CHECK_LAUNCH();
+      if (S->nd) {
+        dim3 blk(32, 8), grd(unsigned((S->dS + 31) / 32), unsigned((S->dS + 31) / 32));
+        k_precond_doubles<<<grd, blk, 0, s>>>(R + int64_t(k) * dim + n1, S->eps, no, S->sv, S->so,
+                                              w[k], v + n1);
+        MLCC_CHECK_LAUNCH();
+      }
+      if (orthonormalise(D, v)) ++D.m;
+    }
+    if (D.m == m0) {
+      // no new direction: the basis spans an invariant subspace
+      conv = true;
+      for (int k = 0; k < nr; ++k) conv = conv && rn[k] < opt->es_res_tol;
+      break;
+    }
+    sigma_batch(S, D.B + int64_t(m0) * dim, D.Sg + int64_t(m0) * dim, D.m - m0, dim, prec);
+    count_sigma(D.m - m0);
+    update_G(D, m0);
+  }
+  (void)tmpv;
+  // sign convention: largest-magnitude element positive
+  {
+    Scope sc4(S->ws);
+    double* mv = S->ws.get<double>(1);
+    for (int k = 0; k < nr; ++k) {
+      k_argmax_abs<<<1, 256, 0, s>>>(X + int64_t(k) * dim, dim, mv);
+      MLCC_CHECK_LAUNCH();
+      if (host_scalar(S, mv) < 0.0) {
+        k_scale<<<nblk(dim), 256, 0, s>>>(X + int64_t(k) * dim, dim, -1.0);
+        MLCC_CHECK_LAUNCH();
+      }
+    }
+  }
+  for (int k = 0; k < nr; ++k) omega_host[k] = w[k];
+  if (r_out) MLCC_CUDA(cudaMemcpyAsync(r_out, X, size_t(nr) * dim * 8, cudaMemcpyDeviceToDevice, s));
+  MLCC_CUDA(cudaStreamSynchronize(s));
+  if (info) {
+    info->iterations = it;
+    info->n_sigma = n_sigma;
+    info->n_sigma_lowp = n_sigma_lowp;
+    info->converged = conv ? 1 : 0;
+    info->complex_pair = complex_pair ? 1 : 0;
+  }
+  if (!conv) return MLCC_E_ES_NOCONV;
+  if (complex_pair) return MLCC_E_COMPLEX_ROOT;
+  return MLCC_OK;
+}
+
+}  // namespace mlcc

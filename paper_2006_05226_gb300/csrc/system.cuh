@@ -1,0 +1,86 @@
+// The device-side state of one MLCC problem and the steps of its hot path.
+#pragma once
+#include "internal.cuh"
+
+namespace mlcc {
+
+// Value or tangent of a tensor in the forward-mode (dual number) evaluation of the
+// residual: sigma = A c = dOmega/dh (x + h c) is the tangent of Omega along c.
+struct Dual {
+  DT v;   // value
+  DT d;   // tangent (d.p == nullptr: zero)
+};
+
+enum class Mode { Value, Tangent };
+
+struct CCSDCache;   // value tensors of the CCSD block at the Jacobian ground state
+
+struct TCGemm;      // tensor-core GEMM plan (mixed precision)
+
+}  // namespace mlcc
+
+struct mlcc_system {
+  mlcc_ctx* ctx = nullptr;
+  int n = 0, no = 0, nv = 0, nj = 0;
+  int so = 0, sv = 0, to = 0, tv = 0;
+  int64_t dS = 0;          // sv * so
+  int64_t nd = 0;          // dS * dS
+  std::vector<int32_t> perm;   // internal -> caller orbital
+  std::vector<double> eps_host;
+  // persistent device buffers
+  double* L = nullptr;     // [nj][n][n] internal order
+  double* h = nullptr;     // [n][n]
+  double* eps = nullptr;   // [n]
+  // current dressing (value)
+  double* Lt = nullptr;    // [nj][n][n]
+  double* ht = nullptr;    // [n][n]
+  double* Ft = nullptr;    // [n][n]
+  double* Lai = nullptr;   // [nj][dS]  Lt[J][no+a][i]
+  double* Lov = nullptr;   // [nj][dS]  Lt[J][j][no+c] stored at c*so + j
+  double* Z = nullptr;     // [nj][dS]  Z^J_bi = u_(bi)(cj) Lov^J_(cj)
+  double* u = nullptr;     // [nd]
+  double* Fov = nullptr;   // [dS]      F~[j][no+b] at b*so + j
+  // Jacobian ground state
+  bool prepared = false;
+  double* t1gs = nullptr;  // [nv][no]
+  double* x2gs = nullptr;  // [nd]
+  mlcc::CCSDCache* ccsd = nullptr;
+  mlcc::Arena persist;     // the buffers above
+  mlcc::Arena ws;          // scratch
+  int64_t workspace_bytes = 0;
+};
+
+namespace mlcc {
+
+// steps (all on sys->ctx->stream)
+void dress(mlcc_system* S, const double* t1, double* Lt, double* ht);
+void dress_tangent(mlcc_system* S, const double* c1, double* dLt, double* dht);
+void build_fock(mlcc_system* S, const double* ht, const double* Lt, double* Ft);
+void build_fock_tangent(mlcc_system* S, const double* dht, const double* dLt, double* dFt);
+void gather_vo(mlcc_system* S, const double* X, double* out);
+void gather_ov(mlcc_system* S, const double* X, double* out);
+void make_u(mlcc_system* S, const double* x2, double* u);
+void omega_eval(mlcc_system* S, const double* t1, const double* x2, bool gs_mode,
+                const double* tT, double* x2_out, double* om1, double* om2, double* energy);
+void jacobian_prepare(mlcc_system* S, const double* t1, const double* x2);
+void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision);
+void ccsd_block(mlcc_system* S, Mode mode, const Dual& Lai, const Dual& Lac, const Dual& Lki,
+                const Dual& Lkc, const Dual& Fvv, const Dual& Foo, const Dual& t, double* om_out,
+                bool cache_values);
+void ccsd_cache_free(mlcc_system* S);
+
+// kernel-family timing (rank_gemm): wraps a callable with events when enabled
+template <class F>
+void timed(mlcc_system* S, const char* fam, double flop, F&& f) {
+  auto& T = S->ctx->timer;
+  if (!T.enabled) {
+    f();
+    return;
+  }
+  cudaEvent_t a, b;
+  T.begin(fam, S->ctx->stream, flop, &a, &b);
+  f();
+  MLCC_CUDA(cudaEventRecord(b, S->ctx->stream));
+}
+
+}  // namespace mlcc

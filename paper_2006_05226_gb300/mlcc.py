@@ -1,0 +1,281 @@
+"""Thin Python binding of libmlcc (include/mlcc.h): argument marshalling only.
+
+Every step of the method runs inside libmlcc.so; this module only moves pointers and
+sizes across the C ABI. torch provides device memory and streams. The library works on
+its own CUDA stream; calls order it after torch's current stream and order torch's
+current stream after it, so tensors can be used on either side without races.
+"""
+import ctypes
+import os
+from ctypes import POINTER, byref, c_char_p, c_double, c_int, c_int8, c_int32, c_int64, c_void_p
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmlcc.so")
+
+MLCC_FP64, MLCC_BF16 = 0, 1
+STATUS = {0: "MLCC_OK", -1: "MLCC_E_ARG", -2: "MLCC_E_OOM", -3: "MLCC_E_GS_NOCONV",
+          -4: "MLCC_E_ES_NOCONV", -5: "MLCC_E_COMPLEX_ROOT", -6: "MLCC_E_NAN",
+          -8: "MLCC_E_CUDA", -9: "MLCC_E_STATE"}
+
+# every symbol include/mlcc.h declares
+EXPORTS = ["mlcc_default_options", "mlcc_ctx_create", "mlcc_ctx_destroy", "mlcc_ctx_stream",
+           "mlcc_last_error", "mlcc_kernel_timing", "mlcc_kernel_time", "mlcc_system_create",
+           "mlcc_system_destroy", "mlcc_system_info", "mlcc_orbital_order", "mlcc_t1_transform",
+           "mlcc_fock_t1", "mlcc_omega", "mlcc_ground_state", "mlcc_jacobian_prepare",
+           "mlcc_sigma", "mlcc_excited_states", "mlcc_solve"]
+
+
+class mlcc_problem(ctypes.Structure):
+    _fields_ = [("n_mo", c_int32), ("n_occ", c_int32), ("n_chol", c_int32),
+                ("level", POINTER(c_int8))]
+
+
+class mlcc_dims(ctypes.Structure):
+    _fields_ = [("n_occ", c_int32), ("n_vir", c_int32), ("s_occ", c_int32), ("s_vir", c_int32),
+                ("t_occ", c_int32), ("t_vir", c_int32), ("n_singles", c_int64),
+                ("n_doubles", c_int64), ("vector_len", c_int64), ("workspace_bytes", c_int64)]
+
+
+class mlcc_options(ctypes.Structure):
+    _fields_ = [("n_roots", c_int32), ("max_gs_iter", c_int32), ("max_es_iter", c_int32),
+                ("diis_dim", c_int32), ("max_subspace", c_int32), ("precision", c_int32),
+                ("refine_fp64", c_int32), ("_pad", c_int32), ("gs_tol", c_double),
+                ("gs_energy_tol", c_double), ("es_res_tol", c_double),
+                ("es_omega_tol", c_double), ("lowp_res_tol", c_double)]
+
+
+class mlcc_gs_info(ctypes.Structure):
+    _fields_ = [("e_hf", c_double), ("e_corr", c_double), ("omega_norm", c_double),
+                ("iterations", c_int32), ("converged", c_int32)]
+
+
+class mlcc_es_info(ctypes.Structure):
+    _fields_ = [("iterations", c_int32), ("n_sigma", c_int32), ("n_sigma_lowp", c_int32),
+                ("converged", c_int32), ("complex_pair", c_int32), ("_pad", c_int32)]
+
+
+class MLCCError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Loads libmlcc.so from the package directory; fails loudly if it is not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    P = c_void_p
+    D = POINTER(c_double)
+    sig = {
+        "mlcc_default_options": (None, [POINTER(mlcc_options)]),
+        "mlcc_ctx_create": (c_int, [c_int, POINTER(c_void_p)]),
+        "mlcc_ctx_destroy": (None, [P]),
+        "mlcc_ctx_stream": (c_void_p, [P]),
+        "mlcc_last_error": (c_char_p, []),
+        "mlcc_kernel_timing": (None, [P, c_int]),
+        "mlcc_kernel_time": (c_int, [P, c_char_p, POINTER(c_int64), D, D]),
+        "mlcc_system_create": (c_int, [P, POINTER(mlcc_problem), P, P, POINTER(c_void_p)]),
+        "mlcc_system_destroy": (None, [P]),
+        "mlcc_system_info": (c_int, [P, POINTER(mlcc_dims)]),
+        "mlcc_orbital_order": (c_int, [P, POINTER(c_int32)]),
+        "mlcc_t1_transform": (c_int, [P, P, P]),
+        "mlcc_fock_t1": (c_int, [P, P, P]),
+        "mlcc_omega": (c_int, [P, P, P, P, P, P]),
+        "mlcc_ground_state": (c_int, [P, POINTER(mlcc_options), P, P, POINTER(mlcc_gs_info)]),
+        "mlcc_jacobian_prepare": (c_int, [P, P, P]),
+        "mlcc_sigma": (c_int, [P, c_int32, P, P, c_int32]),
+        "mlcc_excited_states": (c_int, [P, POINTER(mlcc_options), D, P, POINTER(mlcc_es_info)]),
+        "mlcc_solve": (c_int, [P, POINTER(mlcc_problem), P, P, POINTER(mlcc_options),
+                               POINTER(mlcc_gs_info), D, POINTER(mlcc_es_info), P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != 0:
+        raise MLCCError(status, load().mlcc_last_error().decode())
+
+
+def default_options(**kw):
+    o = mlcc_options()
+    load().mlcc_default_options(byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t):
+    return c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Context:
+    """mlcc_ctx: one device, one stream."""
+
+    def __init__(self, device=0):
+        import torch
+        self._torch = torch
+        h = c_void_p()
+        _check(load().mlcc_ctx_create(device, byref(h)))
+        self.handle = h
+        self.device = device
+        self.stream = torch.cuda.ExternalStream(load().mlcc_ctx_stream(h), device=f"cuda:{device}")
+
+    def before(self, *tensors):
+        self.stream.wait_stream(self._torch.cuda.current_stream(self.device))
+        for t in tensors:
+            if t is not None:
+                t.record_stream(self.stream)
+
+    def after(self):
+        self._torch.cuda.current_stream(self.device).wait_stream(self.stream)
+
+    def kernel_timing(self, enable):
+        load().mlcc_kernel_timing(self.handle, 1 if enable else 0)
+
+    def kernel_time(self, family="rank_gemm"):
+        n, ms, fl = c_int64(), c_double(), c_double()
+        _check(load().mlcc_kernel_time(self.handle, family.encode(), byref(n), byref(ms), byref(fl)))
+        return n.value, ms.value, fl.value
+
+    def close(self):
+        if self.handle:
+            load().mlcc_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class System:
+    """mlcc_system: device copy of one problem (chol [n_chol, n, n], fock [n, n])."""
+
+    def __init__(self, ctx, chol, fock, n_occ, level):
+        torch = ctx._torch
+        assert chol.dtype == torch.float64 and fock.dtype == torch.float64
+        assert chol.is_cuda and fock.is_cuda and chol.is_contiguous() and fock.is_contiguous()
+        self.ctx = ctx
+        self.level = np.ascontiguousarray(np.asarray(level, dtype=np.int8))
+        prob = mlcc_problem(fock.shape[0], n_occ, chol.shape[0],
+                            self.level.ctypes.data_as(POINTER(c_int8)))
+        h = c_void_p()
+        ctx.before(chol, fock)
+        _check(load().mlcc_system_create(ctx.handle, byref(prob), _ptr(chol), _ptr(fock), byref(h)))
+        self.handle = h
+        d = mlcc_dims()
+        _check(load().mlcc_system_info(h, byref(d)))
+        self.dims = d
+        perm = (c_int32 * fock.shape[0])()
+        _check(load().mlcc_orbital_order(h, perm))
+        self.perm = np.array(perm[:], dtype=np.int64)
+        self.n, self.no = fock.shape[0], n_occ
+        self.nv = self.n - n_occ
+        self.n_chol = chol.shape[0]
+
+    def _new(self, *shape):
+        return self.ctx._torch.empty(*shape, dtype=self.ctx._torch.float64,
+                                     device=f"cuda:{self.ctx.device}")
+
+    def t1_transform(self, t1):
+        out = self._new(self.n_chol, self.n, self.n)
+        self.ctx.before(t1, out)
+        _check(load().mlcc_t1_transform(self.handle, _ptr(t1), _ptr(out)))
+        self.ctx.after()
+        return out
+
+    def fock_t1(self, t1):
+        out = self._new(self.n, self.n)
+        self.ctx.before(t1, out)
+        _check(load().mlcc_fock_t1(self.handle, _ptr(t1), _ptr(out)))
+        self.ctx.after()
+        return out
+
+    def omega(self, t1, x2):
+        om1 = self._new(self.dims.n_singles)
+        om2 = self._new(max(self.dims.n_doubles, 1))
+        e = self._new(1)
+        self.ctx.before(t1, x2, om1, om2, e)
+        _check(load().mlcc_omega(self.handle, _ptr(t1), _ptr(x2), _ptr(om1), _ptr(om2), _ptr(e)))
+        self.ctx.after()
+        return om1, om2[: self.dims.n_doubles], e
+
+    def ground_state(self, opts=None):
+        opts = opts or default_options()
+        t1 = self._new(self.dims.n_singles)
+        x2 = self._new(max(self.dims.n_doubles, 1))
+        info = mlcc_gs_info()
+        self.ctx.before(t1, x2)
+        st = load().mlcc_ground_state(self.handle, byref(opts), _ptr(t1), _ptr(x2), byref(info))
+        self.ctx.after()
+        _check(st)
+        return t1, x2[: self.dims.n_doubles], info
+
+    def jacobian_prepare(self, t1, x2):
+        self.ctx.before(t1, x2)
+        _check(load().mlcc_jacobian_prepare(self.handle, _ptr(t1), _ptr(x2)))
+        self.ctx.after()
+
+    def sigma(self, c, precision=MLCC_FP64):
+        c = c.reshape(-1, self.dims.vector_len)
+        out = self._new(c.shape[0], self.dims.vector_len)
+        self.ctx.before(c, out)
+        _check(load().mlcc_sigma(self.handle, c.shape[0], _ptr(c), _ptr(out), precision))
+        self.ctx.after()
+        return out
+
+    def excited_states(self, opts=None, want_vectors=True):
+        opts = opts or default_options()
+        w = (c_double * opts.n_roots)()
+        R = self._new(opts.n_roots, self.dims.vector_len) if want_vectors else None
+        info = mlcc_es_info()
+        self.ctx.before(R)
+        st = load().mlcc_excited_states(self.handle, byref(opts), w, _ptr(R), byref(info))
+        self.ctx.after()
+        _check(st)
+        return np.array(w[:]), R, info
+
+    def close(self):
+        if self.handle:
+            load().mlcc_system_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve(ctx, chol_host, fock_host, n_occ, level, opts=None):
+    """mlcc_solve from host arrays (copies them to the device inside the call)."""
+    chol_host = np.ascontiguousarray(chol_host, dtype=np.float64)
+    fock_host = np.ascontiguousarray(fock_host, dtype=np.float64)
+    level = np.ascontiguousarray(np.asarray(level, dtype=np.int8))
+    opts = opts or default_options()
+    prob = mlcc_problem(fock_host.shape[0], n_occ, chol_host.shape[0],
+                        level.ctypes.data_as(POINTER(c_int8)))
+    gs, es = mlcc_gs_info(), mlcc_es_info()
+    w = (c_double * opts.n_roots)()
+    nv = fock_host.shape[0] - n_occ
+    t1 = np.zeros(nv * n_occ)
+    st = load().mlcc_solve(ctx.handle, byref(prob), c_void_p(chol_host.ctypes.data),
+                           c_void_p(fock_host.ctypes.data), byref(opts), byref(gs), w, byref(es),
+                           c_void_p(t1.ctypes.data))
+    _check(st)
+    return gs, np.array(w[:]), es, t1
