@@ -1,0 +1,315 @@
+#!/usr/bin/env python
+"""Benchmark: Davidson sigma-vectors/s of the MLCC excitation solve on one GB300 per rank.
+
+One step is one pass of the whole hot path over one synthetic system: system set-up with
+the recovery of h (Eq. eff_fock), the DIIS / quasi-Newton ground state (T1-dressing,
+X1-basis Fock matrix, CC2 doubles, MLCCSD doubles residual, singles residual, energy),
+the Jacobian intermediates, and the Davidson solve for the lowest roots with sigma = A c
+(and, on the mixed path, the binary64 refinement). value = sigma-vectors evaluated in the
+Davidson solves of all ranks / max over ranks of the timed wall time (CUDA events).
+
+Workload: 340 orbitals (40 occupied, 300 virtual), 1500 Cholesky vectors, CCSD-active
+10 occupied / 60 virtual, CC2-active the rest, 4 roots (the second configuration of the
+paper-shaped workloads); synthetic seeded inputs (synth/), larger than L2 (L is 1.39 GB).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|bf16] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Davidson sigma-vectors/s"
+UNIT = "sigma-vectors/s"
+WORKLOAD = "mid"
+# FP64 DFMA peak of the GB300 SM: 152 SMs x 2 FP64 FMA/clock x 2 flop x 2.070 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return d, "measured"
+        except Exception:
+            pass
+    return dict(FALLBACK), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        for line in open(self.file.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def cpu_sample_oracle(system, seconds_hint=30.0):
+    """The oracle, as it stands, on the host cores: one Jacobian transformation of the
+    same system by its explicit real-arithmetic MLCC2 formula (Appendix A), at seeded
+    random amplitudes. Returns (sigma-vectors/s, cores, description)."""
+    import numpy as np
+    from oracle.mlcc import MLCCSystem, sigma_mlcc2_paper
+    cores = len(os.sched_getaffinity(0))
+    o = MLCCSystem(system.L, system.fock, system.spec.n_occ, system.level)
+    rng = np.random.default_rng(0)
+    t1 = 0.01 * rng.standard_normal((o.nv, o.no))
+    x2 = 0.01 * rng.standard_normal(o.doubles_shape())
+    x2 = x2 + x2.transpose(2, 3, 0, 1)
+    c1 = rng.standard_normal((o.nv, o.no))
+    c2 = rng.standard_normal(o.doubles_shape())
+    c2 = c2 + c2.transpose(2, 3, 0, 1)
+    t0 = time.perf_counter()
+    sigma_mlcc2_paper(o, t1, x2, c1, c2)
+    dt = time.perf_counter() - t0
+    desc = ("one sigma-vector of the same 340-orbital system by the oracle's explicit MLCC2 "
+            "Jacobian formula (Appendix A; CCSD-block terms not included), FP64 numpy")
+    return 1.0 / dt, cores, desc, dt
+
+
+def set_blas_threads():
+    n = str(len(os.sched_getaffinity(0)))
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(k, n)
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    set_blas_threads()
+    from synth import CONFIGS, make_system
+    system = make_system(CONFIGS[WORKLOAD])
+    for _ in range(args.warmup):
+        cpu_sample_oracle(system)
+    times = []
+    cores, desc = None, None
+    for _ in range(args.steps):
+        v, cores, desc, dt = cpu_sample_oracle(system)
+        times.append(dt)
+    value = args.steps / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(args, "fp64"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(args, prec):
+    from synth import CONFIGS
+    s = CONFIGS[WORKLOAD]
+    return {"workload": f"MLCCSD three-level: {s.n_mo} orbitals ({s.n_occ} occ / {s.n_vir} vir), "
+                        f"{s.n_chol} Cholesky vectors, CCSD-active {s.t_occ}/{s.t_vir}, "
+                        f"CC2-active {s.s_occ}/{s.s_vir}, {s.n_roots} roots",
+            "n_mo": s.n_mo, "n_occ": s.n_occ, "n_chol": s.n_chol, "ccsd_active": [s.t_occ, s.t_vir],
+            "cc2_active": [s.s_occ, s.s_vir], "n_roots": s.n_roots, "precision": prec,
+            "l2": "inputs larger than L2 (L^J_pq is 1.39 GB)", "parallelism": f"replicas{args.gpus}"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", default="bf16", choices=["fp64", "bf16"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    rank, world, local = dist_env()
+    import numpy as np
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2006_05226_gb300 import mlcc
+    from synth import CONFIGS, make_system
+    from dataclasses import replace
+
+    spec = replace(CONFIGS[WORKLOAD], seed=CONFIGS[WORKLOAD].seed + rank)
+    system = make_system(spec)
+    prec = mlcc.MLCC_FP64 if args.precision == "fp64" else mlcc.MLCC_BF16
+    opts = mlcc.default_options(n_roots=spec.n_roots, precision=prec, refine_fp64=1)
+    ctx = mlcc.Context(local)
+    L_dev = torch.as_tensor(system.L, device=f"cuda:{local}")
+    F_dev = torch.as_tensor(system.fock, device=f"cuda:{local}")
+
+    def step():
+        g = mlcc.System(ctx, L_dev, F_dev, spec.n_occ, system.level)
+        t1, x2, gi = g.ground_state(opts)
+        w, _, ei = g.excited_states(opts, want_vectors=False)
+        g.close()
+        return ei.n_sigma, ei.n_sigma_lowp, w, gi
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ctx.kernel_timing(True)
+    launches0 = mlcc.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(ctx.stream)
+    n_sigma = n_lowp = 0
+    omegas, gs = None, None
+    for _ in range(args.steps):
+        ns, nl, omegas, gs = step()
+        n_sigma += ns
+        n_lowp += nl
+    ev1.record(ctx.stream)
+    torch.cuda.synchronize()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    launches = mlcc.launch_count() - launches0
+    k_n, k_ms, k_flop = ctx.kernel_time("rank_gemm")
+    ctx.kernel_timing(False)
+    clk = clocks.stop()
+    barrier(world)
+    t_max = allreduce_max(elapsed, world)
+    total_sigma = allreduce_sum(float(n_sigma), world)
+    value = total_sigma / t_max
+
+    # end to end through the public host-memory entry point (H2D of L and F inside)
+    e2e = None
+    if not args.no_e2e:
+        Lh = np.ascontiguousarray(system.L)
+        Fh = np.ascontiguousarray(system.fock)
+        barrier(world)
+        t0 = time.perf_counter()
+        gi, w2, ei, t1h = mlcc.solve(ctx, Lh, Fh, spec.n_occ, system.level, opts)
+        dt = time.perf_counter() - t0
+        dt = allreduce_max(dt, world)
+        e_val = allreduce_sum(float(ei.n_sigma), world) / dt
+        e2e = {"value": e_val, "unit": UNIT, "h2d_bytes_per_step": int(Lh.nbytes + Fh.nbytes),
+               "d2h_bytes_per_step": int(8 * (len(w2) + t1h.size))}
+
+    if rank != 0:
+        return 0
+    pk, src = peaks()
+    if prec == mlcc.MLCC_FP64:
+        ach = k_flop / (k_ms / 1e3) / 1e12 if k_ms > 0 else None
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": (ach / FP64_PEAK_TFLOPS) if ach else None, "traffic": None,
+                "kernel": "rank_gemm (binary64 DFMA tiles)",
+                "peak_source": "FP64 DFMA rate from unit counts and clock"}
+    else:
+        ach = k_flop / (k_ms / 1e3) / 1e12 if k_ms > 0 else None
+        peak = pk.get("bf16_tflops_sustained", FALLBACK["bf16_tflops_sustained"])
+        roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": (ach / peak) if ach else None, "traffic": None,
+                "kernel": "rank_gemm (tcgen05 bf16, fp32 accumulate)",
+                "peak_source": f"bf16 sustained, of {src}"}
+    roof["launches"] = k_n
+    roof["avg_launch_ms"] = (k_ms / k_n) if k_n else None
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == mlcc.MLCC_FP64 else "bf16+f64",
+            "data": "synthetic", "config": config_dict(args, args.precision),
+            "solves_per_s": args.steps * world / t_max, "sigma_per_step": n_sigma / args.steps,
+            "sigma_lowp_per_step": n_lowp / args.steps,
+            "omega": [float(x) for x in omegas], "e_corr": gs.e_corr,
+            "roofline": roof, "clocks": clk, "gpu_launches": int(launches), "e2e": e2e}
+    if world == 1 and not args.no_cpu_baseline:
+        set_blas_threads()
+        v, cores, desc, dt = cpu_sample_oracle(system)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": desc, "seconds": dt}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

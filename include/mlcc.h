@@ -67,9 +67,12 @@ typedef enum {
 } mlcc_status;
 
 typedef enum {
-  MLCC_FP64 = 0,  /* every contraction in binary64                                  */
-  MLCC_BF16 = 1   /* Cholesky-rank doubles contractions on tcgen05 tensor cores with
-                     bfloat16 operands and fp32 accumulation; the rest in binary64   */
+  MLCC_FP64 = 0,    /* every contraction in binary64                                  */
+  MLCC_BF16 = 1,    /* the Cholesky-rank doubles contractions of sigma on tcgen05 tensor
+                       cores, bfloat16 operands, fp32 accumulation; the rest binary64  */
+  MLCC_BF16X3 = 2,  /* as MLCC_BF16 with operands split x = x0 + x1 (bfloat16 pieces)
+                       and the products x0y0 + x0y1 + x1y0                             */
+  MLCC_BF16X6 = 3   /* three pieces x0 + x1 + x2 and the six products of order <= 2   */
 } mlcc_precision;
 
 typedef enum { MLCC_LEVEL_CCS = 0, MLCC_LEVEL_CC2 = 1, MLCC_LEVEL_CCSD = 2 } mlcc_level;
@@ -146,6 +149,8 @@ const char* mlcc_last_error(void);
 void mlcc_kernel_timing(mlcc_ctx* ctx, int enable);
 mlcc_status mlcc_kernel_time(mlcc_ctx* ctx, const char* family, int64_t* launches,
                              double* total_ms, double* total_flop);
+/* Number of kernels libmlcc has launched in this process (all contexts), for accounting. */
+int64_t mlcc_launch_count(void);
 
 /* ---- system -------------------------------------------------------------------- */
 /* Takes device copies of chol (Sec. 2.4 MO Cholesky vectors) and fock (Eq. eff_fock),

@@ -10,6 +10,7 @@
 
 namespace mlcc {
 const char* last_error_cstr();
+int64_t launch_count();
 mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out, double* x2_out,
                          mlcc_gs_info* info);
 mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omega_host,
@@ -90,7 +91,7 @@ static void setup_system(mlcc_system* S, const mlcc_problem* P, const double* ch
   // persistent buffers
   const size_t per = size_t(nj) * nn * 2 + 3 * size_t(nn) + size_t(n) + 3 * size_t(nj) * dS +
                      size_t(S->nd) * 2 + size_t(dS) + size_t(S->nv) * no;
-  S->persist.reserve(per * 8 + 64 * 256);
+  S->persist.reserve(per * 8 + 96 * 256);
   S->L = S->persist.get<double>(size_t(nj) * nn);
   S->Lt = S->persist.get<double>(size_t(nj) * nn);
   S->h = S->persist.get<double>(nn);
@@ -104,6 +105,8 @@ static void setup_system(mlcc_system* S, const mlcc_problem* P, const double* ch
   S->x2gs = S->persist.get<double>(size_t(S->nd));
   S->Fov = S->persist.get<double>(size_t(dS));
   S->t1gs = S->persist.get<double>(size_t(S->nv) * no);
+  S->tc_err = S->persist.get<int>(64);
+  MLCC_CUDA(cudaMemsetAsync(S->tc_err, 0, 256, s));
   // scratch: enough for sigma (dLt, three doubles-sized arrays, two [nj][dS]) plus GEMM
   // partials and the einsum engine's permuted operands
   const int64_t tl = int64_t(S->tv) * S->to * S->tv * S->to;
@@ -221,10 +224,13 @@ mlcc_status mlcc_ctx_create(int device, mlcc_ctx** out) {
 void mlcc_ctx_destroy(mlcc_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   ctx->timer.reset();
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
+
+int64_t mlcc_launch_count(void) { return launch_count(); }
 
 void* mlcc_ctx_stream(mlcc_ctx* ctx) { return ctx ? static_cast<void*>(ctx->stream) : nullptr; }
 
@@ -383,10 +389,11 @@ mlcc_status mlcc_sigma(mlcc_system* S, int32_t n_vec, const double* c, double* s
   return guard([&] {
     MLCC_REQUIRE(S && c && sigma, "mlcc_sigma: NULL argument");
     MLCC_REQUIRE(n_vec >= 0, "mlcc_sigma: n_vec < 0");
-    MLCC_REQUIRE(precision == MLCC_FP64 || precision == MLCC_BF16, "mlcc_sigma: unknown precision");
+    MLCC_REQUIRE(precision >= MLCC_FP64 && precision <= MLCC_BF16X6, "mlcc_sigma: unknown precision");
     MLCC_CUDA(cudaSetDevice(S->ctx->device));
     const int64_t len = int64_t(S->nv) * S->no + S->nd;
     for (int k = 0; k < n_vec; ++k) sigma_eval(S, c + k * len, sigma + k * len, precision);
+    if (precision != MLCC_FP64) check_tc_error(S);
     return MLCC_OK;
   });
 }

@@ -28,7 +28,13 @@ void set_last_error(const std::string& msg);
                           std::string(#call) + ": " + cudaGetErrorString(e_));       \
     }                                                                                \
   } while (0)
-#define MLCC_CHECK_LAUNCH() MLCC_CUDA(cudaGetLastError())
+// every kernel launch is followed by MLCC_CHECK_LAUNCH(), which also counts it
+void count_launch();
+#define MLCC_CHECK_LAUNCH()          \
+  do {                               \
+    ::mlcc::count_launch();          \
+    MLCC_CUDA(cudaGetLastError());   \
+  } while (0)
 #define MLCC_REQUIRE(cond, msg)                                      \
   do {                                                               \
     if (!(cond)) throw ::mlcc::Error(MLCC_E_ARG, std::string(msg));  \

@@ -316,8 +316,6 @@ void build_fock_tangent(mlcc_system* S, const double* dht, const double* dLt, do
 // replaces them when precision is MLCC_BF16.
 void rank_gemm_f64(mlcc_system* S, bool outer, const double* A, const double* B, double* C,
                    double alpha, double beta);
-void rank_gemm_lowp(mlcc_system* S, bool outer, const double* A, const double* B, double* C,
-                    double alpha, double beta);
 
 void rank_gemm_f64(mlcc_system* S, bool outer, const double* A, const double* B, double* C,
                    double alpha, double beta) {
@@ -338,8 +336,12 @@ void rank_gemm_f64(mlcc_system* S, bool outer, const double* A, const double* B,
 
 static void rank_gemm(mlcc_system* S, int precision, bool outer, const double* A, const double* B,
                       double* C, double alpha, double beta) {
-  if (precision == MLCC_BF16) rank_gemm_lowp(S, outer, A, B, C, alpha, beta);
-  else rank_gemm_f64(S, outer, A, B, C, alpha, beta);
+  if (precision != MLCC_FP64) {
+    if (S->lowp_prec != precision) lowp_prepare(S, precision);
+    rank_gemm_lowp(S, outer, A, B, C, alpha, beta, precision, false);
+  } else {
+    rank_gemm_f64(S, outer, A, B, C, alpha, beta);
+  }
 }
 
 // ---------------------------------------------------------------------------------
@@ -497,6 +499,7 @@ void jacobian_prepare(mlcc_system* S, const double* t1, const double* x2) {
   const int n = S->n, no = S->no, nv = S->nv, so = S->so, sv = S->sv;
   const int64_t dS = S->dS;
   S->prepared = false;
+  S->lowp_prec = -1;
   ccsd_cache_free(S);
   Scope sc(S->ws);
   MLCC_CUDA(cudaMemcpyAsync(S->t1gs, t1, size_t(nv) * no * 8, cudaMemcpyDeviceToDevice, s));

@@ -248,6 +248,7 @@ struct DavState {
 
 static void sigma_batch(mlcc_system* S, const double* C, double* Sg, int nvec, int64_t dim, int prec) {
   for (int k = 0; k < nvec; ++k) sigma_eval(S, C + int64_t(k) * dim, Sg + int64_t(k) * dim, prec);
+  if (prec != MLCC_FP64) check_tc_error(S);
 }
 
 // add the new columns [m0, m) to G
@@ -355,11 +356,12 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
   D.m = nguess;
 
   int prec = opt->precision;
-  const bool two_phase = (prec == MLCC_BF16) && opt->refine_fp64;
+  const bool lowp = prec != MLCC_FP64;
+  const bool two_phase = lowp && opt->refine_fp64;
   int n_sigma = 0, n_sigma_lowp = 0;
   auto count_sigma = [&](int k) {
     n_sigma += k;
-    if (prec == MLCC_BF16) n_sigma_lowp += k;
+    if (prec != MLCC_FP64) n_sigma_lowp += k;
   };
   sigma_batch(S, D.B, D.Sg, D.m, dim, prec);
   count_sigma(D.m);
@@ -404,16 +406,17 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
         if (!std::isfinite(rn[k])) throw Error(MLCC_E_NAN, "Davidson: NaN in a residual");
       }
     }
-    const double rtol = (two_phase && prec == MLCC_BF16) ? opt->lowp_res_tol : opt->es_res_tol;
+    const bool in_lowp = prec != MLCC_FP64;
+    const double rtol = (two_phase && in_lowp) ? opt->lowp_res_tol : opt->es_res_tol;
     std::vector<int> todo;
     for (int k = 0; k < nr; ++k) {
-      const bool ok = (rn[k] < rtol) && (two_phase && prec == MLCC_BF16 ? true
-                                                                       : std::fabs(w[k] - w_old[k]) < opt->es_omega_tol);
+      const bool ok = (rn[k] < rtol) && (two_phase && in_lowp ? true
+                                                              : std::fabs(w[k] - w_old[k]) < opt->es_omega_tol);
       if (!ok) todo.push_back(k);
     }
     w_old = w;
     if (todo.empty()) {
-      if (two_phase && prec == MLCC_BF16) {
+      if (two_phase && in_lowp) {
         // refinement: restart from the low-precision Ritz vectors with binary64 sigma
         prec = MLCC_FP64;
         const int keep = std::min(nr, D.m);

@@ -2,6 +2,8 @@
 #pragma once
 #include "internal.cuh"
 
+#include <cuda_bf16.h>
+
 namespace mlcc {
 
 // Value or tangent of a tensor in the forward-mode (dual number) evaluation of the
@@ -45,6 +47,12 @@ struct mlcc_system {
   double* t1gs = nullptr;  // [nv][no]
   double* x2gs = nullptr;  // [nd]
   mlcc::CCSDCache* ccsd = nullptr;
+  // mixed precision: bfloat16 pieces of the constant GEMM operands, error flag
+  mlcc::Arena lowp_arena;
+  __nv_bfloat16* lai_bf = nullptr;
+  __nv_bfloat16* lov_bf = nullptr;
+  int lowp_prec = -1;
+  int* tc_err = nullptr;
   mlcc::Arena persist;     // the buffers above
   mlcc::Arena ws;          // scratch
   int64_t workspace_bytes = 0;
@@ -68,6 +76,10 @@ void ccsd_block(mlcc_system* S, Mode mode, const Dual& Lai, const Dual& Lac, con
                 const Dual& Lkc, const Dual& Fvv, const Dual& Foo, const Dual& t, double* om_out,
                 bool cache_values);
 void ccsd_cache_free(mlcc_system* S);
+void rank_gemm_lowp(mlcc_system* S, bool outer, const double* A, const double* B, double* C,
+                    double alpha, double beta, int precision, bool b_is_u_source);
+void lowp_prepare(mlcc_system* S, int precision);
+void check_tc_error(mlcc_system* S);
 
 // kernel-family timing (rank_gemm): wraps a callable with events when enabled
 template <class F>

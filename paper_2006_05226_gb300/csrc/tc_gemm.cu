@@ -1,10 +1,453 @@
-// Tensor-core (tcgen05) Cholesky-rank GEMMs for the mixed-precision path.
+// Tensor-core (tcgen05) GEMMs for the Cholesky-rank doubles contractions of the
+// mixed-precision path:  C[m][n] = alpha * sum_k A[m][k] B[n][k] + beta * C[m][n]
+// with A, B bfloat16 and K-major (K contiguous, padded to a multiple of 64), the
+// accumulator fp32 in tensor memory and C binary64.
+//
+// One CTA computes a 128 x 256 tile: TMA (cp.async.bulk.tensor, 128-byte swizzle) fills a
+// 4-stage shared-memory ring; one elected thread issues tcgen05.mma (kind::f16, M = 128,
+// N = 256, K = 16) into a 256-column TMEM accumulator and releases stages with
+// tcgen05.commit; four epilogue warps read the accumulator with tcgen05.ld and write C.
+// Every mbarrier wait is bounded: on timeout the thread records an error flag and the CTA
+// winds down (freeing its TMEM) instead of spinning.
+//
+// Split precision: an operand x is written as x = x0 + x1 + x2 with bfloat16 pieces; the
+// products x0 y0 (MLCC_BF16), + x0 y1 + x1 y0 (MLCC_BF16X3) and + x0 y2 + x1 y1 + x2 y0
+// (MLCC_BF16X6) are laid out as extra K segments, so one GEMM of depth S * K sums them.
 #include "system.cuh"
 
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
 namespace mlcc {
-void rank_gemm_lowp(mlcc_system* S, bool outer, const double* A, const double* B, double* C,
-                    double alpha, double beta) {
-  (void)S; (void)outer; (void)A; (void)B; (void)C; (void)alpha; (void)beta;
-  throw Error(MLCC_E_ARG, "MLCC_BF16 precision is not available in this build");
+
+namespace {
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;             // 16 KB
+constexpr int B_BYTES = BN * BK * 2;             // 32 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;   // 48 KB
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int THREADS = 192;                     // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;  // about 2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; returns false (and flags the error) on timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+  if (mbar_try(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (clock64() - t0 > WAIT_LIMIT_CYCLES) {
+      atomicExch(err, code);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= uint64_t((addr & 0x3FFFF) >> 4);
+  d |= uint64_t(16 >> 4) << 16;     // leading byte offset (unused for swizzled K-major)
+  d |= uint64_t(1024 >> 4) << 32;   // stride byte offset
+  d |= uint64_t(1) << 46;           // descriptor version
+  d |= uint64_t(2) << 61;           // 128-byte swizzle
+  return d;
+}
+// instruction descriptor for kind::f16: bf16 x bf16 -> fp32, both K-major, M = 128, N = BN
+__host__ __device__ constexpr uint32_t instr_desc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
+}
+
+struct TcParams {
+  int64_t M, N;
+  int kblocks;
+  double* C;
+  int64_t ldc;
+  double alpha, beta;
+  int* err;
+  int m_fast;   // 1: blockIdx.x runs over M tiles
+};
+
+__global__ void __launch_bounds__(THREADS, 1)
+k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), accb = smem_u32(bars + 2 * STAGES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t mt = p.m_fast ? blockIdx.x : blockIdx.y;
+  const int64_t nt = p.m_fast ? blockIdx.y : blockIdx.x;
+  const int64_t m0 = mt * BM, n0 = nt * BN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(accb, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)), "r"(BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const int nkb = p.kblocks;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // TMA producer
+      int issued = 0;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % STAGES;
+        if (kb >= STAGES) {
+          if (!mbar_wait(empty0 + 8 * s, ((kb / STAGES) - 1) & 1, p.err, 1)) break;
+        }
+        const uint32_t a_dst = smem_u32(smem + s * STAGE_BYTES);
+        const uint32_t b_dst = a_dst + A_BYTES;
+        mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+        tma_load_2d(a_dst, &tmA, full0 + 8 * s, kb * BK, int(m0));
+        tma_load_2d(b_dst, &tmB, full0 + 8 * s, kb * BK, int(n0));
+        ++issued;
+      }
+      // drain: the copies this thread issued land before the CTA can exit
+      for (int kb = std::max(0, issued - STAGES); kb < issued; ++kb)
+        mbar_wait(full0 + 8 * (kb % STAGES), (kb / STAGES) & 1, p.err, 4);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer
+      constexpr uint32_t idesc = instr_desc();
+      bool ok = true;
+      for (int kb = 0; kb < nkb && ok; ++kb) {
+        const int s = kb % STAGES;
+        if (!mbar_wait(full0 + 8 * s, (kb / STAGES) & 1, p.err, 2)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a_addr = smem_u32(smem + s * STAGE_BYTES);
+        const uint32_t b_addr = a_addr + A_BYTES;
+        const uint64_t ad = smem_desc(a_addr), bd = smem_desc(b_addr);
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k) {
+          const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+          // advance 16 bf16 (32 bytes) along K inside the swizzled 128-byte rows
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(ad + uint64_t(2 * k)), "l"(bd + uint64_t(2 * k)), "r"(idesc), "r"(acc));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty0 + 8 * s)
+                     : "memory");
+      }
+      if (ok) {
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(accb)
+                     : "memory");
+      }
+    }
+  } else {
+    // epilogue: warps 2..5 own TMEM lanes 32*(warp % 4) .. +31, one output row per thread
+    const int q = warp & 3;
+    const bool ok = mbar_wait(accb, 0, p.err, 3);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok && nkb > 0) {
+      const int64_t row = m0 + 32 * q + lane;
+      double* crow = p.C + row * p.ldc;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem + (uint32_t(32 * q) << 16) + uint32_t(c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+            "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+              "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+              "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+              "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (row < p.M) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int64_t col = n0 + c0 + j;
+            if (col < p.N) {
+              const double v = p.alpha * double(__uint_as_float(r[j]));
+              crow[col] = (p.beta == 0.0) ? v : v + p.beta * crow[col];
+            }
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// operand preparation: binary64 -> bfloat16 pieces, K-major, K padded to Kp, S segments
+struct SplitPattern {
+  int S;
+  int a[6];
+  int b[6];
+};
+__host__ __device__ inline SplitPattern pattern(int precision) {
+  SplitPattern p{};
+  if (precision == MLCC_BF16X6) {
+    p.S = 6;
+    const int a[6] = {0, 0, 1, 0, 1, 2}, b[6] = {0, 1, 0, 2, 1, 0};
+    for (int i = 0; i < 6; ++i) { p.a[i] = a[i]; p.b[i] = b[i]; }
+  } else if (precision == MLCC_BF16X3) {
+    p.S = 3;
+    const int a[3] = {0, 0, 1}, b[3] = {0, 1, 0};
+    for (int i = 0; i < 3; ++i) { p.a[i] = a[i]; p.b[i] = b[i]; }
+  } else {
+    p.S = 1;
+    p.a[0] = 0;
+    p.b[0] = 0;
+  }
+  return p;
+}
+__device__ __forceinline__ void split3(double x, __nv_bfloat16 out[3]) {
+  const __nv_bfloat16 h0 = __double2bfloat16(x);
+  const double r1 = x - double(__bfloat162float(h0));
+  const __nv_bfloat16 h1 = __double2bfloat16(r1);
+  const double r2 = r1 - double(__bfloat162float(h1));
+  out[0] = h0;
+  out[1] = h1;
+  out[2] = __double2bfloat16(r2);
+}
+struct CvtArgs {
+  int64_t rows, K, Kp;   // destination rows, true K, padded K
+  int S;
+  int piece[6];          // split piece per segment
+};
+// dst[r][s*Kp + k] = piece_s(src(r, k)); transposed source: src(r, k) = src[k * ld + r]
+__global__ void k_cvt_transpose(const double* src, int64_t ld, CvtArgs a, __nv_bfloat16* dst) {
+  __shared__ double tile[32][33];
+  const int64_t r0 = int64_t(blockIdx.x) * 32, k0 = int64_t(blockIdx.y) * 32;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int64_t k = k0 + y, r = r0 + threadIdx.x;
+    tile[y][threadIdx.x] = (k < a.K && r < a.rows) ? src[k * ld + r] : 0.0;
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int64_t r = r0 + y, k = k0 + threadIdx.x;
+    if (r >= a.rows || k >= a.Kp) continue;
+    __nv_bfloat16 pc[3];
+    split3(tile[threadIdx.x][y], pc);
+    for (int s = 0; s < a.S; ++s) dst[r * (a.S * a.Kp) + s * a.Kp + k] = pc[a.piece[s]];
+  }
+}
+// dst[r][s*Kp + k] = piece_s(src[r * ld + k])  (u_mode: 2 c[r][k] - c[r'][k'] with the
+// occupied indices of the pair (r, k) = (ai, bj) exchanged, u = 2c - c(i <-> j))
+__global__ void k_cvt_direct(const double* src, int64_t ld, CvtArgs a, int u_mode, int sv, int so,
+                             __nv_bfloat16* dst) {
+  const int64_t total = a.rows * a.Kp;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = t / a.Kp, k = t - r * a.Kp;
+    double v = 0.0;
+    if (k < a.K) {
+      v = src[r * ld + k];
+      if (u_mode) {
+        const int aa = int(r / so), i = int(r - int64_t(aa) * so);
+        const int b = int(k / so), j = int(k - int64_t(b) * so);
+        v = 2.0 * v - src[(int64_t(aa) * so + j) * ld + int64_t(b) * so + i];
+      }
+    }
+    __nv_bfloat16 pc[3];
+    split3(v, pc);
+    for (int s = 0; s < a.S; ++s) dst[r * (a.S * a.Kp) + s * a.Kp + k] = pc[a.piece[s]];
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  if (!fn) throw Error(MLCC_E_CUDA, "cuTensorMapEncodeTiled is not available");
+  return fn;
+}
+
+void make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t kp, int box_rows) {
+  MLCC_REQUIRE((reinterpret_cast<uintptr_t>(base) & 15) == 0, "TMA base address must be 16-byte aligned");
+  MLCC_REQUIRE((kp * 2) % 16 == 0, "TMA row stride must be a multiple of 16 bytes");
+  cuuint64_t dims[2] = {cuuint64_t(kp), cuuint64_t(rows)};
+  cuuint64_t strides[1] = {cuuint64_t(kp * 2)};
+  cuuint32_t box[2] = {cuuint32_t(BK), cuuint32_t(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = get_encode()(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
+                            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(MLCC_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(int(r)));
+}
+}  // namespace
+
+static inline int64_t pad64(int64_t k) { return (k + 63) / 64 * 64; }
+
+// C = alpha A B^T + beta C for bf16 K-major operands A [M][Kt], B [N][Kt] (Kt = S * Kp).
+void tc_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t M, int64_t N, int64_t Kt,
+             double* C, int64_t ldc, double alpha, double beta, int* err, bool m_fast,
+             cudaStream_t s) {
+  MLCC_REQUIRE(Kt % BK == 0, "tc_gemm: K must be a multiple of 64");
+  MLCC_REQUIRE(M < (int64_t(1) << 31) && N < (int64_t(1) << 31), "tc_gemm: size too large");
+  static bool attr = false;
+  if (!attr) {
+    MLCC_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    attr = true;
+  }
+  CUtensorMap ma, mb;
+  make_map(&ma, A, M, Kt, BM);
+  make_map(&mb, B, N, Kt, BN);
+  TcParams p;
+  p.M = M;
+  p.N = N;
+  p.kblocks = int(Kt / BK);
+  p.C = C;
+  p.ldc = ldc;
+  p.alpha = alpha;
+  p.beta = beta;
+  p.err = err;
+  p.m_fast = m_fast ? 1 : 0;
+  const int64_t tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
+  dim3 grid = m_fast ? dim3(unsigned(tm), unsigned(tn)) : dim3(unsigned(tn), unsigned(tm));
+  MLCC_REQUIRE((m_fast ? tn : tm) < 65536, "tc_gemm: grid too large");
+  k_tc_gemm<<<grid, THREADS, SMEM_BYTES, s>>>(ma, mb, p);
+  MLCC_CHECK_LAUNCH();
+}
+
+void cvt_operand(const double* src, int64_t ld, int64_t rows, int64_t K, bool transpose, bool u_mode,
+                 int sv, int so, int precision, bool side_a, __nv_bfloat16* dst, cudaStream_t s) {
+  SplitPattern pt = pattern(precision);
+  CvtArgs a;
+  a.rows = rows;
+  a.K = K;
+  a.Kp = pad64(K);
+  a.S = pt.S;
+  for (int i = 0; i < pt.S; ++i) a.piece[i] = side_a ? pt.a[i] : pt.b[i];
+  if (transpose) {
+    dim3 blk(32, 8), grd(unsigned((rows + 31) / 32), unsigned((a.Kp + 31) / 32));
+    k_cvt_transpose<<<grd, blk, 0, s>>>(src, ld, a, dst);
+  } else {
+    const int64_t total = rows * a.Kp;
+    const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 32768)));
+    k_cvt_direct<<<blocks, 256, 0, s>>>(src, ld, a, u_mode ? 1 : 0, sv, so, dst);
+  }
+  MLCC_CHECK_LAUNCH();
+}
+
+int split_segments(int precision) { return pattern(precision).S; }
+
+// The two rank GEMMs of sigma in low precision.
+//   outer: C[dS][dS] = A^T B   with A, B [nj][dS] binary64 (A = the cached Lai)
+//   inner: C[nj][dS] = A B     with A [nj][dS] (the cached Lov), B [dS][dS] = u(c) built here
+void rank_gemm_lowp(mlcc_system* S, bool outer, const double* A, const double* B, double* C,
+                    double alpha, double beta, int precision, bool b_is_u_source) {
+  cudaStream_t s = S->ctx->stream;
+  const int64_t dS = S->dS, nj = S->nj;
+  const int seg = split_segments(precision);
+  Scope sc(S->ws);
+  if (outer) {
+    const int64_t Kp = pad64(nj), Kt = seg * Kp;
+    const __nv_bfloat16* Abf = nullptr;
+    if (S->lowp_prec == precision && S->lai_bf) {
+      Abf = S->lai_bf;
+    } else {
+      __nv_bfloat16* t = S->ws.get<__nv_bfloat16>(size_t(dS) * Kt);
+      cvt_operand(A, dS, dS, nj, true, false, S->sv, S->so, precision, true, t, s);
+      Abf = t;
+    }
+    __nv_bfloat16* Bbf = S->ws.get<__nv_bfloat16>(size_t(dS) * Kt);
+    cvt_operand(B, dS, dS, nj, true, false, S->sv, S->so, precision, false, Bbf, s);
+    timed(S, "rank_gemm", 2.0 * double(dS) * double(dS) * double(Kt),
+          [&] { tc_gemm(Abf, Bbf, dS, dS, Kt, C, dS, alpha, beta, S->tc_err, false, s); });
+  } else {
+    const int64_t Kp = pad64(dS), Kt = seg * Kp;
+    const __nv_bfloat16* Abf = nullptr;
+    if (S->lowp_prec == precision && S->lov_bf) {
+      Abf = S->lov_bf;
+    } else {
+      __nv_bfloat16* t = S->ws.get<__nv_bfloat16>(size_t(nj) * Kt);
+      cvt_operand(A, dS, nj, dS, false, false, S->sv, S->so, precision, true, t, s);
+      Abf = t;
+    }
+    __nv_bfloat16* Bbf = S->ws.get<__nv_bfloat16>(size_t(dS) * Kt);
+    cvt_operand(B, dS, dS, dS, false, b_is_u_source, S->sv, S->so, precision, false, Bbf, s);
+    timed(S, "rank_gemm", 2.0 * double(nj) * double(dS) * double(Kt),
+          [&] { tc_gemm(Abf, Bbf, nj, dS, Kt, C, dS, alpha, beta, S->tc_err, true, s); });
+  }
+}
+
+// bfloat16 copies of the constant operands (Lai, Lov) at the Jacobian ground state
+void lowp_prepare(mlcc_system* S, int precision) {
+  if (S->dS == 0) return;
+  cudaStream_t s = S->ctx->stream;
+  const int64_t dS = S->dS, nj = S->nj;
+  const int seg = split_segments(precision);
+  const size_t need = size_t(dS) * seg * pad64(nj) * 2 + size_t(nj) * seg * pad64(dS) * 2 + 4096;
+  if (S->lowp_arena.capacity() < need) S->lowp_arena.reserve(need);
+  S->lowp_arena.release(0);
+  S->lai_bf = S->lowp_arena.get<__nv_bfloat16>(size_t(dS) * seg * pad64(nj));
+  S->lov_bf = S->lowp_arena.get<__nv_bfloat16>(size_t(nj) * seg * pad64(dS));
+  cvt_operand(S->Lai, dS, dS, nj, true, false, S->sv, S->so, precision, true, S->lai_bf, s);
+  cvt_operand(S->Lov, dS, nj, dS, false, false, S->sv, S->so, precision, true, S->lov_bf, s);
+  S->lowp_prec = precision;
+}
+
+void check_tc_error(mlcc_system* S) {
+  int h = 0;
+  MLCC_CUDA(cudaMemcpyAsync(&h, S->tc_err, 4, cudaMemcpyDeviceToHost, S->ctx->stream));
+  MLCC_CUDA(cudaStreamSynchronize(S->ctx->stream));
+  if (h != 0) {
+    MLCC_CUDA(cudaMemsetAsync(S->tc_err, 0, 4, S->ctx->stream));
+    throw Error(MLCC_E_CUDA, "tensor-core GEMM: a pipeline wait timed out (code " + std::to_string(h) + ")");
+  }
+}
+
 }  // namespace mlcc

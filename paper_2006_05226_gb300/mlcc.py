@@ -5,8 +5,10 @@ sizes across the C ABI. torch provides device memory and streams. The library wo
 its own CUDA stream; calls order it after torch's current stream and order torch's
 current stream after it, so tensors can be used on either side without races.
 """
+import atexit
 import ctypes
 import os
+import weakref
 from ctypes import POINTER, byref, c_char_p, c_double, c_int, c_int8, c_int32, c_int64, c_void_p
 
 import numpy as np
@@ -14,7 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmlcc.so")
 
-MLCC_FP64, MLCC_BF16 = 0, 1
+MLCC_FP64, MLCC_BF16, MLCC_BF16X3, MLCC_BF16X6 = 0, 1, 2, 3
 STATUS = {0: "MLCC_OK", -1: "MLCC_E_ARG", -2: "MLCC_E_OOM", -3: "MLCC_E_GS_NOCONV",
           -4: "MLCC_E_ES_NOCONV", -5: "MLCC_E_COMPLEX_ROOT", -6: "MLCC_E_NAN",
           -8: "MLCC_E_CUDA", -9: "MLCC_E_STATE"}
@@ -24,7 +26,7 @@ EXPORTS = ["mlcc_default_options", "mlcc_ctx_create", "mlcc_ctx_destroy", "mlcc_
            "mlcc_last_error", "mlcc_kernel_timing", "mlcc_kernel_time", "mlcc_system_create",
            "mlcc_system_destroy", "mlcc_system_info", "mlcc_orbital_order", "mlcc_t1_transform",
            "mlcc_fock_t1", "mlcc_omega", "mlcc_ground_state", "mlcc_jacobian_prepare",
-           "mlcc_sigma", "mlcc_excited_states", "mlcc_solve"]
+           "mlcc_sigma", "mlcc_excited_states", "mlcc_solve", "mlcc_launch_count"]
 
 
 class mlcc_problem(ctypes.Structure):
@@ -63,6 +65,7 @@ class MLCCError(RuntimeError):
 
 
 _lib = None
+_live_contexts = weakref.WeakSet()
 
 
 def load():
@@ -83,6 +86,7 @@ def load():
         "mlcc_last_error": (c_char_p, []),
         "mlcc_kernel_timing": (None, [P, c_int]),
         "mlcc_kernel_time": (c_int, [P, c_char_p, POINTER(c_int64), D, D]),
+        "mlcc_launch_count": (c_int64, []),
         "mlcc_system_create": (c_int, [P, POINTER(mlcc_problem), P, P, POINTER(c_void_p)]),
         "mlcc_system_destroy": (None, [P]),
         "mlcc_system_info": (c_int, [P, POINTER(mlcc_dims)]),
@@ -110,6 +114,11 @@ def _check(status):
         raise MLCCError(status, load().mlcc_last_error().decode())
 
 
+def launch_count():
+    """Kernels libmlcc has launched in this process."""
+    return int(load().mlcc_launch_count())
+
+
 def default_options(**kw):
     o = mlcc_options()
     load().mlcc_default_options(byref(o))
@@ -133,12 +142,13 @@ class Context:
         self.handle = h
         self.device = device
         self.stream = torch.cuda.ExternalStream(load().mlcc_ctx_stream(h), device=f"cuda:{device}")
+        self.systems = weakref.WeakSet()
+        _live_contexts.add(self)
 
     def before(self, *tensors):
+        # the library stream waits for torch's stream; after() makes torch's stream wait
+        # for the library, so tensors freed afterwards on torch's stream are safe to reuse
         self.stream.wait_stream(self._torch.cuda.current_stream(self.device))
-        for t in tensors:
-            if t is not None:
-                t.record_stream(self.stream)
 
     def after(self):
         self._torch.cuda.current_stream(self.device).wait_stream(self.stream)
@@ -153,12 +163,24 @@ class Context:
 
     def close(self):
         if self.handle:
+            for sysobj in list(self.systems):
+                sysobj.close()
+            self._torch.cuda.synchronize(self.device)
             load().mlcc_ctx_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
         try:
             self.close()
+        except Exception:
+            pass
+
+
+@atexit.register
+def _close_all():
+    for c in list(_live_contexts):
+        try:
+            c.close()
         except Exception:
             pass
 
@@ -178,6 +200,7 @@ class System:
         ctx.before(chol, fock)
         _check(load().mlcc_system_create(ctx.handle, byref(prob), _ptr(chol), _ptr(fock), byref(h)))
         self.handle = h
+        ctx.systems.add(self)
         d = mlcc_dims()
         _check(load().mlcc_system_info(h, byref(d)))
         self.dims = d
@@ -251,9 +274,9 @@ class System:
         return np.array(w[:]), R, info
 
     def close(self):
-        if self.handle:
+        if self.handle and self.ctx.handle:
             load().mlcc_system_destroy(self.handle)
-            self.handle = None
+        self.handle = None
 
     def __del__(self):
         try:

@@ -213,3 +213,38 @@ def test_invalid_inputs_are_rejected(ctx, sys7):
     with pytest.raises(mlcc.MLCCError) as e:
         g.sigma(torch.zeros(1, g.dims.vector_len, dtype=torch.float64, device="cuda"))
     assert e.value.status == -9
+
+
+# mixed precision: bound of max|sigma_lowp - sigma_fp64| / max|sigma_fp64|
+LOWP = [(1, 3e-2), (2, 1e-3), (3, 1e-4)]
+
+
+@pytest.mark.parametrize("case", ["small", "ragged", "tiny:three_level"])
+@pytest.mark.parametrize("prec,tol", LOWP)
+def test_sigma_low_precision(ctx, request, case, prec, tol):
+    L, F, no, lev = _systems(request, case)
+    g, o, lay = _make(ctx, L, F, no, lev)
+    gs = solve_ground_state(o)
+    g.jacobian_prepare(_dev(lay.t1(gs.t1)), _dev(lay.x2(gs.x2)))
+    rng = np.random.default_rng(8)
+    c = rng.standard_normal((2, g.dims.vector_len))
+    ref = _host(g.sigma(_dev(c)))
+    out = _host(g.sigma(_dev(c), precision=prec))
+    rel = np.abs(out - ref).max() / np.abs(ref).max()
+    print(f"precision {prec}: max relative sigma error {rel:.3e}")
+    assert rel < tol
+
+
+@pytest.mark.parametrize("prec", [1, 2, 3])
+def test_mixed_davidson_refined_to_fp64(ctx, small, prec):
+    """Low-precision Davidson followed by binary64 refinement reaches the oracle roots."""
+    from paper_2006_05226_gb300 import mlcc
+    o = MLCCSystem(small.L, small.fock, small.spec.n_occ, small.level)
+    gs = solve_ground_state(o)
+    ref = oracle_es(o, gs, 3, res_tol=1e-9)
+    g, _, _ = _make(ctx, small.L, small.fock, small.spec.n_occ, small.level)
+    g.ground_state()
+    w, _, info = g.excited_states(mlcc.default_options(n_roots=3, precision=prec, refine_fp64=1,
+                                                       lowp_res_tol=1e-3), want_vectors=False)
+    assert info.converged and info.n_sigma_lowp > 0
+    assert np.abs(w - ref.omega).max() < E_TOL
