@@ -90,7 +90,8 @@ static void setup_system(mlcc_system* S, const mlcc_problem* P, const double* ch
   const int64_t nn = int64_t(n) * n, dS = S->dS;
   // persistent buffers
   const size_t per = size_t(nj) * nn * 2 + 3 * size_t(nn) + size_t(n) + 3 * size_t(nj) * dS +
-                     size_t(S->nd) * 2 + size_t(dS) + size_t(S->nv) * no;
+                     size_t(S->nd) * 2 + size_t(dS) + size_t(S->nv) * no + size_t(no) * S->so +
+                     size_t(S->sv) * S->nv + 2;
   S->persist.reserve(per * 8 + 96 * 256);
   S->L = S->persist.get<double>(size_t(nj) * nn);
   S->Lt = S->persist.get<double>(size_t(nj) * nn);
@@ -105,6 +106,8 @@ static void setup_system(mlcc_system* S, const mlcc_problem* P, const double* ch
   S->x2gs = S->persist.get<double>(size_t(S->nd));
   S->Fov = S->persist.get<double>(size_t(dS));
   S->t1gs = S->persist.get<double>(size_t(S->nv) * no);
+  S->Xji = S->persist.get<double>(size_t(no) * S->so + 1);
+  S->Yab = S->persist.get<double>(size_t(S->sv) * S->nv + 1);
   S->tc_err = S->persist.get<int>(64);
   MLCC_CUDA(cudaMemsetAsync(S->tc_err, 0, 256, s));
   // scratch: enough for sigma (dLt, three doubles-sized arrays, two [nj][dS]) plus GEMM

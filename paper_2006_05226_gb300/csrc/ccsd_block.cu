@@ -12,6 +12,7 @@ namespace mlcc {
 struct CCSDCache {
   Arena arena;
   std::vector<double*> slots;
+  DT G;   // g~_Kcbd = Lt^J_Kc Lt^J_bd, K over all occupied orbitals, c, b, d CCSD-active
 };
 
 void ccsd_cache_free(mlcc_system* S) {
@@ -60,8 +61,10 @@ struct Eval {
     cudaStream_t s = S->ctx->stream;
     if (mode == Mode::Value) {
       MLCC_CUDA(cudaMemcpyAsync(x.v.p, in.v.p, size_t(x.v.size()) * 8, cudaMemcpyDeviceToDevice, s));
-    } else {
+    } else if (in.d.p) {
       MLCC_CUDA(cudaMemcpyAsync(x.d.p, in.d.p, size_t(x.d.size()) * 8, cudaMemcpyDeviceToDevice, s));
+    } else {
+      x.d.p = nullptr;   // zero tangent
     }
     return x;
   }
@@ -82,7 +85,10 @@ struct Eval {
       einsum(spec, alpha, A.v, B.d, b, C.d, S->ws, s, S->ctx->sm_count);
       wrote = true;
     }
-    if (!wrote) axpby(C.d.p, C.d.p, C.d.size(), 0.0, beta, s);
+    if (!wrote) {
+      if (beta == 0.0) fill(C.d.p, C.d.size(), 0.0, s);
+      else axpby(C.d.p, C.d.p, C.d.size(), 0.0, beta, s);
+    }
   }
   // C = alpha perm(A) + beta C (linear)
   void perm(const char* spec, double alpha, const Dual& A, double beta, Dual& C) {
@@ -96,7 +102,7 @@ struct Eval {
 
 void ccsd_block(mlcc_system* S, Mode mode, const Dual& Lai_in, const Dual& Lac_in,
                 const Dual& Lki_in, const Dual& Lkc_in, const Dual& Fvv_in, const Dual& Foo_in,
-                const Dual& t_in, double* om_out, bool cache_values) {
+                const Dual& t_in, double* om_out, bool cache_values, const double* c1) {
   if (mode == Mode::Value && cache_values) {
     ccsd_cache_free(S);
     S->ccsd = new CCSDCache();
@@ -104,19 +110,46 @@ void ccsd_block(mlcc_system* S, Mode mode, const Dual& Lai_in, const Dual& Lac_i
     // every tensor created below, in doubles (generous: inputs + 4-index intermediates)
     const int64_t need = nj * (v * o + v * v + o * o + o * v) + v * v + o * o +
                          v * v * v * v + 14 * (v * o * v * o) + 4 * (o * o * o * o) +
-                         4 * v * v + 4 * o * o;
+                         4 * v * v + 4 * o * o + int64_t(S->no) * v * v * v;
     S->ccsd->arena.reserve(size_t(need) * 8 + 64 * 256);
   }
   Eval E{S, mode, cache_values};
   cudaStream_t s = S->ctx->stream;
-  Dual Lai = E.input(Lai_in), Lac = E.input(Lac_in), Lki = E.input(Lki_in), Lkc = E.input(Lkc_in);
+  Dual Lai = E.input(Lai_in), Lac = E.input(Lac_in), Lki = E.input(Lki_in);
+  Dual Lkc = E.input(Lkc_in);   // in tangent mode the ov block has no tangent (NULL)
   Dual Fvv = E.input(Fvv_in), Foo = E.input(Foo_in), t = E.input(t_in);
   const int64_t o = S->to, v = S->tv;
   const std::vector<int64_t> vovo = {v, o, v, o};
 
   // X1-basis integrals over the CCSD-active orbitals, g~_pqrs = Lt^J_pq Lt^J_rs
   Dual g_acbd = E.make({v, v, v, v});
-  E.ein("Jac,Jbd->acbd", 1.0, Lac, Lac, 0.0, g_acbd);
+  if (mode == Mode::Tangent && c1) {
+    // d g~_acbd = - c_aK g~_Kcbd - c_bK g~_Kdac  (d Lt_ac = - c_aK Lt_Kc, Appendix A's route
+    // through an intermediate built once at the ground state instead of N_J v^4 work)
+    DT cb;
+    cb.p = const_cast<double*>(c1);
+    cb.d = {v, int64_t(S->no)};
+    DT T1;
+    T1.d = {v, v, v, v};
+    T1.p = S->ws.get<double>(size_t(v * v * v * v));
+    einsum("aK,Kcbd->acbd", -1.0, cb, S->ccsd->G, 0.0, T1, S->ws, s, S->ctx->sm_count);
+    eperm("acbd->acbd", 1.0, T1, 0.0, g_acbd.d, s);
+    eperm("bdac->acbd", 1.0, T1, 1.0, g_acbd.d, s);
+  } else {
+    E.ein("Jac,Jbd->acbd", 1.0, Lac, Lac, 0.0, g_acbd);
+  }
+  if (mode == Mode::Value && cache_values) {
+    // g~_Kcbd for the tangent above
+    const int64_t no = S->no, nj = S->nj, n = S->n, nn = n * n;
+    DT LKc;
+    LKc.d = {nj, no, v};
+    LKc.p = S->ws.get<double>(size_t(nj * no * v));
+    int64_t dims[3] = {nj, no, v}, ss[3] = {nn, n, 1}, ds[3] = {no * v, v, 1};
+    permute_f64(3, dims, S->Lt + no, ss, LKc.p, ds, 1.0, 0.0, s);
+    S->ccsd->G.d = {no, v, v, v};
+    S->ccsd->G.p = S->ccsd->arena.get<double>(size_t(no * v * v * v));
+    einsum("JKc,Jbd->Kcbd", 1.0, LKc, Lac.v, 0.0, S->ccsd->G, S->ws, s, S->ctx->sm_count);
+  }
   Dual g_kilj = E.make({o, o, o, o});
   E.ein("Jki,Jlj->kilj", 1.0, Lki, Lki, 0.0, g_kilj);
   Dual g_kcld = E.make({o, v, o, v});

@@ -208,6 +208,91 @@ __global__ void k_reduce_partials(const double* partial, int nsplit, int64_t M, 
     *cp = (beta == 0.0) ? alpha * s : alpha * s + beta * (*cp);
   }
 }
+// Skinny shapes are bandwidth-bound: a 64 x 64 tile would waste up to 63/64 of its work.
+// M <= 16: one thread (or warp, for a transposed B) per output column n.
+template <int MM, bool TA, bool TB>
+__global__ void k_skinny_m(GP p) {
+  if (!TB) {
+    const int64_t n = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (n >= p.N) return;
+    double acc[MM];
+#pragma unroll
+    for (int m = 0; m < MM; ++m) acc[m] = 0.0;
+    for (int64_t k = 0; k < p.K; ++k) {
+      const double b = p.B[k * p.ldb + n];
+#pragma unroll
+      for (int m = 0; m < MM; ++m)
+        if (m < p.M) acc[m] = fma(TA ? p.A[k * p.lda + m] : p.A[m * p.lda + k], b, acc[m]);
+    }
+#pragma unroll
+    for (int m = 0; m < MM; ++m)
+      if (m < p.M) {
+        double* cp = p.C + m * p.ldc + n;
+        const double v = p.alpha * acc[m];
+        *cp = (p.beta == 0.0) ? v : v + p.beta * (*cp);
+      }
+  } else {
+    const int64_t n = blockIdx.x * int64_t(blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (n >= p.N) return;
+    double acc[MM];
+#pragma unroll
+    for (int m = 0; m < MM; ++m) acc[m] = 0.0;
+    for (int64_t k = lane; k < p.K; k += 32) {
+      const double b = p.B[n * p.ldb + k];
+#pragma unroll
+      for (int m = 0; m < MM; ++m)
+        if (m < p.M) acc[m] = fma(TA ? p.A[k * p.lda + m] : p.A[m * p.lda + k], b, acc[m]);
+    }
+#pragma unroll
+    for (int m = 0; m < MM; ++m) {
+      double v = acc[m];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0 && m < p.M) {
+        double* cp = p.C + m * p.ldc + n;
+        const double w = p.alpha * v;
+        *cp = (p.beta == 0.0) ? w : w + p.beta * (*cp);
+      }
+    }
+  }
+}
+// N == 1: y[m] = sum_k op(A)[m][k] x[k]; a warp per row (A row-major) or a thread per row.
+template <bool TA>
+__global__ void k_gemv_n1(GP p) {
+  if (!TA) {
+    const int64_t m = blockIdx.x * int64_t(blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (m >= p.M) return;
+    double acc = 0.0;
+    for (int64_t k = lane; k < p.K; k += 32) acc = fma(p.A[m * p.lda + k], p.B[k * p.ldb], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      double* cp = p.C + m * p.ldc;
+      const double v = p.alpha * acc;
+      *cp = (p.beta == 0.0) ? v : v + p.beta * (*cp);
+    }
+  } else {
+    const int64_t m = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (m >= p.M) return;
+    double acc = 0.0;
+    for (int64_t k = 0; k < p.K; ++k) acc = fma(p.A[k * p.lda + m], p.B[k * p.ldb], acc);
+    double* cp = p.C + m * p.ldc;
+    const double v = p.alpha * acc;
+    *cp = (p.beta == 0.0) ? v : v + p.beta * (*cp);
+  }
+}
+template <int MM>
+static void launch_skinny(const GP& p, bool ta, bool tb, cudaStream_t s) {
+  if (!tb) {
+    const unsigned blocks = unsigned((p.N + 255) / 256);
+    if (ta) k_skinny_m<MM, true, false><<<blocks, 256, 0, s>>>(p);
+    else k_skinny_m<MM, false, false><<<blocks, 256, 0, s>>>(p);
+  } else {
+    const unsigned blocks = unsigned((p.N + 7) / 8);
+    if (ta) k_skinny_m<MM, true, true><<<blocks, 256, 0, s>>>(p);
+    else k_skinny_m<MM, false, true><<<blocks, 256, 0, s>>>(p);
+  }
+}
 }  // namespace
 
 void gemm_f64(const Gemm& g, Arena& ws, cudaStream_t s, int sm_count) {
@@ -231,6 +316,20 @@ void gemm_f64(const Gemm& g, Arena& ws, cudaStream_t s, int sm_count) {
   p.batch = g.batch;
   p.reduce = g.reduce ? 1 : 0;
   p.partial = nullptr;
+  if (!g.reduce && g.batch == 1 && g.M <= 16 && g.N >= 64) {
+    if (g.M <= 1) launch_skinny<1>(p, g.ta, g.tb, s);
+    else if (g.M <= 4) launch_skinny<4>(p, g.ta, g.tb, s);
+    else if (g.M <= 8) launch_skinny<8>(p, g.ta, g.tb, s);
+    else launch_skinny<16>(p, g.ta, g.tb, s);
+    MLCC_CHECK_LAUNCH();
+    return;
+  }
+  if (!g.reduce && g.batch == 1 && g.N == 1 && g.M >= 64) {
+    if (!g.ta) k_gemv_n1<false><<<unsigned((g.M + 7) / 8), 256, 0, s>>>(p);
+    else k_gemv_n1<true><<<unsigned((g.M + 255) / 256), 256, 0, s>>>(p);
+    MLCC_CHECK_LAUNCH();
+    return;
+  }
   const int64_t tm = (g.M + BM - 1) / BM, tn = (g.N + BN - 1) / BN;
   MLCC_REQUIRE(tm < 65536, "gemm_f64: M too large for the grid");
   int64_t gz = 1;

@@ -439,7 +439,7 @@ void omega_eval(mlcc_system* S, const double* t1, const double* x2, bool gs_mode
     extract_box(S, S->Lt, S->Ft, xuse, Lai.v, Lac.v, Lki.v, Lkc.v, Fvv.v, Foo.v, t.v);
     const int64_t tl = int64_t(S->tv) * S->to * S->tv * S->to;
     double* omT = gs_mode ? om2 : S->ws.get<double>(size_t(tl));
-    ccsd_block(S, Mode::Value, Lai, Lac, Lki, Lkc, Fvv, Foo, t, omT, false);
+    ccsd_block(S, Mode::Value, Lai, Lac, Lki, Lkc, Fvv, Foo, t, omT, false, nullptr);
     if (!gs_mode) put_tbox(S, omT, om2);
   }
   // singles (Eq. mlcc2_omega_codable) with u from all doubles
@@ -494,6 +494,8 @@ void omega_eval(mlcc_system* S, const double* t1, const double* x2, bool gs_mode
 }
 
 // ---------------------------------------------------------------------------------
+static void jacobian_intermediates(mlcc_system* S);
+
 void jacobian_prepare(mlcc_system* S, const double* t1, const double* x2) {
   cudaStream_t s = stm(S);
   const int n = S->n, no = S->no, nv = S->nv, so = S->so, sv = S->sv;
@@ -514,6 +516,7 @@ void jacobian_prepare(mlcc_system* S, const double* t1, const double* x2) {
     rank_gemm_f64(S, false, S->Lov, S->u, S->Z, 1.0, 0.0);
     k_fov<<<nblk(dS), 256, 0, s>>>(S->Ft, n, no, sv, so, S->Fov);
     MLCC_CHECK_LAUNCH();
+    jacobian_intermediates(S);
   }
   if (S->to > 0 && S->tv > 0) {
     Scope sb(S->ws);
@@ -521,84 +524,221 @@ void jacobian_prepare(mlcc_system* S, const double* t1, const double* x2) {
     extract_box(S, S->Lt, S->Ft, S->x2gs, Lai.v, Lac.v, Lki.v, Lkc.v, Fvv.v, Foo.v, t.v);
     const int64_t tl = int64_t(S->tv) * S->to * S->tv * S->to;
     double* omT = S->ws.get<double>(size_t(tl));
-    ccsd_block(S, Mode::Value, Lai, Lac, Lki, Lkc, Fvv, Foo, t, omT, true);
+    ccsd_block(S, Mode::Value, Lai, Lac, Lki, Lkc, Fvv, Foo, t, omT, true, nullptr);
   }
   S->prepared = true;
 }
 
-// sigma = dOmega/dh (x_gs + h c) for one trial vector c = (c1, c2).
+// out[A][I] += alpha * sum_J d[J] X[J][r0 + A][c0 + I] over a rows x cols block
+namespace {
+__global__ void k_sum_over_J(const double* d, const double* X, int nj, int n, int r0, int c0,
+                             int rows, int cols, double alpha, double* out, int ldo) {
+  const int64_t total = int64_t(rows) * cols, nn = int64_t(n) * n;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int A = int(t / cols), I = int(t - int64_t(A) * cols);
+    const double* x = X + int64_t(r0 + A) * n + c0 + I;
+    double acc = 0.0;
+    for (int J = 0; J < nj; ++J) acc = fma(d[J], x[J * nn], acc);
+    out[int64_t(A) * ldo + I] += alpha * acc;
+  }
+}
+// out[b*so + k] = F[k][b] for a [so][sv] block F
+__global__ void k_to_fv(const double* F, int so, int sv, double* fv) {
+  const int64_t total = int64_t(sv) * so;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int b = int(t / so), k = int(t - int64_t(b) * so);
+    fv[t] = F[int64_t(k) * sv + b];
+  }
+}
+}  // namespace
+
+static void sum_over_J(mlcc_system* S, const double* d, const double* X, int r0, int c0, int rows,
+                       int cols, double alpha, double* out, int ldo) {
+  if (rows <= 0 || cols <= 0) return;
+  k_sum_over_J<<<nblk(int64_t(rows) * cols), 256, 0, stm(S)>>>(d, X, S->nj, S->n, r0, c0, rows, cols,
+                                                                alpha, out, ldo);
+  MLCC_CHECK_LAUNCH();
+}
+
+// batched over J: C^J (M x N) = alpha A^J B^J + beta C^J, with per-J strides (0: shared)
+static void bgemm(mlcc_system* S, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+                  int64_t lda, int64_t sA, bool ta, const double* B, int64_t ldb, int64_t sB, bool tb,
+                  double beta, double* C, int64_t ldc, int64_t sC, bool reduce) {
+  if (M <= 0 || N <= 0) return;
+  Gemm g;
+  g.ta = ta; g.tb = tb;
+  g.M = M; g.N = N; g.K = K;
+  g.A = A; g.lda = lda; g.sA = sA;
+  g.B = B; g.ldb = ldb; g.sB = sB;
+  g.C = C; g.ldc = ldc; g.sC = sC;
+  g.alpha = alpha; g.beta = beta;
+  g.batch = S->nj;
+  g.reduce = reduce;
+  gemm_f64(g, S->ws, stm(S), smc(S));
+}
+static void gemm1(mlcc_system* S, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+                  int64_t lda, bool ta, const double* B, int64_t ldb, bool tb, double beta, double* C,
+                  int64_t ldc) {
+  if (M <= 0 || N <= 0) return;
+  Gemm g;
+  g.ta = ta; g.tb = tb;
+  g.M = M; g.N = N; g.K = K;
+  g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
+  g.alpha = alpha; g.beta = beta;
+  gemm_f64(g, S->ws, stm(S), smc(S));
+}
+
+// Intermediates of the Jacobian transformation that do not depend on the trial vector
+// (Appendix A, MLCC2 Jacobian): X_Ji = g~_Jbkc u^{cb}_{ki} = sum_K Lt^K_Jb Z^K_bi and
+// Y_aB = g~_kcjB u^{ac}_{jk} = sum_K Z^K_aj Lt^K_jB.
+static void jacobian_intermediates(mlcc_system* S) {
+  const int n = S->n, no = S->no, nv = S->nv, so = S->so, sv = S->sv;
+  const int64_t nn = int64_t(n) * n, dS = S->dS;
+  if (dS == 0) return;
+  // X[J][i]: M = no, N = so, K = sv per Cholesky vector, summed
+  bgemm(S, no, so, sv, 1.0, S->Lt + no, n, nn, false, S->Z, so, dS, false, 0.0, S->Xji, so, 0, true);
+  // Y[a][B]: M = sv, N = nv, K = so
+  bgemm(S, sv, nv, so, 1.0, S->Z, so, dS, false, S->Lt + no, n, nn, false, 0.0, S->Yab, nv, 0, true);
+}
+
+// sigma = dOmega/dh (x_gs + h c) for one trial vector c = (c1, c2), evaluated with the
+// terms of Appendix A: the CCS terms of Eq. mlcc_A_, the MLCC2 singles terms with the
+// intermediates X and Y, the doubles-to-singles terms, the CC2 doubles
+// (L~_bC c_Cj - c_bK L~_Kj) L~_ai symmetrised plus eps c, and the CCSD rows as the tangent
+// of the MLCCSD doubles residual.
 void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision) {
   if (!S->prepared) throw Error(MLCC_E_STATE, "mlcc_sigma: call mlcc_jacobian_prepare first");
   cudaStream_t s = stm(S);
   const int n = S->n, no = S->no, nv = S->nv, nj = S->nj, so = S->so, sv = S->sv;
-  const int64_t nn = int64_t(n) * n, dS = S->dS;
+  const int to = S->to, tv = S->tv;
+  const int64_t nn = int64_t(n) * n, dS = S->dS, vo = int64_t(nv) * no;
   const double* c1 = c;
-  const double* c2 = c + int64_t(nv) * no;
+  const double* c2 = c + vo;
   double* s1 = sigma;
-  double* s2 = sigma + int64_t(nv) * no;
+  double* s2 = sigma + vo;
+  const double* Lvv = S->Lt + int64_t(no) * n + no;   // Lt^J[no+A][no+B]
+  const double* Lvo = S->Lt + int64_t(no) * n;        // Lt^J[no+A][I]
+  const double* Lov = S->Lt + no;                     // Lt^J[I][no+A]
+  const double* Loo = S->Lt;                          // Lt^J[I][K]
   Scope sc(S->ws);
-  double* dLt = S->ws.get<double>(size_t(nj) * nn);
-  double* dht = S->ws.get<double>(size_t(nn));
-  double* dFt = S->ws.get<double>(size_t(nn));
-  dress_tangent(S, c1, dLt, dht);
-  build_fock_tangent(S, dht, dLt, dFt);
-  // singles: tangent of F~_AI
-  block2d(S, nv, no, dFt + int64_t(no) * n, n, s1, no, 1.0, 0.0);
-  if (dS > 0) {
-    // doubles on P_S: d g~_aibj = dLt_ai Lt_bj + Lt_ai dLt_bj, plus eps c
-    {
-      Scope sd(S->ws);
+  // Xc^J = Lt^J_AB c_BI (the steepest CCS contraction) and the tangent of the
+  // virtual-occupied block dLt^J_AI = Xc^J_AI - c_AK Lt^J_KI
+  double* Xc = S->ws.get<double>(size_t(nj) * vo);
+  bgemm(S, nv, no, nv, 1.0, Lvv, n, nn, false, c1, no, 0, false, 0.0, Xc, no, vo, false);
+  double* dvo = S->ws.get<double>(size_t(nj) * vo);
+  MLCC_CUDA(cudaMemcpyAsync(dvo, Xc, size_t(nj) * vo * 8, cudaMemcpyDeviceToDevice, s));
+  bgemm(S, nv, no, no, -1.0, c1, no, 0, false, Loo, n, nn, false, 1.0, dvo, no, vo, false);
+  // Q^J_IK = Lt^J_IB c_BK; d_J = tr Q^J is the tangent of sum_I Lt^J_II
+  double* dJ = S->ws.get<double>(size_t(nj));
+  {
+    double* Q = S->ws.get<double>(size_t(nj) * no * no);
+    bgemm(S, no, no, nv, 1.0, Lov, n, nn, false, c1, no, 0, false, 0.0, Q, no, int64_t(no) * no, false);
+    const int warps = 8;
+    k_trace_occ<<<(nj + warps - 1) / warps, 32 * warps, 0, s>>>(Q, nj, no, no, dJ);
+    MLCC_CHECK_LAUNCH();
+    // CCS: s1 = F~_AB c_BI - c_AJ F~_JI + 2 d_J Lt^J_AI - (Lt^J_AB c_BJ) Lt^J_JI
+    gemm1(S, nv, no, nv, 1.0, S->Ft + int64_t(no) * n + no, n, false, c1, no, false, 0.0, s1, no);
+    gemm1(S, nv, no, no, -1.0, c1, no, false, S->Ft, n, false, 1.0, s1, no);
+    sum_over_J(S, dJ, S->Lt, no, 0, nv, no, 2.0, s1, no);
+    bgemm(S, nv, no, no, -1.0, Xc, no, vo, false, Loo, n, nn, false, 1.0, s1, no, 0, true);
+    if (dS > 0) {
+      // MLCC2 singles: - c_AJ X_Ji - Y_aB c_BI
+      gemm1(S, nv, so, no, -1.0, c1, no, false, S->Xji, so, false, 1.0, s1, no);
+      gemm1(S, sv, no, nv, -1.0, S->Yab, nv, false, c1, no, false, 1.0, s1, no);
+      // tangent of F~_kc (k, c active): 2 d_J Lt^J_kc - (Lt^J_kB c_BJ) Lt^J_Jc
+      double* dF = S->ws.get<double>(size_t(so) * sv);
+      fill(dF, int64_t(so) * sv, 0.0, s);
+      sum_over_J(S, dJ, S->Lt, 0, no, so, sv, 2.0, dF, sv);
+      // Q^J[k][J'] for k < so is the leading block of Q: (Q^J)[k][J'] Lt^J[J'][no+c]
+      bgemm(S, so, sv, no, -1.0, Q, no, int64_t(no) * no, false, Lov, n, nn, false, 1.0, dF, sv, 0, true);
+      double* dfv = S->ws.get<double>(size_t(dS));
+      k_to_fv<<<nblk(dS), 256, 0, s>>>(dF, so, sv, dfv);
+      MLCC_CHECK_LAUNCH();
+      // doubles -> singles
+      double* uc = S->ws.get<double>(size_t(S->nd));
+      make_u(S, c2, uc);
+      double* Zc = S->ws.get<double>(size_t(nj) * dS);
+      rank_gemm(S, precision, false, S->Lov, uc, Zc, 1.0, 0.0);
+      double* tmp = S->ws.get<double>(size_t(dS));
+      gemm1(S, dS, 1, dS, 1.0, S->u, dS, false, dfv, 1, false, 0.0, tmp, 1);
+      gemm1(S, dS, 1, dS, 1.0, uc, dS, false, S->Fov, 1, false, 1.0, tmp, 1);
+      k_scatter_add_ai<<<nblk(dS), 256, 0, s>>>(tmp, sv, so, no, 1.0, s1);
+      MLCC_CHECK_LAUNCH();
+      // (u(c)^{bc}_{ij} Lt^K_jc) Lt^K_Ab  and  - (u(c)^{ab}_{jk} Lt^K_kb) Lt^K_jI
+      bgemm(S, nv, so, sv, 1.0, Lvv, n, nn, false, Zc, so, dS, false, 1.0, s1, no, 0, true);
+      bgemm(S, sv, no, so, -1.0, Zc, so, dS, false, Loo, n, nn, false, 1.0, s1, no, 0, true);
+      // CC2 doubles on P_S
       double* V = S->ws.get<double>(size_t(nj) * dS);
-      gather_vo(S, dLt, V);
+      {
+        int64_t dims[3] = {nj, sv, so}, ss[3] = {vo, no, 1}, ds[3] = {dS, so, 1};
+        permute_f64(3, dims, dvo, ss, V, ds, 1.0, 0.0, s);
+      }
       double* W = S->ws.get<double>(size_t(S->nd));
       rank_gemm(S, precision, true, S->Lai, V, W, 1.0, 0.0);
       dim3 blk(32, 8), grd(unsigned((dS + 31) / 32), unsigned((dS + 31) / 32));
-      k_sigma2_cc2<<<grd, blk, 0, s>>>(W, c2, S->eps, no, sv, so, S->tv, S->to, s2);
+      k_sigma2_cc2<<<grd, blk, 0, s>>>(W, c2, S->eps, no, sv, so, to, tv, s2);
       MLCC_CHECK_LAUNCH();
     }
-    // singles from the u-terms of Eq. mlcc2_omega_codable, by the product rule
-    double* uc = S->ws.get<double>(size_t(S->nd));
-    make_u(S, c2, uc);
-    double* Zc = S->ws.get<double>(size_t(nj) * dS);
-    rank_gemm(S, precision, false, S->Lov, uc, Zc, 1.0, 0.0);
-    Gemm a;
-    a.M = nv; a.N = so; a.K = sv;
-    a.ldb = so; a.sB = dS; a.lda = n; a.sA = nn;
-    a.C = s1; a.ldc = no; a.alpha = 1.0; a.beta = 1.0; a.batch = nj; a.reduce = true;
-    a.A = dLt + int64_t(no) * n + no; a.B = S->Z;
-    gemm_f64(a, S->ws, s, smc(S));
-    a.A = S->Lt + int64_t(no) * n + no; a.B = Zc;
-    gemm_f64(a, S->ws, s, smc(S));
-    Gemm b;
-    b.M = sv; b.N = no; b.K = so;
-    b.lda = so; b.sA = dS; b.ldb = n; b.sB = nn;
-    b.C = s1; b.ldc = no; b.alpha = -1.0; b.beta = 1.0; b.batch = nj; b.reduce = true;
-    b.A = Zc; b.B = S->Lt;
-    gemm_f64(b, S->ws, s, smc(S));
-    b.A = S->Z; b.B = dLt;
-    gemm_f64(b, S->ws, s, smc(S));
-    double* dfv = S->ws.get<double>(size_t(dS));
-    k_fov<<<nblk(dS), 256, 0, s>>>(dFt, n, no, sv, so, dfv);
-    MLCC_CHECK_LAUNCH();
-    double* tmp = S->ws.get<double>(size_t(dS));
-    Gemm cc;
-    cc.M = dS; cc.N = 1; cc.K = dS; cc.lda = dS; cc.ldb = 1; cc.C = tmp; cc.ldc = 1;
-    cc.A = uc; cc.B = S->Fov; cc.beta = 0.0;
-    gemm_f64(cc, S->ws, s, smc(S));
-    cc.A = S->u; cc.B = dfv; cc.beta = 1.0;
-    gemm_f64(cc, S->ws, s, smc(S));
-    k_scatter_add_ai<<<nblk(dS), 256, 0, s>>>(tmp, sv, so, no, 1.0, s1);
-    MLCC_CHECK_LAUNCH();
-  }
-  // CCSD rows: tangent of the CCSD residual around the cached values
-  if (S->to > 0 && S->tv > 0) {
-    Scope sb(S->ws);
-    Dual Lai, Lac, Lki, Lkc, Fvv, Foo, t;
-    extract_box(S, dLt, dFt, c2, Lai.d, Lac.d, Lki.d, Lkc.d, Fvv.d, Foo.d, t.d);
-    const int64_t tl = int64_t(S->tv) * S->to * S->tv * S->to;
-    double* omT = S->ws.get<double>(size_t(tl));
-    ccsd_block(S, Mode::Tangent, Lai, Lac, Lki, Lkc, Fvv, Foo, t, omT, false);
-    put_tbox(S, omT, s2);
+    // CCSD rows: tangent of the CCSD residual around the cached values
+    if (to > 0 && tv > 0) {
+      Scope sb(S->ws);
+      const int64_t oo = int64_t(no) * no;
+      Dual Lai, Lac, Lki, Lkc, Fvv, Foo, t;
+      Lai.d = box_view(S, nj, tv, to);
+      {
+        int64_t dims[3] = {nj, tv, to}, ss[3] = {vo, no, 1}, ds[3] = {int64_t(tv) * to, to, 1};
+        permute_f64(3, dims, dvo, ss, Lai.d.p, ds, 1.0, 0.0, s);
+      }
+      // dLt_ac = - c_aK Lt_Kc ; dLt_ki = Lt_kA c_Ai ; dLt_kc = 0
+      Lac.d = box_view(S, nj, tv, tv);
+      bgemm(S, tv, tv, no, -1.0, c1, no, 0, false, Lov, n, nn, false, 0.0, Lac.d.p, tv, int64_t(tv) * tv, false);
+      Lki.d = box_view(S, nj, to, to);
+      {
+        // the leading to x to block of Q^J = Lt^J_ov c1
+        int64_t dims[3] = {nj, to, to}, ss[3] = {oo, no, 1}, ds[3] = {int64_t(to) * to, to, 1};
+        permute_f64(3, dims, Q, ss, Lki.d.p, ds, 1.0, 0.0, s);
+      }
+      // dF~_bc = dh~_bc + 2 (dLt^J_bc D_J + Lt^J_bc d_J) - dLt^J_bI Lt^J_Ic, dh~_bc = - c_bK h~_Kc
+      Fvv.d.d = {tv, tv};
+      Fvv.d.p = S->ws.get<double>(size_t(tv) * tv);
+      double* D = S->ws.get<double>(size_t(nj));
+      trace_occ(S, S->Lt, D);
+      gemm1(S, tv, tv, no, -1.0, c1, no, false, S->ht + no, n, false, 0.0, Fvv.d.p, tv);
+      {
+        Gemm g;  // + 2 sum_J D_J dLac^J  (M = 1 over the flattened tv*tv block)
+        g.M = 1; g.N = int64_t(tv) * tv; g.K = nj;
+        g.A = D; g.lda = nj; g.B = Lac.d.p; g.ldb = int64_t(tv) * tv; g.C = Fvv.d.p; g.ldc = int64_t(tv) * tv;
+        g.alpha = 2.0; g.beta = 1.0;
+        gemm_f64(g, S->ws, s, smc(S));
+      }
+      sum_over_J(S, dJ, S->Lt, no, no, tv, tv, 2.0, Fvv.d.p, tv);
+      bgemm(S, tv, tv, no, -1.0, dvo, no, vo, false, Lov, n, nn, false, 1.0, Fvv.d.p, tv, 0, true);
+      // dF~_kj = dh~_kj + 2 (dLt^J_kj D_J + Lt^J_kj d_J) - dLt^J_kI Lt^J_Ij - Lt^J_kI dLt^J_Ij
+      //   with dh~_kj = h~_kA c_Aj and dLt^J_kI = Q^J[k][I]
+      Foo.d.d = {to, to};
+      Foo.d.p = S->ws.get<double>(size_t(to) * to);
+      gemm1(S, to, to, nv, 1.0, S->ht + no, n, false, c1, no, false, 0.0, Foo.d.p, to);
+      {
+        Gemm g;
+        g.M = 1; g.N = int64_t(to) * to; g.K = nj;
+        g.A = D; g.lda = nj; g.B = Lki.d.p; g.ldb = int64_t(to) * to; g.C = Foo.d.p; g.ldc = int64_t(to) * to;
+        g.alpha = 2.0; g.beta = 1.0;
+        gemm_f64(g, S->ws, s, smc(S));
+      }
+      sum_over_J(S, dJ, S->Lt, 0, 0, to, to, 2.0, Foo.d.p, to);
+      bgemm(S, to, to, no, -1.0, Q, no, oo, false, Loo, n, nn, false, 1.0, Foo.d.p, to, 0, true);
+      bgemm(S, to, to, no, -1.0, Loo, n, nn, false, Q, no, oo, false, 1.0, Foo.d.p, to, 0, true);
+      t.d.d = {tv, to, tv, to};
+      t.d.p = S->ws.get<double>(size_t(tv) * to * tv * to);
+      take_tbox(S, c2, t.d);
+      Lkc.d.d = {nj, to, tv};   // zero tangent (occupied-virtual block is unchanged)
+      const int64_t tl = int64_t(tv) * to * tv * to;
+      double* omT = S->ws.get<double>(size_t(tl));
+      ccsd_block(S, Mode::Tangent, Lai, Lac, Lki, Lkc, Fvv, Foo, t, omT, false, c1);
+      put_tbox(S, omT, s2);
+    }
   }
 }
 

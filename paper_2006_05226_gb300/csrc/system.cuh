@@ -42,6 +42,8 @@ struct mlcc_system {
   double* Z = nullptr;     // [nj][dS]  Z^J_bi = u_(bi)(cj) Lov^J_(cj)
   double* u = nullptr;     // [nd]
   double* Fov = nullptr;   // [dS]      F~[j][no+b] at b*so + j
+  double* Xji = nullptr;   // [no][so]  X_Ji of the MLCC2 Jacobian
+  double* Yab = nullptr;   // [sv][nv]  Y_aB of the MLCC2 Jacobian
   // Jacobian ground state
   bool prepared = false;
   double* t1gs = nullptr;  // [nv][no]
@@ -72,9 +74,11 @@ void omega_eval(mlcc_system* S, const double* t1, const double* x2, bool gs_mode
                 const double* tT, double* x2_out, double* om1, double* om2, double* energy);
 void jacobian_prepare(mlcc_system* S, const double* t1, const double* x2);
 void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision);
+// c1 (tangent mode only): the singles trial vector; the tangent of g~_acbd is then formed
+// from the cached g~_Kcbd instead of from the Cholesky vectors.
 void ccsd_block(mlcc_system* S, Mode mode, const Dual& Lai, const Dual& Lac, const Dual& Lki,
                 const Dual& Lkc, const Dual& Fvv, const Dual& Foo, const Dual& t, double* om_out,
-                bool cache_values);
+                bool cache_values, const double* c1);
 void ccsd_cache_free(mlcc_system* S);
 void rank_gemm_lowp(mlcc_system* S, bool outer, const double* A, const double* B, double* C,
                     double alpha, double beta, int precision, bool b_is_u_source);

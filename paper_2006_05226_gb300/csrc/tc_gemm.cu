@@ -417,8 +417,11 @@ void rank_gemm_lowp(mlcc_system* S, bool outer, const double* A, const double* B
       cvt_operand(A, dS, nj, dS, false, false, S->sv, S->so, precision, true, t, s);
       Abf = t;
     }
+    // B operand K-major: Bbf[n][k] = B[k][n] (B is u(c), symmetric for physical trial
+    // vectors; the transposed read keeps the map identical to the binary64 one for any c)
     __nv_bfloat16* Bbf = S->ws.get<__nv_bfloat16>(size_t(dS) * Kt);
-    cvt_operand(B, dS, dS, dS, false, b_is_u_source, S->sv, S->so, precision, false, Bbf, s);
+    cvt_operand(B, dS, dS, dS, true, false, S->sv, S->so, precision, false, Bbf, s);
+    (void)b_is_u_source;
     timed(S, "rank_gemm", 2.0 * double(nj) * double(dS) * double(Kt),
           [&] { tc_gemm(Abf, Bbf, nj, dS, Kt, C, dS, alpha, beta, S->tc_err, true, s); });
   }
