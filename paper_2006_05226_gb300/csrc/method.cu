@@ -678,7 +678,7 @@ void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision) {
       double* W = S->ws.get<double>(size_t(S->nd));
       rank_gemm(S, precision, true, S->Lai, V, W, 1.0, 0.0);
       dim3 blk(32, 8), grd(unsigned((dS + 31) / 32), unsigned((dS + 31) / 32));
-      k_sigma2_cc2<<<grd, blk, 0, s>>>(W, c2, S->eps, no, sv, so, to, tv, s2);
+      k_sigma2_cc2<<<grd, blk, 0, s>>>(W, c2, S->eps, no, sv, so, tv, to, s2);
       MLCC_CHECK_LAUNCH();
     }
     // CCSD rows: tangent of the CCSD residual around the cached values
