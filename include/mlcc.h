@@ -105,9 +105,12 @@ typedef struct {
   int32_t diis_dim;       /* DIIS history length                                      */
   int32_t max_subspace;   /* Davidson basis size before collapse (0: 8 n_roots)       */
   int32_t precision;      /* mlcc_precision of sigma inside the Davidson loop          */
-  int32_t refine_fp64;    /* with MLCC_BF16: continue the Davidson loop with binary64
-                             sigma from the converged low-precision vectors            */
-  int32_t _pad;
+  int32_t refine_fp64;    /* with a low precision: continue the ground-state and the
+                             Davidson iterations in binary64 once the low-precision
+                             phase has converged                                       */
+  int32_t gs_precision;   /* mlcc_precision of the ground-state iterations; with a low
+                             precision they run until |Omega| < 1e-7 (or gs_tol), then
+                             in binary64 if refine_fp64 is set                         */
   double gs_tol;          /* |Omega|_2 threshold                                      */
   double gs_energy_tol;   /* |dE| threshold between iterations                        */
   double es_res_tol;      /* |A R - w R|_2 threshold per root                          */

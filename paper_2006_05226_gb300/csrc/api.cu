@@ -198,6 +198,7 @@ void mlcc_default_options(mlcc_options* o) {
   o->max_subspace = 0;
   o->precision = MLCC_FP64;
   o->refine_fp64 = 1;
+  o->gs_precision = MLCC_FP64;
   o->gs_tol = 1e-11;
   o->gs_energy_tol = 1e-12;
   o->es_res_tol = 1e-8;
@@ -363,6 +364,8 @@ mlcc_status mlcc_ground_state(mlcc_system* S, const mlcc_options* opt, double* t
     MLCC_REQUIRE(S && opt && t1, "mlcc_ground_state: NULL argument");
     MLCC_REQUIRE(S->nd == 0 || x2, "mlcc_ground_state: x2 buffer required");
     MLCC_REQUIRE(opt->max_gs_iter >= 1 && opt->diis_dim >= 1, "mlcc_ground_state: bad options");
+    MLCC_REQUIRE(opt->gs_precision >= MLCC_FP64 && opt->gs_precision <= MLCC_BF16X6,
+                 "mlcc_ground_state: unknown gs_precision");
     MLCC_CUDA(cudaSetDevice(S->ctx->device));
     mlcc_gs_info local{};
     mlcc_status st = ground_state(S, opt, t1, x2, info ? info : &local);

@@ -108,6 +108,23 @@ struct Gemm {
 };
 void gemm_f64(const Gemm& g, Arena& ws, cudaStream_t s, int sm_count);
 
+// Low-precision routing: while a LowpScope is alive on this thread, gemm_f64 sends large
+// GEMMs to the tcgen05 tensor-core path (bfloat16 pieces per mlcc_precision, fp32
+// accumulation per split, binary64 reduction); everything else stays binary64.
+struct LowpScope {
+  int prev;
+  int* err;
+  int* prev_err;
+  LowpScope(int precision, int* err_flag);
+  ~LowpScope();
+};
+int lowp_precision();
+int* lowp_error_flag();
+bool gemm_tc(const Gemm& g, int precision, Arena& ws, cudaStream_t s, int sm_count, int* err);
+// C = alpha * sum_s partial[s] + beta * C (deterministic order)
+void reduce_partials(const double* partial, int nsplit, int64_t M, int64_t N, double* C,
+                     int64_t ldc, double alpha, double beta, cudaStream_t s);
+
 // Strided permute-accumulate: dst = alpha * src (re-indexed) + beta * dst, both given by
 // dims and element strides in the order of the destination's loop nest (<= 8 dims).
 void permute_f64(int nd, const int64_t* dims, const double* src, const int64_t* src_strides,

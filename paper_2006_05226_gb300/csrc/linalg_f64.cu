@@ -86,6 +86,7 @@ struct GP {
   int64_t batch;
   int reduce;       // 1: sum over batches inside the CTA's share
   double* partial;  // reduce with several splits: [split][M][N]
+  int64_t kchunk;   // > 0: split K, CTA z takes [z * kchunk, (z + 1) * kchunk)
 };
 
 template <bool TA, bool TB>
@@ -102,33 +103,40 @@ __global__ void __launch_bounds__(NT) k_dgemm(GP p) {
     for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
 
   int64_t b_begin, b_end, b_step;
+  int64_t kb0 = 0, kb1 = p.K;
   if (p.reduce) {
     b_begin = blockIdx.z;
     b_end = p.batch;
     b_step = gridDim.z;
+  } else if (p.kchunk > 0) {
+    b_begin = 0;
+    b_end = 1;
+    b_step = 1;
+    kb0 = int64_t(blockIdx.z) * p.kchunk;
+    kb1 = min(p.K, kb0 + p.kchunk);
   } else {
     b_begin = blockIdx.z;
     b_end = blockIdx.z + 1;
     b_step = 1;
   }
-  const int64_t nk = (p.K + BK - 1) / BK;
+  const int64_t nk = (kb1 - kb0 + BK - 1) / BK;
   for (int64_t b = b_begin; b < b_end; b += b_step) {
     const double* A = p.A + b * p.sA;
     const double* B = p.B + b * p.sB;
     double ra[4], rb[4];
     auto load = [&](int64_t kt) {
-      const int64_t k0 = kt * BK;
+      const int64_t k0 = kb0 + kt * BK;
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         const int e = tid + NT * r;
         int mm, kk;
         if (!TA) { mm = e >> 4; kk = e & 15; } else { kk = e >> 6; mm = e & 63; }
         const int64_t gm = m0 + mm, gk = k0 + kk;
-        ra[r] = (gm < p.M && gk < p.K) ? (TA ? A[gk * p.lda + gm] : A[gm * p.lda + gk]) : 0.0;
+        ra[r] = (gm < p.M && gk < kb1) ? (TA ? A[gk * p.lda + gm] : A[gm * p.lda + gk]) : 0.0;
         int nn, kb;
         if (!TB) { kb = e >> 6; nn = e & 63; } else { nn = e >> 4; kb = e & 15; }
         const int64_t gn = n0 + nn, gkb = k0 + kb;
-        rb[r] = (gn < p.N && gkb < p.K) ? (TB ? B[gn * p.ldb + gkb] : B[gkb * p.ldb + gn]) : 0.0;
+        rb[r] = (gn < p.N && gkb < kb1) ? (TB ? B[gn * p.ldb + gkb] : B[gkb * p.ldb + gn]) : 0.0;
       }
     };
     auto store = [&](int buf) {
@@ -165,7 +173,7 @@ __global__ void __launch_bounds__(NT) k_dgemm(GP p) {
       __syncthreads();
     }
   }
-  if (p.reduce && gridDim.z > 1) {
+  if ((p.reduce || p.kchunk > 0) && gridDim.z > 1) {
     double* P = p.partial + int64_t(blockIdx.z) * p.M * p.N;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -179,7 +187,7 @@ __global__ void __launch_bounds__(NT) k_dgemm(GP p) {
     }
     return;
   }
-  double* C = p.C + (p.reduce ? 0 : int64_t(blockIdx.z) * p.sC);
+  double* C = p.C + ((p.reduce || p.kchunk > 0) ? 0 : int64_t(blockIdx.z) * p.sC);
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const int64_t gm = m0 + ty * 4 + r;
@@ -295,8 +303,33 @@ static void launch_skinny(const GP& p, bool ta, bool tb, cudaStream_t s) {
 }
 }  // namespace
 
+static thread_local int g_lowp = 0;
+static thread_local int* g_lowp_err = nullptr;
+LowpScope::LowpScope(int precision, int* err_flag) : prev(g_lowp), err(err_flag), prev_err(g_lowp_err) {
+  g_lowp = precision;
+  g_lowp_err = err_flag;
+}
+LowpScope::~LowpScope() {
+  g_lowp = prev;
+  g_lowp_err = prev_err;
+}
+int lowp_precision() { return g_lowp; }
+int* lowp_error_flag() { return g_lowp_err; }
+
+void reduce_partials(const double* partial, int nsplit, int64_t M, int64_t N, double* C,
+                     int64_t ldc, double alpha, double beta, cudaStream_t s) {
+  const int64_t total = M * N;
+  const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 4096)));
+  k_reduce_partials<<<blocks, 256, 0, s>>>(partial, nsplit, M, N, C, ldc, alpha, beta);
+  MLCC_CHECK_LAUNCH();
+}
+
 void gemm_f64(const Gemm& g, Arena& ws, cudaStream_t s, int sm_count) {
   if (g.M <= 0 || g.N <= 0) return;
+  if (g_lowp != 0 && g.K > 0 && g.batch > 0) {
+    const double flop = 2.0 * double(g.M) * double(g.N) * double(g.K) * double(g.batch);
+    if (flop >= 2e8 && gemm_tc(g, g_lowp, ws, s, sm_count, g_lowp_err)) return;
+  }
   if (g.K <= 0 || g.batch <= 0) {
     // empty contraction: C = beta * C for each output matrix
     const int64_t nb = g.reduce ? 1 : std::max<int64_t>(g.batch, 1);
@@ -316,6 +349,7 @@ void gemm_f64(const Gemm& g, Arena& ws, cudaStream_t s, int sm_count) {
   p.batch = g.batch;
   p.reduce = g.reduce ? 1 : 0;
   p.partial = nullptr;
+  p.kchunk = 0;
   if (!g.reduce && g.batch == 1 && g.M <= 16 && g.N >= 64) {
     if (g.M <= 1) launch_skinny<1>(p, g.ta, g.tb, s);
     else if (g.M <= 4) launch_skinny<4>(p, g.ta, g.tb, s);
@@ -341,6 +375,18 @@ void gemm_f64(const Gemm& g, Arena& ws, cudaStream_t s, int sm_count) {
     // cap the partial buffer at 1 GiB
     while (gz > 1 && gz * g.M * g.N * 8 > (int64_t(1) << 30)) gz /= 2;
     if (gz > 1) p.partial = ws.get<double>(size_t(gz) * g.M * g.N);
+  } else if (g.batch == 1 && tm * tn < 2LL * std::max(sm_count, 1) && g.K >= 512) {
+    // too few output tiles to fill the GPU: split K over CTAs, reduce the partials
+    const int64_t tiles = tm * tn;
+    const int64_t want = (4LL * std::max(sm_count, 1) + tiles - 1) / tiles;
+    int64_t splits = std::max<int64_t>(1, std::min<int64_t>(want, g.K / 256));
+    while (splits > 1 && splits * g.M * g.N * 8 > (int64_t(1) << 30)) splits /= 2;
+    if (splits > 1) {
+      p.kchunk = ((g.K + splits - 1) / splits + BK - 1) / BK * BK;
+      splits = (g.K + p.kchunk - 1) / p.kchunk;
+      p.partial = ws.get<double>(size_t(splits) * g.M * g.N);
+    }
+    gz = splits;
   } else {
     gz = g.batch;
     MLCC_REQUIRE(gz < 65536, "gemm_f64: batch too large for the grid");
@@ -351,7 +397,7 @@ void gemm_f64(const Gemm& g, Arena& ws, cudaStream_t s, int sm_count) {
   else if (!g.ta && g.tb) k_dgemm<false, true><<<grid, NT, 0, s>>>(p);
   else k_dgemm<true, true><<<grid, NT, 0, s>>>(p);
   MLCC_CHECK_LAUNCH();
-  if (g.reduce && gz > 1) {
+  if ((g.reduce || p.kchunk > 0) && gz > 1) {
     const int64_t total = g.M * g.N;
     const int blocks = int(std::min<int64_t>((total + 255) / 256, 4096));
     k_reduce_partials<<<blocks, 256, 0, s>>>(p.partial, int(gz), g.M, g.N, g.C, g.ldc,

@@ -611,6 +611,7 @@ static void jacobian_intermediates(mlcc_system* S) {
 void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision) {
   if (!S->prepared) throw Error(MLCC_E_STATE, "mlcc_sigma: call mlcc_jacobian_prepare first");
   cudaStream_t s = stm(S);
+  LowpScope lowp(precision == MLCC_FP64 ? 0 : precision, S->tc_err);
   const int n = S->n, no = S->no, nv = S->nv, nj = S->nj, so = S->so, sv = S->sv;
   const int to = S->to, tv = S->tv;
   const int64_t nn = int64_t(n) * n, dS = S->dS, vo = int64_t(nv) * no;

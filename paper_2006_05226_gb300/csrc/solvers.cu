@@ -150,8 +150,15 @@ mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out
   double e_old = 0.0, e = 0.0, norm = 0.0;
   int it = 0;
   bool conv = false;
+  // low-precision phase (gs_precision), then binary64 when refine_fp64 is set
+  int phase_prec = opt->gs_precision;
+  const double lowp_switch = std::max(opt->gs_tol, 1e-7);
   for (it = 1; it <= opt->max_gs_iter; ++it) {
-    omega_eval(S, t1, nullptr, true, tl ? tT : nullptr, x2, om1, tl ? omT : nullptr, energy);
+    {
+      LowpScope lowp(phase_prec, S->tc_err);
+      omega_eval(S, t1, nullptr, true, tl ? tT : nullptr, x2, om1, tl ? omT : nullptr, energy);
+    }
+    if (phase_prec != MLCC_FP64) check_tc_error(S);
     dots(om1, 0, 1, om1, n1, nrm, S->ws, s);
     if (tl) dots(omT, 0, 1, omT, tl, nrm + 1, S->ws, s);
     else fill(nrm + 1, 1, 0.0, s);
@@ -162,7 +169,14 @@ mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out
     norm = std::sqrt(h[1] + h[2]);
     if (!std::isfinite(e) || !std::isfinite(norm))
       throw Error(MLCC_E_NAN, "ground state: NaN or Inf in the residual at iteration " + std::to_string(it));
-    if (norm < opt->gs_tol && std::fabs(e - e_old) < opt->gs_energy_tol) {
+    if (phase_prec != MLCC_FP64 && norm < lowp_switch) {
+      if (!opt->refine_fp64) {
+        conv = true;
+        break;
+      }
+      phase_prec = MLCC_FP64;   // the next iterations in binary64 from these amplitudes
+    } else if (phase_prec == MLCC_FP64 && norm < opt->gs_tol &&
+               std::fabs(e - e_old) < opt->gs_energy_tol) {
       conv = true;
       break;
     }

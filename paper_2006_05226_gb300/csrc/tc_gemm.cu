@@ -89,12 +89,14 @@ __host__ __device__ constexpr uint32_t instr_desc() {
 
 struct TcParams {
   int64_t M, N;
-  int kblocks;
+  int kblocks;      // K blocks in total
+  int kb_per;       // K blocks per split (blockIdx.z); == kblocks without split
   double* C;
   int64_t ldc;
   double alpha, beta;
+  double* partial;  // split-K: [split][M][N] (alpha, beta applied by the reduction)
   int* err;
-  int m_fast;   // 1: blockIdx.x runs over M tiles
+  int m_fast;       // 1: blockIdx.x runs over M tiles
 };
 
 __global__ void __launch_bounds__(THREADS, 1)
@@ -126,7 +128,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const int nkb = p.kblocks;
+  const int kb0 = int(blockIdx.z) * p.kb_per;
+  const int nkb = max(0, min(p.kblocks, kb0 + p.kb_per) - kb0);
 
   if (warp == 0) {
     if (lane == 0) {
@@ -140,8 +143,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         const uint32_t a_dst = smem_u32(smem + s * STAGE_BYTES);
         const uint32_t b_dst = a_dst + A_BYTES;
         mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
-        tma_load_2d(a_dst, &tmA, full0 + 8 * s, kb * BK, int(m0));
-        tma_load_2d(b_dst, &tmB, full0 + 8 * s, kb * BK, int(n0));
+        tma_load_2d(a_dst, &tmA, full0 + 8 * s, (kb0 + kb) * BK, int(m0));
+        tma_load_2d(b_dst, &tmB, full0 + 8 * s, (kb0 + kb) * BK, int(n0));
         ++issued;
       }
       // drain: the copies this thread issued land before the CTA can exit
@@ -187,7 +190,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok && nkb > 0) {
       const int64_t row = m0 + 32 * q + lane;
-      double* crow = p.C + row * p.ldc;
+      double* const part = p.partial ? p.partial + int64_t(blockIdx.z) * p.M * p.N : nullptr;
+      double* crow = part ? part + row * p.N : p.C + row * p.ldc;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         uint32_t r[32];
@@ -207,8 +211,12 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
           for (int j = 0; j < 32; ++j) {
             const int64_t col = n0 + c0 + j;
             if (col < p.N) {
-              const double v = p.alpha * double(__uint_as_float(r[j]));
-              crow[col] = (p.beta == 0.0) ? v : v + p.beta * crow[col];
+              if (part) {
+                crow[col] = double(__uint_as_float(r[j]));
+              } else {
+                const double v = p.alpha * double(__uint_as_float(r[j]));
+                crow[col] = (p.beta == 0.0) ? v : v + p.beta * crow[col];
+              }
             }
           }
         }
@@ -332,9 +340,10 @@ void make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t kp, int 
 static inline int64_t pad64(int64_t k) { return (k + 63) / 64 * 64; }
 
 // C = alpha A B^T + beta C for bf16 K-major operands A [M][Kt], B [N][Kt] (Kt = S * Kp).
-void tc_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t M, int64_t N, int64_t Kt,
-             double* C, int64_t ldc, double alpha, double beta, int* err, bool m_fast,
-             cudaStream_t s) {
+// splits > 1 divides K over CTAs; partial must then hold splits * M * N doubles.
+void tc_gemm_split(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t M, int64_t N, int64_t Kt,
+                   double* C, int64_t ldc, double alpha, double beta, int* err, bool m_fast, int splits,
+                   double* partial, cudaStream_t s) {
   MLCC_REQUIRE(Kt % BK == 0, "tc_gemm: K must be a multiple of 64");
   MLCC_REQUIRE(M < (int64_t(1) << 31) && N < (int64_t(1) << 31), "tc_gemm: size too large");
   static bool attr = false;
@@ -349,17 +358,30 @@ void tc_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t M, int64_t 
   p.M = M;
   p.N = N;
   p.kblocks = int(Kt / BK);
+  splits = std::max(1, std::min(splits, p.kblocks));
+  p.kb_per = (p.kblocks + splits - 1) / splits;
+  splits = (p.kblocks + p.kb_per - 1) / p.kb_per;
   p.C = C;
   p.ldc = ldc;
   p.alpha = alpha;
   p.beta = beta;
+  p.partial = splits > 1 ? partial : nullptr;
+  MLCC_REQUIRE(splits == 1 || partial, "tc_gemm: split-K needs a partial buffer");
   p.err = err;
   p.m_fast = m_fast ? 1 : 0;
   const int64_t tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
-  dim3 grid = m_fast ? dim3(unsigned(tm), unsigned(tn)) : dim3(unsigned(tn), unsigned(tm));
-  MLCC_REQUIRE((m_fast ? tn : tm) < 65536, "tc_gemm: grid too large");
+  dim3 grid = m_fast ? dim3(unsigned(tm), unsigned(tn), unsigned(splits))
+                     : dim3(unsigned(tn), unsigned(tm), unsigned(splits));
+  MLCC_REQUIRE((m_fast ? tn : tm) < 65536 && splits < 65536, "tc_gemm: grid too large");
   k_tc_gemm<<<grid, THREADS, SMEM_BYTES, s>>>(ma, mb, p);
   MLCC_CHECK_LAUNCH();
+  if (splits > 1) reduce_partials(partial, splits, M, N, C, ldc, alpha, beta, s);
+}
+
+void tc_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t M, int64_t N, int64_t Kt,
+             double* C, int64_t ldc, double alpha, double beta, int* err, bool m_fast,
+             cudaStream_t s) {
+  tc_gemm_split(A, B, M, N, Kt, C, ldc, alpha, beta, err, m_fast, 1, nullptr, s);
 }
 
 void cvt_operand(const double* src, int64_t ld, int64_t rows, int64_t K, bool transpose, bool u_mode,
@@ -383,6 +405,115 @@ void cvt_operand(const double* src, int64_t ld, int64_t rows, int64_t K, bool tr
 }
 
 int split_segments(int precision) { return pattern(precision).S; }
+
+namespace {
+// Generic operand for gemm_tc: dst[r][s * Kp + kk] = piece_s(X(r, kk)) with
+//   r  = rb * Mrow + m  (row batches, stride sRow),  kk = kb * Kblk + k  (K batches, stride sK)
+//   X(r, kk) = base[rb * sRow + kb * sK + (tr ? k * ld + m : m * ld + k)]
+struct GOp {
+  const double* base;
+  int64_t R, Mrow, sRow, Ktot, Kblk, sK, ld, Kp;
+  int tr, S;
+  int piece[6];
+};
+__device__ __forceinline__ double gop_load(const GOp& o, int64_t r, int64_t kk) {
+  if (r >= o.R || kk >= o.Ktot) return 0.0;
+  const int64_t rb = r / o.Mrow, m = r - rb * o.Mrow;
+  const int64_t kb = kk / o.Kblk, k = kk - kb * o.Kblk;
+  return o.base[rb * o.sRow + kb * o.sK + (o.tr ? k * o.ld + m : m * o.ld + k)];
+}
+// K contiguous in the source: one thread per destination element, kk fastest
+__global__ void k_gop_direct(GOp o, __nv_bfloat16* dst) {
+  const int64_t total = o.R * o.Kp;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = t / o.Kp, kk = t - r * o.Kp;
+    __nv_bfloat16 pc[3];
+    split3(gop_load(o, r, kk), pc);
+    for (int s2 = 0; s2 < o.S; ++s2) dst[r * (o.S * o.Kp) + s2 * o.Kp + kk] = pc[o.piece[s2]];
+  }
+}
+// rows contiguous in the source: 32 x 32 tiles through shared memory
+__global__ void k_gop_tr(GOp o, __nv_bfloat16* dst) {
+  __shared__ double tile[32][33];
+  const int64_t r0 = int64_t(blockIdx.x) * 32, k0 = int64_t(blockIdx.y) * 32;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) tile[y][threadIdx.x] = gop_load(o, r0 + threadIdx.x, k0 + y);
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int64_t r = r0 + y, kk = k0 + threadIdx.x;
+    if (r >= o.R || kk >= o.Kp) continue;
+    __nv_bfloat16 pc[3];
+    split3(tile[threadIdx.x][y], pc);
+    for (int s2 = 0; s2 < o.S; ++s2) dst[r * (o.S * o.Kp) + s2 * o.Kp + kk] = pc[o.piece[s2]];
+  }
+}
+void convert_gop(GOp o, __nv_bfloat16* dst, cudaStream_t s) {
+  if (!o.tr) {
+    const int64_t total = o.R * o.Kp;
+    const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 32768)));
+    k_gop_direct<<<blocks, 256, 0, s>>>(o, dst);
+  } else {
+    MLCC_REQUIRE((o.R + 31) / 32 < (int64_t(1) << 31) && (o.Kp + 31) / 32 < 65536, "convert: grid");
+    dim3 blk(32, 8), grd(unsigned((o.R + 31) / 32), unsigned((o.Kp + 31) / 32));
+    k_gop_tr<<<grd, blk, 0, s>>>(o, dst);
+  }
+  MLCC_CHECK_LAUNCH();
+}
+}  // namespace
+
+// A binary64 GEMM (the Gemm of internal.cuh) on the tensor cores. Supported: a single
+// product, a batch reduction (batches concatenated along K), and a batch with a shared B
+// whose outputs are stacked rows (batches concatenated along M). Returns false (and does
+// nothing) for other shapes or when the workspace is too small.
+bool gemm_tc(const Gemm& g, int precision, Arena& ws, cudaStream_t s, int sm_count, int* err) {
+  const bool flatten = !g.reduce && g.batch > 1;
+  if (flatten && !(g.sB == 0 && g.sC == g.M * g.ldc)) return false;
+  const int64_t M = flatten ? g.M * g.batch : g.M;
+  const int64_t Ktot = g.reduce ? g.K * g.batch : g.K;
+  const int64_t N = g.N;
+  const SplitPattern pt = pattern(precision);
+  const int64_t Kp = pad64(Ktot), Kt = pt.S * Kp;
+  const size_t need = size_t(M + N) * Kt * 2 + 4 * 256;
+  if (ws.mark() + need + (size_t(1) << 22) > ws.capacity()) return false;
+  Scope sc(ws);
+  __nv_bfloat16* Abf = ws.get<__nv_bfloat16>(size_t(M) * Kt);
+  __nv_bfloat16* Bbf = ws.get<__nv_bfloat16>(size_t(N) * Kt);
+  GOp a{};
+  a.base = g.A;
+  a.R = M;
+  a.Mrow = flatten ? g.M : M;
+  a.sRow = flatten ? g.sA : 0;
+  a.Ktot = Ktot;
+  a.Kblk = g.reduce ? g.K : Ktot;
+  a.sK = g.reduce ? g.sA : 0;
+  a.ld = g.lda;
+  a.Kp = Kp;
+  a.tr = g.ta ? 1 : 0;
+  a.S = pt.S;
+  for (int i = 0; i < pt.S; ++i) a.piece[i] = pt.a[i];
+  GOp b = a;
+  b.base = g.B;
+  b.R = N;
+  b.Mrow = N;
+  b.sRow = 0;
+  b.sK = g.reduce ? g.sB : 0;
+  b.ld = g.ldb;
+  b.tr = g.tb ? 0 : 1;
+  for (int i = 0; i < pt.S; ++i) b.piece[i] = pt.b[i];
+  convert_gop(a, Abf, s);
+  convert_gop(b, Bbf, s);
+  const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+  const int64_t kblocks = Kt / BK;
+  int64_t splits = 1;
+  if (tiles < 2LL * std::max(sm_count, 1)) {
+    splits = std::min<int64_t>((2LL * std::max(sm_count, 1) + tiles - 1) / tiles, kblocks / 4);
+    splits = std::max<int64_t>(splits, 1);
+    while (splits > 1 && size_t(splits) * M * N * 8 + ws.mark() + (size_t(1) << 20) > ws.capacity()) splits /= 2;
+  }
+  double* partial = splits > 1 ? ws.get<double>(size_t(splits) * M * N) : nullptr;
+  tc_gemm_split(Abf, Bbf, M, N, Kt, g.C, g.ldc, g.alpha, g.beta, err, true, int(splits), partial, s);
+  return true;
+}
 
 // The two rank GEMMs of sigma in low precision.
 //   outer: C[dS][dS] = A^T B   with A, B [nj][dS] binary64 (A = the cached Lai)

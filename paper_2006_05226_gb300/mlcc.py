@@ -43,7 +43,7 @@ class mlcc_dims(ctypes.Structure):
 class mlcc_options(ctypes.Structure):
     _fields_ = [("n_roots", c_int32), ("max_gs_iter", c_int32), ("max_es_iter", c_int32),
                 ("diis_dim", c_int32), ("max_subspace", c_int32), ("precision", c_int32),
-                ("refine_fp64", c_int32), ("_pad", c_int32), ("gs_tol", c_double),
+                ("refine_fp64", c_int32), ("gs_precision", c_int32), ("gs_tol", c_double),
                 ("gs_energy_tol", c_double), ("es_res_tol", c_double),
                 ("es_omega_tol", c_double), ("lowp_res_tol", c_double)]
 

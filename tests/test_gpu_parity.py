@@ -248,3 +248,18 @@ def test_mixed_davidson_refined_to_fp64(ctx, small, prec):
                                                        lowp_res_tol=1e-3), want_vectors=False)
     assert info.converged and info.n_sigma_lowp > 0
     assert np.abs(w - ref.omega).max() < E_TOL
+
+
+@pytest.mark.parametrize("case", ["small", "tiny:three_level"])
+def test_mixed_ground_state(ctx, request, case):
+    """Ground state iterated with tensor-core contractions (split bfloat16), then polished
+    in binary64: the oracle energy to 1e-8 Ha; without the polish to 1e-6 Ha."""
+    from paper_2006_05226_gb300 import mlcc
+    L, F, no, lev = _systems(request, case)
+    g, o, lay = _make(ctx, L, F, no, lev)
+    gs = solve_ground_state(o)
+    for refine, tol in ((1, E_TOL), (0, 1e-6)):
+        opts = mlcc.default_options(gs_precision=mlcc.MLCC_BF16X6, refine_fp64=refine)
+        t1, x2, info = g.ground_state(opts)
+        assert info.converged
+        assert abs(info.e_corr - gs.energy) < tol
