@@ -196,7 +196,9 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default="bf16", choices=["fp64", "bf16"])
+    ap.add_argument("--precision", default="bf16x3", choices=["fp64", "bf16", "bf16x3", "bf16x6"])
+    ap.add_argument("--no-fp64-check", action="store_true",
+                    help="skip the plain binary64 reference solve used to report the error")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -217,8 +219,10 @@ def main():
 
     spec = replace(CONFIGS[WORKLOAD], seed=CONFIGS[WORKLOAD].seed + rank)
     system = make_system(spec)
-    prec = mlcc.MLCC_FP64 if args.precision == "fp64" else mlcc.MLCC_BF16
-    opts = mlcc.default_options(n_roots=spec.n_roots, precision=prec, refine_fp64=1)
+    prec = {"fp64": mlcc.MLCC_FP64, "bf16": mlcc.MLCC_BF16, "bf16x3": mlcc.MLCC_BF16X3,
+            "bf16x6": mlcc.MLCC_BF16X6}[args.precision]
+    opts = mlcc.default_options(n_roots=spec.n_roots, precision=prec, gs_precision=prec,
+                                refine_fp64=1, lowp_res_tol=1e-5)
     ctx = mlcc.Context(local)
     L_dev = torch.as_tensor(system.L, device=f"cuda:{local}")
     F_dev = torch.as_tensor(system.fock, device=f"cuda:{local}")
@@ -260,6 +264,16 @@ def main():
     total_sigma = allreduce_sum(float(n_sigma), world)
     value = total_sigma / t_max
 
+    # error against the plain binary64 GPU path (outside the timed region)
+    err_fp64 = None
+    if prec != mlcc.MLCC_FP64 and not args.no_fp64_check:
+        ref_opts = mlcc.default_options(n_roots=spec.n_roots)
+        g = mlcc.System(ctx, L_dev, F_dev, spec.n_occ, system.level)
+        g.ground_state(ref_opts)
+        w_ref, _, _ = g.excited_states(ref_opts, want_vectors=False)
+        g.close()
+        err_fp64 = float(np.max(np.abs(np.asarray(omegas) - w_ref)))
+
     # end to end through the public host-memory entry point (H2D of L and F inside)
     e2e = None
     if not args.no_e2e:
@@ -295,11 +309,12 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if prec == mlcc.MLCC_FP64 else "bf16+f64",
+            "dtype": "f64" if prec == mlcc.MLCC_FP64 else f"{args.precision}+f64",
             "data": "synthetic", "config": config_dict(args, args.precision),
             "solves_per_s": args.steps * world / t_max, "sigma_per_step": n_sigma / args.steps,
             "sigma_lowp_per_step": n_lowp / args.steps,
             "omega": [float(x) for x in omegas], "e_corr": gs.e_corr,
+            "max_abs_omega_err_vs_fp64_gpu_Ha": err_fp64,
             "roofline": roof, "clocks": clk, "gpu_launches": int(launches), "e2e": e2e}
     if world == 1 and not args.no_cpu_baseline:
         set_blas_threads()

@@ -109,6 +109,7 @@ static void setup_system(mlcc_system* S, const mlcc_problem* P, const double* ch
   S->Xji = S->persist.get<double>(size_t(no) * S->so + 1);
   S->Yab = S->persist.get<double>(size_t(S->sv) * S->nv + 1);
   S->tc_err = S->persist.get<int>(64);
+  S->opcache = operand_cache_new();
   MLCC_CUDA(cudaMemsetAsync(S->tc_err, 0, 256, s));
   // scratch: enough for sigma (dLt, three doubles-sized arrays, two [nj][dS]) plus GEMM
   // partials and the einsum engine's permuted operands
@@ -298,6 +299,7 @@ void mlcc_system_destroy(mlcc_system* sys) {
   cudaSetDevice(sys->ctx->device);
   cudaStreamSynchronize(sys->ctx->stream);
   ccsd_cache_free(sys);
+  operand_cache_free(sys->opcache);
   delete sys;
 }
 
@@ -331,6 +333,7 @@ mlcc_status mlcc_t1_transform(mlcc_system* S, const double* t1, double* lt) {
     MLCC_REQUIRE(S && t1 && lt, "mlcc_t1_transform: NULL argument");
     MLCC_CUDA(cudaSetDevice(S->ctx->device));
     S->prepared = false;
+    operand_cache_clear(S->opcache);
     dress(S, t1, lt, nullptr);
     return MLCC_OK;
   });
@@ -341,6 +344,7 @@ mlcc_status mlcc_fock_t1(mlcc_system* S, const double* t1, double* f) {
     MLCC_REQUIRE(S && t1 && f, "mlcc_fock_t1: NULL argument");
     MLCC_CUDA(cudaSetDevice(S->ctx->device));
     S->prepared = false;
+    operand_cache_clear(S->opcache);
     dress(S, t1, S->Lt, S->ht);
     build_fock(S, S->ht, S->Lt, f);
     return MLCC_OK;

@@ -9,12 +9,6 @@
 
 namespace mlcc {
 
-struct CCSDCache {
-  Arena arena;
-  std::vector<double*> slots;
-  DT G;   // g~_Kcbd = Lt^J_Kc Lt^J_bd, K over all occupied orbitals, c, b, d CCSD-active
-};
-
 void ccsd_cache_free(mlcc_system* S) {
   delete S->ccsd;
   S->ccsd = nullptr;

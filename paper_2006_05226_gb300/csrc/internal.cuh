@@ -54,6 +54,7 @@ class Arena {
   void release(size_t m) { top_ = m; }
   size_t capacity() const { return cap_; }
   size_t high_water() const { return hw_; }
+  const char* base() const { return base_; }
  private:
   char* base_ = nullptr;
   size_t cap_ = 0, top_ = 0, hw_ = 0;
@@ -105,21 +106,30 @@ struct Gemm {
   double* C = nullptr; int64_t ldc = 0, sC = 0;
   int64_t batch = 1;
   bool reduce = false;
+  bool a_const = false, b_const = false;   // operand unchanged until the cache is cleared
 };
 void gemm_f64(const Gemm& g, Arena& ws, cudaStream_t s, int sm_count);
 
 // Low-precision routing: while a LowpScope is alive on this thread, gemm_f64 sends large
 // GEMMs to the tcgen05 tensor-core path (bfloat16 pieces per mlcc_precision, fp32
 // accumulation per split, binary64 reduction); everything else stays binary64.
+struct OperandCache;   // bfloat16 pieces of constant GEMM operands (per system)
 struct LowpScope {
   int prev;
   int* err;
   int* prev_err;
-  LowpScope(int precision, int* err_flag);
+  OperandCache* prev_cache;
+  LowpScope(int precision, int* err_flag, OperandCache* cache = nullptr);
   ~LowpScope();
 };
 int lowp_precision();
 int* lowp_error_flag();
+OperandCache* lowp_cache();
+OperandCache* operand_cache_new();
+void operand_cache_clear(OperandCache* c);
+void operand_cache_free(OperandCache* c);
+// device memory ranges whose contents stay fixed while the cache is valid
+void operand_cache_set_ranges(OperandCache* c, const std::vector<std::pair<const char*, size_t>>& r);
 bool gemm_tc(const Gemm& g, int precision, Arena& ws, cudaStream_t s, int sm_count, int* err);
 // C = alpha * sum_s partial[s] + beta * C (deterministic order)
 void reduce_partials(const double* partial, int nsplit, int64_t M, int64_t N, double* C,

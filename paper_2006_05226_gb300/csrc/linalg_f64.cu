@@ -305,16 +305,21 @@ static void launch_skinny(const GP& p, bool ta, bool tb, cudaStream_t s) {
 
 static thread_local int g_lowp = 0;
 static thread_local int* g_lowp_err = nullptr;
-LowpScope::LowpScope(int precision, int* err_flag) : prev(g_lowp), err(err_flag), prev_err(g_lowp_err) {
+static thread_local OperandCache* g_lowp_cache = nullptr;
+LowpScope::LowpScope(int precision, int* err_flag, OperandCache* cache)
+    : prev(g_lowp), err(err_flag), prev_err(g_lowp_err), prev_cache(g_lowp_cache) {
   g_lowp = precision;
   g_lowp_err = err_flag;
+  g_lowp_cache = cache;
 }
 LowpScope::~LowpScope() {
   g_lowp = prev;
   g_lowp_err = prev_err;
+  g_lowp_cache = prev_cache;
 }
 int lowp_precision() { return g_lowp; }
 int* lowp_error_flag() { return g_lowp_err; }
+OperandCache* lowp_cache() { return g_lowp_cache; }
 
 void reduce_partials(const double* partial, int nsplit, int64_t M, int64_t N, double* C,
                      int64_t ldc, double alpha, double beta, cudaStream_t s) {

@@ -414,6 +414,7 @@ void omega_eval(mlcc_system* S, const double* t1, const double* x2, bool gs_mode
   const int n = S->n, no = S->no, nv = S->nv, nj = S->nj, so = S->so, sv = S->sv;
   const int64_t nn = int64_t(n) * n, dS = S->dS;
   S->prepared = false;
+  operand_cache_clear(S->opcache);
   Scope sc(S->ws);
   dress(S, t1, S->Lt, S->ht);
   build_fock(S, S->ht, S->Lt, S->Ft);
@@ -502,6 +503,7 @@ void jacobian_prepare(mlcc_system* S, const double* t1, const double* x2) {
   const int64_t dS = S->dS;
   S->prepared = false;
   S->lowp_prec = -1;
+  operand_cache_clear(S->opcache);
   ccsd_cache_free(S);
   Scope sc(S->ws);
   MLCC_CUDA(cudaMemcpyAsync(S->t1gs, t1, size_t(nv) * no * 8, cudaMemcpyDeviceToDevice, s));
@@ -611,7 +613,12 @@ static void jacobian_intermediates(mlcc_system* S) {
 void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision) {
   if (!S->prepared) throw Error(MLCC_E_STATE, "mlcc_sigma: call mlcc_jacobian_prepare first");
   cudaStream_t s = stm(S);
-  LowpScope lowp(precision == MLCC_FP64 ? 0 : precision, S->tc_err);
+  if (precision != MLCC_FP64 && S->opcache) {
+    std::vector<std::pair<const char*, size_t>> r = {{S->persist.base(), S->persist.capacity()}};
+    if (S->ccsd) r.push_back({S->ccsd->arena_base(), S->ccsd->arena_size()});
+    operand_cache_set_ranges(S->opcache, r);
+  }
+  LowpScope lowp(precision == MLCC_FP64 ? 0 : precision, S->tc_err, S->opcache);
   const int n = S->n, no = S->no, nv = S->nv, nj = S->nj, so = S->so, sv = S->sv;
   const int to = S->to, tv = S->tv;
   const int64_t nn = int64_t(n) * n, dS = S->dS, vo = int64_t(nv) * no;

@@ -175,6 +175,10 @@ mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out
         break;
       }
       phase_prec = MLCC_FP64;   // the next iterations in binary64 from these amplitudes
+      order.clear();            // the low-precision residuals do not belong in DIIS
+      std::fill(Bm.begin(), Bm.end(), 0.0);
+      e_old = e;
+      continue;                 // re-evaluate the residual in binary64 before stepping
     } else if (phase_prec == MLCC_FP64 && norm < opt->gs_tol &&
                std::fabs(e - e_old) < opt->gs_energy_tol) {
       conv = true;
@@ -336,9 +340,12 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
                            double* r_out, mlcc_es_info* info) {
   if (!S->prepared) throw Error(MLCC_E_STATE, "mlcc_excited_states: no prepared ground state");
   cudaStream_t s = S->ctx->stream;
-  const int no = S->no, nv = S->nv, nr = opt->n_roots;
+  const int no = S->no, nv = S->nv, nreq = opt->n_roots;
   const int64_t n1 = int64_t(nv) * no, dim = n1 + S->nd;
-  MLCC_REQUIRE(nr >= 1 && nr <= n1, "n_roots must be in [1, n_vir * n_occ]");
+  MLCC_REQUIRE(nreq >= 1 && nreq <= n1, "n_roots must be in [1, n_vir * n_occ]");
+  // two buffer roots above the requested ones: they steady the convergence of clustered
+  // spectra; only the requested roots decide convergence
+  const int nr = int(std::min<int64_t>(nreq + 2, std::min<int64_t>(n1, dim)));
   int maxsub = opt->max_subspace > 0 ? opt->max_subspace : 8 * nr;
   maxsub = std::max(maxsub, 3 * nr);
   const int collapse = 2 * nr;
@@ -398,7 +405,8 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
     complex_pair = false;
     for (int k = 0; k < nr; ++k) {
       w[k] = ev[k].real();
-      if (std::fabs(ev[k].imag()) > 1e-10 * std::max(1.0, std::fabs(ev[k].real()))) complex_pair = true;
+      if (k < nreq && std::fabs(ev[k].imag()) > 1e-10 * std::max(1.0, std::fabs(ev[k].real())))
+        complex_pair = true;
     }
     std::vector<double> Yt(size_t(nr) * D.m);
     for (int k = 0; k < nr; ++k)
@@ -423,17 +431,20 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
     const bool in_lowp = prec != MLCC_FP64;
     const double rtol = (two_phase && in_lowp) ? opt->lowp_res_tol : opt->es_res_tol;
     std::vector<int> todo;
+    bool req_done = true;
     for (int k = 0; k < nr; ++k) {
       const bool ok = (rn[k] < rtol) && (two_phase && in_lowp ? true
                                                               : std::fabs(w[k] - w_old[k]) < opt->es_omega_tol);
       if (!ok) todo.push_back(k);
+      if (!ok && k < nreq) req_done = false;
     }
     w_old = w;
+    if (req_done) todo.clear();
     if (todo.empty()) {
       if (two_phase && in_lowp) {
         // refinement: restart from the low-precision Ritz vectors with binary64 sigma
         prec = MLCC_FP64;
-        const int keep = std::min(nr, D.m);
+        const int keep = std::min(nr, D.m);   // all tracked Ritz vectors
         MLCC_CUDA(cudaMemcpyAsync(CB, X, size_t(keep) * dim * 8, cudaMemcpyDeviceToDevice, s));
         D.m = 0;
         int added = 0;
@@ -519,7 +530,7 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
     if (D.m == m0) {
       // no new direction: the basis spans an invariant subspace
       conv = true;
-      for (int k = 0; k < nr; ++k) conv = conv && rn[k] < opt->es_res_tol;
+      for (int k = 0; k < nreq; ++k) conv = conv && rn[k] < opt->es_res_tol;
       break;
     }
     sigma_batch(S, D.B + int64_t(m0) * dim, D.Sg + int64_t(m0) * dim, D.m - m0, dim, prec);
@@ -540,8 +551,8 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
       }
     }
   }
-  for (int k = 0; k < nr; ++k) omega_host[k] = w[k];
-  if (r_out) MLCC_CUDA(cudaMemcpyAsync(r_out, X, size_t(nr) * dim * 8, cudaMemcpyDeviceToDevice, s));
+  for (int k = 0; k < nreq; ++k) omega_host[k] = w[k];
+  if (r_out) MLCC_CUDA(cudaMemcpyAsync(r_out, X, size_t(nreq) * dim * 8, cudaMemcpyDeviceToDevice, s));
   MLCC_CUDA(cudaStreamSynchronize(s));
   if (info) {
     info->iterations = it;

@@ -15,7 +15,14 @@ struct Dual {
 
 enum class Mode { Value, Tangent };
 
-struct CCSDCache;   // value tensors of the CCSD block at the Jacobian ground state
+// value tensors of the CCSD block at the Jacobian ground state
+struct CCSDCache {
+  Arena arena;
+  std::vector<double*> slots;
+  DT G;   // g~_Kcbd = Lt^J_Kc Lt^J_bd, K over all occupied orbitals, c, b, d CCSD-active
+  const char* arena_base() const { return arena.base(); }
+  size_t arena_size() const { return arena.capacity(); }
+};
 
 struct TCGemm;      // tensor-core GEMM plan (mixed precision)
 
@@ -55,6 +62,7 @@ struct mlcc_system {
   __nv_bfloat16* lov_bf = nullptr;
   int lowp_prec = -1;
   int* tc_err = nullptr;
+  mlcc::OperandCache* opcache = nullptr;   // bfloat16 pieces of Jacobian-constant operands
   mlcc::Arena persist;     // the buffers above
   mlcc::Arena ws;          // scratch
   int64_t workspace_bytes = 0;

@@ -461,6 +461,66 @@ void convert_gop(GOp o, __nv_bfloat16* dst, cudaStream_t s) {
 }
 }  // namespace
 
+}  // namespace mlcc
+#include <tuple>
+namespace mlcc {
+struct OperandCache {
+  struct Entry {
+    std::tuple<const void*, int64_t, int64_t, int64_t, int64_t, int64_t, int64_t, int64_t, int, int, int> key;
+    __nv_bfloat16* p;
+  };
+  std::vector<Entry> entries;
+  std::vector<void*> blocks;
+  std::vector<std::pair<const char*, size_t>> ranges;
+  bool constant(const void* p) const {
+    const char* q = static_cast<const char*>(p);
+    for (auto& r : ranges)
+      if (q >= r.first && q < r.first + r.second) return true;
+    return false;
+  }
+};
+void operand_cache_set_ranges(OperandCache* c, const std::vector<std::pair<const char*, size_t>>& r) {
+  if (c) c->ranges = r;
+}
+OperandCache* operand_cache_new() { return new OperandCache(); }
+void operand_cache_clear(OperandCache* c) {
+  if (!c) return;
+  for (void* b : c->blocks) cudaFree(b);
+  c->blocks.clear();
+  c->entries.clear();
+}
+void operand_cache_free(OperandCache* c) {
+  operand_cache_clear(c);
+  delete c;
+}
+// converted operand, from the cache when the operand is marked constant
+static const __nv_bfloat16* get_operand(const GOp& o, int side, bool cacheable, Arena& ws, cudaStream_t s) {
+  OperandCache* c = lowp_cache();
+  if (c && !(cacheable || c->constant(o.base))) c = nullptr;
+  const size_t bytes = size_t(o.R) * o.S * o.Kp * 2;
+  if (!c) {
+    __nv_bfloat16* d = ws.get<__nv_bfloat16>(size_t(o.R) * o.S * o.Kp);
+    convert_gop(o, d, s);
+    return d;
+  }
+  auto key = std::make_tuple(static_cast<const void*>(o.base), o.R, o.Mrow, o.sRow, o.Ktot, o.Kblk, o.sK, o.ld,
+                             o.tr, o.S * 16 + o.piece[o.S > 1 ? 1 : 0], side);
+  for (auto& e : c->entries)
+    if (e.key == key) return e.p;
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    __nv_bfloat16* d = ws.get<__nv_bfloat16>(size_t(o.R) * o.S * o.Kp);
+    convert_gop(o, d, s);
+    return d;
+  }
+  c->blocks.push_back(mem);
+  auto* d = static_cast<__nv_bfloat16*>(mem);
+  convert_gop(o, d, s);
+  c->entries.push_back({key, d});
+  return d;
+}
+
 // A binary64 GEMM (the Gemm of internal.cuh) on the tensor cores. Supported: a single
 // product, a batch reduction (batches concatenated along K), and a batch with a shared B
 // whose outputs are stacked rows (batches concatenated along M). Returns false (and does
@@ -476,8 +536,6 @@ bool gemm_tc(const Gemm& g, int precision, Arena& ws, cudaStream_t s, int sm_cou
   const size_t need = size_t(M + N) * Kt * 2 + 4 * 256;
   if (ws.mark() + need + (size_t(1) << 22) > ws.capacity()) return false;
   Scope sc(ws);
-  __nv_bfloat16* Abf = ws.get<__nv_bfloat16>(size_t(M) * Kt);
-  __nv_bfloat16* Bbf = ws.get<__nv_bfloat16>(size_t(N) * Kt);
   GOp a{};
   a.base = g.A;
   a.R = M;
@@ -500,8 +558,8 @@ bool gemm_tc(const Gemm& g, int precision, Arena& ws, cudaStream_t s, int sm_cou
   b.ld = g.ldb;
   b.tr = g.tb ? 0 : 1;
   for (int i = 0; i < pt.S; ++i) b.piece[i] = pt.b[i];
-  convert_gop(a, Abf, s);
-  convert_gop(b, Bbf, s);
+  const __nv_bfloat16* Abf = get_operand(a, 0, g.a_const, ws, s);
+  const __nv_bfloat16* Bbf = get_operand(b, 1, g.b_const, ws, s);
   const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
   const int64_t kblocks = Kt / BK;
   int64_t splits = 1;
