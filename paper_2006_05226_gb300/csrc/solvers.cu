@@ -343,9 +343,7 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
   const int no = S->no, nv = S->nv, nreq = opt->n_roots;
   const int64_t n1 = int64_t(nv) * no, dim = n1 + S->nd;
   MLCC_REQUIRE(nreq >= 1 && nreq <= n1, "n_roots must be in [1, n_vir * n_occ]");
-  // two buffer roots above the requested ones: they steady the convergence of clustered
-  // spectra; only the requested roots decide convergence
-  const int nr = int(std::min<int64_t>(nreq + 2, std::min<int64_t>(n1, dim)));
+  const int nr = nreq;
   int maxsub = opt->max_subspace > 0 ? opt->max_subspace : 8 * nr;
   maxsub = std::max(maxsub, 3 * nr);
   const int collapse = 2 * nr;
