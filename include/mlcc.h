@@ -105,12 +105,14 @@ typedef struct {
   int32_t diis_dim;       /* DIIS history length                                      */
   int32_t max_subspace;   /* Davidson basis size before collapse (0: 8 n_roots)       */
   int32_t precision;      /* mlcc_precision of sigma inside the Davidson loop          */
-  int32_t refine_fp64;    /* with a low precision: continue the ground-state and the
-                             Davidson iterations in binary64 once the low-precision
-                             phase has converged                                       */
-  int32_t gs_precision;   /* mlcc_precision of the ground-state iterations; with a low
-                             precision they run until |Omega| < 1e-7 (or gs_tol), then
-                             in binary64 if refine_fp64 is set                         */
+  int32_t refine_fp64;    /* with a low precision: binary64 iterations after the
+                             low-precision phase. Ground state: if > 0, binary64 until
+                             gs_tol. Davidson: at most refine_fp64 binary64 iterations
+                             (1 = one Rayleigh-Ritz sweep with binary64 sigma on the
+                             low-precision Ritz vectors), fewer if es_res_tol is met    */
+  int32_t gs_precision;   /* mlcc_precision of the ground-state iterations; the low-
+                             precision phase ends when |Omega| < 1e-7 or stops halving
+                             over three iterations                                     */
   double gs_tol;          /* |Omega|_2 threshold                                      */
   double gs_energy_tol;   /* |dE| threshold between iterations                        */
   double es_res_tol;      /* |A R - w R|_2 threshold per root                          */
@@ -130,9 +132,10 @@ typedef struct {
   int32_t iterations;     /* Davidson iterations (both phases)                         */
   int32_t n_sigma;        /* sigma-vectors evaluated                                  */
   int32_t n_sigma_lowp;   /* of which in low precision                                */
-  int32_t converged;
+  int32_t converged;      /* residual thresholds met (or the refinement sweeps done)  */
   int32_t complex_pair;
-  int32_t _pad;
+  int32_t fp64_sweeps;    /* binary64 iterations after a low-precision phase          */
+  double max_residual;    /* max_k |A R_k - w_k R_k|, last evaluation (its precision)  */
 } mlcc_es_info;
 
 /* ---- context ------------------------------------------------------------------ */

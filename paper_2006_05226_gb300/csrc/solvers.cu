@@ -8,6 +8,8 @@
 #include <cmath>
 #include <complex>
 #include <numeric>
+#include <cstdio>
+#include <cstdlib>
 
 namespace mlcc {
 
@@ -113,6 +115,15 @@ __global__ void k_argmax_abs(const double* x, int64_t n, double* out_val) {
 }
 }  // namespace
 
+// MLCC_VERBOSE=1 in the environment: one line per iteration on stderr
+static bool verbose() {
+  static const bool v = [] {
+    const char* e = std::getenv("MLCC_VERBOSE");
+    return e && e[0] && e[0] != '0';
+  }();
+  return v;
+}
+
 static double host_scalar(mlcc_system* S, const double* d) {
   double h;
   copy_d2h(&h, d, 1, S->ctx->stream);
@@ -153,6 +164,7 @@ mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out
   // low-precision phase (gs_precision), then binary64 when refine_fp64 is set
   int phase_prec = opt->gs_precision;
   const double lowp_switch = std::max(opt->gs_tol, 1e-7);
+  std::vector<double> lowp_norms;   // residual norms of the low-precision phase
   for (it = 1; it <= opt->max_gs_iter; ++it) {
     {
       LowpScope lowp(phase_prec, S->tc_err);
@@ -169,7 +181,19 @@ mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out
     norm = std::sqrt(h[1] + h[2]);
     if (!std::isfinite(e) || !std::isfinite(norm))
       throw Error(MLCC_E_NAN, "ground state: NaN or Inf in the residual at iteration " + std::to_string(it));
-    if (phase_prec != MLCC_FP64 && norm < lowp_switch) {
+    if (verbose())
+      std::fprintf(stderr, "[mlcc] GS it %3d prec %d E %.14f |Omega| %.3e\n", it, phase_prec, e, norm);
+    bool stalled = false;
+    if (phase_prec != MLCC_FP64) {
+      lowp_norms.push_back(norm);
+      const size_t q = lowp_norms.size();
+      if (q >= 6) {
+        const double before = *std::min_element(lowp_norms.begin(), lowp_norms.end() - 3);
+        const double recent = *std::min_element(lowp_norms.end() - 3, lowp_norms.end());
+        stalled = recent > 0.5 * before;   // no halving in three iterations: the noise floor
+      }
+    }
+    if (phase_prec != MLCC_FP64 && (norm < lowp_switch || stalled)) {
       if (!opt->refine_fp64) {
         conv = true;
         break;
@@ -376,7 +400,8 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
 
   int prec = opt->precision;
   const bool lowp = prec != MLCC_FP64;
-  const bool two_phase = lowp && opt->refine_fp64;
+  const bool two_phase = lowp && opt->refine_fp64 > 0;
+  int fp64_sweeps = 0;
   int n_sigma = 0, n_sigma_lowp = 0;
   auto count_sigma = [&](int k) {
     n_sigma += k;
@@ -427,12 +452,17 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
       }
     }
     const bool in_lowp = prec != MLCC_FP64;
-    const double rtol = (two_phase && in_lowp) ? opt->lowp_res_tol : opt->es_res_tol;
+    if (verbose()) {
+      std::fprintf(stderr, "[mlcc] ES it %3d prec %d dim %3d", it, prec, D.m);
+      for (int k = 0; k < nr; ++k) std::fprintf(stderr, "  w %.10f r %.2e", w[k], rn[k]);
+      std::fprintf(stderr, "\n");
+    }
+    if (two_phase && !in_lowp) ++fp64_sweeps;
+    const double rtol = in_lowp ? opt->lowp_res_tol : opt->es_res_tol;
     std::vector<int> todo;
     bool req_done = true;
     for (int k = 0; k < nr; ++k) {
-      const bool ok = (rn[k] < rtol) && (two_phase && in_lowp ? true
-                                                              : std::fabs(w[k] - w_old[k]) < opt->es_omega_tol);
+      const bool ok = (rn[k] < rtol) && (in_lowp ? true : std::fabs(w[k] - w_old[k]) < opt->es_omega_tol);
       if (!ok) todo.push_back(k);
       if (!ok && k < nreq) req_done = false;
     }
@@ -462,6 +492,10 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
         continue;
       }
       conv = true;
+      break;
+    }
+    if (two_phase && !in_lowp && fp64_sweeps >= opt->refine_fp64) {
+      conv = true;   // the binary64 refinement budget is spent; max_residual tells how far
       break;
     }
     // new directions
@@ -558,6 +592,10 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
     info->n_sigma_lowp = n_sigma_lowp;
     info->converged = conv ? 1 : 0;
     info->complex_pair = complex_pair ? 1 : 0;
+    info->fp64_sweeps = fp64_sweeps;
+    double mr = 0.0;
+    for (int k = 0; k < nr; ++k) mr = std::max(mr, rn[k]);
+    info->max_residual = mr;
   }
   if (!conv) return MLCC_E_ES_NOCONV;
   if (complex_pair) return MLCC_E_COMPLEX_ROOT;

@@ -55,7 +55,8 @@ class mlcc_gs_info(ctypes.Structure):
 
 class mlcc_es_info(ctypes.Structure):
     _fields_ = [("iterations", c_int32), ("n_sigma", c_int32), ("n_sigma_lowp", c_int32),
-                ("converged", c_int32), ("complex_pair", c_int32), ("_pad", c_int32)]
+                ("converged", c_int32), ("complex_pair", c_int32), ("fp64_sweeps", c_int32),
+                ("max_residual", c_double)]
 
 
 class MLCCError(RuntimeError):

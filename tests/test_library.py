@@ -47,7 +47,7 @@ def test_binding_struct_sizes_match_header(lib):
     assert ctypes.sizeof(mlcc.mlcc_dims) == 56
     assert ctypes.sizeof(mlcc.mlcc_options) == 72
     assert ctypes.sizeof(mlcc.mlcc_gs_info) == 32
-    assert ctypes.sizeof(mlcc.mlcc_es_info) == 24
+    assert ctypes.sizeof(mlcc.mlcc_es_info) == 32
 
 
 def test_product_path_does_not_import_the_oracle():
