@@ -221,8 +221,12 @@ def main():
     system = make_system(spec)
     prec = {"fp64": mlcc.MLCC_FP64, "bf16": mlcc.MLCC_BF16, "bf16x3": mlcc.MLCC_BF16X3,
             "bf16x6": mlcc.MLCC_BF16X6}[args.precision]
+    # mixed path: split-bf16 ground state polished in binary64 to 1e-9, split-bf16 Davidson
+    # to a 1e-5 residual, then one binary64 Rayleigh-Ritz sweep on its Ritz vectors
     opts = mlcc.default_options(n_roots=spec.n_roots, precision=prec, gs_precision=prec,
-                                refine_fp64=1, lowp_res_tol=1e-5)
+                                refine_fp64=1, lowp_res_tol=1e-5,
+                                gs_tol=1e-9 if prec != mlcc.MLCC_FP64 else 1e-11,
+                                gs_energy_tol=1e-10 if prec != mlcc.MLCC_FP64 else 1e-12)
     ctx = mlcc.Context(local)
     L_dev = torch.as_tensor(system.L, device=f"cuda:{local}")
     F_dev = torch.as_tensor(system.fock, device=f"cuda:{local}")
