@@ -260,7 +260,9 @@ def main():
     torch.cuda.synchronize()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     launches = mlcc.launch_count() - launches0
-    k_n, k_ms, k_flop = ctx.kernel_time("rank_gemm")
+    fam = "rank_gemm_f64" if prec == mlcc.MLCC_FP64 else "rank_gemm_tc"
+    k_n, k_ms, k_flop = ctx.kernel_time(fam)
+    f64_n, f64_ms, f64_flop = ctx.kernel_time("rank_gemm_f64")
     ctx.kernel_timing(False)
     clk = clocks.stop()
     barrier(world)
@@ -304,12 +306,20 @@ def main():
     else:
         ach = k_flop / (k_ms / 1e3) / 1e12 if k_ms > 0 else None
         peak = pk.get("bf16_tflops_sustained", FALLBACK["bf16_tflops_sustained"])
+        pieces = {mlcc.MLCC_BF16: 1, mlcc.MLCC_BF16X3: 3, mlcc.MLCC_BF16X6: 6}[prec]
         roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": (ach / peak) if ach else None, "traffic": None,
-                "kernel": "rank_gemm (tcgen05 bf16, fp32 accumulate)",
-                "peak_source": f"bf16 sustained, of {src}"}
+                "kernel": "k_tc_gemm: Cholesky-rank doubles GEMMs (tcgen05, bf16 pieces, fp32 accumulate)",
+                "achieved_is": "algorithmic 2MNK flops of the contraction per launch / launch time",
+                "tensor_ops_per_algorithmic_flop": pieces,
+                "tensor_issue_tflops": (ach * pieces) if ach else None,
+                "peak_source": f"bf16 dense sustained, of {src}"}
     roof["launches"] = k_n
     roof["avg_launch_ms"] = (k_ms / k_n) if k_n else None
+    roof["flop_per_launch"] = (k_flop / k_n) if k_n else None
+    if prec != mlcc.MLCC_FP64:
+        roof["fp64_rank_gemm"] = {"launches": f64_n, "total_ms": f64_ms,
+                                  "tflops": (f64_flop / f64_ms / 1e9) if f64_ms else None}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,

@@ -149,9 +149,11 @@ void mlcc_ctx_destroy(mlcc_ctx* ctx);
 void* mlcc_ctx_stream(mlcc_ctx* ctx);
 const char* mlcc_last_error(void);
 /* Kernel timing: when enabled, the library records CUDA events around each launch of
-   the named kernel family ("rank_gemm": the Cholesky-rank doubles GEMMs) on the
-   context stream; mlcc_kernel_time returns launches, summed milliseconds and summed
-   algorithmic flops since the last reset (it synchronises the stream). */
+   a kernel family on the context stream: "rank_gemm_tc" (the Cholesky-rank doubles GEMMs
+   on tcgen05 tensor cores) and "rank_gemm_f64" (the same GEMMs in binary64).
+   mlcc_kernel_time returns launches, summed milliseconds and summed algorithmic flops
+   (2 M N K of the contraction; split-bfloat16 precisions issue S times as many tensor
+   operations, S = 1, 3, 6) since the last reset; it synchronises. */
 void mlcc_kernel_timing(mlcc_ctx* ctx, int enable);
 mlcc_status mlcc_kernel_time(mlcc_ctx* ctx, const char* family, int64_t* launches,
                              double* total_ms, double* total_flop);

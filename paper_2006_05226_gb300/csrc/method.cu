@@ -330,7 +330,7 @@ void rank_gemm_f64(mlcc_system* S, bool outer, const double* A, const double* B,
   }
   g.alpha = alpha;
   g.beta = beta;
-  timed(S, "rank_gemm", 2.0 * double(g.M) * double(g.N) * double(g.K),
+  timed(S, lowp_precision() ? "rank_gemm_tc" : "rank_gemm_f64", 2.0 * double(g.M) * double(g.N) * double(g.K),
         [&] { gemm_f64(g, S->ws, stm(S), smc(S)); });
 }
 

@@ -594,7 +594,7 @@ void rank_gemm_lowp(mlcc_system* S, bool outer, const double* A, const double* B
     }
     __nv_bfloat16* Bbf = S->ws.get<__nv_bfloat16>(size_t(dS) * Kt);
     cvt_operand(B, dS, dS, nj, true, false, S->sv, S->so, precision, false, Bbf, s);
-    timed(S, "rank_gemm", 2.0 * double(dS) * double(dS) * double(Kt),
+    timed(S, "rank_gemm_tc", 2.0 * double(dS) * double(dS) * double(nj),
           [&] { tc_gemm(Abf, Bbf, dS, dS, Kt, C, dS, alpha, beta, S->tc_err, false, s); });
   } else {
     const int64_t Kp = pad64(dS), Kt = seg * Kp;
@@ -611,7 +611,7 @@ void rank_gemm_lowp(mlcc_system* S, bool outer, const double* A, const double* B
     __nv_bfloat16* Bbf = S->ws.get<__nv_bfloat16>(size_t(dS) * Kt);
     cvt_operand(B, dS, dS, dS, true, false, S->sv, S->so, precision, false, Bbf, s);
     (void)b_is_u_source;
-    timed(S, "rank_gemm", 2.0 * double(nj) * double(dS) * double(Kt),
+    timed(S, "rank_gemm_tc", 2.0 * double(nj) * double(dS) * double(dS),
           [&] { tc_gemm(Abf, Bbf, nj, dS, Kt, C, dS, alpha, beta, S->tc_err, true, s); });
   }
 }

@@ -157,7 +157,7 @@ class Context:
     def kernel_timing(self, enable):
         load().mlcc_kernel_timing(self.handle, 1 if enable else 0)
 
-    def kernel_time(self, family="rank_gemm"):
+    def kernel_time(self, family="rank_gemm_tc"):
         n, ms, fl = c_int64(), c_double(), c_double()
         _check(load().mlcc_kernel_time(self.handle, family.encode(), byref(n), byref(ms), byref(fl)))
         return n.value, ms.value, fl.value
