@@ -214,6 +214,31 @@ mlcc_status mlcc_solve(mlcc_ctx* ctx, const mlcc_problem* prob, const double* ch
                        mlcc_gs_info* gs, double* omega_host, mlcc_es_info* es,
                        double* t1_host);
 
+/* ---- allocation-free variant ------------------------------------------------------ */
+/* The paper has no counterpart to this entry point; it exists for callers that cannot let
+   a library allocate device memory: a program that reserves the device memory for its own
+   pool (so cudaMalloc would fail or escape its accounting), or one that cannot accept the
+   device-wide synchronisation cudaMalloc / cudaFree may cause.
+
+   mlcc_fock_t1_noalloc computes the same quantities as mlcc_t1_transform and mlcc_fock_t1
+   (dressed Cholesky vectors Lt^J = (1 - t1) L^J (1 + t1) and the X1-basis Fock matrix
+   F~ = h~ + sum_J [2 Lt^J (sum_I Lt^J_II) - Lt^J[:, I] Lt^J[I, :]] with
+   h = F - sum_J [2 L^J (sum_I L^J_II) - L^J[:, I] L^J[I, :]]) without a system and
+   without allocating: every buffer is the caller's, in the caller's orbital order
+   (occupied first): chol_dev [n_chol][n_mo][n_mo], fock_dev and ft_dev [n_mo][n_mo],
+   t1_dev [n_mo - n_occ][n_occ], lt_dev [n_chol][n_mo][n_mo]. Work goes on `stream`
+   (a cudaStream_t, NULL for the default stream); the call does not synchronise.
+   Scratch: a static device array of 2 * MLCC_NOALLOC_MAX_CHOL doubles (512 KiB), held by
+   every device that loads the library until the process exits; n_chol above the limit
+   returns MLCC_E_ARG. The first call on a device looks up the array's address with that
+   device current (make that first call before any stream capture). All calls share the
+   array, so calls whose work overlaps on the device race; order them on one stream. */
+#define MLCC_NOALLOC_MAX_CHOL 32768
+mlcc_status mlcc_fock_t1_noalloc(int32_t n_mo, int32_t n_occ, int32_t n_chol,
+                                 const double* chol_dev, const double* fock_dev,
+                                 const double* t1_dev, double* lt_dev, double* ft_dev,
+                                 void* stream);
+
 #ifdef __cplusplus
 }
 #endif

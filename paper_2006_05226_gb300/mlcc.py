@@ -26,7 +26,8 @@ EXPORTS = ["mlcc_default_options", "mlcc_ctx_create", "mlcc_ctx_destroy", "mlcc_
            "mlcc_last_error", "mlcc_kernel_timing", "mlcc_kernel_time", "mlcc_system_create",
            "mlcc_system_destroy", "mlcc_system_info", "mlcc_orbital_order", "mlcc_t1_transform",
            "mlcc_fock_t1", "mlcc_omega", "mlcc_ground_state", "mlcc_jacobian_prepare",
-           "mlcc_sigma", "mlcc_excited_states", "mlcc_solve", "mlcc_launch_count"]
+           "mlcc_sigma", "mlcc_excited_states", "mlcc_solve", "mlcc_launch_count",
+           "mlcc_fock_t1_noalloc"]
 
 
 class mlcc_problem(ctypes.Structure):
@@ -88,6 +89,7 @@ def load():
         "mlcc_kernel_timing": (None, [P, c_int]),
         "mlcc_kernel_time": (c_int, [P, c_char_p, POINTER(c_int64), D, D]),
         "mlcc_launch_count": (c_int64, []),
+        "mlcc_fock_t1_noalloc": (c_int, [c_int32, c_int32, c_int32, P, P, P, P, P, P]),
         "mlcc_system_create": (c_int, [P, POINTER(mlcc_problem), P, P, POINTER(c_void_p)]),
         "mlcc_system_destroy": (None, [P]),
         "mlcc_system_info": (c_int, [P, POINTER(mlcc_dims)]),
@@ -118,6 +120,15 @@ def _check(status):
 def launch_count():
     """Kernels libmlcc has launched in this process."""
     return int(load().mlcc_launch_count())
+
+
+def fock_t1_noalloc(chol, fock, n_occ, t1, lt_out, ft_out, stream=None):
+    """mlcc_fock_t1_noalloc on caller-owned device tensors (caller orbital order); the
+    library allocates nothing. stream: a torch CUDA stream (default: the current one)."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(load().mlcc_fock_t1_noalloc(fock.shape[0], n_occ, chol.shape[0], _ptr(chol), _ptr(fock),
+                                       _ptr(t1), _ptr(lt_out), _ptr(ft_out), c_void_p(st.cuda_stream)))
 
 
 def default_options(**kw):
