@@ -242,14 +242,15 @@ def main():
         step()
     torch.cuda.synchronize()
     barrier(world)
+    profile_range = os.environ.get("MLCC_PROFILE_TIMED", "0") not in ("", "0")
     clocks = ClockSampler(local)
-    clocks.start()
+    if not profile_range:   # nvidia-smi polling next to an ncu capture made ncu fail
+        clocks.start()
     ctx.kernel_timing(True)
     launches0 = mlcc.launch_count()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    profile_range = os.environ.get("MLCC_PROFILE_TIMED", "0") not in ("", "0")
     if profile_range:   # ncu --profile-from-start off captures exactly the timed steps
         torch.cuda.cudart().cudaProfilerStart()
     ev0.record(ctx.stream)

@@ -3,6 +3,7 @@
 #include "internal.cuh"
 
 #include <cuda_bf16.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace mlcc {
 
@@ -97,6 +98,11 @@ void check_tc_error(mlcc_system* S);
 template <class F>
 void timed(mlcc_system* S, const char* fam, double flop, F&& f) {
   auto& T = S->ctx->timer;
+  // NVTX range named after the kernel family (profilers can filter on it)
+  struct Range {
+    explicit Range(const char* n) { nvtxRangePushA(n); }
+    ~Range() { nvtxRangePop(); }
+  } range(fam);
   if (!T.enabled) {
     f();
     return;
