@@ -163,6 +163,9 @@ void axpby(double* y, const double* x, int64_t n, double a, double b, cudaStream
 // Deterministic dot products: out_dev[k] = sum_i x_k[i] y[i] for k < nx (x_k at x + k*ldx).
 void dots(const double* x, int64_t ldx, int nx, const double* y, int64_t n, double* out_dev,
           Arena& ws, cudaStream_t s);
+// out_dev[k * ny + j] = x_k . y_j for k < nx, j < ny (ny <= 4): one pass over each x_k
+void dots_block(const double* x, int64_t ldx, int nx, const double* y, int64_t ldy, int ny,
+                int64_t n, double* out_dev, Arena& ws, cudaStream_t s);
 void copy_d2h(double* h, const double* d, int64_t n, cudaStream_t s);
 void copy_h2d(double* d, const double* h, int64_t n, cudaStream_t s);
 

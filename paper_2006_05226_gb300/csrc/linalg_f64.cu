@@ -221,16 +221,44 @@ __global__ void k_reduce_partials(const double* partial, int nsplit, int64_t M, 
 template <int MM, bool TA, bool TB>
 __global__ void k_skinny_m(GP p) {
   if (!TB) {
+    // the small operand A (M x K, K <= 64 here) is staged in shared memory once per block
+    __shared__ double As[MM * 64];
+    const bool staged = p.K <= 64;
+    if (staged) {
+      for (int t = threadIdx.x; t < MM * 64; t += blockDim.x) {
+        const int m = t / 64, k = t - m * 64;
+        As[t] = (m < p.M && k < p.K) ? (TA ? p.A[int64_t(k) * p.lda + m] : p.A[int64_t(m) * p.lda + k]) : 0.0;
+      }
+      __syncthreads();
+    }
     const int64_t n = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (n >= p.N) return;
     double acc[MM];
 #pragma unroll
     for (int m = 0; m < MM; ++m) acc[m] = 0.0;
-    for (int64_t k = 0; k < p.K; ++k) {
-      const double b = p.B[k * p.ldb + n];
+    if (staged) {
+      int64_t k = 0;
+      for (; k + 4 <= p.K; k += 4) {
+        const double b0 = p.B[k * p.ldb + n], b1 = p.B[(k + 1) * p.ldb + n];
+        const double b2 = p.B[(k + 2) * p.ldb + n], b3 = p.B[(k + 3) * p.ldb + n];
 #pragma unroll
-      for (int m = 0; m < MM; ++m)
-        if (m < p.M) acc[m] = fma(TA ? p.A[k * p.lda + m] : p.A[m * p.lda + k], b, acc[m]);
+        for (int m = 0; m < MM; ++m) {
+          const double* a = As + m * 64 + k;
+          acc[m] = fma(a[0], b0, fma(a[1], b1, fma(a[2], b2, fma(a[3], b3, acc[m]))));
+        }
+      }
+      for (; k < p.K; ++k) {
+        const double b = p.B[k * p.ldb + n];
+#pragma unroll
+        for (int m = 0; m < MM; ++m) acc[m] = fma(As[m * 64 + k], b, acc[m]);
+      }
+    } else {
+      for (int64_t k = 0; k < p.K; ++k) {
+        const double b = p.B[k * p.ldb + n];
+#pragma unroll
+        for (int m = 0; m < MM; ++m)
+          if (m < p.M) acc[m] = fma(TA ? p.A[k * p.lda + m] : p.A[m * p.lda + k], b, acc[m]);
+      }
     }
 #pragma unroll
     for (int m = 0; m < MM; ++m)
@@ -636,26 +664,86 @@ __global__ void k_axpby(double* y, const double* x, int64_t n, double a, double 
     y[i] = (b == 0.0) ? a * x[i] : a * x[i] + b * y[i];
 }
 constexpr int DOT_BLOCKS = 512;
-// partial[k][blk] = sum over the block's grid-stride share of x_k * y
+constexpr int DOT_CHUNK = 8;
+// partial[k][blk] = sum over the block's grid-stride share of x_k * y; each pass over y
+// serves DOT_CHUNK vectors x_k (one read of y per chunk)
 __global__ void k_dots_stage1(const double* x, int64_t ldx, int nx, const double* y, int64_t n,
                               double* partial) {
-  __shared__ double red[256];
-  for (int k = 0; k < nx; ++k) {
-    const double* xk = x + int64_t(k) * ldx;
-    double s = 0.0;
+  __shared__ double red[DOT_CHUNK][256 / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k0 = 0; k0 < nx; k0 += DOT_CHUNK) {
+    const int kc = min(DOT_CHUNK, nx - k0);
+    double acc[DOT_CHUNK];
+#pragma unroll
+    for (int c = 0; c < DOT_CHUNK; ++c) acc[c] = 0.0;
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
-         i += int64_t(gridDim.x) * blockDim.x)
-      s = fma(xk[i], y[i], s);
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-      if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-      __syncthreads();
+         i += int64_t(gridDim.x) * blockDim.x) {
+      const double yi = y[i];
+#pragma unroll
+      for (int c = 0; c < DOT_CHUNK; ++c)
+        if (c < kc) acc[c] = fma(x[int64_t(k0 + c) * ldx + i], yi, acc[c]);
     }
-    if (threadIdx.x == 0) partial[int64_t(k) * gridDim.x + blockIdx.x] = red[0];
+#pragma unroll
+    for (int c = 0; c < DOT_CHUNK; ++c) {
+      double v = acc[c];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[c][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kc) {
+      double v = 0.0;
+      for (int w = 0; w < int(blockDim.x / 32); ++w) v += red[threadIdx.x][w];
+      partial[int64_t(k0 + threadIdx.x) * gridDim.x + blockIdx.x] = v;
+    }
     __syncthreads();
   }
 }
+// partial[(k * ny + j)][blk] for DOT_CHUNK x-vectors per pass and NY <= 4 y-vectors
+template <int NY>
+__global__ void k_dots_block1(const double* x, int64_t ldx, int nx, const double* y, int64_t ldy,
+                              int64_t n, double* partial) {
+  __shared__ double red[DOT_CHUNK * NY][256 / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k0 = 0; k0 < nx; k0 += DOT_CHUNK) {
+    const int kc = min(DOT_CHUNK, nx - k0);
+    double acc[DOT_CHUNK][NY];
+#pragma unroll
+    for (int c = 0; c < DOT_CHUNK; ++c)
+#pragma unroll
+      for (int j = 0; j < NY; ++j) acc[c][j] = 0.0;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x) {
+      double yv[NY];
+#pragma unroll
+      for (int j = 0; j < NY; ++j) yv[j] = y[int64_t(j) * ldy + i];
+#pragma unroll
+      for (int c = 0; c < DOT_CHUNK; ++c) {
+        if (c < kc) {
+          const double xv = x[int64_t(k0 + c) * ldx + i];
+#pragma unroll
+          for (int j = 0; j < NY; ++j) acc[c][j] = fma(xv, yv[j], acc[c][j]);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < DOT_CHUNK; ++c)
+#pragma unroll
+      for (int j = 0; j < NY; ++j) {
+        double v = acc[c][j];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[c * NY + j][warp] = v;
+      }
+    __syncthreads();
+    if (threadIdx.x < kc * NY) {
+      double v = 0.0;
+      for (int w = 0; w < int(blockDim.x / 32); ++w) v += red[threadIdx.x][w];
+      const int c = threadIdx.x / NY, j = threadIdx.x - c * NY;
+      partial[int64_t((k0 + c) * NY + j) * gridDim.x + blockIdx.x] = v;
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void k_dots_stage2(const double* partial, int nblk, double* out) {
   __shared__ double red[256];
   const int k = blockIdx.x;
@@ -695,6 +783,25 @@ void dots(const double* x, int64_t ldx, int nx, const double* y, int64_t n, doub
   k_dots_stage2<<<nx, 256, 0, s>>>(partial, blocks, out_dev);
   MLCC_CHECK_LAUNCH();
 }
+void dots_block(const double* x, int64_t ldx, int nx, const double* y, int64_t ldy, int ny,
+                int64_t n, double* out_dev, Arena& ws, cudaStream_t s) {
+  if (nx <= 0 || ny <= 0) return;
+  MLCC_REQUIRE(ny <= 4, "dots_block: at most 4 y-vectors");
+  Scope sc(ws);
+  int blocks = int(std::min<int64_t>((n + 255) / 256, DOT_BLOCKS));
+  blocks = std::max(blocks, 1);
+  double* partial = ws.get<double>(size_t(nx) * ny * blocks);
+  switch (ny) {
+    case 1: k_dots_block1<1><<<blocks, 256, 0, s>>>(x, ldx, nx, y, ldy, n, partial); break;
+    case 2: k_dots_block1<2><<<blocks, 256, 0, s>>>(x, ldx, nx, y, ldy, n, partial); break;
+    case 3: k_dots_block1<3><<<blocks, 256, 0, s>>>(x, ldx, nx, y, ldy, n, partial); break;
+    default: k_dots_block1<4><<<blocks, 256, 0, s>>>(x, ldx, nx, y, ldy, n, partial); break;
+  }
+  MLCC_CHECK_LAUNCH();
+  k_dots_stage2<<<nx * ny, 256, 0, s>>>(partial, blocks, out_dev);
+  MLCC_CHECK_LAUNCH();
+}
+
 void copy_d2h(double* h, const double* d, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
   MLCC_CUDA(cudaMemcpyAsync(h, d, size_t(n) * 8, cudaMemcpyDeviceToHost, s));

@@ -87,31 +87,57 @@ __global__ void k_scale(double* x, int64_t n, double a) {
     x[i] *= a;
 }
 __global__ void k_set(double* x, int64_t i, double v) { x[i] = v; }
-// index of the largest |x| (first on ties), deterministic two-level reduction in one block
-__global__ void k_argmax_abs(const double* x, int64_t n, double* out_val) {
-  __shared__ double bv[256];
-  __shared__ long long bi[256];
-  double best = -1.0;
-  long long bidx = 0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const double a = fabs(x[i]);
-    if (a > best) { best = a; bidx = i; }
-  }
-  bv[threadIdx.x] = best;
-  bi[threadIdx.x] = bidx;
+// largest |x| with its index (first on ties): per-block candidates, then one block
+__device__ __forceinline__ void better(double& bv, long long& bi, double v, long long i) {
+  if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+}
+__global__ void k_argmax_stage1(const double* x, int64_t n, double* pv, long long* pi) {
+  __shared__ double sv[256];
+  __shared__ long long si[256];
+  double bv = -1.0;
+  long long bi = 0;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x)
+    better(bv, bi, fabs(x[i]), i);
+  sv[threadIdx.x] = bv;
+  si[threadIdx.x] = bi;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
     if (threadIdx.x < w) {
-      const double o = bv[threadIdx.x + w];
-      const long long oi = bi[threadIdx.x + w];
-      if (o > bv[threadIdx.x] || (o == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
-        bv[threadIdx.x] = o;
-        bi[threadIdx.x] = oi;
-      }
+      double v = sv[threadIdx.x];
+      long long ii = si[threadIdx.x];
+      better(v, ii, sv[threadIdx.x + w], si[threadIdx.x + w]);
+      sv[threadIdx.x] = v;
+      si[threadIdx.x] = ii;
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) out_val[0] = x[bi[0]];
+  if (threadIdx.x == 0) {
+    pv[blockIdx.x] = sv[0];
+    pi[blockIdx.x] = si[0];
+  }
+}
+__global__ void k_argmax_stage2(const double* x, const double* pv, const long long* pi, int nb,
+                                double* out_val) {
+  __shared__ double sv[256];
+  __shared__ long long si[256];
+  double bv = -1.0;
+  long long bi = 0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) better(bv, bi, pv[b], pi[b]);
+  sv[threadIdx.x] = bv;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      double v = sv[threadIdx.x];
+      long long ii = si[threadIdx.x];
+      better(v, ii, sv[threadIdx.x + w], si[threadIdx.x + w]);
+      sv[threadIdx.x] = v;
+      si[threadIdx.x] = ii;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out_val[0] = x[si[0]];
 }
 }  // namespace
 
@@ -293,42 +319,68 @@ static void sigma_batch(mlcc_system* S, const double* C, double* Sg, int nvec, i
   if (prec != MLCC_FP64) check_tc_error(S);
 }
 
-// add the new columns [m0, m) to G
+// add the new columns [m0, m) to G: G[i][k] = B_i . S_k and G[k][j] = B_k . S_j, with the
+// basis read once per block of up to four new vectors
 static void update_G(DavState& D, int m0) {
   mlcc_system* S = D.S;
   cudaStream_t s = S->ctx->stream;
   Scope sc(S->ws);
-  double* out = S->ws.get<double>(D.maxsub);
-  std::vector<double> h(D.maxsub);
-  for (int k = m0; k < D.m; ++k) {
-    // G[i][k] = B_i . S_k for i < m
-    dots(D.B, D.dim, D.m, D.Sg + int64_t(k) * D.dim, D.dim, out, S->ws, s);
-    copy_d2h(h.data(), out, D.m, s);
-    for (int i = 0; i < D.m; ++i) D.G[size_t(i) * D.maxsub + k] = h[i];
-    // G[k][j] = B_k . S_j for j < m0
+  double* out = S->ws.get<double>(size_t(D.maxsub) * 4);
+  std::vector<double> h(size_t(D.maxsub) * 4);
+  for (int k0 = m0; k0 < D.m; k0 += 4) {
+    const int nk = std::min(4, D.m - k0);
+    // B_i . S_k for i < m
+    dots_block(D.B, D.dim, D.m, D.Sg + int64_t(k0) * D.dim, D.dim, nk, D.dim, out, S->ws, s);
+    copy_d2h(h.data(), out, int64_t(D.m) * nk, s);
+    for (int i = 0; i < D.m; ++i)
+      for (int j = 0; j < nk; ++j) D.G[size_t(i) * D.maxsub + k0 + j] = h[size_t(i) * nk + j];
+    // B_k . S_j for j < m0
     if (m0 > 0) {
-      dots(D.Sg, D.dim, m0, D.B + int64_t(k) * D.dim, D.dim, out, S->ws, s);
-      copy_d2h(h.data(), out, m0, s);
-      for (int j = 0; j < m0; ++j) D.G[size_t(k) * D.maxsub + j] = h[j];
+      dots_block(D.Sg, D.dim, m0, D.B + int64_t(k0) * D.dim, D.dim, nk, D.dim, out, S->ws, s);
+      copy_d2h(h.data(), out, int64_t(m0) * nk, s);
+      for (int j = 0; j < m0; ++j)
+        for (int q = 0; q < nk; ++q) D.G[size_t(k0 + q) * D.maxsub + j] = h[size_t(j) * nk + q];
     }
   }
 }
 
-// orthonormalise v against B[0..m) (two passes); returns false if v collapses
-static bool orthonormalise(DavState& D, double* v) {
+// orthogonalise the block V = B[m .. m+nv) against B[0..m): two passes of
+// V -= B (B^T V), reading the basis once per pass
+static void block_project(DavState& D, int nv) {
+  mlcc_system* S = D.S;
+  cudaStream_t s = S->ctx->stream;
+  if (D.m == 0 || nv == 0) return;
+  Scope sc(S->ws);
+  double* coef = S->ws.get<double>(size_t(D.m) * 4);
+  double* V = D.B + int64_t(D.m) * D.dim;
+  for (int pass = 0; pass < 2; ++pass) {
+    dots_block(D.B, D.dim, D.m, V, D.dim, nv, D.dim, coef, S->ws, s);   // coef[k][j]
+    Gemm g;  // V_j -= sum_k coef[k][j] B_k : C [nv][dim] = -A^T B with A = coef [m][nv]
+    g.ta = true;
+    g.M = nv; g.N = D.dim; g.K = D.m;
+    g.A = coef; g.lda = nv; g.B = D.B; g.ldb = D.dim; g.C = V; g.ldc = D.dim;
+    g.alpha = -1.0; g.beta = 1.0;
+    gemm_f64(g, S->ws, s, S->ctx->sm_count);
+  }
+}
+
+// orthonormalise v against B[from..m) (two passes); returns false if v collapses
+static bool orthonormalise(DavState& D, double* v, int from = 0) {
   mlcc_system* S = D.S;
   cudaStream_t s = S->ctx->stream;
   Scope sc(S->ws);
-  double* coef = S->ws.get<double>(std::max(D.m, 1));
+  const int cnt = D.m - from;
+  double* coef = S->ws.get<double>(std::max(cnt, 1));
   double* nr = S->ws.get<double>(1);
   dots(v, 0, 1, v, D.dim, nr, S->ws, s);
   const double n0 = std::sqrt(host_scalar(S, nr));
   if (!(n0 > 0.0) || !std::isfinite(n0)) return false;
-  for (int pass = 0; pass < 2 && D.m > 0; ++pass) {
-    dots(D.B, D.dim, D.m, v, D.dim, coef, S->ws, s);
+  const double* Bf = D.B + int64_t(from) * D.dim;
+  for (int pass = 0; pass < 2 && cnt > 0; ++pass) {
+    dots(Bf, D.dim, cnt, v, D.dim, coef, S->ws, s);
     Gemm g;
-    g.M = 1; g.N = D.dim; g.K = D.m;
-    g.A = coef; g.lda = D.m; g.B = D.B; g.ldb = D.dim; g.C = v; g.ldc = D.dim;
+    g.M = 1; g.N = D.dim; g.K = cnt;
+    g.A = coef; g.lda = cnt; g.B = Bf; g.ldb = D.dim; g.C = v; g.ldc = D.dim;
     g.alpha = -1.0; g.beta = 1.0;
     gemm_f64(g, S->ws, s, S->ctx->sm_count);
   }
@@ -546,9 +598,10 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
       update_G(D, 0);
     }
     const int m0 = D.m;
+    int nnew = 0;
     for (int k : todo) {
-      if (D.m >= maxsub) break;
-      double* v = D.B + int64_t(D.m) * dim;
+      if (D.m + nnew >= maxsub || nnew == 4) break;
+      double* v = D.B + int64_t(D.m + nnew) * dim;
       k_precond_singles<<<nblk(n1), 256, 0, s>>>(R + int64_t(k) * dim, S->eps, no, nv, w[k], v);
       MLCC_CHECK_LAUNCH();
       if (S->nd) {
@@ -557,7 +610,18 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
                                               w[k], v + n1);
         MLCC_CHECK_LAUNCH();
       }
-      if (orthonormalise(D, v)) ++D.m;
+      ++nnew;
+    }
+    // the old basis is projected out of the whole block first; the vectors of the block are
+    // then orthonormalised one by one (against the basis and the accepted block members)
+    block_project(D, nnew);
+    for (int q = 0; q < nnew; ++q) {
+      double* v = D.B + int64_t(D.m) * dim;
+      if (D.m != m0 + q) {
+        MLCC_CUDA(cudaMemcpyAsync(v, D.B + int64_t(m0 + q) * dim, size_t(dim) * 8,
+                                  cudaMemcpyDeviceToDevice, s));
+      }
+      if (orthonormalise(D, v, m0)) ++D.m;   // the old basis was projected out above
     }
     if (D.m == m0) {
       // no new direction: the basis spans an invariant subspace
@@ -575,7 +639,12 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
     Scope sc4(S->ws);
     double* mv = S->ws.get<double>(1);
     for (int k = 0; k < nr; ++k) {
-      k_argmax_abs<<<1, 256, 0, s>>>(X + int64_t(k) * dim, dim, mv);
+      const int nb = int(std::min<int64_t>((dim + 255) / 256, 1024));
+      double* pv = S->ws.get<double>(size_t(nb));
+      long long* pi = S->ws.get<long long>(size_t(nb));
+      k_argmax_stage1<<<nb, 256, 0, s>>>(X + int64_t(k) * dim, dim, pv, pi);
+      MLCC_CHECK_LAUNCH();
+      k_argmax_stage2<<<1, 256, 0, s>>>(X + int64_t(k) * dim, pv, pi, nb, mv);
       MLCC_CHECK_LAUNCH();
       if (host_scalar(S, mv) < 0.0) {
         k_scale<<<nblk(dim), 256, 0, s>>>(X + int64_t(k) * dim, dim, -1.0);
