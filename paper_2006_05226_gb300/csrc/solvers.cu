@@ -365,7 +365,8 @@ static void block_project(DavState& D, int nv) {
 }
 
 // orthonormalise v against B[from..m) (two passes); returns false if v collapses
-static bool orthonormalise(DavState& D, double* v, int from = 0) {
+// ref_norm > 0: the norm of v before an earlier projection, for the drop test
+static bool orthonormalise(DavState& D, double* v, int from = 0, double ref_norm = 0.0) {
   mlcc_system* S = D.S;
   cudaStream_t s = S->ctx->stream;
   Scope sc(S->ws);
@@ -373,7 +374,7 @@ static bool orthonormalise(DavState& D, double* v, int from = 0) {
   double* coef = S->ws.get<double>(std::max(cnt, 1));
   double* nr = S->ws.get<double>(1);
   dots(v, 0, 1, v, D.dim, nr, S->ws, s);
-  const double n0 = std::sqrt(host_scalar(S, nr));
+  const double n0 = ref_norm > 0.0 ? ref_norm : std::sqrt(host_scalar(S, nr));
   if (!(n0 > 0.0) || !std::isfinite(n0)) return false;
   const double* Bf = D.B + int64_t(from) * D.dim;
   for (int pass = 0; pass < 2 && cnt > 0; ++pass) {
@@ -613,7 +614,17 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
       ++nnew;
     }
     // the old basis is projected out of the whole block first; the vectors of the block are
-    // then orthonormalised one by one (against the basis and the accepted block members)
+    // then orthonormalised one by one (against the basis and the accepted block members),
+    // dropped when less than 1e-10 of their norm before the projection remains
+    std::vector<double> pre(nnew, 0.0);
+    {
+      Scope sp(S->ws);
+      double* nrm = S->ws.get<double>(4);
+      for (int q = 0; q < nnew; ++q) dots(D.B + int64_t(D.m + q) * dim, 0, 1, D.B + int64_t(D.m + q) * dim, dim, nrm + q, S->ws, s);
+      double hn[4] = {0, 0, 0, 0};
+      if (nnew) copy_d2h(hn, nrm, nnew, s);
+      for (int q = 0; q < nnew; ++q) pre[q] = std::sqrt(hn[q]);
+    }
     block_project(D, nnew);
     for (int q = 0; q < nnew; ++q) {
       double* v = D.B + int64_t(D.m) * dim;
@@ -621,7 +632,7 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
         MLCC_CUDA(cudaMemcpyAsync(v, D.B + int64_t(m0 + q) * dim, size_t(dim) * 8,
                                   cudaMemcpyDeviceToDevice, s));
       }
-      if (orthonormalise(D, v, m0)) ++D.m;   // the old basis was projected out above
+      if (pre[q] > 0.0 && std::isfinite(pre[q]) && orthonormalise(D, v, m0, pre[q])) ++D.m;
     }
     if (D.m == m0) {
       // no new direction: the basis spans an invariant subspace
