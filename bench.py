@@ -12,7 +12,8 @@ Workload: 340 orbitals (40 occupied, 300 virtual), 1500 Cholesky vectors, CCSD-a
 10 occupied / 60 virtual, CC2-active the rest, 4 roots (the second configuration of the
 paper-shaped workloads); synthetic seeded inputs (synth/), larger than L2 (L is 1.39 GB).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|bf16] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|bf16|bf16x3|bf16x6|fp64e]
+                  [--refine fp64|fp64e] [--impl ours|reference]
 """
 import argparse
 import json
@@ -196,7 +197,9 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default="bf16x3", choices=["fp64", "bf16", "bf16x3", "bf16x6"])
+    ap.add_argument("--precision", default="bf16x3", choices=["fp64", "bf16", "bf16x3", "bf16x6", "fp64e"])
+    ap.add_argument("--refine", default="fp64e", choices=["fp64", "fp64e"],
+                    help="precision of the ground-state polish and the Davidson refinement sweep")
     ap.add_argument("--no-fp64-check", action="store_true",
                     help="skip the plain binary64 reference solve used to report the error")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -219,14 +222,16 @@ def main():
 
     spec = replace(CONFIGS[WORKLOAD], seed=CONFIGS[WORKLOAD].seed + rank)
     system = make_system(spec)
-    prec = {"fp64": mlcc.MLCC_FP64, "bf16": mlcc.MLCC_BF16, "bf16x3": mlcc.MLCC_BF16X3,
-            "bf16x6": mlcc.MLCC_BF16X6}[args.precision]
-    # mixed path: split-bf16 ground state polished in binary64 to 1e-9, split-bf16 Davidson
-    # to a 1e-5 residual, then one binary64 Rayleigh-Ritz sweep on its Ritz vectors
+    precs = {"fp64": mlcc.MLCC_FP64, "bf16": mlcc.MLCC_BF16, "bf16x3": mlcc.MLCC_BF16X3,
+             "bf16x6": mlcc.MLCC_BF16X6, "fp64e": mlcc.MLCC_FP64E}
+    prec, refine = precs[args.precision], precs[args.refine]
+    split = prec in (mlcc.MLCC_BF16, mlcc.MLCC_BF16X3, mlcc.MLCC_BF16X6)
+    # mixed path: split-bf16 ground state polished in binary64 (refine precision) to 1e-9,
+    # split-bf16 Davidson to a 1e-5 residual, then one refinement Rayleigh-Ritz sweep
     opts = mlcc.default_options(n_roots=spec.n_roots, precision=prec, gs_precision=prec,
-                                refine_fp64=1, lowp_res_tol=1e-5,
-                                gs_tol=1e-9 if prec != mlcc.MLCC_FP64 else 1e-11,
-                                gs_energy_tol=1e-10 if prec != mlcc.MLCC_FP64 else 1e-12)
+                                refine_fp64=1, lowp_res_tol=1e-5, refine_precision=refine,
+                                gs_tol=1e-9 if split else 1e-11,
+                                gs_energy_tol=1e-10 if split else 1e-12)
     ctx = mlcc.Context(local)
     L_dev = torch.as_tensor(system.L, device=f"cuda:{local}")
     F_dev = torch.as_tensor(system.fock, device=f"cuda:{local}")
@@ -266,9 +271,10 @@ def main():
         torch.cuda.cudart().cudaProfilerStop()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     launches = mlcc.launch_count() - launches0
-    fam = "rank_gemm_f64" if prec == mlcc.MLCC_FP64 else "rank_gemm_tc"
-    k_n, k_ms, k_flop = ctx.kernel_time(fam)
-    f64_n, f64_ms, f64_flop = ctx.kernel_time("rank_gemm_f64")
+    fams = {f: ctx.kernel_time(f) for f in ("rank_gemm_tc", "rank_gemm_f64e", "rank_gemm_f64")}
+    phases = {f: ctx.kernel_time(f) for f in ("gs_omega", "jacobian_prepare", "sigma", "dav_update_G",
+                                              "dav_ritz", "dav_orthonormalise")}
+    breakdown = {f: {"calls": n, "total_ms": ms} for f, (n, ms, _) in phases.items() if n}
     ctx.kernel_timing(False)
     clk = clocks.stop()
     barrier(world)
@@ -303,39 +309,54 @@ def main():
     if rank != 0:
         return 0
     pk, src = peaks()
-    if prec == mlcc.MLCC_FP64:
-        ach = k_flop / (k_ms / 1e3) / 1e12 if k_ms > 0 else None
-        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": (ach / FP64_PEAK_TFLOPS) if ach else None, "traffic": None,
-                "kernel": "rank_gemm (binary64 DFMA tiles)",
-                "peak_source": "FP64 DFMA rate from unit counts and clock"}
-    else:
-        ach = k_flop / (k_ms / 1e3) / 1e12 if k_ms > 0 else None
-        peak = pk.get("bf16_tflops_sustained", FALLBACK["bf16_tflops_sustained"])
-        pieces = {mlcc.MLCC_BF16: 1, mlcc.MLCC_BF16X3: 3, mlcc.MLCC_BF16X6: 6}[prec]
-        roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": (ach / peak) if ach else None, "traffic": None,
-                "kernel": "k_tc_gemm: Cholesky-rank doubles GEMMs (tcgen05, bf16 pieces, fp32 accumulate)",
-                "achieved_is": "algorithmic 2MNK flops of the contraction per launch / launch time",
-                "tensor_ops_per_algorithmic_flop": pieces,
-                "tensor_issue_tflops": (ach * pieces) if ach else None,
-                "peak_source": f"bf16 dense sustained, of {src}"}
-    roof["launches"] = k_n
-    roof["avg_launch_ms"] = (k_ms / k_n) if k_n else None
-    roof["flop_per_launch"] = (k_flop / k_n) if k_n else None
-    if prec != mlcc.MLCC_FP64:
-        roof["fp64_rank_gemm"] = {"launches": f64_n, "total_ms": f64_ms,
-                                  "tflops": (f64_flop / f64_ms / 1e9) if f64_ms else None}
+    bf16_peak = pk.get("bf16_tflops_sustained", FALLBACK["bf16_tflops_sustained"])
+    pieces = {mlcc.MLCC_BF16: 1, mlcc.MLCC_BF16X3: 3, mlcc.MLCC_BF16X6: 6}
+    # tensor-core products per algorithmic flop: split-bf16 pieces, or the 28 digit
+    # products of the binary64 emulation
+    ops = {"rank_gemm_tc": pieces.get(prec, 3), "rank_gemm_f64e": 28, "rank_gemm_f64": None}
+    kernels = {"rank_gemm_tc": "k_tc_gemm: Cholesky-rank doubles GEMMs, split bf16 (tcgen05, fp32 accumulate)",
+               "rank_gemm_f64e": "k_tc_gemm (emulation mode) + k_emu_reduce: Cholesky-rank GEMMs "
+                                 "in binary64 from exact bf16 integer digits",
+               "rank_gemm_f64": "k_dgemm: Cholesky-rank GEMMs on the binary64 FMA units"}
+    families = {}
+    for f, (n, ms, fl) in fams.items():
+        if n == 0:
+            continue
+        ach = fl / (ms / 1e3) / 1e12 if ms > 0 else None
+        families[f] = {"launches": n, "total_ms": ms, "avg_launch_ms": ms / n, "flop_per_launch": fl / n,
+                       "algorithmic_tflops": ach}
+    dom = max(families, key=lambda f: families[f]["total_ms"]) if families else None
+    roof = None
+    if dom is not None:
+        d = families[dom]
+        if ops[dom] is None:
+            roof = {"bound": "alu", "achieved": d["algorithmic_tflops"], "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": d["algorithmic_tflops"] / FP64_PEAK_TFLOPS,
+                    "peak_source": "FP64 DFMA rate from unit counts and clock (152 SMs x 2 FMA/clk x 2.07 GHz)"}
+        else:
+            peak = bf16_peak / ops[dom]
+            roof = {"bound": "tensor", "achieved": d["algorithmic_tflops"], "peak": peak, "unit": "TFLOP/s",
+                    "frac": d["algorithmic_tflops"] / peak,
+                    "tensor_ops_per_algorithmic_flop": ops[dom],
+                    "tensor_issue_tflops": d["algorithmic_tflops"] * ops[dom],
+                    "peak_source": f"bf16 dense sustained ({bf16_peak} TFLOP/s, of {src}) / "
+                                   f"{ops[dom]} bf16 products per algorithmic product"}
+        roof.update({"traffic": None, "kernel": kernels[dom], "family": dom,
+                     "achieved_is": "algorithmic 2MNK flops of the contraction per launch / launch time "
+                                    "(CUDA events on the library stream)",
+                     "launches": d["launches"], "avg_launch_ms": d["avg_launch_ms"],
+                     "flop_per_launch": d["flop_per_launch"], "families": families})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if prec == mlcc.MLCC_FP64 else f"{args.precision}+f64",
-            "data": "synthetic", "config": config_dict(args, args.precision),
+            "dtype": args.precision if not split else f"{args.precision}+{args.refine}",
+            "data": "synthetic", "config": config_dict(args, args.precision if not split else f"{args.precision}+{args.refine}"),
             "solves_per_s": args.steps * world / t_max, "sigma_per_step": n_sigma / args.steps,
             "sigma_lowp_per_step": n_lowp / args.steps,
             "omega": [float(x) for x in omegas], "e_corr": gs.e_corr,
             "max_abs_omega_err_vs_fp64_gpu_Ha": err_fp64,
-            "roofline": roof, "clocks": clk, "gpu_launches": int(launches), "e2e": e2e}
+            "roofline": roof, "clocks": clk, "gpu_launches": int(launches), "e2e": e2e,
+            "breakdown": breakdown}
     if world == 1 and not args.no_cpu_baseline:
         set_blas_threads()
         v, cores, desc, dt = cpu_sample_oracle(system)

@@ -72,7 +72,16 @@ typedef enum {
                        cores, bfloat16 operands, fp32 accumulation; the rest binary64  */
   MLCC_BF16X3 = 2,  /* as MLCC_BF16 with operands split x = x0 + x1 (bfloat16 pieces)
                        and the products x0y0 + x0y1 + x1y0                             */
-  MLCC_BF16X6 = 3   /* three pieces x0 + x1 + x2 and the six products of order <= 2   */
+  MLCC_BF16X6 = 3,  /* three pieces x0 + x1 + x2 and the six products of order <= 2   */
+  MLCC_FP64E = 4    /* binary64 results from the tcgen05 tensor cores: every large GEMM
+                       splits each operand row, scaled by a power of two, into 7 signed
+                       base-2^8 integer digits (exact in bfloat16), sums the 28 digit
+                       products of weight >= 2^-48 of the leading one in fp32 chunks of at
+                       most 1024 products (exact integers), combines the chunks in 64-bit
+                       integers and rounds once to binary64. Error per product about
+                       2^-53 |max row of A| |max column of B|; a row of A or column of B
+                       holding NaN or Inf gives NaN in its output row or column. Small
+                       GEMMs and all element-wise work stay binary64                    */
 } mlcc_precision;
 
 typedef enum { MLCC_LEVEL_CCS = 0, MLCC_LEVEL_CC2 = 1, MLCC_LEVEL_CCSD = 2 } mlcc_level;
@@ -105,11 +114,12 @@ typedef struct {
   int32_t diis_dim;       /* DIIS history length                                      */
   int32_t max_subspace;   /* Davidson basis size before collapse (0: 8 n_roots)       */
   int32_t precision;      /* mlcc_precision of sigma inside the Davidson loop          */
-  int32_t refine_fp64;    /* with a low precision: binary64 iterations after the
-                             low-precision phase. Ground state: if > 0, binary64 until
-                             gs_tol. Davidson: at most refine_fp64 binary64 iterations
-                             (1 = one Rayleigh-Ritz sweep with binary64 sigma on the
-                             low-precision Ritz vectors), fewer if es_res_tol is met    */
+  int32_t refine_fp64;    /* with a split-bfloat16 precision: refinement iterations in
+                             refine_precision after the low-precision phase. Ground
+                             state: if > 0, refine until gs_tol. Davidson: at most
+                             refine_fp64 refinement iterations (1 = one Rayleigh-Ritz
+                             sweep with refine_precision sigma on the low-precision
+                             Ritz vectors), fewer if es_res_tol is met                  */
   int32_t gs_precision;   /* mlcc_precision of the ground-state iterations; the low-
                              precision phase ends when |Omega| < 1e-7 or stops halving
                              over three iterations                                     */
@@ -118,6 +128,10 @@ typedef struct {
   double es_res_tol;      /* |A R - w R|_2 threshold per root                          */
   double es_omega_tol;    /* |dw| threshold per root                                   */
   double lowp_res_tol;    /* residual threshold of the low-precision phase            */
+  int32_t refine_precision; /* precision of the refinement after a low-precision phase
+                             (ground-state polish and Davidson sweeps): MLCC_FP64 or
+                             MLCC_FP64E                                                 */
+  int32_t reserved;       /* zero                                                     */
 } mlcc_options;
 
 typedef struct {
@@ -140,7 +154,8 @@ typedef struct {
 
 /* ---- context ------------------------------------------------------------------ */
 /* Defaults: 3 roots, 200 GS / 200 ES iterations, DIIS 8, FP64, gs_tol 1e-11,
-   gs_energy_tol 1e-12, es_res_tol 1e-8, es_omega_tol 1e-11, lowp_res_tol 1e-4. */
+   gs_energy_tol 1e-12, es_res_tol 1e-8, es_omega_tol 1e-11, lowp_res_tol 1e-4,
+   refine_precision FP64. */
 void mlcc_default_options(mlcc_options* opt);
 /* Creates a context on CUDA device `device` with its own non-blocking stream. */
 mlcc_status mlcc_ctx_create(int device, mlcc_ctx** out);
@@ -150,7 +165,12 @@ void* mlcc_ctx_stream(mlcc_ctx* ctx);
 const char* mlcc_last_error(void);
 /* Kernel timing: when enabled, the library records CUDA events around each launch of
    a kernel family on the context stream: "rank_gemm_tc" (the Cholesky-rank doubles GEMMs
-   on tcgen05 tensor cores) and "rank_gemm_f64" (the same GEMMs in binary64).
+   on tcgen05 tensor cores in a split-bfloat16 precision), "rank_gemm_f64e" (the same
+   GEMMs in MLCC_FP64E) and "rank_gemm_f64" (the same GEMMs on the binary64 FMA units);
+   and phases of the solvers: "gs_omega" (one ground-state residual), "jacobian_prepare",
+   "sigma" (one Jacobian transformation), "dav_update_G" (subspace matrix), "dav_ritz"
+   (Ritz vectors and residuals), "dav_orthonormalise" (Gram-Schmidt of new directions).
+   Phases contain the GEMM families launched inside them.
    mlcc_kernel_time returns launches, summed milliseconds and summed algorithmic flops
    (2 M N K of the contraction; split-bfloat16 precisions issue S times as many tensor
    operations, S = 1, 3, 6) since the last reset; it synchronises. */
@@ -159,6 +179,19 @@ mlcc_status mlcc_kernel_time(mlcc_ctx* ctx, const char* family, int64_t* launche
                              double* total_ms, double* total_flop);
 /* Number of kernels libmlcc has launched in this process (all contexts), for accounting. */
 int64_t mlcc_launch_count(void);
+
+/* Dense GEMM on the context stream, row-major device matrices:
+     C = alpha op(A) op(B) + beta C,  op(A) [M][K] (A[m*lda+k], or A[k*lda+m] if trans_a),
+     op(B) [K][N] (B[k*ldb+n], or B[n*ldb+k] if trans_b), C [M][N] (C[m*ldc+n]).
+   precision MLCC_FP64 runs on the binary64 FMA units; MLCC_BF16, MLCC_BF16X3, MLCC_BF16X6
+   and MLCC_FP64E on the tcgen05 tensor cores as described at mlcc_precision (no fallback:
+   a tensor-core precision with M or N below 64 for MLCC_FP64E, or K above 2^20, returns
+   MLCC_E_ARG). Scratch is allocated for the call and freed before it returns; the call
+   synchronises the stream. This is the contraction engine under every Cholesky-rank
+   step of sigma and Omega, exposed for checking its arithmetic. */
+mlcc_status mlcc_gemm(mlcc_ctx* ctx, int32_t trans_a, int32_t trans_b, int64_t M, int64_t N, int64_t K,
+                      double alpha, const double* a_dev, int64_t lda, const double* b_dev, int64_t ldb,
+                      double beta, double* c_dev, int64_t ldc, int32_t precision);
 
 /* ---- system -------------------------------------------------------------------- */
 /* Takes device copies of chol (Sec. 2.4 MO Cholesky vectors) and fock (Eq. eff_fock),

@@ -205,6 +205,7 @@ void mlcc_default_options(mlcc_options* o) {
   o->es_res_tol = 1e-8;
   o->es_omega_tol = 1e-11;
   o->lowp_res_tol = 1e-4;
+  o->refine_precision = MLCC_FP64;
 }
 
 const char* mlcc_last_error(void) { return last_error_cstr(); }
@@ -368,8 +369,10 @@ mlcc_status mlcc_ground_state(mlcc_system* S, const mlcc_options* opt, double* t
     MLCC_REQUIRE(S && opt && t1, "mlcc_ground_state: NULL argument");
     MLCC_REQUIRE(S->nd == 0 || x2, "mlcc_ground_state: x2 buffer required");
     MLCC_REQUIRE(opt->max_gs_iter >= 1 && opt->diis_dim >= 1, "mlcc_ground_state: bad options");
-    MLCC_REQUIRE(opt->gs_precision >= MLCC_FP64 && opt->gs_precision <= MLCC_BF16X6,
+    MLCC_REQUIRE(opt->gs_precision >= MLCC_FP64 && opt->gs_precision <= MLCC_FP64E,
                  "mlcc_ground_state: unknown gs_precision");
+    MLCC_REQUIRE(opt->refine_precision == MLCC_FP64 || opt->refine_precision == MLCC_FP64E,
+                 "mlcc_ground_state: refine_precision must be MLCC_FP64 or MLCC_FP64E");
     MLCC_CUDA(cudaSetDevice(S->ctx->device));
     mlcc_gs_info local{};
     mlcc_status st = ground_state(S, opt, t1, x2, info ? info : &local);
@@ -399,7 +402,7 @@ mlcc_status mlcc_sigma(mlcc_system* S, int32_t n_vec, const double* c, double* s
   return guard([&] {
     MLCC_REQUIRE(S && c && sigma, "mlcc_sigma: NULL argument");
     MLCC_REQUIRE(n_vec >= 0, "mlcc_sigma: n_vec < 0");
-    MLCC_REQUIRE(precision >= MLCC_FP64 && precision <= MLCC_BF16X6, "mlcc_sigma: unknown precision");
+    MLCC_REQUIRE(precision >= MLCC_FP64 && precision <= MLCC_FP64E, "mlcc_sigma: unknown precision");
     MLCC_CUDA(cudaSetDevice(S->ctx->device));
     const int64_t len = int64_t(S->nv) * S->no + S->nd;
     for (int k = 0; k < n_vec; ++k) sigma_eval(S, c + k * len, sigma + k * len, precision);
@@ -412,11 +415,62 @@ mlcc_status mlcc_excited_states(mlcc_system* S, const mlcc_options* opt, double*
                                 double* r, mlcc_es_info* info) {
   return guard([&] {
     MLCC_REQUIRE(S && opt && omega, "mlcc_excited_states: NULL argument");
+    MLCC_REQUIRE(opt->precision >= MLCC_FP64 && opt->precision <= MLCC_FP64E,
+                 "mlcc_excited_states: unknown precision");
+    MLCC_REQUIRE(opt->refine_precision == MLCC_FP64 || opt->refine_precision == MLCC_FP64E,
+                 "mlcc_excited_states: refine_precision must be MLCC_FP64 or MLCC_FP64E");
     MLCC_CUDA(cudaSetDevice(S->ctx->device));
     mlcc_status st = excited_states(S, opt, omega, r, info);
     if (st == MLCC_E_ES_NOCONV) set_last_error("excited states did not converge");
     if (st == MLCC_E_COMPLEX_ROOT) set_last_error("a wanted Ritz value is complex");
     return st;
+  });
+}
+
+mlcc_status mlcc_gemm(mlcc_ctx* ctx, int32_t trans_a, int32_t trans_b, int64_t M, int64_t N, int64_t K,
+                      double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+                      double beta, double* C, int64_t ldc, int32_t precision) {
+  return guard([&] {
+    MLCC_REQUIRE(ctx != nullptr, "mlcc_gemm: NULL context");
+    MLCC_REQUIRE(M >= 0 && N >= 0 && K >= 0, "mlcc_gemm: negative size");
+    MLCC_REQUIRE(precision >= MLCC_FP64 && precision <= MLCC_FP64E, "mlcc_gemm: unknown precision");
+    if (M == 0 || N == 0) return MLCC_OK;
+    MLCC_REQUIRE(C && (K == 0 || (A && B)), "mlcc_gemm: NULL matrix");
+    MLCC_REQUIRE(ldc >= N && lda >= (trans_a ? M : K) && ldb >= (trans_b ? K : N) && lda >= 1 && ldb >= 1,
+                 "mlcc_gemm: leading dimension too small");
+    MLCC_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    Gemm g;
+    g.ta = trans_a != 0;
+    g.tb = trans_b != 0;
+    g.M = M; g.N = N; g.K = K;
+    g.alpha = alpha; g.beta = beta;
+    g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
+    // scratch for this call: converted operands plus partial sums (split-K, or the
+    // emulation's chunk planes, bounded by panelling over the output columns)
+    const int64_t Kp = (K + 63) / 64 * 64;
+    size_t bytes = (size_t(1) << 30) + (size_t(64) << 20);
+    if (precision != MLCC_FP64) bytes += size_t(M + N) * 8 * Kp * 2 + size_t(M + N) * 4;
+    Arena ws;
+    ws.reserve(bytes);
+    Arena flag;
+    flag.reserve(256);
+    int* err = flag.get<int>(1);
+    MLCC_CUDA(cudaMemsetAsync(err, 0, 4, s));
+    if (precision == MLCC_FP64) {
+      gemm_f64(g, ws, s, ctx->sm_count);
+    } else if (precision == MLCC_FP64E) {
+      MLCC_REQUIRE(gemm_emu(g, ws, s, ctx->sm_count, err),
+                   "mlcc_gemm: shape outside the MLCC_FP64E tensor-core path (M, N >= 64, K <= 2^20)");
+    } else {
+      MLCC_REQUIRE(K > 0 && gemm_tc(g, precision, ws, s, ctx->sm_count, err),
+                   "mlcc_gemm: shape outside the tensor-core path");
+    }
+    int h = 0;
+    MLCC_CUDA(cudaMemcpyAsync(&h, err, 4, cudaMemcpyDeviceToHost, s));
+    MLCC_CUDA(cudaStreamSynchronize(s));
+    if (h != 0) throw Error(MLCC_E_CUDA, "mlcc_gemm: a tensor-core pipeline wait timed out");
+    return MLCC_OK;
   });
 }
 

@@ -123,6 +123,9 @@ struct LowpScope {
   ~LowpScope();
 };
 int lowp_precision();
+// the split-bfloat16 precisions (a low-precision phase); MLCC_FP64 and MLCC_FP64E are
+// binary64-class
+inline bool is_split_precision(int p) { return p == MLCC_BF16 || p == MLCC_BF16X3 || p == MLCC_BF16X6; }
 int* lowp_error_flag();
 OperandCache* lowp_cache();
 OperandCache* operand_cache_new();
@@ -131,6 +134,10 @@ void operand_cache_free(OperandCache* c);
 // device memory ranges whose contents stay fixed while the cache is valid
 void operand_cache_set_ranges(OperandCache* c, const std::vector<std::pair<const char*, size_t>>& r);
 bool gemm_tc(const Gemm& g, int precision, Arena& ws, cudaStream_t s, int sm_count, int* err);
+// MLCC_FP64E: binary64 GEMM from exact integer slices on the tensor cores (tc_emu.cu);
+// gemm_emu returns false, launching nothing, exactly when gemm_emu_fits is false
+bool gemm_emu(const Gemm& g, Arena& ws, cudaStream_t s, int sm_count, int* err);
+bool gemm_emu_fits(const Gemm& g, const Arena& ws);
 // C = alpha * sum_s partial[s] + beta * C (deterministic order)
 void reduce_partials(const double* partial, int nsplit, int64_t M, int64_t N, double* C,
                      int64_t ldc, double alpha, double beta, cudaStream_t s);
@@ -166,6 +173,22 @@ void dots(const double* x, int64_t ldx, int nx, const double* y, int64_t n, doub
 // out_dev[k * ny + j] = x_k . y_j for k < nx, j < ny (ny <= 4): one pass over each x_k
 void dots_block(const double* x, int64_t ldx, int nx, const double* y, int64_t ldy, int ny,
                 int64_t n, double* out_dev, Arena& ws, cudaStream_t s);
+// Binary32 arithmetic on binary64 vectors (vec32.cu): while a Vec32Scope is on for this
+// thread, dots, dots_block and the skinny GEMMs (M <= 16, K <= 64, B not transposed)
+// convert each loaded element to binary32 and multiply-add in binary32 (the Davidson
+// vector work of a split-precision phase); everything else is unchanged.
+struct Vec32Scope {
+  bool prev;
+  explicit Vec32Scope(bool on);
+  ~Vec32Scope();
+  void set(bool on);
+};
+bool vec32_active();
+void dots32(const double* x, int64_t ldx, int nx, const double* y, int64_t n, double* out_dev,
+            Arena& ws, cudaStream_t s);
+void dots_block32(const double* x, int64_t ldx, int nx, const double* y, int64_t ldy, int ny,
+                  int64_t n, double* out_dev, Arena& ws, cudaStream_t s);
+bool skinny32(const Gemm& g, cudaStream_t s);
 void copy_d2h(double* h, const double* d, int64_t n, cudaStream_t s);
 void copy_h2d(double* d, const double* h, int64_t n, cudaStream_t s);
 

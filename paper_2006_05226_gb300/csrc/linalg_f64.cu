@@ -331,6 +331,12 @@ static void launch_skinny(const GP& p, bool ta, bool tb, cudaStream_t s) {
 }
 }  // namespace
 
+static thread_local bool g_vec32 = false;
+Vec32Scope::Vec32Scope(bool on) : prev(g_vec32) { g_vec32 = on; }
+Vec32Scope::~Vec32Scope() { g_vec32 = prev; }
+void Vec32Scope::set(bool on) { g_vec32 = on; }
+bool vec32_active() { return g_vec32; }
+
 static thread_local int g_lowp = 0;
 static thread_local int* g_lowp_err = nullptr;
 static thread_local OperandCache* g_lowp_cache = nullptr;
@@ -384,6 +390,7 @@ void gemm_f64(const Gemm& g, Arena& ws, cudaStream_t s, int sm_count) {
   p.partial = nullptr;
   p.kchunk = 0;
   if (!g.reduce && g.batch == 1 && g.M <= 16 && g.N >= 64) {
+    if (g_vec32 && skinny32(g, s)) return;
     if (g.M <= 1) launch_skinny<1>(p, g.ta, g.tb, s);
     else if (g.M <= 4) launch_skinny<4>(p, g.ta, g.tb, s);
     else if (g.M <= 8) launch_skinny<8>(p, g.ta, g.tb, s);
@@ -774,6 +781,7 @@ void axpby(double* y, const double* x, int64_t n, double a, double b, cudaStream
 void dots(const double* x, int64_t ldx, int nx, const double* y, int64_t n, double* out_dev,
           Arena& ws, cudaStream_t s) {
   if (nx <= 0) return;
+  if (g_vec32) return dots32(x, ldx, nx, y, n, out_dev, ws, s);
   Scope sc(ws);
   int blocks = int(std::min<int64_t>((n + 255) / 256, DOT_BLOCKS));
   blocks = std::max(blocks, 1);
@@ -786,6 +794,7 @@ void dots(const double* x, int64_t ldx, int nx, const double* y, int64_t n, doub
 void dots_block(const double* x, int64_t ldx, int nx, const double* y, int64_t ldy, int ny,
                 int64_t n, double* out_dev, Arena& ws, cudaStream_t s) {
   if (nx <= 0 || ny <= 0) return;
+  if (g_vec32) return dots_block32(x, ldx, nx, y, ldy, ny, n, out_dev, ws, s);
   MLCC_REQUIRE(ny <= 4, "dots_block: at most 4 y-vectors");
   Scope sc(ws);
   int blocks = int(std::min<int64_t>((n + 255) / 256, DOT_BLOCKS));

@@ -312,8 +312,8 @@ void build_fock_tangent(mlcc_system* S, const double* dht, const double* dLt, do
 
 // ---------------------------------------------------------------------------------
 // The Cholesky-rank doubles GEMMs (the dominant work): C[dS x dS] = A^T B with A, B
-// [nj][dS], or C[nj x dS] = A[nj x dS] B[dS x dS]. Binary64 here; the tensor-core path
-// replaces them when precision is MLCC_BF16.
+// [nj][dS], or C[nj x dS] = A[nj x dS] B[dS x dS]. Binary64 (FMA units, or MLCC_FP64E on
+// the tensor cores) here; the split-bfloat16 precisions go through rank_gemm_lowp.
 void rank_gemm_f64(mlcc_system* S, bool outer, const double* A, const double* B, double* C,
                    double alpha, double beta);
 
@@ -330,13 +330,21 @@ void rank_gemm_f64(mlcc_system* S, bool outer, const double* A, const double* B,
   }
   g.alpha = alpha;
   g.beta = beta;
-  timed(S, lowp_precision() ? "rank_gemm_tc" : "rank_gemm_f64", 2.0 * double(g.M) * double(g.N) * double(g.K),
+  const int lp = lowp_precision();
+  const double flop = 2.0 * double(g.M) * double(g.N) * double(g.K);
+  if (lp == MLCC_FP64E && gemm_emu_fits(g, S->ws)) {
+    timed(S, "rank_gemm_f64e", flop, [&] { gemm_emu(g, S->ws, stm(S), smc(S), lowp_error_flag()); });
+    return;
+  }
+  // binary64 FMA units (also MLCC_FP64E when the workspace cannot hold the emulation)
+  LowpScope scope(lp == MLCC_FP64E ? 0 : lp, lowp_error_flag(), lowp_cache());
+  timed(S, lp && lp != MLCC_FP64E ? "rank_gemm_tc" : "rank_gemm_f64", flop,
         [&] { gemm_f64(g, S->ws, stm(S), smc(S)); });
 }
 
 static void rank_gemm(mlcc_system* S, int precision, bool outer, const double* A, const double* B,
                       double* C, double alpha, double beta) {
-  if (precision != MLCC_FP64) {
+  if (is_split_precision(precision)) {
     if (S->lowp_prec != precision) lowp_prepare(S, precision);
     rank_gemm_lowp(S, outer, A, B, C, alpha, beta, precision, false);
   } else {

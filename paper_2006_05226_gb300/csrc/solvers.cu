@@ -187,16 +187,19 @@ mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out
   double e_old = 0.0, e = 0.0, norm = 0.0;
   int it = 0;
   bool conv = false;
-  // low-precision phase (gs_precision), then binary64 when refine_fp64 is set
+  // low-precision phase (gs_precision), then refine_precision when refine_fp64 is set
   int phase_prec = opt->gs_precision;
   const double lowp_switch = std::max(opt->gs_tol, 1e-7);
   std::vector<double> lowp_norms;   // residual norms of the low-precision phase
   for (it = 1; it <= opt->max_gs_iter; ++it) {
     {
       LowpScope lowp(phase_prec, S->tc_err);
-      omega_eval(S, t1, nullptr, true, tl ? tT : nullptr, x2, om1, tl ? omT : nullptr, energy);
+      timed(S, "gs_omega", 0.0, [&] {
+        omega_eval(S, t1, nullptr, true, tl ? tT : nullptr, x2, om1, tl ? omT : nullptr, energy);
+      });
     }
     if (phase_prec != MLCC_FP64) check_tc_error(S);
+    const bool split_phase = is_split_precision(phase_prec);
     dots(om1, 0, 1, om1, n1, nrm, S->ws, s);
     if (tl) dots(omT, 0, 1, omT, tl, nrm + 1, S->ws, s);
     else fill(nrm + 1, 1, 0.0, s);
@@ -210,7 +213,7 @@ mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out
     if (verbose())
       std::fprintf(stderr, "[mlcc] GS it %3d prec %d E %.14f |Omega| %.3e\n", it, phase_prec, e, norm);
     bool stalled = false;
-    if (phase_prec != MLCC_FP64) {
+    if (split_phase) {
       lowp_norms.push_back(norm);
       const size_t q = lowp_norms.size();
       if (q >= 6) {
@@ -219,17 +222,17 @@ mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out
         stalled = recent > 0.5 * before;   // no halving in three iterations: the noise floor
       }
     }
-    if (phase_prec != MLCC_FP64 && (norm < lowp_switch || stalled)) {
+    if (split_phase && (norm < lowp_switch || stalled)) {
       if (!opt->refine_fp64) {
         conv = true;
         break;
       }
-      phase_prec = MLCC_FP64;   // the next iterations in binary64 from these amplitudes
+      phase_prec = opt->refine_precision;   // the next iterations refine these amplitudes
       order.clear();            // the low-precision residuals do not belong in DIIS
       std::fill(Bm.begin(), Bm.end(), 0.0);
       e_old = e;
       continue;                 // re-evaluate the residual in binary64 before stepping
-    } else if (phase_prec == MLCC_FP64 && norm < opt->gs_tol &&
+    } else if (!split_phase && norm < opt->gs_tol &&
                std::fabs(e - e_old) < opt->gs_energy_tol) {
       conv = true;
       break;
@@ -295,7 +298,7 @@ mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out
     info->converged = conv ? 1 : 0;
   }
   // the Jacobian is taken at the returned amplitudes
-  jacobian_prepare(S, t1_out, x2_out);
+  timed(S, "jacobian_prepare", 0.0, [&] { jacobian_prepare(S, t1_out, x2_out); });
   MLCC_CUDA(cudaStreamSynchronize(s));
   return conv ? MLCC_OK : MLCC_E_GS_NOCONV;
 }
@@ -315,13 +318,18 @@ struct DavState {
 }  // namespace
 
 static void sigma_batch(mlcc_system* S, const double* C, double* Sg, int nvec, int64_t dim, int prec) {
-  for (int k = 0; k < nvec; ++k) sigma_eval(S, C + int64_t(k) * dim, Sg + int64_t(k) * dim, prec);
+  for (int k = 0; k < nvec; ++k)
+    timed(S, "sigma", 0.0, [&] { sigma_eval(S, C + int64_t(k) * dim, Sg + int64_t(k) * dim, prec); });
   if (prec != MLCC_FP64) check_tc_error(S);
 }
 
 // add the new columns [m0, m) to G: G[i][k] = B_i . S_k and G[k][j] = B_k . S_j, with the
 // basis read once per block of up to four new vectors
+static void update_G_body(DavState& D, int m0);
 static void update_G(DavState& D, int m0) {
+  timed(D.S, "dav_update_G", 0.0, [&] { update_G_body(D, m0); });
+}
+static void update_G_body(DavState& D, int m0) {
   mlcc_system* S = D.S;
   cudaStream_t s = S->ctx->stream;
   Scope sc(S->ws);
@@ -346,7 +354,11 @@ static void update_G(DavState& D, int m0) {
 
 // orthogonalise the block V = B[m .. m+nv) against B[0..m): two passes of
 // V -= B (B^T V), reading the basis once per pass
+static void block_project_body(DavState& D, int nv);
 static void block_project(DavState& D, int nv) {
+  timed(D.S, "dav_orthonormalise", 0.0, [&] { block_project_body(D, nv); });
+}
+static void block_project_body(DavState& D, int nv) {
   mlcc_system* S = D.S;
   cudaStream_t s = S->ctx->stream;
   if (D.m == 0 || nv == 0) return;
@@ -366,7 +378,13 @@ static void block_project(DavState& D, int nv) {
 
 // orthonormalise v against B[from..m) (two passes); returns false if v collapses
 // ref_norm > 0: the norm of v before an earlier projection, for the drop test
+static bool orthonormalise_body(DavState& D, double* v, int from, double ref_norm);
 static bool orthonormalise(DavState& D, double* v, int from = 0, double ref_norm = 0.0) {
+  bool ok = false;
+  timed(D.S, "dav_orthonormalise", 0.0, [&] { ok = orthonormalise_body(D, v, from, ref_norm); });
+  return ok;
+}
+static bool orthonormalise_body(DavState& D, double* v, int from, double ref_norm) {
   mlcc_system* S = D.S;
   cudaStream_t s = S->ctx->stream;
   Scope sc(S->ws);
@@ -387,15 +405,23 @@ static bool orthonormalise(DavState& D, double* v, int from = 0, double ref_norm
   }
   dots(v, 0, 1, v, D.dim, nr, S->ws, s);
   const double n1 = std::sqrt(host_scalar(S, nr));
-  if (!(n1 > 1e-10 * n0)) return false;
+  // what is left of a direction inside the span is rounding noise: near 1e-16 of its norm
+  // in binary64, near 1e-7 with binary32 vector arithmetic
+  if (!(n1 > (vec32_active() ? 1e-5 : 1e-10) * n0)) return false;
   k_scale<<<nblk(D.dim), 256, 0, s>>>(v, D.dim, 1.0 / n1);
   MLCC_CHECK_LAUNCH();
   return true;
 }
 
 // X = Y^T B, R = Y^T S - w X for the wanted Ritz pairs
+static void ritz_body(DavState& D, const std::vector<double>& Yt, int nr, const std::vector<double>& w,
+                      double* X, double* R);
 static void ritz(DavState& D, const std::vector<double>& Yt, int nr, const std::vector<double>& w,
                  double* X, double* R) {
+  timed(D.S, "dav_ritz", 0.0, [&] { ritz_body(D, Yt, nr, w, X, R); });
+}
+static void ritz_body(DavState& D, const std::vector<double>& Yt, int nr, const std::vector<double>& w,
+                      double* X, double* R) {
   mlcc_system* S = D.S;
   cudaStream_t s = S->ctx->stream;
   Scope sc(S->ws);
@@ -452,23 +478,28 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
   D.m = nguess;
 
   int prec = opt->precision;
-  const bool lowp = prec != MLCC_FP64;
+  const bool lowp = is_split_precision(prec);
   const bool two_phase = lowp && opt->refine_fp64 > 0;
   int fp64_sweeps = 0;
   int n_sigma = 0, n_sigma_lowp = 0;
   auto count_sigma = [&](int k) {
     n_sigma += k;
-    if (prec != MLCC_FP64) n_sigma_lowp += k;
+    if (is_split_precision(prec)) n_sigma_lowp += k;
   };
   sigma_batch(S, D.B, D.Sg, D.m, dim, prec);
   count_sigma(D.m);
-  update_G(D, 0);
+  {
+    Vec32Scope v32(lowp);
+    update_G(D, 0);
+  }
 
   std::vector<double> w_old(nr, 1e300), w(nr), rn(nr);
   bool conv = false, complex_pair = false;
   int it = 0;
   const int max_it = std::max(1, opt->max_es_iter);
   for (it = 1; it <= max_it; ++it) {
+    // vector arithmetic in binary32 while the sigma-vectors are split-precision
+    Vec32Scope v32(is_split_precision(prec));
     // subspace eigenproblem (host, binary64)
     std::vector<double> Gm(size_t(D.m) * D.m);
     for (int i = 0; i < D.m; ++i)
@@ -504,7 +535,7 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
         if (!std::isfinite(rn[k])) throw Error(MLCC_E_NAN, "Davidson: NaN in a residual");
       }
     }
-    const bool in_lowp = prec != MLCC_FP64;
+    const bool in_lowp = is_split_precision(prec);
     if (verbose()) {
       std::fprintf(stderr, "[mlcc] ES it %3d prec %d dim %3d", it, prec, D.m);
       for (int k = 0; k < nr; ++k) std::fprintf(stderr, "  w %.10f r %.2e", w[k], rn[k]);
@@ -523,8 +554,9 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
     if (req_done) todo.clear();
     if (todo.empty()) {
       if (two_phase && in_lowp) {
-        // refinement: restart from the low-precision Ritz vectors with binary64 sigma
-        prec = MLCC_FP64;
+        // refinement: restart from the low-precision Ritz vectors with refine_precision sigma
+        prec = opt->refine_precision;
+        v32.set(false);
         const int keep = std::min(nr, D.m);   // all tracked Ritz vectors
         MLCC_CUDA(cudaMemcpyAsync(CB, X, size_t(keep) * dim * 8, cudaMemcpyDeviceToDevice, s));
         D.m = 0;

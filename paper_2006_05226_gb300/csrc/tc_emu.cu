@@ -1,0 +1,341 @@
+// Binary64 GEMM emulated on the tcgen05 tensor cores with exact integer slices
+// (the error-free splitting of Ozaki's scheme, arranged for bfloat16 and fp32 accumulate).
+//
+// GB300 issues about two binary64 FMAs per SM and clock, so a binary64 contraction with
+// operand reuse is bound by the FP64 pipe, not by HBM. Here each operand row r (a row of
+// A, or a column of B, along the contraction index k) is scaled by 2^(F - E_r), E_r the
+// exponent of the row's largest magnitude (|x| < 2^E_r), and rounded to an integer X of at
+// most F = 7 + 8 (S - 1) bits, written as S signed digits of base 2^8:
+//     X = sum_{s<S} q_s 2^(8 (S - 1 - s)),   |q_s| <= 128   (each exact in bfloat16).
+// Then, with 0-based digit indices,
+//     C_mn = 2^(E_m + E_n - 2F) sum_{s,t} 2^(8 (2S - 2 - s - t)) sum_k qA_s[m][k] qB_t[n][k]
+// of which the pairs with s + t <= S - 1 are kept: every term down to 2^(-8 (S - 1)) of the
+// leading one, the rest lies below the rounding of X. A product of two digits is at most
+// 2^14 in magnitude, so an fp32 tensor-core accumulation of at most 1024 of them stays an
+// exact integer (|sum| <= 2^24). The GEMM kernel sums each group g = s + t in chunks of at
+// most 1024 products and writes the exact chunk sums; a reduction combines them in 64-bit
+// integers and rounds the total once to binary64, then applies 2^(E_m + E_n ...), alpha
+// and beta. With S = 7 the truncation and the rounding of X cost about 2^-53 of
+// 2^(E_m + E_n) per product, the binary64 level of a product of the row maxima.
+#include "system.cuh"
+#include "tc_common.cuh"
+
+#include <algorithm>
+
+namespace mlcc {
+
+namespace {
+
+constexpr int EMU_S = 7;              // digits per operand element
+constexpr int EMU_CH = 16;            // K blocks of 64 per exact fp32 chunk (1024 products)
+constexpr int EMU_NONFINITE = 1 << 30;
+constexpr int64_t EMU_MAX_K = int64_t(1) << 20;   // keeps the 64-bit combination exact
+
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7FFFFFFFFFFFFFFFull;
+}
+// E with max|x| < 2^E from the bit pattern of the largest magnitude (integer compares
+// order non-negative binary64 values, NaN and Inf above every finite value)
+__device__ __forceinline__ int exponent_of_max(unsigned long long m) {
+  if (m == 0) return 0;   // zero row: every digit is zero
+  const int ef = int(m >> 52);
+  if (ef == 0x7FF) return EMU_NONFINITE;
+  if (ef > 0) return ef - 1022;          // m = 1.f * 2^(ef - 1023)
+  const int p = 63 - __clzll(m);         // subnormal: m = fraction * 2^-1074
+  return p + 1 - 1074;
+}
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+  return a > b ? a : b;
+}
+
+// K contiguous in the source: one warp per row
+__global__ void k_emu_rowexp_direct(GOp o, int* ex) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t r = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; r < o.R; r += nwarps) {
+    unsigned long long m = 0;
+    for (int64_t kk = lane; kk < o.Ktot; kk += 32) m = umax64(m, abs_bits(gop_load(o, r, kk)));
+    for (int off = 16; off > 0; off >>= 1) m = umax64(m, __shfl_xor_sync(0xFFFFFFFFu, m, off));
+    if (lane == 0) ex[r] = exponent_of_max(m);
+  }
+}
+// rows contiguous in the source: 32 rows per block, 8 lanes over k each
+__global__ void k_emu_rowexp_tr(GOp o, int* ex) {
+  __shared__ unsigned long long red[8][33];
+  const int64_t r = int64_t(blockIdx.x) * 32 + threadIdx.x;
+  unsigned long long m = 0;
+  if (r < o.R)
+    for (int64_t kk = threadIdx.y; kk < o.Ktot; kk += 8) m = umax64(m, abs_bits(gop_load(o, r, kk)));
+  red[threadIdx.y][threadIdx.x] = m;
+  __syncthreads();
+  if (threadIdx.y == 0 && r < o.R) {
+    for (int y = 1; y < 8; ++y) m = umax64(m, red[y][threadIdx.x]);
+    ex[r] = exponent_of_max(m);
+  }
+}
+
+// bfloat16 bit pattern of an integer |q| <= 128 (exact)
+__device__ __forceinline__ __nv_bfloat16 small_int_bf16(int q) {
+  unsigned short h = 0;
+  if (q != 0) {
+    const unsigned a = unsigned(q < 0 ? -q : q);
+    const int p = 31 - __clz(a);   // a = 2^p (1 + f), p <= 7
+    h = static_cast<unsigned short>((q < 0 ? 0x8000u : 0u) | (unsigned(p + 127) << 7) | ((a << (7 - p)) & 0x7Fu));
+  }
+  return __ushort_as_bfloat16(h);
+}
+// The EMU_S digits of X = round(x 2^(F - E)), most significant first, by integer
+// arithmetic on the binary64 fields (round half away from zero on the magnitude, then
+// round-to-nearest digits so every digit stays within [-128, 128]).
+__device__ __forceinline__ void emu_digits(double x, int E, __nv_bfloat16 q[EMU_S]) {
+  constexpr int F = 7 + 8 * (EMU_S - 1);
+  long long X = 0;
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int ef = int((b >> 52) & 0x7FF);
+  if (E != EMU_NONFINITE && ef != 0x7FF && (b << 1) != 0) {
+    const unsigned long long mant = (b & ((1ull << 52) - 1)) | (ef ? (1ull << 52) : 0ull);
+    const int e = ef ? ef : 1;                 // |x| = mant * 2^(e - 1075)
+    const int sh = e - 1075 + F - E;           // |X| = mant * 2^sh < 2^F since |x| < 2^E
+    unsigned long long mag;
+    if (sh >= 0) mag = mant << sh;
+    else if (sh > -63) mag = (mant + (1ull << (-sh - 1))) >> (-sh);
+    else mag = 0;
+    X = (b >> 63) ? -static_cast<long long>(mag) : static_cast<long long>(mag);
+  }
+#pragma unroll
+  for (int s = 0; s < EMU_S; ++s) {
+    const int shift = 8 * (EMU_S - 1 - s);
+    long long d = X;
+    if (shift > 0) d = (X + (1LL << (shift - 1))) >> shift;   // arithmetic shift: floor
+    X -= d * (1LL << shift);
+    q[s] = small_int_bf16(int(d));
+  }
+}
+
+// K contiguous in the source: dst[r][s * Kp + kk], one thread per (r, kk), kk fastest
+__global__ void k_emu_slice_direct(GOp o, const int* ex, __nv_bfloat16* dst) {
+  const int64_t total = o.R * o.Kp;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = t / o.Kp, kk = t - r * o.Kp;
+    __nv_bfloat16 q[EMU_S];
+    emu_digits(gop_load(o, r, kk), ex[r], q);
+#pragma unroll
+    for (int s = 0; s < EMU_S; ++s) dst[r * (EMU_S * o.Kp) + s * o.Kp + kk] = q[s];
+  }
+}
+// rows contiguous in the source: 32 x 32 tiles through shared memory
+__global__ void k_emu_slice_tr(GOp o, const int* ex, __nv_bfloat16* dst) {
+  __shared__ double tile[32][33];
+  const int64_t r0 = int64_t(blockIdx.x) * 32, k0 = int64_t(blockIdx.y) * 32;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) tile[y][threadIdx.x] = gop_load(o, r0 + threadIdx.x, k0 + y);
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int64_t r = r0 + y, kk = k0 + threadIdx.x;
+    if (r >= o.R || kk >= o.Kp) continue;
+    __nv_bfloat16 q[EMU_S];
+    emu_digits(tile[threadIdx.x][y], ex[r], q);
+#pragma unroll
+    for (int s = 0; s < EMU_S; ++s) dst[r * (EMU_S * o.Kp) + s * o.Kp + kk] = q[s];
+  }
+}
+
+struct EmuRed {
+  const float* P;          // [chunk][M][ldp] exact chunk sums
+  int64_t M, Nw, ldp;
+  int gstart[TC_EMU_MAX_S + 1];
+  const int* ea;           // [M] row exponents of A
+  const int* eb;           // [Nw] row exponents of B (this panel)
+  double alpha, beta;
+  double* C;               // [M][ldc], this panel's first column
+  int64_t ldc;
+};
+// C = alpha 2^(E_m + E_n - 14 - 8 (S - 1)) T + beta C with T = sum_g 2^(8 (S - 1 - g)) G_g,
+// G_g the integer sum of group g's chunks; T is held exactly as hi 2^32 + lo and rounded once.
+__global__ void k_emu_reduce(EmuRed r) {
+  const int64_t total = r.M * r.Nw, plane = r.M * r.ldp;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t m = t / r.Nw, n = t - m * r.Nw;
+    const float* p = r.P + m * r.ldp + n;
+    long long hi = 0, lo = 0;
+#pragma unroll
+    for (int g = 0; g < EMU_S; ++g) {
+      long long G = 0;
+      for (int z = r.gstart[g]; z < r.gstart[g + 1]; ++z) G += static_cast<long long>(__float2int_rn(p[z * plane]));
+      const int sh = 8 * (EMU_S - 1 - g);
+      if (sh >= 32) hi += G * (1LL << (sh - 32));
+      else lo += G * (1LL << sh);
+    }
+    const int ea = r.ea[m], eb = r.eb[n];
+    double v;
+    if (ea == EMU_NONFINITE || eb == EMU_NONFINITE) {
+      v = __longlong_as_double(0x7FF8000000000000LL);
+    } else {
+      v = fma(static_cast<double>(hi), 4294967296.0, static_cast<double>(lo));
+      v = ldexp(v, ea + eb - 14 - 8 * (EMU_S - 1));
+    }
+    double* c = r.C + m * r.ldc + n;
+    double out = (r.alpha == 0.0) ? 0.0 : r.alpha * v;
+    if (r.beta != 0.0) out += r.beta * *c;
+    *c = out;
+  }
+}
+
+int grid_for(int64_t total, int threads) {
+  return int(std::max<int64_t>(1, std::min<int64_t>((total + threads - 1) / threads, 65535)));
+}
+
+void emu_convert(const GOp& o, int* ex, __nv_bfloat16* dst, cudaStream_t s) {
+  if (!o.tr) {
+    k_emu_rowexp_direct<<<grid_for(o.R * 32, 256), 256, 0, s>>>(o, ex);
+    MLCC_CHECK_LAUNCH();
+    k_emu_slice_direct<<<grid_for(o.R * o.Kp, 256), 256, 0, s>>>(o, ex, dst);
+    MLCC_CHECK_LAUNCH();
+  } else {
+    MLCC_REQUIRE((o.R + 31) / 32 < (int64_t(1) << 31) && (o.Kp + 31) / 32 < 65536, "gemm_emu: grid");
+    k_emu_rowexp_tr<<<unsigned((o.R + 31) / 32), dim3(32, 8), 0, s>>>(o, ex);
+    MLCC_CHECK_LAUNCH();
+    dim3 blk(32, 8), grd(unsigned((o.R + 31) / 32), unsigned((o.Kp + 31) / 32));
+    k_emu_slice_tr<<<grd, blk, 0, s>>>(o, ex, dst);
+    MLCC_CHECK_LAUNCH();
+  }
+}
+
+size_t slice_bytes(const GOp& o) { return size_t(o.R) * EMU_S * o.Kp * 2; }
+
+// slices and row exponents of an operand, from the cache when it is marked constant
+const __nv_bfloat16* emu_operand(const GOp& o, int side, bool cacheable, Arena& ws, cudaStream_t s,
+                                 const int** ex_out) {
+  OperandCache* c = lowp_cache();
+  if (c && !(cacheable || c->constant(o.base))) c = nullptr;
+  const size_t sb = slice_bytes(o), bytes = sb + size_t(o.R) * 4;
+  auto fresh = [&](void* mem) {
+    auto* d = static_cast<__nv_bfloat16*>(mem);
+    int* ex = reinterpret_cast<int*>(static_cast<char*>(mem) + sb);
+    emu_convert(o, ex, d, s);
+    *ex_out = ex;
+    return d;
+  };
+  if (!c) return fresh(ws.alloc(bytes));
+  auto key = std::make_tuple(static_cast<const void*>(o.base), o.R, o.Mrow, o.sRow, o.Ktot, o.Kblk, o.sK, o.ld,
+                             o.tr, 1000 + EMU_S, side);
+  for (auto& e : c->entries)
+    if (e.key == key) {
+      *ex_out = reinterpret_cast<const int*>(reinterpret_cast<const char*>(e.p) + sb);
+      return e.p;
+    }
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fresh(ws.alloc(bytes));
+  }
+  c->blocks.push_back(mem);
+  __nv_bfloat16* d = fresh(mem);
+  c->entries.push_back({key, d});
+  return d;
+}
+
+}  // namespace
+
+namespace {
+struct EmuPlan {
+  GOp a, b;
+  int64_t M, N, Kp, Np;
+  int gstart[TC_EMU_MAX_S + 1];
+  int nch;
+};
+// shapes, chunk table and output panel width; false when the emulation cannot run
+bool emu_plan(const Gemm& g, const Arena& ws, EmuPlan& P) {
+  const bool flatten = !g.reduce && g.batch > 1;
+  if (flatten && !(g.sB == 0 && g.sC == g.M * g.ldc)) return false;
+  const int64_t M = flatten ? g.M * g.batch : g.M;
+  const int64_t Ktot = g.reduce ? g.K * g.batch : g.K;
+  const int64_t N = g.N;
+  if (M < 64 || N < 64 || Ktot < 1 || Ktot > EMU_MAX_K) return false;
+  const int64_t Kp = pad64(Ktot), kbp = Kp / 64;
+  for (int q = 0; q <= TC_EMU_MAX_S; ++q) P.gstart[q] = 0;
+  for (int q = 0; q < EMU_S; ++q) P.gstart[q + 1] = P.gstart[q] + int(((q + 1) * kbp + EMU_CH - 1) / EMU_CH);
+  for (int q = EMU_S + 1; q <= TC_EMU_MAX_S; ++q) P.gstart[q] = P.gstart[EMU_S];
+  P.nch = P.gstart[EMU_S];
+  if (P.nch >= 65536) return false;
+  GOp& a = P.a;
+  a = GOp{};
+  a.base = g.A;
+  a.R = M;
+  a.Mrow = flatten ? g.M : M;
+  a.sRow = flatten ? g.sA : 0;
+  a.Ktot = Ktot;
+  a.Kblk = g.reduce ? g.K : Ktot;
+  a.sK = g.reduce ? g.sA : 0;
+  a.ld = g.lda;
+  a.Kp = Kp;
+  a.tr = g.ta ? 1 : 0;
+  a.S = EMU_S;
+  GOp& b = P.b;
+  b = a;
+  b.base = g.B;
+  b.R = N;
+  b.Mrow = N;
+  b.sRow = 0;
+  b.sK = g.reduce ? g.sB : 0;
+  b.ld = g.ldb;
+  b.tr = g.tb ? 0 : 1;
+  // workspace: slices of both operands (unless cached), then the chunk planes of a panel
+  // of output columns as wide as the rest allows (a multiple of 256, the tile width)
+  const size_t ops = slice_bytes(a) + slice_bytes(b) + size_t(M + N) * 4 + 4 * 256;
+  const size_t free_bytes = ws.capacity() > ws.mark() + ops + (size_t(1) << 22)
+                                ? ws.capacity() - ws.mark() - ops - (size_t(1) << 22) : 0;
+  const size_t per_col = size_t(P.nch) * M * 4;
+  const int64_t cols = int64_t(free_bytes / per_col) / 4 * 4;   // partial rows padded to 4
+  int64_t Np = (N + 3) / 4 * 4 <= cols ? N : (cols >= 256 ? cols / 256 * 256 : cols);
+  if (Np < 1) return false;
+  P.M = M;
+  P.N = N;
+  P.Kp = Kp;
+  P.Np = Np;
+  return true;
+}
+}  // namespace
+
+bool gemm_emu_fits(const Gemm& g, const Arena& ws) {
+  EmuPlan P;
+  return emu_plan(g, ws, P);
+}
+
+bool gemm_emu(const Gemm& g, Arena& ws, cudaStream_t s, int sm_count, int* err) {
+  (void)sm_count;
+  EmuPlan P;
+  if (!emu_plan(g, ws, P)) return false;
+  const GOp &a = P.a, &b = P.b;
+  const int64_t M = P.M, N = P.N, Kp = P.Kp, Np = P.Np;
+  const int nch = P.nch;
+  const int* gstart = P.gstart;
+  Scope sc(ws);
+  const int *ea = nullptr, *eb = nullptr;
+  const __nv_bfloat16* As = emu_operand(a, 0, g.a_const, ws, s, &ea);
+  const __nv_bfloat16* Bs = emu_operand(b, 1, g.b_const, ws, s, &eb);
+  const int64_t ldp = (Np + 3) / 4 * 4;
+  float* part = ws.get<float>(size_t(nch) * M * ldp);
+  for (int64_t n0 = 0; n0 < N; n0 += Np) {
+    const int64_t nw = std::min(Np, N - n0), ldw = (nw + 3) / 4 * 4;
+    tc_gemm_emu_launch(As, Bs + n0 * EMU_S * Kp, M, nw, EMU_S, Kp, EMU_CH, gstart, part, ldw, err, s);
+    EmuRed r;
+    r.P = part;
+    r.M = M;
+    r.Nw = nw;
+    r.ldp = ldw;
+    for (int q = 0; q <= TC_EMU_MAX_S; ++q) r.gstart[q] = q <= EMU_S ? gstart[q] : nch;
+    r.ea = ea;
+    r.eb = eb + n0;
+    r.alpha = g.alpha;
+    r.beta = g.beta;
+    r.C = g.C + n0;
+    r.ldc = g.ldc;
+    k_emu_reduce<<<grid_for(M * nw, 256), 256, 0, s>>>(r);
+    MLCC_CHECK_LAUNCH();
+  }
+  return true;
+}
+
+}  // namespace mlcc

@@ -14,6 +14,7 @@
 // products x0 y0 (MLCC_BF16), + x0 y1 + x1 y0 (MLCC_BF16X3) and + x0 y2 + x1 y1 + x2 y0
 // (MLCC_BF16X6) are laid out as extra K segments, so one GEMM of depth S * K sums them.
 #include "system.cuh"
+#include "tc_common.cuh"
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -33,6 +34,7 @@ constexpr int STAGE_BYTES = A_BYTES + B_BYTES;   // 48 KB
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 constexpr int THREADS = 192;                     // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;  // about 2 s at 2 GHz
+constexpr int EMU_MAX_S = TC_EMU_MAX_S;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -97,6 +99,13 @@ struct TcParams {
   double* partial;  // split-K: [split][M][N] (alpha, beta applied by the reduction)
   int* err;
   int m_fast;       // 1: blockIdx.x runs over M tiles
+  // binary64 emulation (emu_S > 0): the operands hold emu_S integer slices of emu_kbp K
+  // blocks each; slice pair (i, j) belongs to group g = i + j. blockIdx.z is one chunk of
+  // at most emu_ch K blocks inside one group, written as fp32 to part32[z][M][ldp].
+  int emu_S, emu_kbp, emu_ch;
+  int emu_gstart[EMU_MAX_S + 1];   // first chunk of group g; emu_gstart[emu_S] = chunks
+  float* part32;
+  int64_t ldp;
 };
 
 __global__ void __launch_bounds__(THREADS, 1)
@@ -129,7 +138,14 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   const int kb0 = int(blockIdx.z) * p.kb_per;
-  const int nkb = max(0, min(p.kblocks, kb0 + p.kb_per) - kb0);
+  int nkb = max(0, min(p.kblocks, kb0 + p.kb_per) - kb0);
+  int grp = 0, loc0 = 0;   // emulation: slice-pair group and first group-local K block
+  if (p.emu_S > 0) {
+    const int z = int(blockIdx.z);
+    while (grp + 1 < p.emu_S && z >= p.emu_gstart[grp + 1]) ++grp;
+    loc0 = (z - p.emu_gstart[grp]) * p.emu_ch;
+    nkb = max(0, min(p.emu_ch, (grp + 1) * p.emu_kbp - loc0));
+  }
 
   if (warp == 0) {
     if (lane == 0) {
@@ -142,9 +158,16 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         }
         const uint32_t a_dst = smem_u32(smem + s * STAGE_BYTES);
         const uint32_t b_dst = a_dst + A_BYTES;
+        int xa = (kb0 + kb) * BK, xb = xa;
+        if (p.emu_S > 0) {
+          // group-local block -> slice pair (i, grp - i) and block kk inside the slice
+          const int loc = loc0 + kb, i = loc / p.emu_kbp, kk = loc - i * p.emu_kbp;
+          xa = (i * p.emu_kbp + kk) * BK;
+          xb = ((grp - i) * p.emu_kbp + kk) * BK;
+        }
         mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
-        tma_load_2d(a_dst, &tmA, full0 + 8 * s, (kb0 + kb) * BK, int(m0));
-        tma_load_2d(b_dst, &tmB, full0 + 8 * s, (kb0 + kb) * BK, int(n0));
+        tma_load_2d(a_dst, &tmA, full0 + 8 * s, xa, int(m0));
+        tma_load_2d(b_dst, &tmB, full0 + 8 * s, xb, int(n0));
         ++issued;
       }
       // drain: the copies this thread issued land before the CTA can exit
@@ -206,7 +229,20 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
               "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (row < p.M) {
+        if (p.part32 && row < p.M) {
+          // exact fp32 chunk sums of the emulation, one plane per chunk
+          float* prow = p.part32 + int64_t(blockIdx.z) * p.M * p.ldp + row * p.ldp + n0 + c0;
+          if (n0 + c0 + 32 <= p.N) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4)
+              *reinterpret_cast<float4*>(prow + j) =
+                  make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
+                              __uint_as_float(r[j + 3]));
+          } else {
+            for (int j = 0; j < 32; ++j)
+              if (n0 + c0 + j < p.N) prow[j] = __uint_as_float(r[j]);
+          }
+        } else if (row < p.M) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int64_t col = n0 + c0 + j;
@@ -337,7 +373,52 @@ void make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t kp, int 
 }
 }  // namespace
 
-static inline int64_t pad64(int64_t k) { return (k + 63) / 64 * 64; }
+
+static void ensure_smem_attr() {
+  static std::once_flag once;
+  static cudaError_t e = cudaSuccess;
+  std::call_once(once, [] {
+    e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  });
+  MLCC_CUDA(e);
+}
+
+void tc_gemm_emu_launch(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t M, int64_t N, int S,
+                        int64_t Kp, int ch, const int* gstart, float* part, int64_t ldp, int* err,
+                        cudaStream_t s) {
+  MLCC_REQUIRE(S >= 1 && S <= EMU_MAX_S && Kp % BK == 0 && ch >= 1, "tc_gemm_emu: bad slicing");
+  MLCC_REQUIRE(M < (int64_t(1) << 31) && N < (int64_t(1) << 31), "tc_gemm_emu: size too large");
+  MLCC_REQUIRE(ldp % 4 == 0 && ldp >= N, "tc_gemm_emu: partial rows must be padded to 4");
+  const int nch = gstart[S];
+  MLCC_REQUIRE(nch >= 1 && nch < 65536, "tc_gemm_emu: chunk count out of range");
+  ensure_smem_attr();
+  CUtensorMap ma, mb;
+  make_map(&ma, A, M, S * Kp, BM);
+  make_map(&mb, B, N, S * Kp, BN);
+  TcParams p;
+  p.M = M;
+  p.N = N;
+  p.kblocks = nch * ch;
+  p.kb_per = ch;
+  p.C = nullptr;
+  p.ldc = 0;
+  p.alpha = 1.0;
+  p.beta = 0.0;
+  p.partial = nullptr;
+  p.err = err;
+  p.m_fast = 1;
+  p.emu_S = S;
+  p.emu_kbp = int(Kp / BK);
+  p.emu_ch = ch;
+  for (int g = 0; g <= EMU_MAX_S; ++g) p.emu_gstart[g] = g <= S ? gstart[g] : nch;
+  p.part32 = part;
+  p.ldp = ldp;
+  const int64_t tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
+  MLCC_REQUIRE(tn < 65536, "tc_gemm_emu: grid too large");
+  const dim3 grid{unsigned(tm), unsigned(tn), unsigned(nch)};
+  k_tc_gemm<<<grid, THREADS, SMEM_BYTES, s>>>(ma, mb, p);
+  MLCC_CHECK_LAUNCH();
+}
 
 // C = alpha A B^T + beta C for bf16 K-major operands A [M][Kt], B [N][Kt] (Kt = S * Kp).
 // splits > 1 divides K over CTAs; partial must then hold splits * M * N doubles.
@@ -346,11 +427,7 @@ void tc_gemm_split(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t M, in
                    double* partial, cudaStream_t s) {
   MLCC_REQUIRE(Kt % BK == 0, "tc_gemm: K must be a multiple of 64");
   MLCC_REQUIRE(M < (int64_t(1) << 31) && N < (int64_t(1) << 31), "tc_gemm: size too large");
-  static bool attr = false;
-  if (!attr) {
-    MLCC_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    attr = true;
-  }
+  ensure_smem_attr();
   CUtensorMap ma, mb;
   make_map(&ma, A, M, Kt, BM);
   make_map(&mb, B, N, Kt, BN);
@@ -369,6 +446,12 @@ void tc_gemm_split(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t M, in
   MLCC_REQUIRE(splits == 1 || partial, "tc_gemm: split-K needs a partial buffer");
   p.err = err;
   p.m_fast = m_fast ? 1 : 0;
+  p.emu_S = 0;
+  p.emu_kbp = 0;
+  p.emu_ch = 0;
+  for (int g = 0; g <= EMU_MAX_S; ++g) p.emu_gstart[g] = 0;
+  p.part32 = nullptr;
+  p.ldp = 0;
   const int64_t tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
   dim3 grid = m_fast ? dim3(unsigned(tm), unsigned(tn), unsigned(splits))
                      : dim3(unsigned(tn), unsigned(tm), unsigned(splits));
@@ -407,21 +490,6 @@ void cvt_operand(const double* src, int64_t ld, int64_t rows, int64_t K, bool tr
 int split_segments(int precision) { return pattern(precision).S; }
 
 namespace {
-// Generic operand for gemm_tc: dst[r][s * Kp + kk] = piece_s(X(r, kk)) with
-//   r  = rb * Mrow + m  (row batches, stride sRow),  kk = kb * Kblk + k  (K batches, stride sK)
-//   X(r, kk) = base[rb * sRow + kb * sK + (tr ? k * ld + m : m * ld + k)]
-struct GOp {
-  const double* base;
-  int64_t R, Mrow, sRow, Ktot, Kblk, sK, ld, Kp;
-  int tr, S;
-  int piece[6];
-};
-__device__ __forceinline__ double gop_load(const GOp& o, int64_t r, int64_t kk) {
-  if (r >= o.R || kk >= o.Ktot) return 0.0;
-  const int64_t rb = r / o.Mrow, m = r - rb * o.Mrow;
-  const int64_t kb = kk / o.Kblk, k = kk - kb * o.Kblk;
-  return o.base[rb * o.sRow + kb * o.sK + (o.tr ? k * o.ld + m : m * o.ld + k)];
-}
 // K contiguous in the source: one thread per destination element, kk fastest
 __global__ void k_gop_direct(GOp o, __nv_bfloat16* dst) {
   const int64_t total = o.R * o.Kp;
@@ -461,24 +529,6 @@ void convert_gop(GOp o, __nv_bfloat16* dst, cudaStream_t s) {
 }
 }  // namespace
 
-}  // namespace mlcc
-#include <tuple>
-namespace mlcc {
-struct OperandCache {
-  struct Entry {
-    std::tuple<const void*, int64_t, int64_t, int64_t, int64_t, int64_t, int64_t, int64_t, int, int, int> key;
-    __nv_bfloat16* p;
-  };
-  std::vector<Entry> entries;
-  std::vector<void*> blocks;
-  std::vector<std::pair<const char*, size_t>> ranges;
-  bool constant(const void* p) const {
-    const char* q = static_cast<const char*>(p);
-    for (auto& r : ranges)
-      if (q >= r.first && q < r.first + r.second) return true;
-    return false;
-  }
-};
 void operand_cache_set_ranges(OperandCache* c, const std::vector<std::pair<const char*, size_t>>& r) {
   if (c) c->ranges = r;
 }
@@ -526,6 +576,7 @@ static const __nv_bfloat16* get_operand(const GOp& o, int side, bool cacheable, 
 // whose outputs are stacked rows (batches concatenated along M). Returns false (and does
 // nothing) for other shapes or when the workspace is too small.
 bool gemm_tc(const Gemm& g, int precision, Arena& ws, cudaStream_t s, int sm_count, int* err) {
+  if (precision == MLCC_FP64E) return gemm_emu(g, ws, s, sm_count, err);
   const bool flatten = !g.reduce && g.batch > 1;
   if (flatten && !(g.sB == 0 && g.sC == g.M * g.ldc)) return false;
   const int64_t M = flatten ? g.M * g.batch : g.M;

@@ -1,0 +1,222 @@
+// Davidson vector arithmetic of the split-precision phase in binary32.
+//
+// GB300 issues about two binary64 FMAs per SM and clock, less than HBM feeds these
+// kernels as soon as a loaded element takes part in more than one product: the
+// multi-vector dot products and the skinny subspace GEMMs of the Davidson solver were
+// bound by the FP64 pipe, not by memory. In the low-precision phase (whose sigma-vectors
+// carry relative errors near 1e-7) the same operations read the binary64 vectors, convert
+// every element to binary32 with integer operations (truncation; magnitudes below the
+// binary32 normal range become 0, NaN becomes Inf) and multiply-add in binary32. Per-thread
+// partial sums are widened to binary64 for the cross-thread reduction and for the
+// alpha / beta update of the output, so no binary64 arithmetic runs per element.
+#include "internal.cuh"
+
+#include <algorithm>
+
+namespace mlcc {
+
+namespace {
+
+__device__ __forceinline__ float d2f(double x) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const unsigned hi = unsigned(b >> 32), lo = unsigned(b);
+  const int e = int((hi >> 20) & 0x7FF) - 896;   // binary32 biased exponent
+  unsigned r = hi & 0x80000000u;
+  if (e >= 255) r |= 0x7F800000u;
+  else if (e > 0) r |= (unsigned(e) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const int e = int((u >> 23) & 0xFF);
+  unsigned long long r = static_cast<unsigned long long>(u & 0x80000000u) << 32;
+  const unsigned long long m = static_cast<unsigned long long>(u & 0x7FFFFFu) << 29;
+  if (e == 255) r |= 0x7FF0000000000000ull | m;
+  else if (e > 0) r |= (static_cast<unsigned long long>(e + 896) << 52) | m;
+  return __longlong_as_double(static_cast<long long>(r));
+}
+
+constexpr int DOT32_BLOCKS = 1216;   // 8 blocks of 256 threads per SM of a GB300
+constexpr int DOT32_CHUNK = 8;
+
+// partial[k][blk]: the block's share of x_k . y, DOT32_CHUNK vectors x_k per pass over y
+__global__ void k_dots32(const double* x, int64_t ldx, int nx, const double* y, int64_t n, double* partial) {
+  __shared__ double red[DOT32_CHUNK][256 / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k0 = 0; k0 < nx; k0 += DOT32_CHUNK) {
+    const int kc = min(DOT32_CHUNK, nx - k0);
+    float acc[DOT32_CHUNK];
+#pragma unroll
+    for (int c = 0; c < DOT32_CHUNK; ++c) acc[c] = 0.0f;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+      const float yi = d2f(y[i]);
+#pragma unroll
+      for (int c = 0; c < DOT32_CHUNK; ++c)
+        if (c < kc) acc[c] = fmaf(d2f(x[int64_t(k0 + c) * ldx + i]), yi, acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < DOT32_CHUNK; ++c) {
+      double v = f2d(acc[c]);
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[c][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kc) {
+      double v = 0.0;
+      for (int w = 0; w < int(blockDim.x / 32); ++w) v += red[threadIdx.x][w];
+      partial[int64_t(k0 + threadIdx.x) * gridDim.x + blockIdx.x] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// partial[(k * NY + j)][blk] for DOT32_CHUNK x-vectors per pass and NY <= 4 y-vectors
+template <int NY>
+__global__ void k_dots_block32(const double* x, int64_t ldx, int nx, const double* y, int64_t ldy, int64_t n,
+                               double* partial) {
+  __shared__ double red[DOT32_CHUNK * NY][256 / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k0 = 0; k0 < nx; k0 += DOT32_CHUNK) {
+    const int kc = min(DOT32_CHUNK, nx - k0);
+    float acc[DOT32_CHUNK][NY];
+#pragma unroll
+    for (int c = 0; c < DOT32_CHUNK; ++c)
+#pragma unroll
+      for (int j = 0; j < NY; ++j) acc[c][j] = 0.0f;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+      float yv[NY];
+#pragma unroll
+      for (int j = 0; j < NY; ++j) yv[j] = d2f(y[int64_t(j) * ldy + i]);
+#pragma unroll
+      for (int c = 0; c < DOT32_CHUNK; ++c) {
+        if (c < kc) {
+          const float xv = d2f(x[int64_t(k0 + c) * ldx + i]);
+#pragma unroll
+          for (int j = 0; j < NY; ++j) acc[c][j] = fmaf(xv, yv[j], acc[c][j]);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < DOT32_CHUNK; ++c)
+#pragma unroll
+      for (int j = 0; j < NY; ++j) {
+        double v = f2d(acc[c][j]);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[c * NY + j][warp] = v;
+      }
+    __syncthreads();
+    if (threadIdx.x < kc * NY) {
+      double v = 0.0;
+      for (int w = 0; w < int(blockDim.x / 32); ++w) v += red[threadIdx.x][w];
+      const int c = threadIdx.x / NY, j = threadIdx.x - c * NY;
+      partial[int64_t((k0 + c) * NY + j) * gridDim.x + blockIdx.x] = v;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_dots32_stage2(const double* partial, int nblk, double* out) {
+  __shared__ double red[256];
+  const int k = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += partial[int64_t(k) * nblk + i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[k] = red[0];
+}
+
+// C[m][n] = alpha sum_k op(A)[m][k] B[k][n] + beta C[m][n] for M <= MM, one thread per
+// column n; op(A) (K <= 64) is staged in shared memory as binary32
+template <int MM, bool TA>
+__global__ void k_skinny32(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, const double* B,
+                           int64_t ldb, double* C, int64_t ldc, double alpha, double beta) {
+  __shared__ float As[MM * 64];
+  for (int t = threadIdx.x; t < MM * 64; t += blockDim.x) {
+    const int m = t / 64, k = t - m * 64;
+    As[t] = (m < M && k < K) ? d2f(TA ? A[int64_t(k) * lda + m] : A[int64_t(m) * lda + k]) : 0.0f;
+  }
+  __syncthreads();
+  const int64_t n = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (n >= N) return;
+  float acc[MM];
+#pragma unroll
+  for (int m = 0; m < MM; ++m) acc[m] = 0.0f;
+  int64_t k = 0;
+  for (; k + 4 <= K; k += 4) {
+    const float b0 = d2f(B[k * ldb + n]), b1 = d2f(B[(k + 1) * ldb + n]);
+    const float b2 = d2f(B[(k + 2) * ldb + n]), b3 = d2f(B[(k + 3) * ldb + n]);
+#pragma unroll
+    for (int m = 0; m < MM; ++m) {
+      const float* a = As + m * 64 + k;
+      acc[m] = fmaf(a[0], b0, fmaf(a[1], b1, fmaf(a[2], b2, fmaf(a[3], b3, acc[m]))));
+    }
+  }
+  for (; k < K; ++k) {
+    const float b = d2f(B[k * ldb + n]);
+#pragma unroll
+    for (int m = 0; m < MM; ++m) acc[m] = fmaf(As[m * 64 + k], b, acc[m]);
+  }
+#pragma unroll
+  for (int m = 0; m < MM; ++m)
+    if (m < M) {
+      double* cp = C + m * ldc + n;
+      const double v = alpha * f2d(acc[m]);
+      *cp = (beta == 0.0) ? v : v + beta * (*cp);
+    }
+}
+
+template <int MM>
+void launch_skinny32(const Gemm& g, cudaStream_t s) {
+  const unsigned blocks = unsigned((g.N + 255) / 256);
+  if (g.ta) k_skinny32<MM, true><<<blocks, 256, 0, s>>>(g.M, g.N, g.K, g.A, g.lda, g.B, g.ldb, g.C, g.ldc, g.alpha, g.beta);
+  else k_skinny32<MM, false><<<blocks, 256, 0, s>>>(g.M, g.N, g.K, g.A, g.lda, g.B, g.ldb, g.C, g.ldc, g.alpha, g.beta);
+  MLCC_CHECK_LAUNCH();
+}
+
+}  // namespace
+
+void dots32(const double* x, int64_t ldx, int nx, const double* y, int64_t n, double* out_dev, Arena& ws,
+            cudaStream_t s) {
+  if (nx <= 0) return;
+  Scope sc(ws);
+  const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, DOT32_BLOCKS)));
+  double* partial = ws.get<double>(size_t(nx) * blocks);
+  k_dots32<<<blocks, 256, 0, s>>>(x, ldx, nx, y, n, partial);
+  MLCC_CHECK_LAUNCH();
+  k_dots32_stage2<<<nx, 256, 0, s>>>(partial, blocks, out_dev);
+  MLCC_CHECK_LAUNCH();
+}
+
+void dots_block32(const double* x, int64_t ldx, int nx, const double* y, int64_t ldy, int ny, int64_t n,
+                  double* out_dev, Arena& ws, cudaStream_t s) {
+  if (nx <= 0 || ny <= 0) return;
+  MLCC_REQUIRE(ny <= 4, "dots_block: at most 4 y-vectors");
+  Scope sc(ws);
+  const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, DOT32_BLOCKS)));
+  double* partial = ws.get<double>(size_t(nx) * ny * blocks);
+  switch (ny) {
+    case 1: k_dots_block32<1><<<blocks, 256, 0, s>>>(x, ldx, nx, y, ldy, n, partial); break;
+    case 2: k_dots_block32<2><<<blocks, 256, 0, s>>>(x, ldx, nx, y, ldy, n, partial); break;
+    case 3: k_dots_block32<3><<<blocks, 256, 0, s>>>(x, ldx, nx, y, ldy, n, partial); break;
+    default: k_dots_block32<4><<<blocks, 256, 0, s>>>(x, ldx, nx, y, ldy, n, partial); break;
+  }
+  MLCC_CHECK_LAUNCH();
+  k_dots32_stage2<<<nx * ny, 256, 0, s>>>(partial, blocks, out_dev);
+  MLCC_CHECK_LAUNCH();
+}
+
+bool skinny32(const Gemm& g, cudaStream_t s) {
+  if (g.tb || g.reduce || g.batch != 1 || g.M < 1 || g.M > 16 || g.K > 64 || g.N < 1) return false;
+  MLCC_REQUIRE((g.N + 255) / 256 < (int64_t(1) << 31), "skinny32: N too large");
+  if (g.M <= 1) launch_skinny32<1>(g, s);
+  else if (g.M <= 4) launch_skinny32<4>(g, s);
+  else if (g.M <= 8) launch_skinny32<8>(g, s);
+  else launch_skinny32<16>(g, s);
+  return true;
+}
+
+}  // namespace mlcc

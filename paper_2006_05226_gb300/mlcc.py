@@ -16,7 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmlcc.so")
 
-MLCC_FP64, MLCC_BF16, MLCC_BF16X3, MLCC_BF16X6 = 0, 1, 2, 3
+MLCC_FP64, MLCC_BF16, MLCC_BF16X3, MLCC_BF16X6, MLCC_FP64E = 0, 1, 2, 3, 4
 STATUS = {0: "MLCC_OK", -1: "MLCC_E_ARG", -2: "MLCC_E_OOM", -3: "MLCC_E_GS_NOCONV",
           -4: "MLCC_E_ES_NOCONV", -5: "MLCC_E_COMPLEX_ROOT", -6: "MLCC_E_NAN",
           -8: "MLCC_E_CUDA", -9: "MLCC_E_STATE"}
@@ -27,7 +27,7 @@ EXPORTS = ["mlcc_default_options", "mlcc_ctx_create", "mlcc_ctx_destroy", "mlcc_
            "mlcc_system_destroy", "mlcc_system_info", "mlcc_orbital_order", "mlcc_t1_transform",
            "mlcc_fock_t1", "mlcc_omega", "mlcc_ground_state", "mlcc_jacobian_prepare",
            "mlcc_sigma", "mlcc_excited_states", "mlcc_solve", "mlcc_launch_count",
-           "mlcc_fock_t1_noalloc"]
+           "mlcc_fock_t1_noalloc", "mlcc_gemm"]
 
 
 class mlcc_problem(ctypes.Structure):
@@ -46,7 +46,8 @@ class mlcc_options(ctypes.Structure):
                 ("diis_dim", c_int32), ("max_subspace", c_int32), ("precision", c_int32),
                 ("refine_fp64", c_int32), ("gs_precision", c_int32), ("gs_tol", c_double),
                 ("gs_energy_tol", c_double), ("es_res_tol", c_double),
-                ("es_omega_tol", c_double), ("lowp_res_tol", c_double)]
+                ("es_omega_tol", c_double), ("lowp_res_tol", c_double),
+                ("refine_precision", c_int32), ("reserved", c_int32)]
 
 
 class mlcc_gs_info(ctypes.Structure):
@@ -90,6 +91,8 @@ def load():
         "mlcc_kernel_time": (c_int, [P, c_char_p, POINTER(c_int64), D, D]),
         "mlcc_launch_count": (c_int64, []),
         "mlcc_fock_t1_noalloc": (c_int, [c_int32, c_int32, c_int32, P, P, P, P, P, P]),
+        "mlcc_gemm": (c_int, [P, c_int32, c_int32, c_int64, c_int64, c_int64, c_double, P, c_int64,
+                              P, c_int64, c_double, P, c_int64, c_int32]),
         "mlcc_system_create": (c_int, [P, POINTER(mlcc_problem), P, P, POINTER(c_void_p)]),
         "mlcc_system_destroy": (None, [P]),
         "mlcc_system_info": (c_int, [P, POINTER(mlcc_dims)]),
@@ -172,6 +175,19 @@ class Context:
         n, ms, fl = c_int64(), c_double(), c_double()
         _check(load().mlcc_kernel_time(self.handle, family.encode(), byref(n), byref(ms), byref(fl)))
         return n.value, ms.value, fl.value
+
+    def gemm(self, a, b, c, alpha=1.0, beta=0.0, trans_a=False, trans_b=False,
+             precision=MLCC_FP64):
+        """mlcc_gemm on contiguous row-major float64 device tensors:
+        c = alpha op(a) op(b) + beta c."""
+        M, N = c.shape
+        K = a.shape[0] if trans_a else a.shape[1]
+        self.before()
+        _check(load().mlcc_gemm(self.handle, int(trans_a), int(trans_b), M, N, K, alpha, _ptr(a),
+                                a.shape[1], _ptr(b), b.shape[1], beta, _ptr(c), c.shape[1],
+                                precision))
+        self.after()
+        return c
 
     def close(self):
         if self.handle:

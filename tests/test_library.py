@@ -36,7 +36,8 @@ def test_default_options(lib):
     from paper_2006_05226_gb300 import mlcc
     o = mlcc.default_options()
     assert o.n_roots == 3 and o.diis_dim == 8 and o.precision == mlcc.MLCC_FP64
-    assert o.gs_tol == 1e-11 and o.es_res_tol == 1e-8
+    assert o.gs_tol == 1e-11 and o.es_res_tol == 1e-8 and o.lowp_res_tol == 1e-4
+    assert o.refine_precision == mlcc.MLCC_FP64 and o.reserved == 0
 
 
 def test_binding_struct_sizes_match_header(lib):
@@ -45,7 +46,7 @@ def test_binding_struct_sizes_match_header(lib):
     # layouts fixed by include/mlcc.h (natural alignment, no packing)
     assert ctypes.sizeof(mlcc.mlcc_problem) == 24
     assert ctypes.sizeof(mlcc.mlcc_dims) == 56
-    assert ctypes.sizeof(mlcc.mlcc_options) == 72
+    assert ctypes.sizeof(mlcc.mlcc_options) == 80
     assert ctypes.sizeof(mlcc.mlcc_gs_info) == 32
     assert ctypes.sizeof(mlcc.mlcc_es_info) == 32
 
