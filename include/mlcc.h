@@ -185,7 +185,7 @@ int64_t mlcc_launch_count(void);
      op(B) [K][N] (B[k*ldb+n], or B[n*ldb+k] if trans_b), C [M][N] (C[m*ldc+n]).
    precision MLCC_FP64 runs on the binary64 FMA units; MLCC_BF16, MLCC_BF16X3, MLCC_BF16X6
    and MLCC_FP64E on the tcgen05 tensor cores as described at mlcc_precision (no fallback:
-   a tensor-core precision with M or N below 64 for MLCC_FP64E, or K above 2^20, returns
+   a tensor-core precision with M or N below 16 for MLCC_FP64E, or K above 2^20, returns
    MLCC_E_ARG). Scratch is allocated for the call and freed before it returns; the call
    synchronises the stream. This is the contraction engine under every Cholesky-rank
    step of sigma and Omega, exposed for checking its arithmetic. */

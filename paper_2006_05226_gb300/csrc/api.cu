@@ -461,7 +461,7 @@ mlcc_status mlcc_gemm(mlcc_ctx* ctx, int32_t trans_a, int32_t trans_b, int64_t M
       gemm_f64(g, ws, s, ctx->sm_count);
     } else if (precision == MLCC_FP64E) {
       MLCC_REQUIRE(gemm_emu(g, ws, s, ctx->sm_count, err),
-                   "mlcc_gemm: shape outside the MLCC_FP64E tensor-core path (M, N >= 64, K <= 2^20)");
+                   "mlcc_gemm: shape outside the MLCC_FP64E tensor-core path (M, N >= 16, K <= 2^20)");
     } else {
       MLCC_REQUIRE(K > 0 && gemm_tc(g, precision, ws, s, ctx->sm_count, err),
                    "mlcc_gemm: shape outside the tensor-core path");

@@ -2,6 +2,7 @@
 // ground-state solver (Sec. 2.1) and the Davidson solver for the lowest right
 // eigenpairs of the non-symmetric Jacobian (Sec. 2.1, excitation energies).
 #include "system.cuh"
+#include "fp_convert.cuh"
 #include "small_eig.h"
 
 #include <algorithm>
@@ -55,9 +56,11 @@ __global__ void k_precond_singles(const double* r, const double* eps, int no, in
     d[k] = r[k] / den;
   }
 }
+__device__ __forceinline__ float epsf(const double* eps, int p) { return d2f_bits(eps[p]); }
 __global__ void k_precond_doubles(const double* r, const double* eps, int no, int sv, int so,
                                   double w, double* d) {
   __shared__ double tile[32][33];
+  const float wf = float(w);
   const int64_t dS = int64_t(sv) * so;
   const int64_t r0 = int64_t(blockIdx.y) * 32, c0 = int64_t(blockIdx.x) * 32;
   for (int y = threadIdx.y; y < 32; y += blockDim.y) {
@@ -70,9 +73,11 @@ __global__ void k_precond_doubles(const double* r, const double* eps, int no, in
     if (row >= dS || col >= dS) continue;
     const int a = int(row / so), i = int(row - int64_t(a) * so);
     const int b = int(col / so), j = int(col - int64_t(b) * so);
-    double den = w - (eps[no + a] - eps[i] + eps[no + b] - eps[j]);
-    if (fabs(den) < 1e-8) den = den < 0 ? -1e-8 : 1e-8;
-    d[row * dS + col] = 0.5 * (r[row * dS + col] + tile[threadIdx.x][y]) / den;
+    // binary32 arithmetic: the preconditioner only steers the expansion direction
+    float den = wf - ((epsf(eps, no + a) - epsf(eps, i)) + (epsf(eps, no + b) - epsf(eps, j)));
+    if (fabsf(den) < 1e-8f) den = den < 0.0f ? -1e-8f : 1e-8f;
+    const float v = 0.5f * (d2f_bits(r[row * dS + col]) + d2f_bits(tile[threadIdx.x][y]));
+    d[row * dS + col] = f2d_bits(__fdividef(v, den));
   }
 }
 // R_k -= w_k X_k
@@ -297,8 +302,14 @@ mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out
     info->iterations = it;
     info->converged = conv ? 1 : 0;
   }
-  // the Jacobian is taken at the returned amplitudes
-  timed(S, "jacobian_prepare", 0.0, [&] { jacobian_prepare(S, t1_out, x2_out); });
+  // the Jacobian is taken at the returned amplitudes, in the binary64-class precision of
+  // the last phase (the refinement precision after a split-precision phase)
+  const int prep = is_split_precision(phase_prec) ? opt->refine_precision : phase_prec;
+  {
+    LowpScope lowp(prep == MLCC_FP64 ? 0 : prep, S->tc_err);
+    timed(S, "jacobian_prepare", 0.0, [&] { jacobian_prepare(S, t1_out, x2_out); });
+  }
+  if (prep != MLCC_FP64) check_tc_error(S);
   MLCC_CUDA(cudaStreamSynchronize(s));
   return conv ? MLCC_OK : MLCC_E_GS_NOCONV;
 }

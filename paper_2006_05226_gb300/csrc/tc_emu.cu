@@ -30,6 +30,7 @@ constexpr int EMU_S = 7;              // digits per operand element
 constexpr int EMU_CH = 16;            // K blocks of 64 per exact fp32 chunk (1024 products)
 constexpr int EMU_NONFINITE = 1 << 30;
 constexpr int64_t EMU_MAX_K = int64_t(1) << 20;   // keeps the 64-bit combination exact
+constexpr int64_t EMU_MIN_MN = 16;                 // narrower products stay on the FMA units
 
 __device__ __forceinline__ unsigned long long abs_bits(double x) {
   return static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7FFFFFFFFFFFFFFFull;
@@ -147,8 +148,10 @@ struct EmuRed {
   const int* ea;           // [M] row exponents of A
   const int* eb;           // [Nw] row exponents of B (this panel)
   double alpha, beta;
-  double* C;               // [M][ldc], this panel's first column
+  double* C;               // [M][ldc]
   int64_t ldc;
+  int64_t n0;              // first output column of the panel
+  int64_t nb, sCb;         // batched output columns (nb > 0): column b nb + c at C + b sCb + c
 };
 // C = alpha 2^(E_m + E_n - 14 - 8 (S - 1)) T + beta C with T = sum_g 2^(8 (S - 1 - g)) G_g,
 // G_g the integer sum of group g's chunks; T is held exactly as hi 2^32 + lo and rounded once.
@@ -175,7 +178,12 @@ __global__ void k_emu_reduce(EmuRed r) {
       v = fma(static_cast<double>(hi), 4294967296.0, static_cast<double>(lo));
       v = ldexp(v, ea + eb - 14 - 8 * (EMU_S - 1));
     }
-    double* c = r.C + m * r.ldc + n;
+    int64_t col = r.n0 + n, cb = 0;
+    if (r.nb > 0) {
+      cb = col / r.nb;
+      col -= cb * r.nb;
+    }
+    double* c = r.C + cb * r.sCb + m * r.ldc + col;
     double out = (r.alpha == 0.0) ? 0.0 : r.alpha * v;
     if (r.beta != 0.0) out += r.beta * *c;
     *c = out;
@@ -242,17 +250,22 @@ namespace {
 struct EmuPlan {
   GOp a, b;
   int64_t M, N, Kp, Np;
+  int64_t nb, sCb;   // batched output columns (a batch sharing A flattened along N)
   int gstart[TC_EMU_MAX_S + 1];
   int nch;
 };
 // shapes, chunk table and output panel width; false when the emulation cannot run
 bool emu_plan(const Gemm& g, const Arena& ws, EmuPlan& P) {
-  const bool flatten = !g.reduce && g.batch > 1;
-  if (flatten && !(g.sB == 0 && g.sC == g.M * g.ldc)) return false;
+  const bool batched = !g.reduce && g.batch > 1;
+  const bool flatten = batched && g.sB == 0 && g.sC == g.M * g.ldc;
+  const bool flat_n = batched && !flatten && g.sA == 0;
+  if (batched && !flatten && !flat_n) return false;
   const int64_t M = flatten ? g.M * g.batch : g.M;
   const int64_t Ktot = g.reduce ? g.K * g.batch : g.K;
-  const int64_t N = g.N;
-  if (M < 64 || N < 64 || Ktot < 1 || Ktot > EMU_MAX_K) return false;
+  const int64_t N = flat_n ? g.N * g.batch : g.N;
+  if (M < EMU_MIN_MN || N < EMU_MIN_MN || Ktot < 1 || Ktot > EMU_MAX_K) return false;
+  P.nb = flat_n ? g.N : 0;
+  P.sCb = flat_n ? g.sC : 0;
   const int64_t Kp = pad64(Ktot), kbp = Kp / 64;
   for (int q = 0; q <= TC_EMU_MAX_S; ++q) P.gstart[q] = 0;
   for (int q = 0; q < EMU_S; ++q) P.gstart[q + 1] = P.gstart[q] + int(((q + 1) * kbp + EMU_CH - 1) / EMU_CH);
@@ -276,8 +289,8 @@ bool emu_plan(const Gemm& g, const Arena& ws, EmuPlan& P) {
   b = a;
   b.base = g.B;
   b.R = N;
-  b.Mrow = N;
-  b.sRow = 0;
+  b.Mrow = flat_n ? g.N : N;
+  b.sRow = flat_n ? g.sB : 0;
   b.sK = g.reduce ? g.sB : 0;
   b.ld = g.ldb;
   b.tr = g.tb ? 0 : 1;
@@ -330,8 +343,11 @@ bool gemm_emu(const Gemm& g, Arena& ws, cudaStream_t s, int sm_count, int* err) 
     r.eb = eb + n0;
     r.alpha = g.alpha;
     r.beta = g.beta;
-    r.C = g.C + n0;
+    r.C = g.C;
     r.ldc = g.ldc;
+    r.n0 = n0;
+    r.nb = P.nb;
+    r.sCb = P.sCb;
     k_emu_reduce<<<grid_for(M * nw, 256), 256, 0, s>>>(r);
     MLCC_CHECK_LAUNCH();
   }

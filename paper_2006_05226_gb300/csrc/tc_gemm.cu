@@ -106,6 +106,9 @@ struct TcParams {
   int emu_gstart[EMU_MAX_S + 1];   // first chunk of group g; emu_gstart[emu_S] = chunks
   float* part32;
   int64_t ldp;
+  // batched output columns (nb > 0): column b * nb + c of the product lands at
+  // C + b * sCb + row * ldc + c (a batch of products that share A, flattened along N)
+  int64_t nb, sCb;
 };
 
 __global__ void __launch_bounds__(THREADS, 1)
@@ -243,6 +246,11 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
               if (n0 + c0 + j < p.N) prow[j] = __uint_as_float(r[j]);
           }
         } else if (row < p.M) {
+          int64_t cb = 0, cc = n0 + c0;
+          if (p.nb > 0) {
+            cb = cc / p.nb;
+            cc -= cb * p.nb;
+          }
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int64_t col = n0 + c0 + j;
@@ -250,9 +258,14 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
               if (part) {
                 crow[col] = double(__uint_as_float(r[j]));
               } else {
+                double* cp = p.nb > 0 ? p.C + cb * p.sCb + row * p.ldc + cc : crow + col;
                 const double v = p.alpha * double(__uint_as_float(r[j]));
-                crow[col] = (p.beta == 0.0) ? v : v + p.beta * crow[col];
+                *cp = (p.beta == 0.0) ? v : v + p.beta * *cp;
               }
+            }
+            if (p.nb > 0 && ++cc == p.nb) {
+              cc = 0;
+              ++cb;
             }
           }
         }
@@ -413,6 +426,8 @@ void tc_gemm_emu_launch(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t 
   for (int g = 0; g <= EMU_MAX_S; ++g) p.emu_gstart[g] = g <= S ? gstart[g] : nch;
   p.part32 = part;
   p.ldp = ldp;
+  p.nb = 0;
+  p.sCb = 0;
   const int64_t tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
   MLCC_REQUIRE(tn < 65536, "tc_gemm_emu: grid too large");
   const dim3 grid{unsigned(tm), unsigned(tn), unsigned(nch)};
@@ -424,7 +439,7 @@ void tc_gemm_emu_launch(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t 
 // splits > 1 divides K over CTAs; partial must then hold splits * M * N doubles.
 void tc_gemm_split(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t M, int64_t N, int64_t Kt,
                    double* C, int64_t ldc, double alpha, double beta, int* err, bool m_fast, int splits,
-                   double* partial, cudaStream_t s) {
+                   double* partial, cudaStream_t s, int64_t nb = 0, int64_t sCb = 0) {
   MLCC_REQUIRE(Kt % BK == 0, "tc_gemm: K must be a multiple of 64");
   MLCC_REQUIRE(M < (int64_t(1) << 31) && N < (int64_t(1) << 31), "tc_gemm: size too large");
   ensure_smem_attr();
@@ -452,6 +467,9 @@ void tc_gemm_split(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t M, in
   for (int g = 0; g <= EMU_MAX_S; ++g) p.emu_gstart[g] = 0;
   p.part32 = nullptr;
   p.ldp = 0;
+  p.nb = nb;
+  p.sCb = sCb;
+  MLCC_REQUIRE(nb == 0 || splits == 1, "tc_gemm: batched output columns without split-K");
   const int64_t tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
   dim3 grid = m_fast ? dim3(unsigned(tm), unsigned(tn), unsigned(splits))
                      : dim3(unsigned(tn), unsigned(tm), unsigned(splits));
@@ -577,11 +595,15 @@ static const __nv_bfloat16* get_operand(const GOp& o, int side, bool cacheable, 
 // nothing) for other shapes or when the workspace is too small.
 bool gemm_tc(const Gemm& g, int precision, Arena& ws, cudaStream_t s, int sm_count, int* err) {
   if (precision == MLCC_FP64E) return gemm_emu(g, ws, s, sm_count, err);
-  const bool flatten = !g.reduce && g.batch > 1;
-  if (flatten && !(g.sB == 0 && g.sC == g.M * g.ldc)) return false;
+  // a batch sharing B with stacked outputs flattens along M; a batch sharing A flattens
+  // along N (batched output columns)
+  const bool batched = !g.reduce && g.batch > 1;
+  const bool flatten = batched && g.sB == 0 && g.sC == g.M * g.ldc;
+  const bool flat_n = batched && !flatten && g.sA == 0;
+  if (batched && !flatten && !flat_n) return false;
   const int64_t M = flatten ? g.M * g.batch : g.M;
   const int64_t Ktot = g.reduce ? g.K * g.batch : g.K;
-  const int64_t N = g.N;
+  const int64_t N = flat_n ? g.N * g.batch : g.N;
   const SplitPattern pt = pattern(precision);
   const int64_t Kp = pad64(Ktot), Kt = pt.S * Kp;
   const size_t need = size_t(M + N) * Kt * 2 + 4 * 256;
@@ -603,8 +625,8 @@ bool gemm_tc(const Gemm& g, int precision, Arena& ws, cudaStream_t s, int sm_cou
   GOp b = a;
   b.base = g.B;
   b.R = N;
-  b.Mrow = N;
-  b.sRow = 0;
+  b.Mrow = flat_n ? g.N : N;
+  b.sRow = flat_n ? g.sB : 0;
   b.sK = g.reduce ? g.sB : 0;
   b.ld = g.ldb;
   b.tr = g.tb ? 0 : 1;
@@ -614,13 +636,14 @@ bool gemm_tc(const Gemm& g, int precision, Arena& ws, cudaStream_t s, int sm_cou
   const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
   const int64_t kblocks = Kt / BK;
   int64_t splits = 1;
-  if (tiles < 2LL * std::max(sm_count, 1)) {
+  if (!flat_n && tiles < 2LL * std::max(sm_count, 1)) {
     splits = std::min<int64_t>((2LL * std::max(sm_count, 1) + tiles - 1) / tiles, kblocks / 4);
     splits = std::max<int64_t>(splits, 1);
     while (splits > 1 && size_t(splits) * M * N * 8 + ws.mark() + (size_t(1) << 20) > ws.capacity()) splits /= 2;
   }
   double* partial = splits > 1 ? ws.get<double>(size_t(splits) * M * N) : nullptr;
-  tc_gemm_split(Abf, Bbf, M, N, Kt, g.C, g.ldc, g.alpha, g.beta, err, true, int(splits), partial, s);
+  tc_gemm_split(Abf, Bbf, M, N, Kt, g.C, g.ldc, g.alpha, g.beta, err, true, int(splits), partial, s,
+                flat_n ? g.N : 0, flat_n ? g.sC : 0);
   return true;
 }
 

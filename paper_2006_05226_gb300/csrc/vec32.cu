@@ -10,6 +10,7 @@
 // partial sums are widened to binary64 for the cross-thread reduction and for the
 // alpha / beta update of the output, so no binary64 arithmetic runs per element.
 #include "internal.cuh"
+#include "fp_convert.cuh"
 
 #include <algorithm>
 
@@ -17,27 +18,11 @@ namespace mlcc {
 
 namespace {
 
-__device__ __forceinline__ float d2f(double x) {
-  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
-  const unsigned hi = unsigned(b >> 32), lo = unsigned(b);
-  const int e = int((hi >> 20) & 0x7FF) - 896;   // binary32 biased exponent
-  unsigned r = hi & 0x80000000u;
-  if (e >= 255) r |= 0x7F800000u;
-  else if (e > 0) r |= (unsigned(e) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
-  return __uint_as_float(r);
-}
-__device__ __forceinline__ double f2d(float f) {
-  const unsigned u = __float_as_uint(f);
-  const int e = int((u >> 23) & 0xFF);
-  unsigned long long r = static_cast<unsigned long long>(u & 0x80000000u) << 32;
-  const unsigned long long m = static_cast<unsigned long long>(u & 0x7FFFFFu) << 29;
-  if (e == 255) r |= 0x7FF0000000000000ull | m;
-  else if (e > 0) r |= (static_cast<unsigned long long>(e + 896) << 52) | m;
-  return __longlong_as_double(static_cast<long long>(r));
-}
+__device__ __forceinline__ float d2f(double x) { return d2f_bits(x); }
+__device__ __forceinline__ double f2d(float f) { return f2d_bits(f); }
 
 constexpr int DOT32_BLOCKS = 1216;   // 8 blocks of 256 threads per SM of a GB300
-constexpr int DOT32_CHUNK = 8;
+constexpr int DOT32_CHUNK = 16;   // x-vectors per pass over the y-vectors
 
 // partial[k][blk]: the block's share of x_k . y, DOT32_CHUNK vectors x_k per pass over y
 __global__ void k_dots32(const double* x, int64_t ldx, int nx, const double* y, int64_t n, double* partial) {
@@ -71,9 +56,10 @@ __global__ void k_dots32(const double* x, int64_t ldx, int nx, const double* y, 
 }
 
 // partial[(k * NY + j)][blk] for DOT32_CHUNK x-vectors per pass and NY <= 4 y-vectors
-template <int NY>
+template <int NY, int CH = (NY >= 3 ? 8 : DOT32_CHUNK)>   // CH * NY accumulators per thread
 __global__ void k_dots_block32(const double* x, int64_t ldx, int nx, const double* y, int64_t ldy, int64_t n,
                                double* partial) {
+  constexpr int DOT32_CHUNK = CH;
   __shared__ double red[DOT32_CHUNK * NY][256 / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int k0 = 0; k0 < nx; k0 += DOT32_CHUNK) {

@@ -154,7 +154,7 @@ def test_nonfinite_rows_give_nan(ctx):
 
 def test_shapes_outside_the_path_are_rejected(ctx):
     from paper_2006_05226_gb300 import mlcc
-    A = np.ones((32, 100))
+    A = np.ones((8, 100))
     B = np.ones((100, 256))
     with pytest.raises(mlcc.MLCCError) as e:
         _gemm(ctx, A, B, False, False, mlcc.MLCC_FP64E)
