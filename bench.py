@@ -272,8 +272,10 @@ def main():
     elapsed = ev0.elapsed_time(ev1) / 1e3
     launches = mlcc.launch_count() - launches0
     fams = {f: ctx.kernel_time(f) for f in ("rank_gemm_tc", "rank_gemm_f64e", "rank_gemm_f64")}
-    phases = {f: ctx.kernel_time(f) for f in ("gs_omega", "jacobian_prepare", "sigma", "dav_update_G",
-                                              "dav_ritz", "dav_orthonormalise")}
+    phases = {f: ctx.kernel_time(f) for f in ("gs_omega", "jacobian_prepare", "sigma", "sigma_singles",
+                                              "sigma_doubles_to_singles", "sigma_cc2_doubles",
+                                              "sigma_ccsd_rows", "dav_update_G", "dav_ritz",
+                                              "dav_orthonormalise")}
     breakdown = {f: {"calls": n, "total_ms": ms} for f, (n, ms, _) in phases.items() if n}
     ctx.kernel_timing(False)
     clk = clocks.stop()

@@ -168,7 +168,8 @@ const char* mlcc_last_error(void);
    on tcgen05 tensor cores in a split-bfloat16 precision), "rank_gemm_f64e" (the same
    GEMMs in MLCC_FP64E) and "rank_gemm_f64" (the same GEMMs on the binary64 FMA units);
    and phases of the solvers: "gs_omega" (one ground-state residual), "jacobian_prepare",
-   "sigma" (one Jacobian transformation), "dav_update_G" (subspace matrix), "dav_ritz"
+   "sigma" (one Jacobian transformation; inside it "sigma_singles", "sigma_doubles_to_singles",
+   "sigma_cc2_doubles", "sigma_ccsd_rows"), "dav_update_G" (subspace matrix), "dav_ritz"
    (Ritz vectors and residuals), "dav_orthonormalise" (Gram-Schmidt of new directions).
    Phases contain the GEMM families launched inside them.
    mlcc_kernel_time returns launches, summed milliseconds and summed algorithmic flops

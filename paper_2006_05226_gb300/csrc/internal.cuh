@@ -189,6 +189,17 @@ void dots32(const double* x, int64_t ldx, int nx, const double* y, int64_t n, do
 void dots_block32(const double* x, int64_t ldx, int nx, const double* y, int64_t ldy, int ny,
                   int64_t n, double* out_dev, Arena& ws, cudaStream_t s);
 bool skinny32(const Gemm& g, cudaStream_t s);
+// binary32 vector storage: dot products, C = alpha op(A) B + beta C with B [K][N] binary32
+// and C binary32 (c_f32) or binary64 (M <= 16, K <= 64), conversions, scaling
+void dots_f32(const float* x, int64_t ldx, int nx, const float* y, int64_t n, double* out_dev,
+              Arena& ws, cudaStream_t s);
+void dots_block_f32(const float* x, int64_t ldx, int nx, const float* y, int64_t ldy, int ny,
+                    int64_t n, double* out_dev, Arena& ws, cudaStream_t s);
+void combine_f32(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, bool ta, const float* B,
+                 int64_t ldb, void* C, bool c_f32, int64_t ldc, double alpha, double beta, cudaStream_t s);
+void cvt_d2f(const double* x, float* y, int64_t n, cudaStream_t s);
+void cvt_f2d(const float* x, double* y, int64_t n, cudaStream_t s);
+void scale_f32(float* x, int64_t n, double a, cudaStream_t s);
 void copy_d2h(double* h, const double* d, int64_t n, cudaStream_t s);
 void copy_h2d(double* d, const double* h, int64_t n, cudaStream_t s);
 

@@ -639,6 +639,8 @@ void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision) {
   const double* Lov = S->Lt + no;                     // Lt^J[I][no+A]
   const double* Loo = S->Lt;                          // Lt^J[I][K]
   Scope sc(S->ws);
+  PhaseMarks phase(S);
+  phase.mark("sigma_singles");
   // Xc^J = Lt^J_AB c_BI (the steepest CCS contraction) and the tangent of the
   // virtual-occupied block dLt^J_AI = Xc^J_AI - c_AK Lt^J_KI
   double* Xc = S->ws.get<double>(size_t(nj) * vo);
@@ -672,6 +674,7 @@ void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision) {
       double* dfv = S->ws.get<double>(size_t(dS));
       k_to_fv<<<nblk(dS), 256, 0, s>>>(dF, so, sv, dfv);
       MLCC_CHECK_LAUNCH();
+      phase.mark("sigma_doubles_to_singles");
       // doubles -> singles
       double* uc = S->ws.get<double>(size_t(S->nd));
       make_u(S, c2, uc);
@@ -685,6 +688,7 @@ void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision) {
       // (u(c)^{bc}_{ij} Lt^K_jc) Lt^K_Ab  and  - (u(c)^{ab}_{jk} Lt^K_kb) Lt^K_jI
       bgemm(S, nv, so, sv, 1.0, Lvv, n, nn, false, Zc, so, dS, false, 1.0, s1, no, 0, true);
       bgemm(S, sv, no, so, -1.0, Zc, so, dS, false, Loo, n, nn, false, 1.0, s1, no, 0, true);
+      phase.mark("sigma_cc2_doubles");
       // CC2 doubles on P_S
       double* V = S->ws.get<double>(size_t(nj) * dS);
       {
@@ -697,6 +701,7 @@ void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision) {
       k_sigma2_cc2<<<grd, blk, 0, s>>>(W, c2, S->eps, no, sv, so, tv, to, s2);
       MLCC_CHECK_LAUNCH();
     }
+    phase.mark("sigma_ccsd_rows");
     // CCSD rows: tangent of the CCSD residual around the cached values
     if (to > 0 && tv > 0) {
       Scope sb(S->ws);

@@ -45,20 +45,24 @@ __global__ void k_qn(const double* t1, const double* tT, const double* om1, cons
 }
 
 // Davidson preconditioner: d = (w - eps_mu)^-1 r, doubles symmetrised over (ai) <-> (bj)
-__global__ void k_precond_singles(const double* r, const double* eps, int no, int nv, double w,
-                                  double* d) {
+__device__ __forceinline__ void st_out(double* p, double v) { *p = v; }
+__device__ __forceinline__ void st_out(float* p, double v) { *p = d2f_bits(v); }
+__device__ __forceinline__ void st_out32(double* p, float v) { *p = f2d_bits(v); }
+__device__ __forceinline__ void st_out32(float* p, float v) { *p = v; }
+template <typename T>
+__global__ void k_precond_singles(const double* r, const double* eps, int no, int nv, double w, T* d) {
   const int64_t n1 = int64_t(nv) * no;
   for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < n1;
        k += int64_t(gridDim.x) * blockDim.x) {
     const int a = int(k / no), i = int(k - int64_t(a) * no);
     double den = w - (eps[no + a] - eps[i]);
     if (fabs(den) < 1e-8) den = den < 0 ? -1e-8 : 1e-8;
-    d[k] = r[k] / den;
+    st_out(d + k, r[k] / den);
   }
 }
 __device__ __forceinline__ float epsf(const double* eps, int p) { return d2f_bits(eps[p]); }
-__global__ void k_precond_doubles(const double* r, const double* eps, int no, int sv, int so,
-                                  double w, double* d) {
+template <typename T>
+__global__ void k_precond_doubles(const double* r, const double* eps, int no, int sv, int so, double w, T* d) {
   __shared__ double tile[32][33];
   const float wf = float(w);
   const int64_t dS = int64_t(sv) * so;
@@ -77,7 +81,7 @@ __global__ void k_precond_doubles(const double* r, const double* eps, int no, in
     float den = wf - ((epsf(eps, no + a) - epsf(eps, i)) + (epsf(eps, no + b) - epsf(eps, j)));
     if (fabsf(den) < 1e-8f) den = den < 0.0f ? -1e-8f : 1e-8f;
     const float v = 0.5f * (d2f_bits(r[row * dS + col]) + d2f_bits(tile[threadIdx.x][y]));
-    d[row * dS + col] = f2d_bits(__fdividef(v, den));
+    st_out32(d + row * dS + col, __fdividef(v, den));
   }
 }
 // R_k -= w_k X_k
@@ -317,20 +321,105 @@ mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out
 // =================================================================================
 // Davidson
 namespace {
+// Basis and sigma-vectors of the Davidson solver. In a split-precision phase they are
+// stored in binary32 (es = 4: half the HBM traffic of every subspace pass; their
+// sigma-vectors carry ~1e-7 relative errors anyway); in a binary64 phase in binary64.
 struct DavState {
   mlcc_system* S;
   int64_t dim;
   int maxsub;
-  double* B;   // [maxsub][dim]
-  double* Sg;  // [maxsub][dim]
+  char* Bp;    // basis [maxsub][dim]
+  char* Sp;    // sigma-vectors [maxsub][dim]
+  int es = 8;  // bytes per stored element
   int m = 0;
   std::vector<double> G;  // [maxsub][maxsub] host, G[i][j] = B_i . S_j
+  void* B(int64_t k) const { return Bp + k * dim * es; }
+  void* Sg(int64_t k) const { return Sp + k * dim * es; }
+  bool f32() const { return es == 4; }
 };
+
+__global__ void k_set_f(float* v, int64_t i, float x) { v[i] = x; }
+
+// out[k * ny + j] = x_k . y_j for stored vectors x_k, y_j (k < nx, j < ny <= 4)
+void vdots_block(DavState& D, const void* x, int nx, const void* y, int ny, double* out) {
+  mlcc_system* S = D.S;
+  if (D.f32())
+    dots_block_f32(static_cast<const float*>(x), D.dim, nx, static_cast<const float*>(y), D.dim, ny, D.dim, out,
+                   S->ws, S->ctx->stream);
+  else
+    dots_block(static_cast<const double*>(x), D.dim, nx, static_cast<const double*>(y), D.dim, ny, D.dim, out,
+               S->ws, S->ctx->stream);
+}
+// out[k] = x_k . y
+void vdots(DavState& D, const void* x, int nx, const void* y, double* out) {
+  mlcc_system* S = D.S;
+  if (D.f32())
+    dots_f32(static_cast<const float*>(x), D.dim, nx, static_cast<const float*>(y), D.dim, out, S->ws,
+             S->ctx->stream);
+  else
+    dots(static_cast<const double*>(x), D.dim, nx, static_cast<const double*>(y), D.dim, out, S->ws, S->ctx->stream);
+}
+// C_i = alpha sum_k op(A)[i][k] V_k + beta C_i (i < M, k < K) with V stored vectors and C
+// stored vectors (c_store) or binary64 vectors; A [M][K] (or [K][M] if ta), lda its row length
+void vcombine(DavState& D, int M, int K, const double* A, int lda, bool ta, const void* V, void* C, bool c_store,
+              double alpha, double beta) {
+  mlcc_system* S = D.S;
+  cudaStream_t s = S->ctx->stream;
+  if (!D.f32()) {
+    Gemm g;
+    g.ta = ta;
+    g.M = M; g.N = D.dim; g.K = K;
+    g.A = A; g.lda = lda; g.B = static_cast<const double*>(V); g.ldb = D.dim;
+    g.C = static_cast<double*>(C); g.ldc = D.dim;
+    g.alpha = alpha; g.beta = beta;
+    gemm_f64(g, S->ws, s, S->ctx->sm_count);
+    return;
+  }
+  const size_t ces = c_store ? 4 : 8;
+  for (int i0 = 0; i0 < M; i0 += 16) {
+    const int mi = std::min(16, M - i0);
+    for (int k0 = 0; k0 < K || k0 == 0; k0 += 64) {
+      const int kk = std::min(64, K - k0);
+      const double* Ab = ta ? A + int64_t(k0) * lda + i0 : A + int64_t(i0) * lda + k0;
+      combine_f32(mi, D.dim, std::max(kk, 0), Ab, lda, ta, static_cast<const float*>(V) + int64_t(k0) * D.dim, D.dim,
+                  static_cast<char*>(C) + size_t(i0) * D.dim * ces, c_store, D.dim, alpha, k0 == 0 ? beta : 1.0, s);
+      if (K <= 0) break;
+    }
+  }
+}
+void vscale(DavState& D, void* v, double a) {
+  if (D.f32()) {
+    scale_f32(static_cast<float*>(v), D.dim, a, D.S->ctx->stream);
+  } else {
+    k_scale<<<nblk(D.dim), 256, 0, D.S->ctx->stream>>>(static_cast<double*>(v), D.dim, a);
+    MLCC_CHECK_LAUNCH();
+  }
+}
+void vcopy(DavState& D, void* dst, const void* src, int64_t count) {
+  if (dst == src || count <= 0) return;
+  MLCC_CUDA(cudaMemcpyAsync(dst, src, size_t(count) * D.dim * D.es, cudaMemcpyDeviceToDevice, D.S->ctx->stream));
+}
 }  // namespace
 
 static void sigma_batch(mlcc_system* S, const double* C, double* Sg, int nvec, int64_t dim, int prec) {
   for (int k = 0; k < nvec; ++k)
     timed(S, "sigma", 0.0, [&] { sigma_eval(S, C + int64_t(k) * dim, Sg + int64_t(k) * dim, prec); });
+  if (prec != MLCC_FP64) check_tc_error(S);
+}
+// sigma-vectors of the stored vectors [k0, k0 + nvec); binary32 storage goes through the
+// binary64 buffers tc (trial vector) and ts (sigma-vector)
+static void sigma_stored(DavState& D, int k0, int nvec, int prec, double* tc, double* ts) {
+  mlcc_system* S = D.S;
+  if (!D.f32()) {
+    sigma_batch(S, static_cast<const double*>(D.B(k0)), static_cast<double*>(D.Sg(k0)), nvec, D.dim, prec);
+    return;
+  }
+  cudaStream_t s = S->ctx->stream;
+  for (int k = 0; k < nvec; ++k) {
+    cvt_f2d(static_cast<const float*>(D.B(k0 + k)), tc, D.dim, s);
+    timed(S, "sigma", 0.0, [&] { sigma_eval(S, tc, ts, prec); });
+    cvt_d2f(ts, static_cast<float*>(D.Sg(k0 + k)), D.dim, s);
+  }
   if (prec != MLCC_FP64) check_tc_error(S);
 }
 
@@ -349,13 +438,13 @@ static void update_G_body(DavState& D, int m0) {
   for (int k0 = m0; k0 < D.m; k0 += 4) {
     const int nk = std::min(4, D.m - k0);
     // B_i . S_k for i < m
-    dots_block(D.B, D.dim, D.m, D.Sg + int64_t(k0) * D.dim, D.dim, nk, D.dim, out, S->ws, s);
+    vdots_block(D, D.B(0), D.m, D.Sg(k0), nk, out);
     copy_d2h(h.data(), out, int64_t(D.m) * nk, s);
     for (int i = 0; i < D.m; ++i)
       for (int j = 0; j < nk; ++j) D.G[size_t(i) * D.maxsub + k0 + j] = h[size_t(i) * nk + j];
     // B_k . S_j for j < m0
     if (m0 > 0) {
-      dots_block(D.Sg, D.dim, m0, D.B + int64_t(k0) * D.dim, D.dim, nk, D.dim, out, S->ws, s);
+      vdots_block(D, D.Sg(0), m0, D.B(k0), nk, out);
       copy_d2h(h.data(), out, int64_t(m0) * nk, s);
       for (int j = 0; j < m0; ++j)
         for (int q = 0; q < nk; ++q) D.G[size_t(k0 + q) * D.maxsub + j] = h[size_t(j) * nk + q];
@@ -371,60 +460,47 @@ static void block_project(DavState& D, int nv) {
 }
 static void block_project_body(DavState& D, int nv) {
   mlcc_system* S = D.S;
-  cudaStream_t s = S->ctx->stream;
   if (D.m == 0 || nv == 0) return;
   Scope sc(S->ws);
   double* coef = S->ws.get<double>(size_t(D.m) * 4);
-  double* V = D.B + int64_t(D.m) * D.dim;
   for (int pass = 0; pass < 2; ++pass) {
-    dots_block(D.B, D.dim, D.m, V, D.dim, nv, D.dim, coef, S->ws, s);   // coef[k][j]
-    Gemm g;  // V_j -= sum_k coef[k][j] B_k : C [nv][dim] = -A^T B with A = coef [m][nv]
-    g.ta = true;
-    g.M = nv; g.N = D.dim; g.K = D.m;
-    g.A = coef; g.lda = nv; g.B = D.B; g.ldb = D.dim; g.C = V; g.ldc = D.dim;
-    g.alpha = -1.0; g.beta = 1.0;
-    gemm_f64(g, S->ws, s, S->ctx->sm_count);
+    vdots_block(D, D.B(0), D.m, D.B(D.m), nv, coef);   // coef[k][j]
+    // V_j -= sum_k coef[k][j] B_k
+    vcombine(D, nv, D.m, coef, nv, true, D.B(0), D.B(D.m), true, -1.0, 1.0);
   }
 }
 
 // orthonormalise v against B[from..m) (two passes); returns false if v collapses
 // ref_norm > 0: the norm of v before an earlier projection, for the drop test
-static bool orthonormalise_body(DavState& D, double* v, int from, double ref_norm);
-static bool orthonormalise(DavState& D, double* v, int from = 0, double ref_norm = 0.0) {
+static bool orthonormalise_body(DavState& D, void* v, int from, double ref_norm);
+static bool orthonormalise(DavState& D, void* v, int from = 0, double ref_norm = 0.0) {
   bool ok = false;
   timed(D.S, "dav_orthonormalise", 0.0, [&] { ok = orthonormalise_body(D, v, from, ref_norm); });
   return ok;
 }
-static bool orthonormalise_body(DavState& D, double* v, int from, double ref_norm) {
+static bool orthonormalise_body(DavState& D, void* v, int from, double ref_norm) {
   mlcc_system* S = D.S;
-  cudaStream_t s = S->ctx->stream;
   Scope sc(S->ws);
   const int cnt = D.m - from;
   double* coef = S->ws.get<double>(std::max(cnt, 1));
   double* nr = S->ws.get<double>(1);
-  dots(v, 0, 1, v, D.dim, nr, S->ws, s);
+  vdots(D, v, 1, v, nr);
   const double n0 = ref_norm > 0.0 ? ref_norm : std::sqrt(host_scalar(S, nr));
   if (!(n0 > 0.0) || !std::isfinite(n0)) return false;
-  const double* Bf = D.B + int64_t(from) * D.dim;
   for (int pass = 0; pass < 2 && cnt > 0; ++pass) {
-    dots(Bf, D.dim, cnt, v, D.dim, coef, S->ws, s);
-    Gemm g;
-    g.M = 1; g.N = D.dim; g.K = cnt;
-    g.A = coef; g.lda = cnt; g.B = Bf; g.ldb = D.dim; g.C = v; g.ldc = D.dim;
-    g.alpha = -1.0; g.beta = 1.0;
-    gemm_f64(g, S->ws, s, S->ctx->sm_count);
+    vdots(D, D.B(from), cnt, v, coef);
+    vcombine(D, 1, cnt, coef, cnt, false, D.B(from), v, true, -1.0, 1.0);
   }
-  dots(v, 0, 1, v, D.dim, nr, S->ws, s);
+  vdots(D, v, 1, v, nr);
   const double n1 = std::sqrt(host_scalar(S, nr));
   // what is left of a direction inside the span is rounding noise: near 1e-16 of its norm
-  // in binary64, near 1e-7 with binary32 vector arithmetic
-  if (!(n1 > (vec32_active() ? 1e-5 : 1e-10) * n0)) return false;
-  k_scale<<<nblk(D.dim), 256, 0, s>>>(v, D.dim, 1.0 / n1);
-  MLCC_CHECK_LAUNCH();
+  // in binary64, near 1e-7 with binary32 storage or arithmetic
+  if (!(n1 > (D.f32() || vec32_active() ? 1e-5 : 1e-10) * n0)) return false;
+  vscale(D, v, 1.0 / n1);
   return true;
 }
 
-// X = Y^T B, R = Y^T S - w X for the wanted Ritz pairs
+// X = Y^T B, R = Y^T S - w X for the wanted Ritz pairs (X, R binary64)
 static void ritz_body(DavState& D, const std::vector<double>& Yt, int nr, const std::vector<double>& w,
                       double* X, double* R);
 static void ritz(DavState& D, const std::vector<double>& Yt, int nr, const std::vector<double>& w,
@@ -438,12 +514,8 @@ static void ritz_body(DavState& D, const std::vector<double>& Yt, int nr, const 
   Scope sc(S->ws);
   double* y = S->ws.get<double>(size_t(nr) * D.m);
   copy_h2d(y, Yt.data(), int64_t(nr) * D.m, s);
-  Gemm g;
-  g.M = nr; g.N = D.dim; g.K = D.m;
-  g.A = y; g.lda = D.m; g.B = D.B; g.ldb = D.dim; g.C = X; g.ldc = D.dim;
-  gemm_f64(g, S->ws, s, S->ctx->sm_count);
-  g.B = D.Sg; g.C = R;
-  gemm_f64(g, S->ws, s, S->ctx->sm_count);
+  vcombine(D, nr, D.m, y, D.m, false, D.B(0), X, false, 1.0, 0.0);
+  vcombine(D, nr, D.m, y, D.m, false, D.Sg(0), R, false, 1.0, 0.0);
   for (int k = 0; k < nr; ++k) {
     k_resid<<<nblk(D.dim), 256, 0, s>>>(R + int64_t(k) * D.dim, X + int64_t(k) * D.dim, D.dim, w[k]);
     MLCC_CHECK_LAUNCH();
@@ -463,15 +535,17 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
   const int collapse = 2 * nr;
   // Davidson memory: basis and sigma vectors, Ritz vectors, residuals, collapse scratch
   Arena dav;
-  const size_t need = size_t(dim) * 8 * size_t(2 * maxsub + 2 * nr + 2 * collapse + 2) + (1 << 20);
+  const size_t need = size_t(dim) * 8 * size_t(2 * maxsub + 2 * nr + 2 * collapse + 3) + (1 << 20);
   dav.reserve(need);
-  DavState D{S, dim, maxsub, dav.get<double>(size_t(maxsub) * dim), dav.get<double>(size_t(maxsub) * dim)};
+  DavState D{S, dim, maxsub, static_cast<char*>(dav.alloc(size_t(maxsub) * dim * 8)),
+             static_cast<char*>(dav.alloc(size_t(maxsub) * dim * 8))};
   D.G.assign(size_t(maxsub) * maxsub, 0.0);
   double* X = dav.get<double>(size_t(nr) * dim);
   double* R = dav.get<double>(size_t(nr) * dim);
-  double* CB = dav.get<double>(size_t(collapse) * dim);
-  double* CS = dav.get<double>(size_t(collapse) * dim);
-  double* tmpv = dav.get<double>(size_t(dim));
+  char* CB = static_cast<char*>(dav.alloc(size_t(collapse) * dim * 8));   // collapse scratch (stored type)
+  char* CS = static_cast<char*>(dav.alloc(size_t(collapse) * dim * 8));
+  double* tmpv = dav.get<double>(size_t(dim));   // binary64 trial vector / refinement restart
+  double* tmps = dav.get<double>(size_t(dim));   // binary64 sigma-vector of a binary32 basis
 
   // start vectors: 2 n_roots unit singles with the lowest eps_a - eps_i
   std::vector<double> eh(S->n);
@@ -483,13 +557,17 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
     return ex < ey;
   });
   const int nguess = int(std::min<int64_t>(2 * nr, n1));
-  MLCC_CUDA(cudaMemsetAsync(D.B, 0, size_t(nguess) * dim * 8, s));
-  for (int k = 0; k < nguess; ++k) k_set<<<1, 1, 0, s>>>(D.B + int64_t(k) * dim, idx[k], 1.0);
+  int prec = opt->precision;
+  const bool lowp = is_split_precision(prec);
+  D.es = lowp ? 4 : 8;
+  MLCC_CUDA(cudaMemsetAsync(D.B(0), 0, size_t(nguess) * dim * D.es, s));
+  for (int k = 0; k < nguess; ++k) {
+    if (D.f32()) k_set_f<<<1, 1, 0, s>>>(static_cast<float*>(D.B(k)), idx[k], 1.0f);
+    else k_set<<<1, 1, 0, s>>>(static_cast<double*>(D.B(k)), idx[k], 1.0);
+  }
   MLCC_CHECK_LAUNCH();
   D.m = nguess;
 
-  int prec = opt->precision;
-  const bool lowp = is_split_precision(prec);
   const bool two_phase = lowp && opt->refine_fp64 > 0;
   int fp64_sweeps = 0;
   int n_sigma = 0, n_sigma_lowp = 0;
@@ -497,7 +575,7 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
     n_sigma += k;
     if (is_split_precision(prec)) n_sigma_lowp += k;
   };
-  sigma_batch(S, D.B, D.Sg, D.m, dim, prec);
+  sigma_stored(D, 0, D.m, prec, tmpv, tmps);
   count_sigma(D.m);
   {
     Vec32Scope v32(lowp);
@@ -568,19 +646,20 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
         // refinement: restart from the low-precision Ritz vectors with refine_precision sigma
         prec = opt->refine_precision;
         v32.set(false);
-        const int keep = std::min(nr, D.m);   // all tracked Ritz vectors
+        D.es = 8;   // binary64 storage from here on
+        const int keep = std::min(nr, D.m);   // all tracked Ritz vectors (binary64)
         MLCC_CUDA(cudaMemcpyAsync(CB, X, size_t(keep) * dim * 8, cudaMemcpyDeviceToDevice, s));
         D.m = 0;
         int added = 0;
         for (int k = 0; k < keep; ++k) {
-          MLCC_CUDA(cudaMemcpyAsync(D.B + int64_t(D.m) * dim, CB + int64_t(k) * dim, size_t(dim) * 8,
+          MLCC_CUDA(cudaMemcpyAsync(D.B(D.m), CB + size_t(k) * dim * 8, size_t(dim) * 8,
                                     cudaMemcpyDeviceToDevice, s));
-          if (orthonormalise(D, D.B + int64_t(D.m) * dim)) {
+          if (orthonormalise(D, D.B(D.m))) {
             ++D.m;
             ++added;
           }
         }
-        sigma_batch(S, D.B, D.Sg, D.m, dim, prec);
+        sigma_stored(D, 0, D.m, prec, tmpv, tmps);
         count_sigma(D.m);
         std::fill(D.G.begin(), D.G.end(), 0.0);
         update_G(D, 0);
@@ -606,37 +685,28 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
         Scope sc3(S->ws);
         double* y = S->ws.get<double>(size_t(c) * D.m);
         copy_h2d(y, Yc.data(), int64_t(c) * D.m, s);
-        Gemm g;
-        g.M = c; g.N = dim; g.K = D.m;
-        g.A = y; g.lda = D.m; g.B = D.B; g.ldb = dim; g.C = CB; g.ldc = dim;
-        gemm_f64(g, S->ws, s, S->ctx->sm_count);
-        g.B = D.Sg; g.C = CS;
-        gemm_f64(g, S->ws, s, S->ctx->sm_count);
+        vcombine(D, c, D.m, y, D.m, false, D.B(0), CB, true, 1.0, 0.0);
+        vcombine(D, c, D.m, y, D.m, false, D.Sg(0), CS, true, 1.0, 0.0);
         // Gram-Schmidt on CB with the same combinations on CS
         double* coef = S->ws.get<double>(size_t(c));
         double* nx = S->ws.get<double>(1);
+        const size_t vb = size_t(dim) * D.es;
         for (int k = 0; k < c; ++k) {
-          double* bk = CB + int64_t(k) * dim;
-          double* sk = CS + int64_t(k) * dim;
+          void* bk = CB + k * vb;
+          void* sk = CS + k * vb;
           for (int pass = 0; pass < 2 && k > 0; ++pass) {
-            dots(CB, dim, k, bk, dim, coef, S->ws, s);
-            Gemm h;
-            h.M = 1; h.N = dim; h.K = k;
-            h.A = coef; h.lda = k; h.B = CB; h.ldb = dim; h.C = bk; h.ldc = dim;
-            h.alpha = -1.0; h.beta = 1.0;
-            gemm_f64(h, S->ws, s, S->ctx->sm_count);
-            h.B = CS; h.C = sk;
-            gemm_f64(h, S->ws, s, S->ctx->sm_count);
+            vdots(D, CB, k, bk, coef);
+            vcombine(D, 1, k, coef, k, false, CB, bk, true, -1.0, 1.0);
+            vcombine(D, 1, k, coef, k, false, CS, sk, true, -1.0, 1.0);
           }
-          dots(bk, 0, 1, bk, dim, nx, S->ws, s);
+          vdots(D, bk, 1, bk, nx);
           const double nk = std::sqrt(host_scalar(S, nx));
-          k_scale<<<nblk(dim), 256, 0, s>>>(bk, dim, 1.0 / nk);
-          k_scale<<<nblk(dim), 256, 0, s>>>(sk, dim, 1.0 / nk);
-          MLCC_CHECK_LAUNCH();
+          vscale(D, bk, 1.0 / nk);
+          vscale(D, sk, 1.0 / nk);
         }
       }
-      MLCC_CUDA(cudaMemcpyAsync(D.B, CB, size_t(c) * dim * 8, cudaMemcpyDeviceToDevice, s));
-      MLCC_CUDA(cudaMemcpyAsync(D.Sg, CS, size_t(c) * dim * 8, cudaMemcpyDeviceToDevice, s));
+      vcopy(D, D.B(0), CB, c);
+      vcopy(D, D.Sg(0), CS, c);
       D.m = c;
       std::fill(D.G.begin(), D.G.end(), 0.0);
       update_G(D, 0);
@@ -645,15 +715,20 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
     int nnew = 0;
     for (int k : todo) {
       if (D.m + nnew >= maxsub || nnew == 4) break;
-      double* v = D.B + int64_t(D.m + nnew) * dim;
-      k_precond_singles<<<nblk(n1), 256, 0, s>>>(R + int64_t(k) * dim, S->eps, no, nv, w[k], v);
-      MLCC_CHECK_LAUNCH();
-      if (S->nd) {
-        dim3 blk(32, 8), grd(unsigned((S->dS + 31) / 32), unsigned((S->dS + 31) / 32));
-        k_precond_doubles<<<grd, blk, 0, s>>>(R + int64_t(k) * dim + n1, S->eps, no, S->sv, S->so,
-                                              w[k], v + n1);
-        MLCC_CHECK_LAUNCH();
+      void* v = D.B(D.m + nnew);
+      dim3 blk(32, 8), grd(unsigned((S->dS + 31) / 32), unsigned((S->dS + 31) / 32));
+      if (D.f32()) {
+        float* vf = static_cast<float*>(v);
+        k_precond_singles<<<nblk(n1), 256, 0, s>>>(R + int64_t(k) * dim, S->eps, no, nv, w[k], vf);
+        if (S->nd)
+          k_precond_doubles<<<grd, blk, 0, s>>>(R + int64_t(k) * dim + n1, S->eps, no, S->sv, S->so, w[k], vf + n1);
+      } else {
+        double* vd = static_cast<double*>(v);
+        k_precond_singles<<<nblk(n1), 256, 0, s>>>(R + int64_t(k) * dim, S->eps, no, nv, w[k], vd);
+        if (S->nd)
+          k_precond_doubles<<<grd, blk, 0, s>>>(R + int64_t(k) * dim + n1, S->eps, no, S->sv, S->so, w[k], vd + n1);
       }
+      MLCC_CHECK_LAUNCH();
       ++nnew;
     }
     // the old basis is projected out of the whole block first; the vectors of the block are
@@ -663,18 +738,15 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
     {
       Scope sp(S->ws);
       double* nrm = S->ws.get<double>(4);
-      for (int q = 0; q < nnew; ++q) dots(D.B + int64_t(D.m + q) * dim, 0, 1, D.B + int64_t(D.m + q) * dim, dim, nrm + q, S->ws, s);
+      for (int q = 0; q < nnew; ++q) vdots(D, D.B(D.m + q), 1, D.B(D.m + q), nrm + q);
       double hn[4] = {0, 0, 0, 0};
       if (nnew) copy_d2h(hn, nrm, nnew, s);
       for (int q = 0; q < nnew; ++q) pre[q] = std::sqrt(hn[q]);
     }
     block_project(D, nnew);
     for (int q = 0; q < nnew; ++q) {
-      double* v = D.B + int64_t(D.m) * dim;
-      if (D.m != m0 + q) {
-        MLCC_CUDA(cudaMemcpyAsync(v, D.B + int64_t(m0 + q) * dim, size_t(dim) * 8,
-                                  cudaMemcpyDeviceToDevice, s));
-      }
+      void* v = D.B(D.m);
+      if (D.m != m0 + q) vcopy(D, v, D.B(m0 + q), 1);
       if (pre[q] > 0.0 && std::isfinite(pre[q]) && orthonormalise(D, v, m0, pre[q])) ++D.m;
     }
     if (D.m == m0) {
@@ -683,11 +755,10 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
       for (int k = 0; k < nreq; ++k) conv = conv && rn[k] < opt->es_res_tol;
       break;
     }
-    sigma_batch(S, D.B + int64_t(m0) * dim, D.Sg + int64_t(m0) * dim, D.m - m0, dim, prec);
+    sigma_stored(D, m0, D.m - m0, prec, tmpv, tmps);
     count_sigma(D.m - m0);
     update_G(D, m0);
   }
-  (void)tmpv;
   // sign convention: largest-magnitude element positive
   {
     Scope sc4(S->ws);

@@ -113,4 +113,28 @@ void timed(mlcc_system* S, const char* fam, double flop, F&& f) {
   MLCC_CUDA(cudaEventRecord(b, S->ctx->stream));
 }
 
+// Consecutive timed phases of one routine: mark("name") closes the open phase and opens
+// the next (kernel-timing family "name"); the destructor closes the last one.
+struct PhaseMarks {
+  mlcc_system* S;
+  cudaEvent_t open_end = nullptr;
+  explicit PhaseMarks(mlcc_system* sys) : S(sys) {}
+  void close() {
+    if (open_end) {
+      MLCC_CUDA(cudaEventRecord(open_end, S->ctx->stream));
+      open_end = nullptr;
+    }
+  }
+  void mark(const char* fam) {
+    close();
+    auto& T = S->ctx->timer;
+    if (!T.enabled) return;
+    cudaEvent_t a;
+    T.begin(fam, S->ctx->stream, 0.0, &a, &open_end);
+  }
+  ~PhaseMarks() {
+    if (open_end) cudaEventRecord(open_end, S->ctx->stream);
+  }
+};
+
 }  // namespace mlcc

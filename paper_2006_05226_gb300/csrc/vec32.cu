@@ -19,13 +19,22 @@ namespace mlcc {
 namespace {
 
 __device__ __forceinline__ float d2f(double x) { return d2f_bits(x); }
+__device__ __forceinline__ float d2f(float x) { return x; }
 __device__ __forceinline__ double f2d(float f) { return f2d_bits(f); }
+// store of a binary32 result: widened exactly, or kept
+__device__ __forceinline__ void st32(double* p, float v) { *p = f2d_bits(v); }
+__device__ __forceinline__ void st32(float* p, float v) { *p = v; }
+__device__ __forceinline__ double ld64(const double* p) { return *p; }
+__device__ __forceinline__ void st64(double* p, double v) { *p = v; }
+__device__ __forceinline__ void st64(float* p, double v) { *p = d2f_bits(v); }
+__device__ __forceinline__ double ld64(const float* p) { return f2d_bits(*p); }
 
 constexpr int DOT32_BLOCKS = 1216;   // 8 blocks of 256 threads per SM of a GB300
 constexpr int DOT32_CHUNK = 16;   // x-vectors per pass over the y-vectors
 
 // partial[k][blk]: the block's share of x_k . y, DOT32_CHUNK vectors x_k per pass over y
-__global__ void k_dots32(const double* x, int64_t ldx, int nx, const double* y, int64_t n, double* partial) {
+template <typename TX, typename TY>
+__global__ void k_dots32(const TX* x, int64_t ldx, int nx, const TY* y, int64_t n, double* partial) {
   __shared__ double red[DOT32_CHUNK][256 / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int k0 = 0; k0 < nx; k0 += DOT32_CHUNK) {
@@ -56,8 +65,8 @@ __global__ void k_dots32(const double* x, int64_t ldx, int nx, const double* y, 
 }
 
 // partial[(k * NY + j)][blk] for DOT32_CHUNK x-vectors per pass and NY <= 4 y-vectors
-template <int NY, int CH = (NY >= 3 ? 8 : DOT32_CHUNK)>   // CH * NY accumulators per thread
-__global__ void k_dots_block32(const double* x, int64_t ldx, int nx, const double* y, int64_t ldy, int64_t n,
+template <int NY, typename TX, typename TY, int CH = (NY >= 3 ? 8 : DOT32_CHUNK)>   // CH * NY accumulators
+__global__ void k_dots_block32(const TX* x, int64_t ldx, int nx, const TY* y, int64_t ldy, int64_t n,
                                double* partial) {
   constexpr int DOT32_CHUNK = CH;
   __shared__ double red[DOT32_CHUNK * NY][256 / 32];
@@ -117,9 +126,9 @@ __global__ void k_dots32_stage2(const double* partial, int nblk, double* out) {
 
 // C[m][n] = alpha sum_k op(A)[m][k] B[k][n] + beta C[m][n] for M <= MM, one thread per
 // column n; op(A) (K <= 64) is staged in shared memory as binary32
-template <int MM, bool TA>
-__global__ void k_skinny32(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, const double* B,
-                           int64_t ldb, double* C, int64_t ldc, double alpha, double beta) {
+template <int MM, bool TA, typename TB, typename TC>
+__global__ void k_skinny32(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, const TB* B,
+                           int64_t ldb, TC* C, int64_t ldc, double alpha, double beta) {
   __shared__ float As[MM * 64];
   for (int t = threadIdx.x; t < MM * 64; t += blockDim.x) {
     const int m = t / 64, k = t - m * 64;
@@ -149,60 +158,127 @@ __global__ void k_skinny32(int64_t M, int64_t N, int64_t K, const double* A, int
 #pragma unroll
   for (int m = 0; m < MM; ++m)
     if (m < M) {
-      double* cp = C + m * ldc + n;
-      const double v = alpha * f2d(acc[m]);
-      *cp = (beta == 0.0) ? v : v + beta * (*cp);
+      TC* cp = C + m * ldc + n;
+      const float a = float(alpha), b = float(beta);
+      if (sizeof(TC) == 8) {
+        const double v = alpha * f2d(acc[m]);
+        st64(cp, (beta == 0.0) ? v : v + beta * ld64(cp));
+      } else {
+        st32(cp, (b == 0.0f) ? a * acc[m] : fmaf(a, acc[m], b * d2f(*cp)));
+      }
     }
 }
 
-template <int MM>
-void launch_skinny32(const Gemm& g, cudaStream_t s) {
-  const unsigned blocks = unsigned((g.N + 255) / 256);
-  if (g.ta) k_skinny32<MM, true><<<blocks, 256, 0, s>>>(g.M, g.N, g.K, g.A, g.lda, g.B, g.ldb, g.C, g.ldc, g.alpha, g.beta);
-  else k_skinny32<MM, false><<<blocks, 256, 0, s>>>(g.M, g.N, g.K, g.A, g.lda, g.B, g.ldb, g.C, g.ldc, g.alpha, g.beta);
+template <int MM, typename TB, typename TC>
+void launch_skinny32(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, bool ta, const TB* B,
+                     int64_t ldb, TC* C, int64_t ldc, double alpha, double beta, cudaStream_t s) {
+  const unsigned blocks = unsigned((N + 255) / 256);
+  if (ta) k_skinny32<MM, true, TB, TC><<<blocks, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, alpha, beta);
+  else k_skinny32<MM, false, TB, TC><<<blocks, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, alpha, beta);
   MLCC_CHECK_LAUNCH();
 }
+template <typename TB, typename TC>
+bool skinny32_t(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, bool ta, const TB* B, int64_t ldb,
+                TC* C, int64_t ldc, double alpha, double beta, cudaStream_t s) {
+  if (M < 1 || M > 16 || K > 64 || K < 0 || N < 1) return false;
+  MLCC_REQUIRE((N + 255) / 256 < (int64_t(1) << 31), "skinny32: N too large");
+  if (M <= 1) launch_skinny32<1>(M, N, K, A, lda, ta, B, ldb, C, ldc, alpha, beta, s);
+  else if (M <= 4) launch_skinny32<4>(M, N, K, A, lda, ta, B, ldb, C, ldc, alpha, beta, s);
+  else if (M <= 8) launch_skinny32<8>(M, N, K, A, lda, ta, B, ldb, C, ldc, alpha, beta, s);
+  else launch_skinny32<16>(M, N, K, A, lda, ta, B, ldb, C, ldc, alpha, beta, s);
+  return true;
+}
 
-}  // namespace
-
-void dots32(const double* x, int64_t ldx, int nx, const double* y, int64_t n, double* out_dev, Arena& ws,
-            cudaStream_t s) {
+template <typename TX, typename TY>
+void dots32_t(const TX* x, int64_t ldx, int nx, const TY* y, int64_t n, double* out_dev, Arena& ws,
+              cudaStream_t s) {
   if (nx <= 0) return;
   Scope sc(ws);
   const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, DOT32_BLOCKS)));
   double* partial = ws.get<double>(size_t(nx) * blocks);
-  k_dots32<<<blocks, 256, 0, s>>>(x, ldx, nx, y, n, partial);
+  k_dots32<TX, TY><<<blocks, 256, 0, s>>>(x, ldx, nx, y, n, partial);
   MLCC_CHECK_LAUNCH();
   k_dots32_stage2<<<nx, 256, 0, s>>>(partial, blocks, out_dev);
   MLCC_CHECK_LAUNCH();
 }
 
-void dots_block32(const double* x, int64_t ldx, int nx, const double* y, int64_t ldy, int ny, int64_t n,
-                  double* out_dev, Arena& ws, cudaStream_t s) {
+template <typename TX, typename TY>
+void dots_block32_t(const TX* x, int64_t ldx, int nx, const TY* y, int64_t ldy, int ny, int64_t n,
+                    double* out_dev, Arena& ws, cudaStream_t s) {
   if (nx <= 0 || ny <= 0) return;
   MLCC_REQUIRE(ny <= 4, "dots_block: at most 4 y-vectors");
   Scope sc(ws);
   const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, DOT32_BLOCKS)));
   double* partial = ws.get<double>(size_t(nx) * ny * blocks);
   switch (ny) {
-    case 1: k_dots_block32<1><<<blocks, 256, 0, s>>>(x, ldx, nx, y, ldy, n, partial); break;
-    case 2: k_dots_block32<2><<<blocks, 256, 0, s>>>(x, ldx, nx, y, ldy, n, partial); break;
-    case 3: k_dots_block32<3><<<blocks, 256, 0, s>>>(x, ldx, nx, y, ldy, n, partial); break;
-    default: k_dots_block32<4><<<blocks, 256, 0, s>>>(x, ldx, nx, y, ldy, n, partial); break;
+    case 1: k_dots_block32<1, TX, TY><<<blocks, 256, 0, s>>>(x, ldx, nx, y, ldy, n, partial); break;
+    case 2: k_dots_block32<2, TX, TY><<<blocks, 256, 0, s>>>(x, ldx, nx, y, ldy, n, partial); break;
+    case 3: k_dots_block32<3, TX, TY><<<blocks, 256, 0, s>>>(x, ldx, nx, y, ldy, n, partial); break;
+    default: k_dots_block32<4, TX, TY><<<blocks, 256, 0, s>>>(x, ldx, nx, y, ldy, n, partial); break;
   }
   MLCC_CHECK_LAUNCH();
   k_dots32_stage2<<<nx * ny, 256, 0, s>>>(partial, blocks, out_dev);
   MLCC_CHECK_LAUNCH();
 }
 
+__global__ void k_cvt_d2f(const double* x, float* y, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    y[i] = d2f_bits(x[i]);
+}
+__global__ void k_cvt_f2d(const float* x, double* y, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    y[i] = f2d_bits(x[i]);
+}
+__global__ void k_scale_f(float* x, int64_t n, float a) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    x[i] *= a;
+}
+int stream_blocks(int64_t n) { return int(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 65535))); }
+
+}  // namespace
+
+void dots32(const double* x, int64_t ldx, int nx, const double* y, int64_t n, double* out_dev, Arena& ws,
+            cudaStream_t s) {
+  dots32_t(x, ldx, nx, y, n, out_dev, ws, s);
+}
+void dots_block32(const double* x, int64_t ldx, int nx, const double* y, int64_t ldy, int ny, int64_t n,
+                  double* out_dev, Arena& ws, cudaStream_t s) {
+  dots_block32_t(x, ldx, nx, y, ldy, ny, n, out_dev, ws, s);
+}
 bool skinny32(const Gemm& g, cudaStream_t s) {
-  if (g.tb || g.reduce || g.batch != 1 || g.M < 1 || g.M > 16 || g.K > 64 || g.N < 1) return false;
-  MLCC_REQUIRE((g.N + 255) / 256 < (int64_t(1) << 31), "skinny32: N too large");
-  if (g.M <= 1) launch_skinny32<1>(g, s);
-  else if (g.M <= 4) launch_skinny32<4>(g, s);
-  else if (g.M <= 8) launch_skinny32<8>(g, s);
-  else launch_skinny32<16>(g, s);
-  return true;
+  if (g.tb || g.reduce || g.batch != 1) return false;
+  return skinny32_t(g.M, g.N, g.K, g.A, g.lda, g.ta, g.B, g.ldb, g.C, g.ldc, g.alpha, g.beta, s);
+}
+
+// binary32 vector storage (the Davidson basis of a split-precision phase)
+void dots_f32(const float* x, int64_t ldx, int nx, const float* y, int64_t n, double* out_dev, Arena& ws,
+              cudaStream_t s) {
+  dots32_t(x, ldx, nx, y, n, out_dev, ws, s);
+}
+void dots_block_f32(const float* x, int64_t ldx, int nx, const float* y, int64_t ldy, int ny, int64_t n,
+                    double* out_dev, Arena& ws, cudaStream_t s) {
+  dots_block32_t(x, ldx, nx, y, ldy, ny, n, out_dev, ws, s);
+}
+void combine_f32(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, bool ta, const float* B,
+                 int64_t ldb, void* C, bool c_f32, int64_t ldc, double alpha, double beta, cudaStream_t s) {
+  const bool ok = c_f32 ? skinny32_t(M, N, K, A, lda, ta, B, ldb, static_cast<float*>(C), ldc, alpha, beta, s)
+                        : skinny32_t(M, N, K, A, lda, ta, B, ldb, static_cast<double*>(C), ldc, alpha, beta, s);
+  MLCC_REQUIRE(ok, "combine_f32: at most 16 outputs of at most 64 vectors");
+}
+void cvt_d2f(const double* x, float* y, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  k_cvt_d2f<<<stream_blocks(n), 256, 0, s>>>(x, y, n);
+  MLCC_CHECK_LAUNCH();
+}
+void cvt_f2d(const float* x, double* y, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  k_cvt_f2d<<<stream_blocks(n), 256, 0, s>>>(x, y, n);
+  MLCC_CHECK_LAUNCH();
+}
+void scale_f32(float* x, int64_t n, double a, cudaStream_t s) {
+  if (n <= 0) return;
+  k_scale_f<<<stream_blocks(n), 256, 0, s>>>(x, n, float(a));
+  MLCC_CHECK_LAUNCH();
 }
 
 }  // namespace mlcc

@@ -230,3 +230,21 @@ def test_excited_states_fp64e(ctx, small_prepared):
                                   want_vectors=False)
     assert info.converged and info.n_sigma_lowp > 0 and info.fp64_sweeps >= 1
     assert np.abs(w - ref.omega).max() < E_TOL
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 3e-2), (2, 1e-3), (3, 1e-4)])
+def test_split_bf16_precisions(ctx, prec, tol):
+    """The split-bfloat16 precisions of the same engine (fp32 accumulation): relative error
+    against numpy within the bounds the sigma-vectors meet (BF16 ~ 2^-8, BF16X3 and BF16X6
+    limited by fp32 accumulation over K)."""
+    rng = np.random.default_rng(17)
+    M, N, K = 300, 520, 1500
+    A = rng.standard_normal((M, K))
+    B = rng.standard_normal((K, N))
+    out = _gemm(ctx, A, B, False, False, prec)
+    ref = A @ B
+    rel = np.abs(out - ref).max() / np.abs(ref).max()
+    assert rel < tol, rel
+    if prec > 1:   # the extra pieces help
+        out1 = _gemm(ctx, A, B, False, False, 1)
+        assert rel < np.abs(out1 - ref).max() / np.abs(ref).max()
