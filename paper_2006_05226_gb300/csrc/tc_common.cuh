@@ -23,8 +23,16 @@ struct GOp {
 };
 __device__ __forceinline__ double gop_load(const GOp& o, int64_t r, int64_t kk) {
   if (r >= o.R || kk >= o.Ktot) return 0.0;
-  const int64_t rb = r / o.Mrow, m = r - rb * o.Mrow;
-  const int64_t kb = kk / o.Kblk, k = kk - kb * o.Kblk;
+  // the batch divisions only when the operand is batched (uniform branches)
+  int64_t rb = 0, m = r, kb = 0, k = kk;
+  if (o.Mrow < o.R) {
+    rb = r / o.Mrow;
+    m = r - rb * o.Mrow;
+  }
+  if (o.Kblk < o.Ktot) {
+    kb = kk / o.Kblk;
+    k = kk - kb * o.Kblk;
+  }
   return o.base[rb * o.sRow + kb * o.sK + (o.tr ? k * o.ld + m : m * o.ld + k)];
 }
 

@@ -49,30 +49,38 @@ __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsig
   return a > b ? a : b;
 }
 
+// Largest |x| per operand row as binary64 bit patterns, merged over K chunks with
+// atomicMax (blockIdx.y is the chunk), then turned into exponents.
 // K contiguous in the source: one warp per row
-__global__ void k_emu_rowexp_direct(GOp o, int* ex) {
+__global__ void k_emu_rowmax_direct(GOp o, int64_t kchunk, unsigned long long* mx) {
   const int lane = threadIdx.x & 31;
+  const int64_t k0 = int64_t(blockIdx.y) * kchunk, k1 = min(o.Ktot, k0 + kchunk);
   const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
   for (int64_t r = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; r < o.R; r += nwarps) {
     unsigned long long m = 0;
-    for (int64_t kk = lane; kk < o.Ktot; kk += 32) m = umax64(m, abs_bits(gop_load(o, r, kk)));
+    for (int64_t kk = k0 + lane; kk < k1; kk += 32) m = umax64(m, abs_bits(gop_load(o, r, kk)));
     for (int off = 16; off > 0; off >>= 1) m = umax64(m, __shfl_xor_sync(0xFFFFFFFFu, m, off));
-    if (lane == 0) ex[r] = exponent_of_max(m);
+    if (lane == 0 && m) atomicMax(mx + r, m);
   }
 }
 // rows contiguous in the source: 32 rows per block, 8 lanes over k each
-__global__ void k_emu_rowexp_tr(GOp o, int* ex) {
+__global__ void k_emu_rowmax_tr(GOp o, int64_t kchunk, unsigned long long* mx) {
   __shared__ unsigned long long red[8][33];
   const int64_t r = int64_t(blockIdx.x) * 32 + threadIdx.x;
+  const int64_t k0 = int64_t(blockIdx.y) * kchunk, k1 = min(o.Ktot, k0 + kchunk);
   unsigned long long m = 0;
   if (r < o.R)
-    for (int64_t kk = threadIdx.y; kk < o.Ktot; kk += 8) m = umax64(m, abs_bits(gop_load(o, r, kk)));
+    for (int64_t kk = k0 + threadIdx.y; kk < k1; kk += 8) m = umax64(m, abs_bits(gop_load(o, r, kk)));
   red[threadIdx.y][threadIdx.x] = m;
   __syncthreads();
   if (threadIdx.y == 0 && r < o.R) {
     for (int y = 1; y < 8; ++y) m = umax64(m, red[y][threadIdx.x]);
-    ex[r] = exponent_of_max(m);
+    if (m) atomicMax(mx + r, m);
   }
+}
+__global__ void k_emu_exponents(const unsigned long long* mx, int64_t R, int* ex) {
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < R; r += int64_t(gridDim.x) * blockDim.x)
+    ex[r] = exponent_of_max(mx[r]);
 }
 
 // bfloat16 bit pattern of an integer |q| <= 128 (exact)
@@ -194,16 +202,28 @@ int grid_for(int64_t total, int threads) {
   return int(std::max<int64_t>(1, std::min<int64_t>((total + threads - 1) / threads, 65535)));
 }
 
-void emu_convert(const GOp& o, int* ex, __nv_bfloat16* dst, cudaStream_t s) {
-  if (!o.tr) {
-    k_emu_rowexp_direct<<<grid_for(o.R * 32, 256), 256, 0, s>>>(o, ex);
+void emu_convert(const GOp& o, int* ex, __nv_bfloat16* dst, Arena& ws, cudaStream_t s) {
+  {
+    // row maxima: enough (row block, K chunk) blocks to fill the GPU even for few rows
+    Scope sc(ws);
+    unsigned long long* mx = ws.get<unsigned long long>(size_t(o.R));
+    MLCC_CUDA(cudaMemsetAsync(mx, 0, size_t(o.R) * 8, s));
+    const int64_t rblocks = o.tr ? (o.R + 31) / 32 : (o.R + 7) / 8;
+    const int64_t nk = std::max<int64_t>(1, std::min<int64_t>({(o.Ktot + 255) / 256, (1216 + rblocks - 1) / rblocks, 65535}));
+    const int64_t kchunk = (o.Ktot + nk - 1) / nk;
+    MLCC_REQUIRE(rblocks < (int64_t(1) << 31), "gemm_emu: grid");
+    const dim3 grid{unsigned(std::min<int64_t>(rblocks, o.tr ? (int64_t(1) << 31) - 1 : 65535)), unsigned(nk), 1};
+    if (!o.tr) k_emu_rowmax_direct<<<grid, 256, 0, s>>>(o, kchunk, mx);
+    else k_emu_rowmax_tr<<<grid, dim3(32, 8), 0, s>>>(o, kchunk, mx);
     MLCC_CHECK_LAUNCH();
+    k_emu_exponents<<<grid_for(o.R, 256), 256, 0, s>>>(mx, o.R, ex);
+    MLCC_CHECK_LAUNCH();
+  }
+  if (!o.tr) {
     k_emu_slice_direct<<<grid_for(o.R * o.Kp, 256), 256, 0, s>>>(o, ex, dst);
     MLCC_CHECK_LAUNCH();
   } else {
     MLCC_REQUIRE((o.R + 31) / 32 < (int64_t(1) << 31) && (o.Kp + 31) / 32 < 65536, "gemm_emu: grid");
-    k_emu_rowexp_tr<<<unsigned((o.R + 31) / 32), dim3(32, 8), 0, s>>>(o, ex);
-    MLCC_CHECK_LAUNCH();
     dim3 blk(32, 8), grd(unsigned((o.R + 31) / 32), unsigned((o.Kp + 31) / 32));
     k_emu_slice_tr<<<grd, blk, 0, s>>>(o, ex, dst);
     MLCC_CHECK_LAUNCH();
@@ -221,7 +241,7 @@ const __nv_bfloat16* emu_operand(const GOp& o, int side, bool cacheable, Arena& 
   auto fresh = [&](void* mem) {
     auto* d = static_cast<__nv_bfloat16*>(mem);
     int* ex = reinterpret_cast<int*>(static_cast<char*>(mem) + sb);
-    emu_convert(o, ex, d, s);
+    emu_convert(o, ex, d, ws, s);
     *ex_out = ex;
     return d;
   };

@@ -99,13 +99,6 @@ struct TcParams {
   double* partial;  // split-K: [split][M][N] (alpha, beta applied by the reduction)
   int* err;
   int m_fast;       // 1: blockIdx.x runs over M tiles
-  // binary64 emulation (emu_S > 0): the operands hold emu_S integer slices of emu_kbp K
-  // blocks each; slice pair (i, j) belongs to group g = i + j. blockIdx.z is one chunk of
-  // at most emu_ch K blocks inside one group, written as fp32 to part32[z][M][ldp].
-  int emu_S, emu_kbp, emu_ch;
-  int emu_gstart[EMU_MAX_S + 1];   // first chunk of group g; emu_gstart[emu_S] = chunks
-  float* part32;
-  int64_t ldp;
   // batched output columns (nb > 0): column b * nb + c of the product lands at
   // C + b * sCb + row * ldc + c (a batch of products that share A, flattened along N)
   int64_t nb, sCb;
@@ -141,14 +134,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   const int kb0 = int(blockIdx.z) * p.kb_per;
-  int nkb = max(0, min(p.kblocks, kb0 + p.kb_per) - kb0);
-  int grp = 0, loc0 = 0;   // emulation: slice-pair group and first group-local K block
-  if (p.emu_S > 0) {
-    const int z = int(blockIdx.z);
-    while (grp + 1 < p.emu_S && z >= p.emu_gstart[grp + 1]) ++grp;
-    loc0 = (z - p.emu_gstart[grp]) * p.emu_ch;
-    nkb = max(0, min(p.emu_ch, (grp + 1) * p.emu_kbp - loc0));
-  }
+  const int nkb = max(0, min(p.kblocks, kb0 + p.kb_per) - kb0);
 
   if (warp == 0) {
     if (lane == 0) {
@@ -161,13 +147,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         }
         const uint32_t a_dst = smem_u32(smem + s * STAGE_BYTES);
         const uint32_t b_dst = a_dst + A_BYTES;
-        int xa = (kb0 + kb) * BK, xb = xa;
-        if (p.emu_S > 0) {
-          // group-local block -> slice pair (i, grp - i) and block kk inside the slice
-          const int loc = loc0 + kb, i = loc / p.emu_kbp, kk = loc - i * p.emu_kbp;
-          xa = (i * p.emu_kbp + kk) * BK;
-          xb = ((grp - i) * p.emu_kbp + kk) * BK;
-        }
+        const int xa = (kb0 + kb) * BK, xb = xa;
         mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
         tma_load_2d(a_dst, &tmA, full0 + 8 * s, xa, int(m0));
         tma_load_2d(b_dst, &tmB, full0 + 8 * s, xb, int(n0));
@@ -232,20 +212,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
               "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (p.part32 && row < p.M) {
-          // exact fp32 chunk sums of the emulation, one plane per chunk
-          float* prow = p.part32 + int64_t(blockIdx.z) * p.M * p.ldp + row * p.ldp + n0 + c0;
-          if (n0 + c0 + 32 <= p.N) {
-#pragma unroll
-            for (int j = 0; j < 32; j += 4)
-              *reinterpret_cast<float4*>(prow + j) =
-                  make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
-                              __uint_as_float(r[j + 3]));
-          } else {
-            for (int j = 0; j < 32; ++j)
-              if (n0 + c0 + j < p.N) prow[j] = __uint_as_float(r[j]);
-          }
-        } else if (row < p.M) {
+        if (row < p.M) {
           int64_t cb = 0, cc = n0 + c0;
           if (p.nb > 0) {
             cb = cc / p.nb;
@@ -277,6 +244,185 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Emulation mode (binary64 from integer digits, tc_emu.cu): the operands hold S digit
+// slices of kbp K blocks each; digit pair (i, j) belongs to group g = i + j. Chunk z of
+// group g (gstart[g] <= z < gstart[g + 1]) sums at most ch K blocks of the pairs
+// (i, g - i), concatenated in i, into the fp32 plane part32[z][M][ldp]. Each CTA takes
+// chunks [z0, z0 + cpb) of one 128 x 256 tile and accumulates them into two TMEM
+// accumulators in turn: the epilogue drains chunk c while the MMAs of chunk c + 1 run.
+struct EmuParams {
+  int64_t M, N;
+  int S, kbp, ch, nch, cpb;
+  int gstart[EMU_MAX_S + 1];
+  float* part32;
+  int64_t ldp;
+  int* err;
+};
+__device__ __forceinline__ void emu_chunk(const EmuParams& p, int z, int& grp, int& loc0, int& nkb) {
+  grp = 0;
+  while (grp + 1 < p.S && z >= p.gstart[grp + 1]) ++grp;
+  loc0 = (z - p.gstart[grp]) * p.ch;
+  nkb = max(0, min(p.ch, (grp + 1) * p.kbp - loc0));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+k_tc_gemm_emu(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EmuParams p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // barriers: full[STAGES], empty[STAGES], acc_full[2], acc_empty[2]; then the TMEM slot
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
+  const uint32_t accf0 = smem_u32(bars + 2 * STAGES), acce0 = smem_u32(bars + 2 * STAGES + 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = int64_t(blockIdx.x) * BM, n0 = int64_t(blockIdx.y) * BN;
+  const int z0 = int(blockIdx.z) * p.cpb;
+  const int nc = max(0, min(p.nch, z0 + p.cpb) - z0);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf0 + 8 * b, 1);
+      mbar_init(acce0 + 8 * b, 4);   // one arrival per epilogue warp
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)), "r"(2 * BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // TMA producer over the K blocks of every chunk of this CTA
+      int it = 0;
+      bool ok = true;
+      for (int c = 0; c < nc && ok; ++c) {
+        int grp, loc0, nkb;
+        emu_chunk(p, z0 + c, grp, loc0, nkb);
+        for (int kb = 0; kb < nkb; ++kb) {
+          const int s = it % STAGES;
+          if (it >= STAGES && !mbar_wait(empty0 + 8 * s, ((it / STAGES) - 1) & 1, p.err, 11)) {
+            ok = false;
+            break;
+          }
+          // group-local block -> digit pair (i, grp - i) and block kk inside the slice
+          const int loc = loc0 + kb, i = loc / p.kbp, kk = loc - i * p.kbp;
+          const uint32_t a_dst = smem_u32(smem + s * STAGE_BYTES);
+          mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+          tma_load_2d(a_dst, &tmA, full0 + 8 * s, (i * p.kbp + kk) * BK, int(m0));
+          tma_load_2d(a_dst + A_BYTES, &tmB, full0 + 8 * s, ((grp - i) * p.kbp + kk) * BK, int(n0));
+          ++it;
+        }
+      }
+      // drain: the copies this thread issued land before the CTA can exit
+      for (int j = max(0, it - STAGES); j < it; ++j) mbar_wait(full0 + 8 * (j % STAGES), (j / STAGES) & 1, p.err, 14);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer: chunk c accumulates into TMEM columns (c & 1) * BN
+      constexpr uint32_t idesc = instr_desc();
+      int it = 0;
+      bool ok = true;
+      for (int c = 0; c < nc && ok; ++c) {
+        const int b = c & 1;
+        // the epilogue has drained chunk c - 2 from this accumulator
+        if (c >= 2 && !mbar_wait(acce0 + 8 * b, ((c >> 1) - 1) & 1, p.err, 15)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        int grp, loc0, nkb;
+        emu_chunk(p, z0 + c, grp, loc0, nkb);
+        const uint32_t acc_tmem = tmem + uint32_t(b * BN);
+        for (int kb = 0; kb < nkb; ++kb) {
+          const int s = it % STAGES;
+          if (!mbar_wait(full0 + 8 * s, (it / STAGES) & 1, p.err, 12)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a_addr = smem_u32(smem + s * STAGE_BYTES);
+          const uint64_t ad = smem_desc(a_addr), bd = smem_desc(a_addr + A_BYTES);
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k) {
+            const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_tmem),
+                "l"(ad + uint64_t(2 * k)), "l"(bd + uint64_t(2 * k)), "r"(idesc), "r"(acc));
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty0 + 8 * s)
+                       : "memory");
+          ++it;
+        }
+        if (ok)
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(accf0 + 8 * b)
+                       : "memory");
+      }
+    }
+  } else {
+    // epilogue: warps 2..5 own TMEM lanes 32*(warp % 4) .. +31, one output row per thread
+    const int q = warp & 3;
+    const int64_t row = m0 + 32 * q + lane;
+    for (int c = 0; c < nc; ++c) {
+      const int b = c & 1;
+      if (!mbar_wait(accf0 + 8 * b, (c >> 1) & 1, p.err, 13)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      float* prow = p.part32 + int64_t(z0 + c) * p.M * p.ldp + row * p.ldp + n0;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem + (uint32_t(32 * q) << 16) + uint32_t(b * BN + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+            "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+              "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+              "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+              "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (row < p.M) {
+          if (n0 + c0 + 32 <= p.N) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4)
+              *reinterpret_cast<float4*>(prow + c0 + j) =
+                  make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
+                              __uint_as_float(r[j + 3]));
+          } else {
+            for (int j = 0; j < 32; ++j)
+              if (n0 + c0 + j < p.N) prow[c0 + j] = __uint_as_float(r[j]);
+          }
+        }
+      }
+      // this warp has read the accumulator: the MMAs of chunk c + 2 may overwrite it
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acce0 + 8 * b);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN));
   }
 }
 
@@ -403,35 +549,36 @@ void tc_gemm_emu_launch(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t 
   MLCC_REQUIRE(M < (int64_t(1) << 31) && N < (int64_t(1) << 31), "tc_gemm_emu: size too large");
   MLCC_REQUIRE(ldp % 4 == 0 && ldp >= N, "tc_gemm_emu: partial rows must be padded to 4");
   const int nch = gstart[S];
-  MLCC_REQUIRE(nch >= 1 && nch < 65536, "tc_gemm_emu: chunk count out of range");
-  ensure_smem_attr();
+  MLCC_REQUIRE(nch >= 1, "tc_gemm_emu: no chunks");
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(k_tc_gemm_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  });
+  MLCC_CUDA(attr);
   CUtensorMap ma, mb;
   make_map(&ma, A, M, S * Kp, BM);
   make_map(&mb, B, N, S * Kp, BN);
-  TcParams p;
+  EmuParams p;
   p.M = M;
   p.N = N;
-  p.kblocks = nch * ch;
-  p.kb_per = ch;
-  p.C = nullptr;
-  p.ldc = 0;
-  p.alpha = 1.0;
-  p.beta = 0.0;
-  p.partial = nullptr;
-  p.err = err;
-  p.m_fast = 1;
-  p.emu_S = S;
-  p.emu_kbp = int(Kp / BK);
-  p.emu_ch = ch;
-  for (int g = 0; g <= EMU_MAX_S; ++g) p.emu_gstart[g] = g <= S ? gstart[g] : nch;
+  p.S = S;
+  p.kbp = int(Kp / BK);
+  p.ch = ch;
+  p.nch = nch;
+  const int64_t tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
+  // chunks per CTA: enough CTAs for two waves, at most 8 chunks each
+  const int64_t tiles = tm * tn;
+  int cpb = int(std::max<int64_t>(1, std::min<int64_t>(8, (tiles * nch) / (2 * 152))));
+  p.cpb = cpb;
+  for (int g = 0; g <= EMU_MAX_S; ++g) p.gstart[g] = g <= S ? gstart[g] : nch;
   p.part32 = part;
   p.ldp = ldp;
-  p.nb = 0;
-  p.sCb = 0;
-  const int64_t tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
-  MLCC_REQUIRE(tn < 65536, "tc_gemm_emu: grid too large");
-  const dim3 grid{unsigned(tm), unsigned(tn), unsigned(nch)};
-  k_tc_gemm<<<grid, THREADS, SMEM_BYTES, s>>>(ma, mb, p);
+  p.err = err;
+  const int64_t nz = (nch + cpb - 1) / cpb;
+  MLCC_REQUIRE(tn < 65536 && nz < 65536, "tc_gemm_emu: grid too large");
+  const dim3 grid{unsigned(tm), unsigned(tn), unsigned(nz)};
+  k_tc_gemm_emu<<<grid, THREADS, SMEM_BYTES, s>>>(ma, mb, p);
   MLCC_CHECK_LAUNCH();
 }
 
@@ -461,12 +608,6 @@ void tc_gemm_split(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t M, in
   MLCC_REQUIRE(splits == 1 || partial, "tc_gemm: split-K needs a partial buffer");
   p.err = err;
   p.m_fast = m_fast ? 1 : 0;
-  p.emu_S = 0;
-  p.emu_kbp = 0;
-  p.emu_ch = 0;
-  for (int g = 0; g <= EMU_MAX_S; ++g) p.emu_gstart[g] = 0;
-  p.part32 = nullptr;
-  p.ldp = 0;
   p.nb = nb;
   p.sCb = sCb;
   MLCC_REQUIRE(nb == 0 || splits == 1, "tc_gemm: batched output columns without split-K");

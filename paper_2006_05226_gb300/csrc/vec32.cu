@@ -32,17 +32,31 @@ __device__ __forceinline__ double ld64(const float* p) { return f2d_bits(*p); }
 constexpr int DOT32_BLOCKS = 1216;   // 8 blocks of 256 threads per SM of a GB300
 constexpr int DOT32_CHUNK = 16;   // x-vectors per pass over the y-vectors
 
-// partial[k][blk]: the block's share of x_k . y, DOT32_CHUNK vectors x_k per pass over y
+// partial[k][blk]: the block's share of x_k . y, DOT32_CHUNK vectors x_k per pass over y.
+// Four strided elements per iteration keep several loads in flight per thread (a single
+// vector pair per thread is otherwise latency-bound).
 template <typename TX, typename TY>
 __global__ void k_dots32(const TX* x, int64_t ldx, int nx, const TY* y, int64_t n, double* partial) {
   __shared__ double red[DOT32_CHUNK][256 / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t st = int64_t(gridDim.x) * blockDim.x;
   for (int k0 = 0; k0 < nx; k0 += DOT32_CHUNK) {
     const int kc = min(DOT32_CHUNK, nx - k0);
     float acc[DOT32_CHUNK];
 #pragma unroll
     for (int c = 0; c < DOT32_CHUNK; ++c) acc[c] = 0.0f;
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    for (; i + 3 * st < n; i += 4 * st) {
+      const float y0 = d2f(y[i]), y1 = d2f(y[i + st]), y2 = d2f(y[i + 2 * st]), y3 = d2f(y[i + 3 * st]);
+#pragma unroll
+      for (int c = 0; c < DOT32_CHUNK; ++c)
+        if (c < kc) {
+          const TX* xc = x + int64_t(k0 + c) * ldx;
+          const float a0 = d2f(xc[i]), a1 = d2f(xc[i + st]), a2 = d2f(xc[i + 2 * st]), a3 = d2f(xc[i + 3 * st]);
+          acc[c] = fmaf(a0, y0, fmaf(a1, y1, fmaf(a2, y2, fmaf(a3, y3, acc[c]))));
+        }
+    }
+    for (; i < n; i += st) {
       const float yi = d2f(y[i]);
 #pragma unroll
       for (int c = 0; c < DOT32_CHUNK; ++c)
@@ -78,7 +92,25 @@ __global__ void k_dots_block32(const TX* x, int64_t ldx, int nx, const TY* y, in
     for (int c = 0; c < DOT32_CHUNK; ++c)
 #pragma unroll
       for (int j = 0; j < NY; ++j) acc[c][j] = 0.0f;
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t st = int64_t(gridDim.x) * blockDim.x;
+    int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    for (; i + st < n; i += 2 * st) {   // two strided elements per iteration
+      float yv[NY], yw[NY];
+#pragma unroll
+      for (int j = 0; j < NY; ++j) {
+        yv[j] = d2f(y[int64_t(j) * ldy + i]);
+        yw[j] = d2f(y[int64_t(j) * ldy + i + st]);
+      }
+#pragma unroll
+      for (int c = 0; c < DOT32_CHUNK; ++c) {
+        if (c < kc) {
+          const float xv = d2f(x[int64_t(k0 + c) * ldx + i]), xw = d2f(x[int64_t(k0 + c) * ldx + i + st]);
+#pragma unroll
+          for (int j = 0; j < NY; ++j) acc[c][j] = fmaf(xv, yv[j], fmaf(xw, yw[j], acc[c][j]));
+        }
+      }
+    }
+    for (; i < n; i += st) {
       float yv[NY];
 #pragma unroll
       for (int j = 0; j < NY; ++j) yv[j] = d2f(y[int64_t(j) * ldy + i]);
