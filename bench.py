@@ -107,24 +107,40 @@ def barrier(world):
         dist.barrier()
 
 
-def allreduce_max(x, world):
+def _reduce(x, world, op):
+    """All-reduce of one float over the ranks (CUDA tensor under NCCL, host tensor under gloo)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def allreduce_max(x, world):
+    import torch.distributed as dist
+    return _reduce(x, world, dist.ReduceOp.MAX) if world > 1 else x
 
 
 def allreduce_sum(x, world):
-    if world == 1:
-        return x
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(x, world, dist.ReduceOp.SUM) if world > 1 else x
+
+
+def aggregate(n_sigma_local, seconds_local, world):
+    """Whole-job throughput: sigma-vectors of all ranks / the slowest rank's time."""
+    t_max = allreduce_max(seconds_local, world)
+    total = allreduce_sum(float(n_sigma_local), world)
+    return total / t_max, t_max, total
+
+
+def rank_spec(rank):
+    """The workload of one replica: the same shapes, the seed offset by the rank."""
+    from dataclasses import replace
+    from synth import CONFIGS
+    return replace(CONFIGS[WORKLOAD], seed=CONFIGS[WORKLOAD].seed + rank)
 
 
 def cpu_sample_oracle(system, seconds_hint=30.0):
@@ -220,7 +236,7 @@ def main():
     from synth import CONFIGS, make_system
     from dataclasses import replace
 
-    spec = replace(CONFIGS[WORKLOAD], seed=CONFIGS[WORKLOAD].seed + rank)
+    spec = rank_spec(rank)
     system = make_system(spec)
     precs = {"fp64": mlcc.MLCC_FP64, "bf16": mlcc.MLCC_BF16, "bf16x3": mlcc.MLCC_BF16X3,
              "bf16x6": mlcc.MLCC_BF16X6, "fp64e": mlcc.MLCC_FP64E}
@@ -280,9 +296,7 @@ def main():
     ctx.kernel_timing(False)
     clk = clocks.stop()
     barrier(world)
-    t_max = allreduce_max(elapsed, world)
-    total_sigma = allreduce_sum(float(n_sigma), world)
-    value = total_sigma / t_max
+    value, t_max, total_sigma = aggregate(n_sigma, elapsed, world)
 
     # error against the plain binary64 GPU path (outside the timed region)
     err_fp64 = None
