@@ -365,7 +365,9 @@ void reduce_partials(const double* partial, int nsplit, int64_t M, int64_t N, do
 
 void gemm_f64(const Gemm& g, Arena& ws, cudaStream_t s, int sm_count) {
   if (g.M <= 0 || g.N <= 0) return;
-  if (g_lowp != 0 && g.K > 0 && g.batch > 0) {
+  // large products go to the tensor cores; GEMV-like shapes (a side below 16) are bound
+  // by reading their large operand once, which the binary64 kernels do without converting it
+  if (g_lowp != 0 && g.K > 0 && g.batch > 0 && g.M >= 16 && g.N >= 16) {
     const double flop = 2.0 * double(g.M) * double(g.N) * double(g.K) * double(g.batch);
     if (flop >= 2e8 && gemm_tc(g, g_lowp, ws, s, sm_count, g_lowp_err)) return;
   }

@@ -32,6 +32,9 @@ constexpr int A_BYTES = BM * BK * 2;             // 16 KB
 constexpr int B_BYTES = BN * BK * 2;             // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;   // 48 KB
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+// emulation kernel: plus a 32 x 33 fp32 staging block per epilogue warp (coalesced stores)
+constexpr int EMU_STAGE_FLOATS = 32 * 33;
+constexpr int SMEM_BYTES_EMU = SMEM_BYTES + 4 * EMU_STAGE_FLOATS * 4;
 constexpr int THREADS = 192;                     // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;  // about 2 s at 2 GHz
 constexpr int EMU_MAX_S = TC_EMU_MAX_S;
@@ -377,14 +380,16 @@ k_tc_gemm_emu(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
       }
     }
   } else {
-    // epilogue: warps 2..5 own TMEM lanes 32*(warp % 4) .. +31, one output row per thread
+    // epilogue: warps 2..5 own TMEM lanes 32*(warp % 4) .. +31; each 32 x 32 block goes
+    // through shared memory so that every warp store writes 32 consecutive floats of a row
     const int q = warp & 3;
-    const int64_t row = m0 + 32 * q + lane;
+    float* stg = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256) + q * EMU_STAGE_FLOATS;
+    const int64_t rbase = m0 + 32 * q;
     for (int c = 0; c < nc; ++c) {
       const int b = c & 1;
       if (!mbar_wait(accf0 + 8 * b, (c >> 1) & 1, p.err, 13)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      float* prow = p.part32 + int64_t(z0 + c) * p.M * p.ldp + row * p.ldp + n0;
+      float* plane = p.part32 + int64_t(z0 + c) * p.M * p.ldp;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         uint32_t r[32];
@@ -399,18 +404,18 @@ k_tc_gemm_emu(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
               "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (row < p.M) {
-          if (n0 + c0 + 32 <= p.N) {
+        // lane = row of the block: stage it, then lane = column: store row by row
 #pragma unroll
-            for (int j = 0; j < 32; j += 4)
-              *reinterpret_cast<float4*>(prow + c0 + j) =
-                  make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
-                              __uint_as_float(r[j + 3]));
-          } else {
-            for (int j = 0; j < 32; ++j)
-              if (n0 + c0 + j < p.N) prow[c0 + j] = __uint_as_float(r[j]);
+        for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = __uint_as_float(r[j]);
+        __syncwarp();
+        const int64_t col = n0 + c0 + lane;
+        if (col < p.N) {
+          for (int i = 0; i < 32; ++i) {
+            const int64_t row = rbase + i;
+            if (row < p.M) plane[row * p.ldp + col] = stg[i * 33 + lane];
           }
         }
+        __syncwarp();
       }
       // this warp has read the accumulator: the MMAs of chunk c + 2 may overwrite it
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -553,7 +558,7 @@ void tc_gemm_emu_launch(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t 
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(k_tc_gemm_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    attr = cudaFuncSetAttribute(k_tc_gemm_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES_EMU);
   });
   MLCC_CUDA(attr);
   CUtensorMap ma, mb;
@@ -578,7 +583,7 @@ void tc_gemm_emu_launch(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t 
   const int64_t nz = (nch + cpb - 1) / cpb;
   MLCC_REQUIRE(tn < 65536 && nz < 65536, "tc_gemm_emu: grid too large");
   const dim3 grid{unsigned(tm), unsigned(tn), unsigned(nz)};
-  k_tc_gemm_emu<<<grid, THREADS, SMEM_BYTES, s>>>(ma, mb, p);
+  k_tc_gemm_emu<<<grid, THREADS, SMEM_BYTES_EMU, s>>>(ma, mb, p);
   MLCC_CHECK_LAUNCH();
 }
 
