@@ -1,0 +1,151 @@
+"""Folded CC2 effective Jacobian (test infrastructure: only tests/ may use this module).
+
+For CC2 the paper points to the strategies of CC2 response theory (Sec. 2.1), where the
+doubles are folded into an energy-dependent effective Jacobian. In the three-level model
+(rows with all four indices CCSD-active, P_T, obey the CCSD equation built from P_T
+amplitudes; the other CC2-active rows, P_S, obey g~ + eps x = 0) the Jacobian blocks on
+P_S are
+    A_SS = diag(eps_aibj),   A_ST = 0,   A_TS = 0,
+so an eigenpair (omega, c) of A has c_S = (omega - eps_S)^-1 A_S1 c1, and (c1, c_T) is an
+eigenvector with eigenvalue omega of
+    A_eff(omega) = [[A_11 + A_1S (omega - eps_S)^-1 A_S1, A_1T],
+                    [A_T1,                                A_TT]].
+sigma_eff applies A_eff(omega) with two evaluations of the oracle's sigma (the definition
+A = dOmega/dx): one with c2 = 0, whose P_S rows are A_S1 c1, and one with
+c2 = c_S(omega) + c_T, whose singles and P_T rows are the result.
+
+excited_states_folded solves the nonlinear problem on small systems: its roots below the
+lowest P_S denominator are the zeros of det(A_eff(omega) - omega), with A_eff assembled
+from sigma applications (fold_parts). A plain fixed-point iteration omega <- lambda_k(omega)
+need not converge when the coupling to the doubles is strong (roots near the poles).
+"""
+import numpy as np
+
+from .mlcc import sigma as sigma_def
+
+
+def sigma_eff(sys, gs, c1, cT, omega, sigma_fn=None):
+    """A_eff(omega) (c1, c_T). cT is a doubles array of which only the P_T entries are
+    used; the result is (s1, s2) with s2 zero outside P_T."""
+    sigma_fn = sigma_fn or sigma_def
+    zero = np.zeros(sys.doubles_shape())
+    _, r2 = sigma_fn(sys, gs.t1, gs.x2, c1, zero)          # P_S rows: A_S1 c1
+    cS = np.where(sys.mask_S, r2 / (omega - sys.eps_aibj), 0.0)
+    c2 = np.where(sys.mask_T, cT, cS)
+    s1, s2 = sigma_fn(sys, gs.t1, gs.x2, c1, c2)
+    return s1, np.where(sys.mask_T, s2, 0.0)
+
+
+def unfold(sys, gs, c1, cT, omega, sigma_fn=None):
+    """The full doubles vector of a folded vector: c_S(omega) on P_S, c_T on P_T."""
+    sigma_fn = sigma_fn or sigma_def
+    _, r2 = sigma_fn(sys, gs.t1, gs.x2, c1, np.zeros(sys.doubles_shape()))
+    cS = np.where(sys.mask_S, r2 / (omega - sys.eps_aibj), 0.0)
+    return np.where(sys.mask_T, cT, cS)
+
+
+def packed_T(sys):
+    """Independent P_T parameters: (a, i, b, j) with (ai) <= (bj), all four CCSD-active."""
+    sv, so = sys.sv, sys.so
+    return [(a, i, b, j) for a in range(sv) for i in range(so) for b in range(sv) for j in range(so)
+            if sys.mask_T[a, i, b, j] and a * so + i <= b * so + j]
+
+
+def folded_matrix(sys, gs, omega, sigma_fn=None):
+    """Dense A_eff(omega) over (singles, packed P_T), column by column."""
+    nv, no = sys.nv, sys.no
+    sh = sys.doubles_shape()
+    n1 = nv * no
+    pk = packed_T(sys)
+    cols = []
+    for m in range(n1 + len(pk)):
+        c1 = np.zeros(n1)
+        cT = np.zeros(sh)
+        if m < n1:
+            c1[m] = 1.0
+        else:
+            a, i, b, j = pk[m - n1]
+            cT[a, i, b, j] = cT[b, j, a, i] = 1.0
+        s1, s2 = sigma_eff(sys, gs, c1.reshape(nv, no), cT, omega, sigma_fn)
+        cols.append(np.concatenate([s1.ravel(), [s2[p] for p in pk]]))
+    return np.array(cols).T
+
+
+def fold_parts(sys, gs, sigma_fn=None):
+    """The omega-independent pieces of A_eff, from sigma applications to unit vectors:
+    P = [[A_11, A_1T], [A_T1, A_TT]] over (singles, packed P_T); U = A_1S and V = A_S1
+    over the packed P_S pairs; d = eps on those pairs. A_eff(omega) = P + the singles
+    block U diag(1 / (omega - d)) V."""
+    sigma_fn = sigma_fn or sigma_def
+    nv, no = sys.nv, sys.no
+    n1 = nv * no
+    sh = sys.doubles_shape()
+    so = sh[1]
+    pk_all = [(a, i, b, j) for a in range(sh[0]) for i in range(so) for b in range(sh[2]) for j in range(so)
+              if a * so + i <= b * so + j]
+    pT = [q for q in pk_all if sys.mask_T[q]]
+    pS = [q for q in pk_all if not sys.mask_T[q]]
+    zero1, zero2 = np.zeros((nv, no)), np.zeros(sh)
+    P = np.zeros((n1 + len(pT), n1 + len(pT)))
+    V = np.zeros((len(pS), n1))
+    U = np.zeros((n1, len(pS)))
+    for m in range(n1):
+        e1 = np.zeros(n1)
+        e1[m] = 1.0
+        s1, s2 = sigma_fn(sys, gs.t1, gs.x2, e1.reshape(nv, no), zero2)
+        P[:n1, m] = s1.ravel()
+        P[n1:, m] = [s2[q] for q in pT]
+        V[:, m] = [s2[q] for q in pS]
+    for col, q in enumerate(pT + pS):
+        e2 = np.zeros(sh)
+        e2[q] = e2[q[2], q[3], q[0], q[1]] = 1.0
+        s1, s2 = sigma_fn(sys, gs.t1, gs.x2, zero1, e2)
+        if col < len(pT):
+            P[:n1, n1 + col] = s1.ravel()
+            P[n1:, n1 + col] = [s2[r] for r in pT]
+        else:
+            U[:, col - len(pT)] = s1.ravel()
+    d = np.array([sys.eps_aibj[q] for q in pS])
+    return P, U, V, d
+
+
+def excited_states_folded(sys, gs, n_roots, sigma_fn=None, grid=4000):
+    """Lowest solutions omega of A_eff(omega) c = omega c with 0 < omega < min(eps_S), the
+    regime below the doubles denominators that the fold is for (at most n_roots, ascending).
+    They are the zeros of det(A_eff(omega) - omega): located by sign changes on a grid and
+    refined by bisection. Without P_S pairs A_eff is the plain Jacobian."""
+    P, U, V, d = fold_parts(sys, gs, sigma_fn)
+    n1 = U.shape[0]
+    if d.size == 0:
+        w = np.linalg.eigvals(P)
+        w = np.sort(w.real[np.abs(w.imag) < 1e-9])
+        return w[w > 0][:n_roots]
+
+    def f(w):
+        M = P.copy()
+        M[:n1, :n1] += (U / (w - d)) @ V
+        sign, logdet = np.linalg.slogdet(M - w * np.eye(M.shape[0]))
+        return sign
+
+    hi = d.min() * (1.0 - 1e-9)
+    xs = np.linspace(0.0, hi, grid)
+    fs = [f(x) for x in xs]
+    roots = []
+    for x0, x1, f0, f1 in zip(xs[:-1], xs[1:], fs[:-1], fs[1:]):
+        if f0 == 0.0:
+            roots.append(x0)
+        elif f0 != f1:
+            a, b, fa = x0, x1, f0
+            for _ in range(200):
+                m = 0.5 * (a + b)
+                fm = f(m)
+                if fm == fa:
+                    a, fa = m, fm
+                else:
+                    b = m
+                if b - a < 1e-15 * max(1.0, abs(m)):
+                    break
+            roots.append(0.5 * (a + b))
+        if len(roots) >= n_roots:
+            break
+    return np.array(roots)
