@@ -1,6 +1,9 @@
 // Binary64 building blocks of libmlcc: device arena, kernel timers, a tiled DGEMM on the
 // CUDA cores (batched and batch-reduced), strided permutations, a pairwise einsum engine
-// built from those two, and deterministic reductions.
+// built from those two, and deterministic reductions. gemm_f64 is the one entry of every
+// contraction: under a LowpScope its large products go to the tensor cores (split
+// bfloat16, or the binary64 emulation), under a Vec32Scope its skinny products and the dot
+// products multiply in binary32 (vec32.cu).
 #include "internal.cuh"
 
 #include <algorithm>

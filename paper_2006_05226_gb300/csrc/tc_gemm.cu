@@ -13,6 +13,11 @@
 // Split precision: an operand x is written as x = x0 + x1 + x2 with bfloat16 pieces; the
 // products x0 y0 (MLCC_BF16), + x0 y1 + x1 y0 (MLCC_BF16X3) and + x0 y2 + x1 y1 + x2 y0
 // (MLCC_BF16X6) are laid out as extra K segments, so one GEMM of depth S * K sums them.
+//
+// k_tc_gemm_emu is the same pipeline for the binary64 emulation (MLCC_FP64E, tc_emu.cu):
+// exact fp32 sums of integer-digit products, several K chunks per CTA into two TMEM
+// accumulators in turn, each chunk drained through shared memory to its own fp32 plane.
+// Batches that share A are flattened along N with a batched output-column mapping.
 #include "system.cuh"
 #include "tc_common.cuh"
 
