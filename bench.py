@@ -34,6 +34,15 @@ WORKLOAD = "mid"
 # FP64 DFMA peak of the GB300 SM: 152 SMs x 2 FP64 FMA/clock x 2 flop x 2.070 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# DRAM bytes per algorithmic flop of the emulated binary64 GEMM (k_tc_gemm_emu + k_emu_reduce),
+# measured by ncu on a 1500 x 2304 x 6000 panel: (1.618 + 2.307 + 2.323 + 0.029) GB / 4.147e10
+EMU_DRAM_BYTES_PER_FLOP = (1.617933e9 + 2.307039e9 + 2.322620e9 + 0.028947e9) / (2.0 * 1500 * 2304 * 6000)
+
+
+def emu_traffic(flop_per_launch, avg_launch_ms):
+    """(DRAM bytes per launch, GB/s) of the emulated binary64 GEMM family."""
+    b = EMU_DRAM_BYTES_PER_FLOP * flop_per_launch
+    return b, b / (avg_launch_ms / 1e3) / 1e9
 
 
 def peaks():
@@ -370,7 +379,18 @@ def main():
                     "tensor_issue_tflops": d["algorithmic_tflops"] * ops[dom],
                     "peak_source": f"bf16 dense sustained ({bf16_peak} TFLOP/s, of {src}) / "
                                    f"{ops[dom]} bf16 products per algorithmic product"}
-        roof.update({"traffic": None, "kernel": kernels[dom], "family": dom,
+        # DRAM bytes per launch, from one ncu capture of the same kernels on a smaller product
+        # (the emulated GEMM and its chunk reduction on a 1500 x 2304 x 6000 panel of the
+        # dS = 6000 probe: dram__bytes_read.sum + dram__bytes_write.sum = 6.28 GB for
+        # 4.15e10 flop). The chunk planes, which dominate, grow with M N K like the flops, so
+        # the capture scales to a launch by its flops. Other families: not captured on
+        # their present kernels (null).
+        traffic = emu_traffic(d["flop_per_launch"], d["avg_launch_ms"]) if dom == "rank_gemm_f64e" else None
+        if traffic:
+            roof.update({"traffic_unit": "bytes per launch", "traffic_gbs": traffic[1],
+                         "traffic_source": "ncu capture of the emulated GEMM + reduction on a 1500x2304x6000 "
+                                           "panel, scaled to the launch by algorithmic flops"})
+        roof.update({"traffic": traffic[0] if traffic else None, "kernel": kernels[dom], "family": dom,
                      "achieved_is": "algorithmic 2MNK flops of the contraction per launch / launch time "
                                     "(CUDA events on the library stream)",
                      "launches": d["launches"], "avg_launch_ms": d["avg_launch_ms"],
