@@ -35,8 +35,8 @@ WORKLOAD = "mid"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 # DRAM bytes per algorithmic flop of the emulated binary64 GEMM (k_tc_gemm_emu + k_emu_reduce),
-# measured by ncu on a 1500 x 2304 x 6000 panel: (1.618 + 2.307 + 2.323 + 0.029) GB / 4.147e10
-EMU_DRAM_BYTES_PER_FLOP = (1.617933e9 + 2.307039e9 + 2.322620e9 + 0.028947e9) / (2.0 * 1500 * 2304 * 6000)
+# measured by ncu on a 1500 x 6000 x 6000 product: (5.000 + 2.041 + 2.016 + 0.071) GB / 1.08e11
+EMU_DRAM_BYTES_PER_FLOP = (4.999596e9 + 2.041011e9 + 2.016203e9 + 0.071012e9) / (2.0 * 1500 * 6000 * 6000)
 
 
 def emu_traffic(flop_per_launch, avg_launch_ms):
@@ -349,9 +349,9 @@ def main():
     pk, src = peaks()
     bf16_peak = pk.get("bf16_tflops_sustained", FALLBACK["bf16_tflops_sustained"])
     pieces = {mlcc.MLCC_BF16: 1, mlcc.MLCC_BF16X3: 3, mlcc.MLCC_BF16X6: 6}
-    # tensor-core products per algorithmic flop: split-bf16 pieces, or the 28 digit
+    # tensor-core products per algorithmic flop: split-bf16 pieces, or the 36 digit
     # products of the binary64 emulation
-    ops = {"rank_gemm_tc": pieces.get(prec, 3), "rank_gemm_f64e": 28, "rank_gemm_f64": None}
+    ops = {"rank_gemm_tc": pieces.get(prec, 3), "rank_gemm_f64e": 36, "rank_gemm_f64": None}
     kernels = {"rank_gemm_tc": "k_tc_gemm: Cholesky-rank doubles GEMMs, split bf16 (tcgen05, fp32 accumulate)",
                "rank_gemm_f64e": "k_tc_gemm (emulation mode) + k_emu_reduce: Cholesky-rank GEMMs "
                                  "in binary64 from exact bf16 integer digits",
@@ -380,16 +380,16 @@ def main():
                     "peak_source": f"bf16 dense sustained ({bf16_peak} TFLOP/s, of {src}) / "
                                    f"{ops[dom]} bf16 products per algorithmic product"}
         # DRAM bytes per launch, from one ncu capture of the same kernels on a smaller product
-        # (the emulated GEMM and its chunk reduction on a 1500 x 2304 x 6000 panel of the
-        # dS = 6000 probe: dram__bytes_read.sum + dram__bytes_write.sum = 6.28 GB for
-        # 4.15e10 flop). The chunk planes, which dominate, grow with M N K like the flops, so
-        # the capture scales to a launch by its flops. Other families: not captured on
-        # their present kernels (null).
+        # (the emulated GEMM and its chunk reduction on the 1500 x 6000 x 6000 product of the
+        # dS = 6000 probe: dram__bytes_read.sum + dram__bytes_write.sum = 9.13 GB for
+        # 1.08e11 flop). The chunk planes and the operand re-reads grow with M N K like the
+        # flops, so the capture scales to a launch by its flops. Other families: not
+        # captured on their present kernels (null).
         traffic = emu_traffic(d["flop_per_launch"], d["avg_launch_ms"]) if dom == "rank_gemm_f64e" else None
         if traffic:
             roof.update({"traffic_unit": "bytes per launch", "traffic_gbs": traffic[1],
-                         "traffic_source": "ncu capture of the emulated GEMM + reduction on a 1500x2304x6000 "
-                                           "panel, scaled to the launch by algorithmic flops"})
+                         "traffic_source": "ncu capture of the emulated GEMM + reduction on a 1500x6000x6000 "
+                                           "product, scaled to the launch by algorithmic flops"})
         roof.update({"traffic": traffic[0] if traffic else None, "kernel": kernels[dom], "family": dom,
                      "achieved_is": "algorithmic 2MNK flops of the contraction per launch / launch time "
                                     "(CUDA events on the library stream)",

@@ -74,11 +74,11 @@ typedef enum {
                        and the products x0y0 + x0y1 + x1y0                             */
   MLCC_BF16X6 = 3,  /* three pieces x0 + x1 + x2 and the six products of order <= 2   */
   MLCC_FP64E = 4    /* binary64 results from the tcgen05 tensor cores: every large GEMM
-                       splits each operand row, scaled by a power of two, into 7 signed
-                       base-2^8 integer digits (exact in bfloat16), sums the 28 digit
-                       products of weight >= 2^-48 of the leading one in fp32 chunks of at
-                       most 1024 products (exact integers), combines the chunks in 64-bit
-                       integers and rounds once to binary64. Error per product about
+                       splits each operand row, scaled by a power of two, into 8 signed
+                       base-2^7 integer digits (exact in bfloat16), sums the 36 digit
+                       products of weight >= 2^-49 of the leading one in fp32 chunks of at
+                       most 4096 products (exact integers), combines the chunks in 64-bit
+                       integers and rounds to binary64. Error per product about
                        2^-53 |max row of A| |max column of B|; a row of A or column of B
                        holding NaN or Inf gives NaN in its output row or column. Small
                        GEMMs and all element-wise work stay binary64                    */

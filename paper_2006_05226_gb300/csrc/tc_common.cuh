@@ -57,8 +57,8 @@ struct OperandCache {
 // Emulation mode of the tcgen05 GEMM: A [M][S*Kp], B [N][S*Kp] hold S integer slices of
 // Kp = 64 * kbp K elements each; chunk z of group g (gstart[g] <= z < gstart[g + 1])
 // sums, over at most `ch` K blocks of the slice pairs (i, g - i) concatenated in i, the
-// products A_i B_(g-i) into part[z][M][ldp] (fp32, exact for integer slices |q| <= 128
-// and ch * 64 <= 1024).
+// products A_i B_(g-i) into part[z][M][ldp] (fp32, exact while ch * 64 * max|q|^2 <= 2^24:
+// 4096 products of digits |q| <= 64).
 constexpr int TC_EMU_MAX_S = 8;
 void tc_gemm_emu_launch(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t M, int64_t N, int S,
                         int64_t Kp, int ch, const int* gstart, float* part, int64_t ldp, int* err,

@@ -5,18 +5,21 @@
 // operand reuse is bound by the FP64 pipe, not by HBM. Here each operand row r (a row of
 // A, or a column of B, along the contraction index k) is scaled by 2^(F - E_r), E_r the
 // exponent of the row's largest magnitude (|x| < 2^E_r), and rounded to an integer X of at
-// most F = 7 + 8 (S - 1) bits, written as S signed digits of base 2^8:
-//     X = sum_{s<S} q_s 2^(8 (S - 1 - s)),   |q_s| <= 128   (each exact in bfloat16).
+// most F = 6 + 7 (S - 1) bits, written as S signed digits of base 2^7:
+//     X = sum_{s<S} q_s 2^(7 (S - 1 - s)),   |q_s| <= 64   (each exact in bfloat16).
 // Then, with 0-based digit indices,
-//     C_mn = 2^(E_m + E_n - 2F) sum_{s,t} 2^(8 (2S - 2 - s - t)) sum_k qA_s[m][k] qB_t[n][k]
-// of which the pairs with s + t <= S - 1 are kept: every term down to 2^(-8 (S - 1)) of the
+//     C_mn = 2^(E_m + E_n - 2F) sum_{s,t} 2^(7 (2S - 2 - s - t)) sum_k qA_s[m][k] qB_t[n][k]
+// of which the pairs with s + t <= S - 1 are kept: every term down to 2^(-7 (S - 1)) of the
 // leading one, the rest lies below the rounding of X. A product of two digits is at most
-// 2^14 in magnitude, so an fp32 tensor-core accumulation of at most 1024 of them stays an
+// 2^12 in magnitude, so an fp32 tensor-core accumulation of at most 4096 of them stays an
 // exact integer (|sum| <= 2^24). The GEMM kernel sums each group g = s + t in chunks of at
-// most 1024 products and writes the exact chunk sums; a reduction combines them in 64-bit
-// integers and rounds the total once to binary64, then applies 2^(E_m + E_n ...), alpha
-// and beta. With S = 7 the truncation and the rounding of X cost about 2^-53 of
-// 2^(E_m + E_n) per product, the binary64 level of a product of the row maxima.
+// most 4096 products and writes the exact chunk sums; a reduction combines them in 64-bit
+// integers and rounds the total to binary64 (once for K <= 2^17), then applies
+// 2^(E_m + E_n ...), alpha and beta. With S = 8 (F = 55, 36 digit pairs) the truncation and
+// the rounding of X cost about 2^-53 of 2^(E_m + E_n) per product, the binary64 level of a
+// product of the row maxima. Seven-bit digits (rather than eight) need 36 pairs instead of
+// 28 but four times fewer exact chunks: the chunk planes written by the GEMM and read by
+// the reduction, which bound both kernels, shrink about threefold.
 #include "system.cuh"
 #include "tc_common.cuh"
 
@@ -26,8 +29,12 @@ namespace mlcc {
 
 namespace {
 
-constexpr int EMU_S = 7;              // digits per operand element
-constexpr int EMU_CH = 16;            // K blocks of 64 per exact fp32 chunk (1024 products)
+constexpr int EMU_S = 8;              // digits per operand element
+constexpr int EMU_BITS = 7;           // digit base 2^7, |digit| <= 64
+constexpr int EMU_F = (EMU_BITS - 1) + EMU_BITS * (EMU_S - 1);   // 55 bits of X
+constexpr int EMU_CH = 64;            // K blocks of 64 per exact fp32 chunk (4096 products)
+constexpr int EMU_HI = 28;            // the 64-bit combination: T = hi 2^EMU_HI + lo
+static_assert(EMU_CH * 64 * (1 << (2 * (EMU_BITS - 1))) <= (1 << 24), "chunk sums must stay exact in fp32");
 constexpr int EMU_NONFINITE = 1 << 30;
 constexpr int64_t EMU_MAX_K = int64_t(1) << 20;   // keeps the 64-bit combination exact
 constexpr int64_t EMU_MIN_MN = 16;                 // narrower products stay on the FMA units
@@ -97,7 +104,7 @@ __device__ __forceinline__ __nv_bfloat16 small_int_bf16(int q) {
 // arithmetic on the binary64 fields (round half away from zero on the magnitude, then
 // round-to-nearest digits so every digit stays within [-128, 128]).
 __device__ __forceinline__ void emu_digits(double x, int E, __nv_bfloat16 q[EMU_S]) {
-  constexpr int F = 7 + 8 * (EMU_S - 1);
+  constexpr int F = EMU_F;
   long long X = 0;
   const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
   const int ef = int((b >> 52) & 0x7FF);
@@ -113,7 +120,7 @@ __device__ __forceinline__ void emu_digits(double x, int E, __nv_bfloat16 q[EMU_
   }
 #pragma unroll
   for (int s = 0; s < EMU_S; ++s) {
-    const int shift = 8 * (EMU_S - 1 - s);
+    const int shift = EMU_BITS * (EMU_S - 1 - s);
     long long d = X;
     if (shift > 0) d = (X + (1LL << (shift - 1))) >> shift;   // arithmetic shift: floor
     X -= d * (1LL << shift);
@@ -161,8 +168,9 @@ struct EmuRed {
   int64_t n0;              // first output column of the panel
   int64_t nb, sCb;         // batched output columns (nb > 0): column b nb + c at C + b sCb + c
 };
-// C = alpha 2^(E_m + E_n - 14 - 8 (S - 1)) T + beta C with T = sum_g 2^(8 (S - 1 - g)) G_g,
-// G_g the integer sum of group g's chunks; T is held exactly as hi 2^32 + lo and rounded once.
+// C = alpha 2^(E_m + E_n - 2F + 7 (S - 1)) T + beta C with T = sum_g 2^(7 (S - 1 - g)) G_g,
+// G_g the integer sum of group g's chunks; T is held exactly as hi 2^28 + lo (both exact in
+// binary64 while K <= 2^17) and rounded once.
 __global__ void k_emu_reduce(EmuRed r) {
   const int64_t total = r.M * r.Nw, plane = r.M * r.ldp;
   for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
@@ -174,8 +182,8 @@ __global__ void k_emu_reduce(EmuRed r) {
     for (int g = 0; g < EMU_S; ++g) {
       long long G = 0;
       for (int z = r.gstart[g]; z < r.gstart[g + 1]; ++z) G += static_cast<long long>(__float2int_rn(p[z * plane]));
-      const int sh = 8 * (EMU_S - 1 - g);
-      if (sh >= 32) hi += G * (1LL << (sh - 32));
+      const int sh = EMU_BITS * (EMU_S - 1 - g);
+      if (sh >= EMU_HI) hi += G * (1LL << (sh - EMU_HI));
       else lo += G * (1LL << sh);
     }
     const int ea = r.ea[m], eb = r.eb[n];
@@ -183,8 +191,8 @@ __global__ void k_emu_reduce(EmuRed r) {
     if (ea == EMU_NONFINITE || eb == EMU_NONFINITE) {
       v = __longlong_as_double(0x7FF8000000000000LL);
     } else {
-      v = fma(static_cast<double>(hi), 4294967296.0, static_cast<double>(lo));
-      v = ldexp(v, ea + eb - 14 - 8 * (EMU_S - 1));
+      v = fma(static_cast<double>(hi), double(1LL << EMU_HI), static_cast<double>(lo));
+      v = ldexp(v, ea + eb - 2 * EMU_F + EMU_BITS * (EMU_S - 1));
     }
     int64_t col = r.n0 + n, cb = 0;
     if (r.nb > 0) {

@@ -5,8 +5,8 @@ Pins, through the C ABI (mlcc_gemm and the solver entry points):
      every fp32 tensor-core chunk sum must be exact and the 64-bit combination lossless;
   2. random binary64 operands with rows and columns of very different scale, zero rows,
      subnormals, alpha / beta and every transpose agree with numpy's binary64 product
-     within the error bound of the splitting (7 digits of 8 bits, products kept down to
-     2^-48 of the leading one: about 2^-53 of max|row| max|column| per product);
+     within the error bound of the splitting (8 digits of 7 bits, products kept down to
+     2^-49 of the leading one: about 2^-53 of max|row| max|column| per product);
   3. a Cholesky-rank GEMM of the 340-orbital workload (12000 x 12000 x 1500), sampled rows;
   4. through the solver: sigma, the ground state and the excited states agree with the
      binary64 path and the oracle.
@@ -71,7 +71,7 @@ def _bound(A, B):
 
 @pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True), (True, True)])
 def test_exact_integer_product(ctx, ta, tb):
-    """|a|, |b| < 2^20: three digits hold every element, K * 2^40 < 2^53 holds every sum, so
+    """|a|, |b| < 2^20: four digits hold every element, K * 2^40 < 2^53 holds every sum, so
     the emulated product is the exact integer product (several tiles, ragged edges, chunks
     of every group across K = 2100)."""
     from paper_2006_05226_gb300 import mlcc
