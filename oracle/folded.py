@@ -14,6 +14,11 @@ sigma_eff applies A_eff(omega) with two evaluations of the oracle's sigma (the d
 A = dOmega/dx): one with c2 = 0, whose P_S rows are A_S1 c1, and one with
 c2 = c_S(omega) + c_T, whose singles and P_T rows are the result.
 
+excited_states_folded_iterative does it by iteration for larger systems whose roots lie
+well below the P_S denominators. On the 48-orbital workload it needs about 4x the
+sigma-vector count of the unfolded Davidson (each sigma_eff is two sigma evaluations here),
+so a production solver has to reuse its subspace across omega updates.
+
 excited_states_folded solves the nonlinear problem on small systems: its roots below the
 lowest P_S denominator are the zeros of det(A_eff(omega) - omega), with A_eff assembled
 from sigma applications (fold_parts). A plain fixed-point iteration omega <- lambda_k(omega)
@@ -149,3 +154,59 @@ def excited_states_folded(sys, gs, n_roots, sigma_fn=None, grid=4000):
         if len(roots) >= n_roots:
             break
     return np.array(roots)
+
+
+def excited_states_folded_iterative(sys, gs, n_roots, tol=1e-10, res_tol=1e-9, max_macro=40, sigma_fn=None):
+    """The folded problem by iteration, for systems whose roots lie well below the P_S
+    denominators (then lambda_k(omega) depends weakly on omega):
+      1. a linear Davidson for the n_roots lowest eigenpairs of A_eff(omega_0), omega_0 = 0;
+      2. per root k, the fixed point omega <- lambda_k(omega), where lambda_k is the k-th
+         lowest eigenvalue of A_eff(omega) from a linear Davidson warm-started on the
+         previous eigenvectors.
+    Vectors are (singles, doubles) with the doubles restricted to P_T. Returns
+    (roots ascending, number of sigma_eff applications)."""
+    from .davidson import davidson
+    nv, no = sys.nv, sys.no
+    n1 = nv * no
+    sh = sys.doubles_shape()
+    maskT = sys.mask_T.ravel()
+    count = [0]
+
+    def apply_eff(omega):
+        def apply(V):
+            out = np.zeros_like(V)
+            for k in range(V.shape[1]):
+                c1 = V[:n1, k].reshape(nv, no)
+                cT = V[n1:, k].reshape(sh)
+                s1, s2 = sigma_eff(sys, gs, c1, cT, omega, sigma_fn)
+                out[:n1, k] = s1.ravel()
+                out[n1:, k] = s2.ravel()
+                count[0] += 1
+            return out
+        return apply
+
+    def project(v):
+        d = np.where(maskT, v[n1:], 0.0).reshape(sh)
+        return np.concatenate([v[:n1], (0.5 * (d + d.transpose(2, 3, 0, 1))).ravel()])
+
+    # outside P_T the preconditioner denominator is huge: those components stay zero
+    diag = np.concatenate([sys.eps_ai.ravel(), np.where(maskT, sys.eps_aibj.ravel(), 1e30)])
+    n_guess = min(2 * n_roots, n1)
+    order = np.argsort(sys.eps_ai.ravel(), kind="stable")[:n_guess]
+    guess = np.zeros((diag.size, n_guess))
+    guess[order, np.arange(n_guess)] = 1.0
+    first = davidson(apply_eff(0.0), diag, n_roots, guess, res_tol=1e-6, w_tol=1e-8, project=project)
+    roots = []
+    for k in range(n_roots):
+        omega, X = first.omega[k], first.vectors[:, :k + 1]
+        for _ in range(max_macro):
+            r = davidson(apply_eff(omega), diag, k + 1, X, res_tol=res_tol, w_tol=tol, project=project)
+            lam, X = r.omega[k], r.vectors
+            done = abs(lam - omega) < tol
+            omega = lam
+            if done:
+                break
+        else:
+            raise RuntimeError(f"folded root {k}: no fixed point in {max_macro} iterations")
+        roots.append(omega)
+    return np.sort(np.array(roots)), count[0]

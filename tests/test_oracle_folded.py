@@ -110,3 +110,19 @@ def test_unfolded_eigenvector_is_an_eigenvector_of_A(sys7, name, lev):
     # and sigma_eff leaves (c1, c_T) with eigenvalue w0
     e1, e2 = sigma_eff(osys, gs, c1, cT, w0)
     assert np.abs(e1 - w0 * c1).max() < 1e-9 and np.abs(e2 - w0 * np.where(osys.mask_T, cT, 0)).max() < 1e-9
+
+
+def test_iterative_folded_solver_on_the_48_orbital_workload():
+    """The iterative solver (linear Davidson on A_eff(omega), fixed point in omega) gives the
+    unfolded roots of the 48-orbital, three-level workload, whose P_S denominators (>= 0.96
+    Ha) lie far above its roots."""
+    from oracle.davidson import excited_states
+    from oracle.folded import excited_states_folded_iterative
+    from synth import CONFIGS, make_system
+    s = make_system(CONFIGS["small"])
+    osys = MLCCSystem(s.L, s.fock, s.spec.n_occ, s.level)
+    gs = solve_ground_state(osys)
+    ref = excited_states(osys, gs, 3, res_tol=1e-9)
+    roots, n_eff = excited_states_folded_iterative(osys, gs, 3)
+    assert np.abs(roots - ref.omega).max() < 1e-9
+    assert osys.eps_aibj[osys.mask_S].min() > 2.5 * roots.max()
