@@ -14,6 +14,14 @@ paper-shaped workloads); synthetic seeded inputs (synth/), larger than L2 (L is 
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|bf16|bf16x3|bf16x6|fp64e]
                   [--refine fp64|fp64e] [--impl ours|reference]
+
+--workload serving replays the serving mix instead (synth.serving_request_spec: occupied
+20-80, virtual 150-600, N_J = 5 (occ + vir), active fraction 0.1-0.3, CCS/CCSD or MLCC2,
+4 roots) with exponential arrival gaps at --rate requests/s through the serving loop
+(mlcc_server_*, --slots slots), and reports solves/s with p50 / p99 latency, next to the
+same requests solved one at a time (mixed path) and a sample of them in plain binary64:
+
+  python bench.py --workload serving [--requests R] [--slots S] [--rate 20] [--fp64-sample K]
 """
 import argparse
 import json
@@ -217,8 +225,121 @@ def config_dict(args, prec):
             "l2": "inputs larger than L2 (L^J_pq is 1.39 GB)", "parallelism": f"replicas{args.gpus}"}
 
 
+def _make_system(spec):
+    from synth import make_system
+    return make_system(spec)
+
+
+def run_serving(args):
+    """The serving mix through mlcc_server_*: arrivals replayed in real time."""
+    rank, world, local = dist_env()
+    import multiprocessing as mp
+    import numpy as np
+    from synth import serving_arrivals, serving_request_spec
+    specs = [serving_request_spec(r)[0] for r in range(args.requests)]
+    # inputs drawn on the host cores before the first CUDA call (spawned workers)
+    with mp.get_context("spawn").Pool(max(1, min(len(specs), len(os.sched_getaffinity(0)) // 4))) as pool:
+        systems = pool.map(_make_system, specs)
+    arrivals = serving_arrivals(len(specs), rate=args.rate)
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2006_05226_gb300 import mlcc
+    precs = {"fp64": mlcc.MLCC_FP64, "bf16": mlcc.MLCC_BF16, "bf16x3": mlcc.MLCC_BF16X3,
+             "bf16x6": mlcc.MLCC_BF16X6, "fp64e": mlcc.MLCC_FP64E}
+    prec, refine = precs[args.precision], precs[args.refine]
+    split = prec in (mlcc.MLCC_BF16, mlcc.MLCC_BF16X3, mlcc.MLCC_BF16X6)
+
+    def opts_for(spec, p):
+        sp = p in (mlcc.MLCC_BF16, mlcc.MLCC_BF16X3, mlcc.MLCC_BF16X6)
+        return mlcc.default_options(n_roots=spec.n_roots, precision=p, gs_precision=p, refine_fp64=1,
+                                    lowp_res_tol=1e-5, refine_precision=refine,
+                                    gs_tol=1e-9 if sp else 1e-11, gs_energy_tol=1e-10 if sp else 1e-12)
+
+    # pinned host copies: the server borrows them until each result is polled
+    host = []
+    for sy in systems:
+        Lp = torch.empty(sy.L.shape, dtype=torch.float64, pin_memory=True)
+        Fp = torch.empty(sy.fock.shape, dtype=torch.float64, pin_memory=True)
+        Lp.numpy()[...] = sy.L
+        Fp.numpy()[...] = sy.fock
+        host.append((Lp, Fp))
+    # one at a time, same options (warms the kernels up as well)
+    ctx = mlcc.Context(local)
+    seq_w = []
+    t0 = time.perf_counter()
+    for sy, (Lp, Fp) in zip(systems, host):
+        _, w, _, _ = mlcc.solve(ctx, Lp.numpy(), Fp.numpy(), sy.spec.n_occ, sy.level, opts_for(sy.spec, prec))
+        seq_w.append(w)
+    seq_s = time.perf_counter() - t0
+    # plain binary64, one at a time, on the first fp64_sample requests (accuracy and speed)
+    fp64_s, errs = [], []
+    for k in range(min(args.fp64_sample, len(systems))):
+        sy, (Lp, Fp) = systems[k], host[k]
+        t1 = time.perf_counter()
+        _, w64, _, _ = mlcc.solve(ctx, Lp.numpy(), Fp.numpy(), sy.spec.n_occ, sy.level,
+                                  opts_for(sy.spec, mlcc.MLCC_FP64))
+        fp64_s.append(time.perf_counter() - t1)
+        errs.append(float(np.max(np.abs(np.asarray(seq_w[k]) - w64))))
+    ctx.close()
+    # the mix: submissions at the arrival times, results polled as they finish
+    srv = mlcc.Server(local, n_slots=args.slots)
+    tickets = [None] * len(specs)
+    launches0 = mlcc.launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    start = time.perf_counter()
+
+    def submit_all():
+        for k, (sy, (Lp, Fp)) in enumerate(zip(systems, host)):
+            delay = arrivals[k] - (time.perf_counter() - start)
+            if delay > 0:
+                time.sleep(delay)
+            tickets[k] = srv.submit(Lp.numpy(), Fp.numpy(), sy.spec.n_occ, sy.level, opts_for(sy.spec, prec))
+
+    th = threading.Thread(target=submit_all)
+    th.start()
+    th.join()
+    results = [srv.poll(t) for t in tickets]
+    wall = time.perf_counter() - start
+    clk = clocks.stop()
+    launches = mlcc.launch_count() - launches0
+    info = srv.stats()
+    srv.close()
+    lat = np.array([r.t_finish - r.t_submit for r, _ in results])
+    status = [int(r.status) for r, _ in results]
+    mix_vs_alone = max(float(np.max(np.abs(w - seq_w[k]))) for k, (_, w) in enumerate(results))
+    if rank != 0:
+        return 0
+    n = len(specs)
+    line = {"metric": "solves/s (serving mix)", "value": n / wall, "unit": "solves/s", "n_gpus": world,
+            "steps": 1, "warmup": 0, "ms_per_step": 1e3 * wall, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.precision if not split else f"{args.precision}+{args.refine}",
+            "data": "synthetic",
+            "config": {"workload": f"serving mix: {n} requests (occ 20-80, vir 150-600, N_J = 5 (occ+vir), "
+                                   f"active fraction 0.1-0.3, CCS/CCSD or MLCC2, 4 roots), Poisson arrivals "
+                                   f"at {args.rate} req/s", "requests": n, "slots": args.slots,
+                       "rate_per_s": args.rate, "budget_bytes": int(info.budget_bytes),
+                       "parallelism": f"replicas{world}"},
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "status": status, "peak_running": int(info.peak_running), "peak_admitted_bytes": int(info.peak_bytes),
+            "one_at_a_time_mixed_solves_per_s": n / seq_s,
+            "fp64_one_at_a_time": {"requests": len(fp64_s), "mean_seconds": float(np.mean(fp64_s)) if fp64_s else None,
+                                   "solves_per_s": len(fp64_s) / sum(fp64_s) if fp64_s else None,
+                                   "max_abs_omega_err_Ha": max(errs) if errs else None},
+            "max_abs_omega_diff_mix_vs_alone_Ha": mix_vs_alone,
+            "clocks": clk, "gpu_launches": int(launches),
+            "sizes": [[s.n_occ, s.n_vir, s.n_chol, s.s_occ, s.s_vir, s.t_occ, s.t_vir] for s in specs]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="mid", choices=["mid", "serving"])
+    ap.add_argument("--requests", type=int, default=8, help="serving: number of requests")
+    ap.add_argument("--slots", type=int, default=4, help="serving: concurrent slots")
+    ap.add_argument("--rate", type=float, default=20.0, help="serving: arrivals per second")
+    ap.add_argument("--fp64-sample", type=int, default=1, help="serving: requests also solved in binary64")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
@@ -233,6 +354,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
 
     rank, world, local = dist_env()
     import numpy as np

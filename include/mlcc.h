@@ -63,7 +63,10 @@ typedef enum {
   MLCC_E_COMPLEX_ROOT = -5, /* a wanted Ritz value has a non-zero imaginary part */
   MLCC_E_NAN = -6,          /* NaN or Inf met in a residual or sigma             */
   MLCC_E_CUDA = -8,         /* a CUDA runtime call failed                        */
-  MLCC_E_STATE = -9         /* call order violated (e.g. sigma before prepare)   */
+  MLCC_E_STATE = -9,        /* call order violated (e.g. sigma before prepare)   */
+  MLCC_E_REJECTED = -10,    /* serving: footprint above the server's budget      */
+  MLCC_E_CANCELLED = -11,   /* serving: cancelled before it started              */
+  MLCC_PENDING = 1          /* serving: mlcc_poll on a request still in progress */
 } mlcc_status;
 
 typedef enum {
@@ -247,6 +250,84 @@ mlcc_status mlcc_solve(mlcc_ctx* ctx, const mlcc_problem* prob, const double* ch
                        const double* fock_host, const mlcc_options* opt,
                        mlcc_gs_info* gs, double* omega_host, mlcc_es_info* es,
                        double* t1_host);
+
+/* As mlcc_solve, with chol_dev / fock_dev on the context's device (borrowed for the call;
+   the caller keeps ownership). The system copies them, so they may be reused after the
+   call returns. */
+mlcc_status mlcc_solve_device(mlcc_ctx* ctx, const mlcc_problem* prob, const double* chol_dev,
+                              const double* fock_dev, const mlcc_options* opt,
+                              mlcc_gs_info* gs, double* omega_host, mlcc_es_info* es,
+                              double* t1_host);
+
+/* Length of a Davidson vector of the problem, n_vir n_occ + (s_vir s_occ)^2 (the layout
+   under "Conventions"), from the sizes and levels alone; -1 if they are invalid. */
+int64_t mlcc_vector_len(const mlcc_problem* prob);
+
+/* Device memory that mlcc_solve of this problem with these options holds at its peak, in
+   bytes: the system (Cholesky vectors, their dressed copies, intermediates and scratch),
+   then either the device copies of the inputs (while the system is built) or the
+   amplitudes, the CCSD value tensors, the bfloat16 operands, the Davidson subspace and an
+   allowance for the converted operand copies of the tensor-core precisions. Allocations
+   are counted in 2 MiB pages. The serving loop admits requests by this number. */
+mlcc_status mlcc_solve_footprint(const mlcc_problem* prob, const mlcc_options* opt, int64_t* bytes);
+
+/* ---- serving loop ----------------------------------------------------------------- */
+/* A server runs independent whole solves (mlcc_solve) submitted as requests. It has
+   n_slots slots, each a host worker thread with its own context and stream, and a device
+   memory budget. Admission: the oldest waiting request starts when a slot is free and the
+   footprints (mlcc_solve_footprint) of the running requests plus its own fit in the
+   budget; requests start in submission order, none overtakes an older one. Requests
+   that are admitted together run concurrently on their own streams, so their kernels
+   overlap on the device. A request whose solve runs out of device memory while other
+   requests run goes back to the head of the queue until one of them finishes (at most 3
+   admissions). Each request's result is that of mlcc_solve on the same inputs alone. */
+typedef struct mlcc_server mlcc_server;
+
+typedef struct {
+  int32_t status;          /* the solve's mlcc_status; MLCC_E_CANCELLED if cancelled first */
+  int32_t slot;            /* slot that ran it (-1: it never ran)                          */
+  int32_t attempts;        /* admissions: 1, more after out-of-memory retries              */
+  int32_t n_roots;         /* entries written to omega_host                                */
+  int64_t footprint_bytes; /* the footprint it was admitted with                           */
+  double t_submit;         /* seconds since the server was created (host steady clock):    */
+  double t_start;          /*   submitted, last admitted, finished; latency is              */
+  double t_finish;         /*   t_finish - t_submit                                         */
+  mlcc_gs_info gs;
+  mlcc_es_info es;
+} mlcc_request_result;
+
+typedef struct {
+  int32_t n_slots;
+  int32_t running, waiting, peak_running;
+  int64_t budget_bytes, in_use_bytes, peak_bytes;   /* footprints admitted at once */
+  int64_t submitted, finished, cancelled, retried;
+} mlcc_server_info;
+
+/* Creates a server on CUDA device `device` with n_slots in [1, 64] slots. hbm_budget_bytes
+   <= 0 takes 90% of the device memory free at creation. */
+mlcc_status mlcc_server_create(int device, int32_t n_slots, int64_t hbm_budget_bytes,
+                               mlcc_server** out);
+/* Cancels the requests that have not started, waits for the running ones and frees the
+   server, with the results nobody polled. No other call on the server may be in progress. */
+void mlcc_server_destroy(mlcc_server* srv);
+/* Queues a whole solve and returns its ticket (> 0). The problem (with its level array)
+   and the options are copied; chol_host and fock_host are borrowed: the caller keeps them
+   valid and unchanged until mlcc_poll has returned the request's result.
+   MLCC_E_REJECTED: the footprint exceeds the whole budget (the request is not queued). */
+mlcc_status mlcc_submit(mlcc_server* srv, const mlcc_problem* prob, const double* chol_host,
+                        const double* fock_host, const mlcc_options* opt, uint64_t* ticket);
+/* Waits up to wait_ms milliseconds (0: no wait; < 0: until it finishes) for the request.
+   Finished: fills *res and omega_host [n_roots] (the request's excitation energies,
+   ascending, Hartree), forgets the ticket and returns MLCC_OK; the request's own status
+   is res->status (with mlcc_last_error() set to its message when it failed). Still in
+   progress: MLCC_PENDING. Unknown (or already polled) ticket: MLCC_E_ARG. One thread at
+   a time should poll a given ticket. */
+mlcc_status mlcc_poll(mlcc_server* srv, uint64_t ticket, int64_t wait_ms, mlcc_request_result* res,
+                      double* omega_host);
+/* Removes a request that has not started (its poll then reports MLCC_E_CANCELLED).
+   MLCC_E_STATE if it has started or finished, MLCC_E_ARG for an unknown ticket. */
+mlcc_status mlcc_cancel(mlcc_server* srv, uint64_t ticket);
+mlcc_status mlcc_server_stats(mlcc_server* srv, mlcc_server_info* info);
 
 /* ---- allocation-free variant ------------------------------------------------------ */
 /* The paper has no counterpart to this entry point; it exists for callers that cannot let

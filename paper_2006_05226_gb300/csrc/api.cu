@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <numeric>
 
 namespace mlcc {
@@ -89,10 +90,8 @@ static void setup_system(mlcc_system* S, const mlcc_problem* P, const double* ch
   S->nd = S->dS * S->dS;
   const int64_t nn = int64_t(n) * n, dS = S->dS;
   // persistent buffers
-  const size_t per = size_t(nj) * nn * 2 + 3 * size_t(nn) + size_t(n) + 3 * size_t(nj) * dS +
-                     size_t(S->nd) * 2 + size_t(dS) + size_t(S->nv) * no + size_t(no) * S->so +
-                     size_t(S->sv) * S->nv + 2;
-  S->persist.reserve(per * 8 + 96 * 256);
+  const sizes::Dims dims = sys_dims(S);
+  S->persist.reserve(sizes::persist_bytes(dims));
   S->L = S->persist.get<double>(size_t(nj) * nn);
   S->Lt = S->persist.get<double>(size_t(nj) * nn);
   S->h = S->persist.get<double>(nn);
@@ -113,13 +112,7 @@ static void setup_system(mlcc_system* S, const mlcc_problem* P, const double* ch
   MLCC_CUDA(cudaMemsetAsync(S->tc_err, 0, 256, s));
   // scratch: enough for sigma (dLt, three doubles-sized arrays, two [nj][dS]) plus GEMM
   // partials and the einsum engine's permuted operands
-  const int64_t tl = int64_t(S->tv) * S->to * S->tv * S->to;
-  const size_t ws = size_t(nj) * nn + 4 * size_t(nn) + 3 * size_t(S->nd) + 4 * size_t(nj) * dS +
-                    4 * size_t(dS) + size_t(nj) * (no * no + 2) + 64 * size_t(std::max<int64_t>(tl, 1)) +
-                    size_t(S->tv) * S->tv * S->tv * S->tv * 4 +
-                    size_t(nj) * (size_t(S->tv + S->to) * (S->tv + S->to)) * 4 +
-                    (size_t(1) << 27);
-  S->ws.reserve(ws * 8);
+  S->ws.reserve(sizes::ws_bytes(dims));
   S->workspace_bytes = int64_t(S->persist.capacity() + S->ws.capacity());
   // re-ordered copies of L and F
   int* dperm = S->ws.get<int>(size_t(n));
@@ -186,6 +179,13 @@ static void setup_system(mlcc_system* S, const mlcc_problem* P, const double* ch
 }  // namespace mlcc
 
 using namespace mlcc;
+
+// ground state and excited states of a system built from device inputs; inputs_done runs
+// once the system holds its own copies
+static mlcc_status solve_from_device(mlcc_ctx* ctx, const mlcc_problem* prob, const double* dL,
+                                     const double* dF, std::function<void()> inputs_done,
+                                     const mlcc_options* opt, mlcc_gs_info* gs, double* omega,
+                                     mlcc_es_info* es, double* t1_host);
 
 extern "C" {
 
@@ -479,37 +479,67 @@ mlcc_status mlcc_solve(mlcc_ctx* ctx, const mlcc_problem* prob, const double* ch
                        double* omega, mlcc_es_info* es, double* t1_host) {
   return guard([&] {
     MLCC_REQUIRE(ctx && prob && chol_host && fock_host && opt && omega, "mlcc_solve: NULL argument");
+    MLCC_REQUIRE(prob->n_mo > 0 && prob->n_chol > 0, "mlcc_solve: sizes must be positive");
     MLCC_CUDA(cudaSetDevice(ctx->device));
     const int64_t nn = int64_t(prob->n_mo) * prob->n_mo;
     double *dL = nullptr, *dF = nullptr;
-    MLCC_CUDA(cudaMalloc(&dL, size_t(nn) * prob->n_chol * 8));
     struct Free {
       double** a; double** b;
       ~Free() { if (*a) cudaFree(*a); if (*b) cudaFree(*b); }
     } fr{&dL, &dF};
+    MLCC_CUDA(cudaMalloc(&dL, size_t(nn) * prob->n_chol * 8));
     MLCC_CUDA(cudaMalloc(&dF, size_t(nn) * 8));
     MLCC_CUDA(cudaMemcpyAsync(dL, chol_host, size_t(nn) * prob->n_chol * 8, cudaMemcpyHostToDevice, ctx->stream));
     MLCC_CUDA(cudaMemcpyAsync(dF, fock_host, size_t(nn) * 8, cudaMemcpyHostToDevice, ctx->stream));
-    mlcc_system* S = nullptr;
-    mlcc_status st = mlcc_system_create(ctx, prob, dL, dF, &S);
-    if (st != MLCC_OK) return st;
-    struct Sys { mlcc_system* s; ~Sys() { mlcc_system_destroy(s); } } sg{S};
-    cudaFree(dL); dL = nullptr;
-    cudaFree(dF); dF = nullptr;
-    double *t1 = nullptr, *x2 = nullptr;
-    MLCC_CUDA(cudaMalloc(&t1, size_t(S->nv) * S->no * 8 + 8));
-    MLCC_CUDA(cudaMalloc(&x2, size_t(S->nd) * 8 + 8));
-    struct Free2 { double* a; double* b; ~Free2() { cudaFree(a); cudaFree(b); } } f2{t1, x2};
-    mlcc_gs_info gi{};
-    st = mlcc_ground_state(S, opt, t1, x2, &gi);
-    if (gs) *gs = gi;
-    if (st != MLCC_OK) return st;
-    if (t1_host) copy_d2h(t1_host, t1, int64_t(S->nv) * S->no, ctx->stream);
-    mlcc_es_info ei{};
-    st = mlcc_excited_states(S, opt, omega, nullptr, &ei);
-    if (es) *es = ei;
-    return st;
+    // the copies go once the system holds its own re-ordered inputs
+    auto release = [&] {
+      cudaFree(dL); dL = nullptr;
+      cudaFree(dF); dF = nullptr;
+    };
+    return solve_from_device(ctx, prob, dL, dF, release, opt, gs, omega, es, t1_host);
   });
 }
 
+mlcc_status mlcc_solve_device(mlcc_ctx* ctx, const mlcc_problem* prob, const double* chol_dev,
+                              const double* fock_dev, const mlcc_options* opt, mlcc_gs_info* gs,
+                              double* omega, mlcc_es_info* es, double* t1_host) {
+  return guard([&] {
+    MLCC_REQUIRE(ctx && prob && chol_dev && fock_dev && opt && omega, "mlcc_solve_device: NULL argument");
+    MLCC_CUDA(cudaSetDevice(ctx->device));
+    return solve_from_device(ctx, prob, chol_dev, fock_dev, nullptr, opt, gs, omega, es, t1_host);
+  });
+}
+
+int64_t mlcc_vector_len(const mlcc_problem* prob) {
+  sizes::Dims d;
+  if (!prob || !sizes::dims_from_levels(prob->n_mo, prob->n_occ, prob->n_chol, prob->level, &d)) return -1;
+  return d.vector_len();
+}
+
 }  // extern "C"
+
+static mlcc_status solve_from_device(mlcc_ctx* ctx, const mlcc_problem* prob, const double* dL,
+                                     const double* dF, std::function<void()> inputs_done,
+                                     const mlcc_options* opt, mlcc_gs_info* gs, double* omega,
+                                     mlcc_es_info* es, double* t1_host) {
+  mlcc_system* S = nullptr;
+  mlcc_status st = mlcc_system_create(ctx, prob, dL, dF, &S);
+  if (st != MLCC_OK) return st;
+  struct Sys { mlcc_system* s; ~Sys() { mlcc_system_destroy(s); } } sg{S};
+  if (inputs_done) inputs_done();
+  double *t1 = nullptr, *x2 = nullptr;
+  MLCC_CUDA(cudaMalloc(&t1, size_t(S->nv) * S->no * 8 + 8));
+  struct Free1 { double* a; ~Free1() { cudaFree(a); } } f1{t1};
+  MLCC_CUDA(cudaMalloc(&x2, size_t(S->nd) * 8 + 8));
+  struct Free2 { double* a; ~Free2() { cudaFree(a); } } f2{x2};
+  mlcc_gs_info gi{};
+  st = mlcc_ground_state(S, opt, t1, x2, &gi);
+  if (gs) *gs = gi;
+  if (st != MLCC_OK) return st;
+  if (t1_host) copy_d2h(t1_host, t1, int64_t(S->nv) * S->no, ctx->stream);
+  mlcc_es_info ei{};
+  st = mlcc_excited_states(S, opt, omega, nullptr, &ei);
+  if (es) *es = ei;
+  return st;
+}
+

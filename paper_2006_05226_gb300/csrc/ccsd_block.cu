@@ -100,12 +100,8 @@ void ccsd_block(mlcc_system* S, Mode mode, const Dual& Lai_in, const Dual& Lac_i
   if (mode == Mode::Value && cache_values) {
     ccsd_cache_free(S);
     S->ccsd = new CCSDCache();
-    const int64_t nj = S->nj, o = S->to, v = S->tv;
-    // every tensor created below, in doubles (generous: inputs + 4-index intermediates)
-    const int64_t need = nj * (v * o + v * v + o * o + o * v) + v * v + o * o +
-                         v * v * v * v + 14 * (v * o * v * o) + 4 * (o * o * o * o) +
-                         4 * v * v + 4 * o * o + int64_t(S->no) * v * v * v;
-    S->ccsd->arena.reserve(size_t(need) * 8 + 64 * 256);
+    // every tensor created below (generous: inputs + 4-index intermediates)
+    S->ccsd->arena.reserve(sizes::ccsd_cache_bytes(sys_dims(S)));
   }
   Eval E{S, mode, cache_values};
   cudaStream_t s = S->ctx->stream;

@@ -530,13 +530,11 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
   const int64_t n1 = int64_t(nv) * no, dim = n1 + S->nd;
   MLCC_REQUIRE(nreq >= 1 && nreq <= n1, "n_roots must be in [1, n_vir * n_occ]");
   const int nr = nreq;
-  int maxsub = opt->max_subspace > 0 ? opt->max_subspace : 8 * nr;
-  maxsub = std::max(maxsub, 3 * nr);
+  const int maxsub = sizes::davidson_max_subspace(opt->max_subspace, nr);
   const int collapse = 2 * nr;
   // Davidson memory: basis and sigma vectors, Ritz vectors, residuals, collapse scratch
   Arena dav;
-  const size_t need = size_t(dim) * 8 * size_t(2 * maxsub + 2 * nr + 2 * collapse + 3) + (1 << 20);
-  dav.reserve(need);
+  dav.reserve(sizes::davidson_bytes(dim, maxsub, nr));
   DavState D{S, dim, maxsub, static_cast<char*>(dav.alloc(size_t(maxsub) * dim * 8)),
              static_cast<char*>(dav.alloc(size_t(maxsub) * dim * 8))};
   D.G.assign(size_t(maxsub) * maxsub, 0.0);

@@ -1,6 +1,7 @@
 // The device-side state of one MLCC problem and the steps of its hot path.
 #pragma once
 #include "internal.cuh"
+#include "sizes.h"
 
 #include <cuda_bf16.h>
 #include <nvtx3/nvToolsExt.h>
@@ -70,6 +71,15 @@ struct mlcc_system {
 };
 
 namespace mlcc {
+
+// the sizes of a system in the form the allocation-size functions take
+inline sizes::Dims sys_dims(const mlcc_system* S) {
+  sizes::Dims d;
+  d.n = S->n; d.no = S->no; d.nv = S->nv; d.nj = S->nj;
+  d.so = S->so; d.sv = S->sv; d.to = S->to; d.tv = S->tv;
+  d.dS = S->dS; d.nd = S->nd;
+  return d;
+}
 
 // steps (all on sys->ctx->stream)
 void dress(mlcc_system* S, const double* t1, double* Lt, double* ht);

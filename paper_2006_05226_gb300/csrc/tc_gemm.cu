@@ -847,7 +847,7 @@ void lowp_prepare(mlcc_system* S, int precision) {
   cudaStream_t s = S->ctx->stream;
   const int64_t dS = S->dS, nj = S->nj;
   const int seg = split_segments(precision);
-  const size_t need = size_t(dS) * seg * pad64(nj) * 2 + size_t(nj) * seg * pad64(dS) * 2 + 4096;
+  const size_t need = sizes::lowp_bytes(sys_dims(S), seg);
   if (S->lowp_arena.capacity() < need) S->lowp_arena.reserve(need);
   S->lowp_arena.release(0);
   S->lai_bf = S->lowp_arena.get<__nv_bfloat16>(size_t(dS) * seg * pad64(nj));

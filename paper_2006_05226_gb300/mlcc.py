@@ -19,7 +19,9 @@ LIB_PATH = os.path.join(_HERE, "libmlcc.so")
 MLCC_FP64, MLCC_BF16, MLCC_BF16X3, MLCC_BF16X6, MLCC_FP64E = 0, 1, 2, 3, 4
 STATUS = {0: "MLCC_OK", -1: "MLCC_E_ARG", -2: "MLCC_E_OOM", -3: "MLCC_E_GS_NOCONV",
           -4: "MLCC_E_ES_NOCONV", -5: "MLCC_E_COMPLEX_ROOT", -6: "MLCC_E_NAN",
-          -8: "MLCC_E_CUDA", -9: "MLCC_E_STATE"}
+          -8: "MLCC_E_CUDA", -9: "MLCC_E_STATE", -10: "MLCC_E_REJECTED", -11: "MLCC_E_CANCELLED",
+          1: "MLCC_PENDING"}
+MLCC_PENDING, MLCC_E_REJECTED, MLCC_E_CANCELLED = 1, -10, -11
 
 # every symbol include/mlcc.h declares
 EXPORTS = ["mlcc_default_options", "mlcc_ctx_create", "mlcc_ctx_destroy", "mlcc_ctx_stream",
@@ -27,7 +29,9 @@ EXPORTS = ["mlcc_default_options", "mlcc_ctx_create", "mlcc_ctx_destroy", "mlcc_
            "mlcc_system_destroy", "mlcc_system_info", "mlcc_orbital_order", "mlcc_t1_transform",
            "mlcc_fock_t1", "mlcc_omega", "mlcc_ground_state", "mlcc_jacobian_prepare",
            "mlcc_sigma", "mlcc_excited_states", "mlcc_solve", "mlcc_launch_count",
-           "mlcc_fock_t1_noalloc", "mlcc_gemm"]
+           "mlcc_fock_t1_noalloc", "mlcc_gemm", "mlcc_solve_device", "mlcc_vector_len",
+           "mlcc_solve_footprint", "mlcc_server_create", "mlcc_server_destroy", "mlcc_submit",
+           "mlcc_poll", "mlcc_cancel", "mlcc_server_stats"]
 
 
 class mlcc_problem(ctypes.Structure):
@@ -59,6 +63,19 @@ class mlcc_es_info(ctypes.Structure):
     _fields_ = [("iterations", c_int32), ("n_sigma", c_int32), ("n_sigma_lowp", c_int32),
                 ("converged", c_int32), ("complex_pair", c_int32), ("fp64_sweeps", c_int32),
                 ("max_residual", c_double)]
+
+
+class mlcc_request_result(ctypes.Structure):
+    _fields_ = [("status", c_int32), ("slot", c_int32), ("attempts", c_int32), ("n_roots", c_int32),
+                ("footprint_bytes", c_int64), ("t_submit", c_double), ("t_start", c_double),
+                ("t_finish", c_double), ("gs", mlcc_gs_info), ("es", mlcc_es_info)]
+
+
+class mlcc_server_info(ctypes.Structure):
+    _fields_ = [("n_slots", c_int32), ("running", c_int32), ("waiting", c_int32),
+                ("peak_running", c_int32), ("budget_bytes", c_int64), ("in_use_bytes", c_int64),
+                ("peak_bytes", c_int64), ("submitted", c_int64), ("finished", c_int64),
+                ("cancelled", c_int64), ("retried", c_int64)]
 
 
 class MLCCError(RuntimeError):
@@ -106,6 +123,16 @@ def load():
         "mlcc_excited_states": (c_int, [P, POINTER(mlcc_options), D, P, POINTER(mlcc_es_info)]),
         "mlcc_solve": (c_int, [P, POINTER(mlcc_problem), P, P, POINTER(mlcc_options),
                                POINTER(mlcc_gs_info), D, POINTER(mlcc_es_info), P]),
+        "mlcc_solve_device": (c_int, [P, POINTER(mlcc_problem), P, P, POINTER(mlcc_options),
+                                      POINTER(mlcc_gs_info), D, POINTER(mlcc_es_info), P]),
+        "mlcc_vector_len": (c_int64, [POINTER(mlcc_problem)]),
+        "mlcc_solve_footprint": (c_int, [POINTER(mlcc_problem), POINTER(mlcc_options), POINTER(c_int64)]),
+        "mlcc_server_create": (c_int, [c_int, c_int32, c_int64, POINTER(c_void_p)]),
+        "mlcc_server_destroy": (None, [P]),
+        "mlcc_submit": (c_int, [P, POINTER(mlcc_problem), P, P, POINTER(mlcc_options), POINTER(ctypes.c_uint64)]),
+        "mlcc_poll": (c_int, [P, ctypes.c_uint64, c_int64, POINTER(mlcc_request_result), D]),
+        "mlcc_cancel": (c_int, [P, ctypes.c_uint64]),
+        "mlcc_server_stats": (c_int, [P, POINTER(mlcc_server_info)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -330,3 +357,93 @@ def solve(ctx, chol_host, fock_host, n_occ, level, opts=None):
                            c_void_p(t1.ctypes.data))
     _check(st)
     return gs, np.array(w[:]), es, t1
+
+
+def _problem(n_mo, n_occ, n_chol, level):
+    """(mlcc_problem, the int8 level array it points into: keep both alive together)."""
+    level = np.ascontiguousarray(np.asarray(level, dtype=np.int8))
+    return mlcc_problem(n_mo, n_occ, n_chol, level.ctypes.data_as(POINTER(c_int8))), level
+
+
+def solve_device(ctx, chol, fock, n_occ, level, opts=None):
+    """mlcc_solve_device on float64 CUDA tensors (borrowed for the call)."""
+    opts = opts or default_options()
+    prob, lev = _problem(fock.shape[0], n_occ, chol.shape[0], level)
+    gs, es = mlcc_gs_info(), mlcc_es_info()
+    w = (c_double * opts.n_roots)()
+    ctx.before()
+    st = load().mlcc_solve_device(ctx.handle, byref(prob), _ptr(chol), _ptr(fock), byref(opts),
+                                  byref(gs), w, byref(es), None)
+    ctx.after()
+    _check(st)
+    return gs, np.array(w[:]), es
+
+
+def vector_len(n_mo, n_occ, n_chol, level):
+    """mlcc_vector_len: Davidson vector length of a problem (-1 if invalid)."""
+    prob, lev = _problem(n_mo, n_occ, n_chol, level)
+    return int(load().mlcc_vector_len(byref(prob)))
+
+
+def solve_footprint(n_mo, n_occ, n_chol, level, opts=None):
+    """mlcc_solve_footprint: device bytes mlcc_solve of the problem holds at its peak."""
+    opts = opts or default_options()
+    prob, lev = _problem(n_mo, n_occ, n_chol, level)
+    b = c_int64(0)
+    _check(load().mlcc_solve_footprint(byref(prob), byref(opts), byref(b)))
+    return int(b.value)
+
+
+class Server:
+    """mlcc_server: whole solves submitted as requests, admitted by footprint into slots.
+
+    submit() keeps the host arrays of each request alive until its result is polled."""
+
+    def __init__(self, device=0, n_slots=4, budget_bytes=0):
+        h = c_void_p()
+        _check(load().mlcc_server_create(device, n_slots, budget_bytes, byref(h)))
+        self.handle = h
+        self._held = {}
+
+    def submit(self, chol_host, fock_host, n_occ, level, opts=None):
+        chol_host = np.ascontiguousarray(chol_host, dtype=np.float64)
+        fock_host = np.ascontiguousarray(fock_host, dtype=np.float64)
+        opts = opts or default_options()
+        prob, lev = _problem(fock_host.shape[0], n_occ, chol_host.shape[0], level)
+        t = ctypes.c_uint64(0)
+        _check(load().mlcc_submit(self.handle, byref(prob), c_void_p(chol_host.ctypes.data),
+                                  c_void_p(fock_host.ctypes.data), byref(opts), byref(t)))
+        self._held[t.value] = (chol_host, fock_host, opts.n_roots)
+        return t.value
+
+    def poll(self, ticket, wait_ms=-1):
+        """(mlcc_request_result, omega array) once finished, None while pending."""
+        n_roots = self._held[ticket][2] if ticket in self._held else 1
+        res = mlcc_request_result()
+        w = (c_double * max(1, n_roots))()
+        st = load().mlcc_poll(self.handle, ticket, wait_ms, byref(res), w)
+        if st == MLCC_PENDING:
+            return None
+        _check(st)
+        self._held.pop(ticket, None)
+        return res, np.array(w[:res.n_roots])
+
+    def cancel(self, ticket):
+        _check(load().mlcc_cancel(self.handle, ticket))
+
+    def stats(self):
+        info = mlcc_server_info()
+        _check(load().mlcc_server_stats(self.handle, byref(info)))
+        return info
+
+    def close(self):
+        if self.handle:
+            load().mlcc_server_destroy(self.handle)
+        self.handle = None
+        self._held.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

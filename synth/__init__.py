@@ -8,8 +8,9 @@ Fock matrix F_pq, Sec. 2.3 Eq. eff_fock), and assigns orbitals to the CCS / CC2 
 levels. Everything downstream (T1-dressing, residuals, Jacobian, Davidson) lives elsewhere.
 """
 from .generator import (ModelHamiltonian, draw_model_hamiltonian, SystemSpec, MOSystem, default_scale,
-                        make_system, level_map, CONFIGS)
+                        make_system, level_map, CONFIGS, serving_request_spec, serving_arrivals)
 from .rhf import rhf, RHFResult
 
 __all__ = ["ModelHamiltonian", "draw_model_hamiltonian", "SystemSpec", "MOSystem", "default_scale",
-           "make_system", "level_map", "CONFIGS", "rhf", "RHFResult"]
+           "make_system", "level_map", "CONFIGS", "serving_request_spec", "serving_arrivals", "rhf",
+           "RHFResult"]

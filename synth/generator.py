@@ -135,3 +135,41 @@ CONFIGS = {
     # 560 orbitals, 60 occupied, 2500 vectors; CCSD 20 / 140 in CC2 40 / 300, CCS rest
     "three_level": _spec("three_level", 60, 500, 2500, 40, 300, 20, 140, 4),
 }
+
+
+# Serving mix: independent excitation requests of uneven sizes (one synthetic snapshot
+# Hamiltonian each). Request r draws from its own stream (seed_base + r):
+#   occupied ~ U{20..80}, virtual ~ U{150..600}, N_J = 5 (occ + vir), tau = N_J / 5;
+#   active fraction f ~ U[0.1, 0.3), applied to the occupied and the virtual orbitals
+#   (rounded, at least 1);
+#   kind: "ccs_ccsd" (two levels: the active orbitals CCSD, the rest CCS) or "mlcc2" (the
+#   active orbitals CC2, the rest CCS), each with probability 1/2;
+#   4 roots.
+# Arrival times: exponential gaps at `rate` requests per second from a stream of their own.
+SERVING_OCC = (20, 80)
+SERVING_VIR = (150, 600)
+SERVING_FRACTION = (0.1, 0.3)
+
+
+def serving_request_spec(r, seed_base=0):
+    rng = np.random.default_rng(seed_base + r)
+    no = int(rng.integers(SERVING_OCC[0], SERVING_OCC[1] + 1))
+    nv = int(rng.integers(SERVING_VIR[0], SERVING_VIR[1] + 1))
+    f = float(rng.uniform(*SERVING_FRACTION))
+    kind = "ccs_ccsd" if rng.random() < 0.5 else "mlcc2"
+    ao = max(1, int(round(f * no)))
+    av = max(1, int(round(f * nv)))
+    nj = 5 * (no + nv)
+    tau = nj / 5.0
+    t_o, t_v = (ao, av) if kind == "ccs_ccsd" else (0, 0)
+    spec = SystemSpec(f"serve{r}_{kind}", no, nv, nj, tau, ao, av, t_o, t_v, 4, seed_base + r,
+                      default_scale(tau))
+    return spec, kind, f
+
+
+def serving_arrivals(n, rate=20.0, seed=1 << 20):
+    """Arrival times (seconds from the first request) of n requests: exponential gaps."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=n)
+    gaps[0] = 0.0
+    return np.cumsum(gaps)

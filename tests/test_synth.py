@@ -8,14 +8,18 @@ Checked on draws large enough for the statistics to be tight:
   * RHF output: canonical (diagonal) Fock matrix, aufbau occupation (every occupied orbital
     energy below every virtual one), ERIs g = sum_J L^J L^J positive semidefinite;
   * levels nested, CCSD at the highest occupied and lowest virtual orbitals;
-  * the workload table: tau = N_J / 5 and scale = 0.5 / sqrt(tau).
+  * the workload table: tau = N_J / 5 and scale = 0.5 / sqrt(tau);
+  * the serving mix: sizes, Cholesky counts, active fractions and the two request kinds in
+    their stated ranges and proportions, one stream per request, exponential arrival gaps
+    at the stated rate.
 """
 import math
 
 import numpy as np
 import pytest
 
-from synth.generator import CONFIGS, SystemSpec, default_scale, draw_model_hamiltonian, level_map, make_system
+from synth.generator import (CONFIGS, SystemSpec, default_scale, draw_model_hamiltonian, level_map, make_system,
+                             serving_arrivals, serving_request_spec)
 
 
 def test_one_electron_matrix():
@@ -86,3 +90,33 @@ def test_workload_table(name):
     assert isinstance(s, SystemSpec)
     assert s.tau == s.n_chol / 5.0 and s.scale == default_scale(s.tau) == 0.5 / math.sqrt(s.tau)
     assert 0 <= s.t_occ <= s.s_occ <= s.n_occ and 0 <= s.t_vir <= s.s_vir <= s.n_vir
+
+
+def test_serving_mix_recipe():
+    specs = [serving_request_spec(r) for r in range(256)]
+    kinds = [k for _, k, _ in specs]
+    for s, k, f in specs:
+        assert 20 <= s.n_occ <= 80 and 150 <= s.n_vir <= 600
+        assert s.n_chol == 5 * (s.n_occ + s.n_vir) and s.tau == s.n_chol / 5.0
+        assert 0.1 <= f < 0.3 and s.n_roots == 4
+        assert s.s_occ == max(1, round(f * s.n_occ)) and s.s_vir == max(1, round(f * s.n_vir))
+        if k == "ccs_ccsd":
+            assert (s.t_occ, s.t_vir) == (s.s_occ, s.s_vir)
+        else:
+            assert (s.t_occ, s.t_vir) == (0, 0)
+    # both kinds about equally often (binomial(256, 1/2): sd 8)
+    assert abs(kinds.count("mlcc2") - 128) < 40
+    occ = np.array([s.n_occ for s, _, _ in specs])
+    assert abs(occ.mean() - 50.0) < 4.0       # U{20..80}: mean 50, sd 17.6 / sqrt(256)
+    # request r depends on its own seed only
+    assert serving_request_spec(17)[0] == specs[17][0]
+    assert serving_request_spec(0, seed_base=1)[0].n_occ == specs[1][0].n_occ
+
+
+def test_serving_arrivals():
+    t = serving_arrivals(4096, rate=20.0)
+    assert t[0] == 0.0 and np.all(np.diff(t) >= 0)
+    gaps = np.diff(t)
+    assert abs(gaps.mean() - 0.05) < 0.004    # mean 1 / rate, sd 0.05 / sqrt(4095)
+    assert abs(np.median(gaps) - 0.05 * math.log(2)) < 0.004
+    assert np.array_equal(serving_arrivals(10), serving_arrivals(10))
