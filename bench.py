@@ -409,15 +409,22 @@ def main():
     ev0.record(ctx.stream)
     n_sigma = n_lowp = 0
     omegas, gs = None, None
-    for _ in range(args.steps):
+    step_ev = [ev0]
+    for k in range(args.steps):
         ns, nl, omegas, gs = step()
         n_sigma += ns
         n_lowp += nl
+        if k + 1 < args.steps:   # per-solve latency: events between consecutive steps
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(ctx.stream)
+            step_ev.append(e)
     ev1.record(ctx.stream)
+    step_ev.append(ev1)
     torch.cuda.synchronize()
     if profile_range:
         torch.cuda.cudart().cudaProfilerStop()
     elapsed = ev0.elapsed_time(ev1) / 1e3
+    step_s = [a.elapsed_time(b) / 1e3 for a, b in zip(step_ev[:-1], step_ev[1:])]
     launches = mlcc.launch_count() - launches0
     fams = {f: ctx.kernel_time(f) for f in ("rank_gemm_tc", "rank_gemm_f64e", "rank_gemm_f64")}
     phases = {f: ctx.kernel_time(f) for f in ("gs_omega", "jacobian_prepare", "sigma", "sigma_singles",
@@ -533,7 +540,10 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": args.precision if not split else f"{args.precision}+{args.refine}",
             "data": "synthetic", "config": config_dict(args, args.precision if not split else f"{args.precision}+{args.refine}"),
-            "solves_per_s": args.steps * world / t_max, "sigma_per_step": n_sigma / args.steps,
+            "solves_per_s": args.steps * world / t_max,
+            "latency_p50_s": float(np.percentile(step_s, 50)), "latency_p99_s": float(np.percentile(step_s, 99)),
+            "latency_of": "one whole solve (one step) on rank 0, CUDA events between steps",
+            "sigma_per_step": n_sigma / args.steps,
             "sigma_lowp_per_step": n_lowp / args.steps,
             "omega": [float(x) for x in omegas], "e_corr": gs.e_corr,
             "max_abs_omega_err_vs_fp64_gpu_Ha": err_fp64, "fp64_gpu_solve": fp64_solve,

@@ -60,3 +60,34 @@ def test_sigma_full_size_mlcc2(ctx):
         err = float(np.abs(out - ref).max())
         assert err <= REL * scale, f"max error {err:.3e} > {REL:.0e} * {scale:.3e}"
     g.close()
+
+
+def test_ground_state_full_size_against_the_stored_oracle(ctx):
+    """The benchmark workload itself (340 orbitals, 1500 Cholesky vectors, CCSD-active
+    10 / 60 inside CC2-active 40 / 300): the reference and ground-state correlation
+    energies of the binary64 path and of the mixed path (split bfloat16 iterations polished
+    in MLCC_FP64E, the benchmark's options) against the oracle's, stored by
+    tests/golden/make_golden.py, to 1e-8 Ha."""
+    import json
+    import os
+    from paper_2006_05226_gb300 import mlcc
+    from synth import CONFIGS, make_system
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "mid_oracle.json")
+    if not os.path.exists(path):
+        pytest.skip("no stored oracle values for the 340-orbital workload")
+    ref = json.load(open(path))
+    spec = CONFIGS["mid"]
+    s = make_system(spec)
+    L = torch.as_tensor(s.L, device="cuda")
+    F = torch.as_tensor(s.fock, device="cuda")
+    fp64 = mlcc.default_options(n_roots=spec.n_roots)
+    mixed = mlcc.default_options(n_roots=spec.n_roots, precision=mlcc.MLCC_BF16X3, gs_precision=mlcc.MLCC_BF16X3,
+                                 refine_fp64=1, lowp_res_tol=1e-5, refine_precision=mlcc.MLCC_FP64E,
+                                 gs_tol=1e-9, gs_energy_tol=1e-10)
+    for opts in (fp64, mixed):
+        g = mlcc.System(ctx, L, F, spec.n_occ, s.level)
+        _, _, info = g.ground_state(opts)
+        g.close()
+        assert info.converged
+        assert abs(info.e_hf - ref["e_hf"]) < 1e-8
+        assert abs(info.e_corr - ref["e_corr"]) < 1e-8, (opts.precision, info.e_corr, ref["e_corr"])
