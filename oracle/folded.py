@@ -19,6 +19,15 @@ well below the P_S denominators. On the 48-orbital workload it needs about 4x th
 sigma-vector count of the unfolded Davidson (each sigma_eff is two sigma evaluations here),
 so a production solver has to reuse its subspace across omega updates.
 
+excited_states_folded_linearised keeps its subspaces across omega updates: each trial
+vector b stores A_eff(w_b) b and dA_eff/domega (w_b) b = -A_1S (w_b - eps_S)^-2 A_S1 b1 at
+the omega w_b it was applied at, and the projected problem at omega uses the first-order
+model A_eff(omega) b ~ A_eff(w_b) b + (omega - w_b) dA_eff/domega b. Stage 1 finds all roots
+roughly with every vector applied at one omega; stage 2 refines each root in a subspace of
+its own, restarting from the Ritz vector applied exactly at the current omega until the
+model is exact at convergence. On the 48-orbital workload it needs fewer applications than
+the plain fixed point above.
+
 excited_states_folded solves the nonlinear problem on small systems: its roots below the
 lowest P_S denominator are the zeros of det(A_eff(omega) - omega), with A_eff assembled
 from sigma applications (fold_parts). A plain fixed-point iteration omega <- lambda_k(omega)
@@ -209,4 +218,147 @@ def excited_states_folded_iterative(sys, gs, n_roots, tol=1e-10, res_tol=1e-9, m
         else:
             raise RuntimeError(f"folded root {k}: no fixed point in {max_macro} iterations")
         roots.append(omega)
+    return np.sort(np.array(roots)), count[0]
+
+
+def sigma_eff_domega(sys, gs, c1, omega, sigma_fn=None):
+    """dA_eff/domega (c1, c_T) = (-A_1S (omega - eps_S)^-2 A_S1 c1, 0): only the singles
+    block of A_eff depends on omega. A_S1 c1 are the P_S rows of sigma(c1, 0); A_1S x_S are
+    the singles of sigma(0, x_S)."""
+    sigma_fn = sigma_fn or sigma_def
+    zero1, zero2 = np.zeros_like(c1), np.zeros(sys.doubles_shape())
+    _, r2 = sigma_fn(sys, gs.t1, gs.x2, c1, zero2)
+    xS = np.where(sys.mask_S, -r2 / (omega - sys.eps_aibj) ** 2, 0.0)
+    d1, _ = sigma_fn(sys, gs.t1, gs.x2, zero1, xS)
+    return d1
+
+
+def excited_states_folded_linearised(sys, gs, n_roots, res_tol=1e-9, max_iter=100, stage1_tol=1e-3,
+                                     exact_dw=1e-7, sigma_fn=None):
+    """Lowest n_roots solutions of A_eff(omega) c = omega c below the P_S denominators, with
+    subspaces kept across omega updates (first-order model in omega per trial vector):
+
+    stage 1 (all roots): trial vectors applied at one omega_0 (the lowest eps_ai); for each
+      root the k-th eigenvalue of the projected model V^T (S0 + (omega - omega_0) S1) is
+      made self-consistent in omega; new directions are the preconditioned residuals
+      (eps_mu - omega_k)^-1 r_k; stop when every model residual is below stage1_tol;
+    stage 2 (each root k): a subspace of its own, started from the stage-1 Ritz vector
+      applied at omega_k; each step takes the Ritz pair of the projected model (vector b
+      applied at w_b contributes S0_b + (omega - w_b) S1_b) that overlaps most with the
+      previous one, made self-consistent in omega, and adds its preconditioned residual
+      applied at the current omega. When the model residual is below res_tol the root is
+      done if every vector of the subspace was applied within exact_dw of omega (the model
+      error is second order in omega - w_b); otherwise the subspace restarts from the Ritz
+      vector applied exactly at omega.
+
+    Returns (roots ascending, number of A_eff applications)."""
+    nv, no = sys.nv, sys.no
+    n1 = nv * no
+    sh = sys.doubles_shape()
+    maskT = sys.mask_T.ravel()
+    count = [0]
+
+    def project(v):
+        d = np.where(maskT, v[n1:], 0.0).reshape(sh)
+        return np.concatenate([v[:n1], (0.5 * (d + d.transpose(2, 3, 0, 1))).ravel()])
+
+    def apply(w, v):
+        c1 = v[:n1].reshape(nv, no)
+        cT = v[n1:].reshape(sh)
+        s1, s2 = sigma_eff(sys, gs, c1, cT, w, sigma_fn)
+        d1 = sigma_eff_domega(sys, gs, c1, w, sigma_fn)
+        count[0] += 1
+        return (np.concatenate([s1.ravel(), s2.ravel()]),
+                np.concatenate([d1.ravel(), np.zeros(v.size - n1)]))
+
+    def orth(V, v):
+        for _ in range(2):
+            if V.shape[1]:
+                v = v - V @ (V.T @ v)
+        return v
+
+    diag = np.concatenate([sys.eps_ai.ravel(), np.where(maskT, sys.eps_aibj.ravel(), 1e30)])
+
+    def precondition(r, w):
+        den = diag - w
+        return project(r / np.where(np.abs(den) < 1e-8, 1e-8, den))
+
+    def model_pair(V, S0, S1, wv, w, pick):
+        """Self-consistent (omega, y) of the projected first-order model; pick(lam, Y)
+        chooses the Ritz pair."""
+        G0, G1 = V.T @ S0, V.T @ S1
+        for _ in range(100):
+            lam, Y = np.linalg.eig(G0 + G1 * (w - wv)[None, :])
+            j = pick(lam, Y)
+            if abs(lam[j].real - w) < 1e-14 * max(1.0, abs(w)):
+                break
+            w = lam[j].real
+        y = Y[:, j].real
+        y = y / np.linalg.norm(y)
+        x = V @ y
+        r = S0 @ y + S1 @ ((w - wv) * y) - w * x
+        return w, y, x, r
+
+    # stage 1
+    n_guess = min(2 * n_roots, n1)
+    order = np.argsort(sys.eps_ai.ravel(), kind="stable")[:n_guess]
+    w0 = float(sys.eps_ai.ravel()[order[0]])
+    V = np.zeros((diag.size, n_guess))
+    V[order, np.arange(n_guess)] = 1.0
+    cols = [apply(w0, V[:, i]) for i in range(n_guess)]
+    S0 = np.column_stack([c[0] for c in cols])
+    S1 = np.column_stack([c[1] for c in cols])
+    om = np.full(n_roots, w0)
+    X = [None] * n_roots
+    for _ in range(max_iter):
+        wv = np.full(V.shape[1], w0)
+        R = []
+        for k in range(n_roots):
+            om[k], _, X[k], r = model_pair(V, S0, S1, wv, om[k],
+                                           lambda lam, Y, k=k: int(np.argsort(lam.real)[k]))
+            R.append(r)
+        if max(np.linalg.norm(r) for r in R) < stage1_tol:
+            break
+        for k in range(n_roots):
+            t = orth(V, precondition(R[k], om[k]))
+            nt = np.linalg.norm(t)
+            if nt < 1e-10:
+                continue
+            t /= nt
+            a, b = apply(w0, t)
+            V, S0, S1 = np.column_stack([V, t]), np.column_stack([S0, a]), np.column_stack([S1, b])
+    # stage 2
+    roots = []
+    for k in range(n_roots):
+        w = om[k]
+
+        def restart(x, w):
+            x = x / np.linalg.norm(x)
+            a, b = apply(w, x)
+            return x[:, None], a[:, None], b[:, None], np.array([w]), np.array([1.0])
+
+        V, S0, S1, wv, yprev = restart(X[k], w)
+        for _ in range(max_iter):
+            def overlap(lam, Y, yprev=yprev):
+                Yr = Y.real
+                return int(np.argmax(np.abs(Yr[:yprev.size].T @ yprev) / np.linalg.norm(Yr, axis=0)))
+            w, y, x, r = model_pair(V, S0, S1, wv, w, overlap)
+            if np.linalg.norm(r) < res_tol:
+                if np.max(np.abs(w - wv)) < exact_dw:
+                    break
+                V, S0, S1, wv, yprev = restart(x, w)
+                continue
+            t = orth(V, precondition(r, w))
+            nt = np.linalg.norm(t)
+            if nt < 1e-12 or V.shape[1] >= 8 * n_roots:
+                V, S0, S1, wv, yprev = restart(x, w)
+                continue
+            t /= nt
+            a, b = apply(w, t)
+            V, S0, S1 = np.column_stack([V, t]), np.column_stack([S0, a]), np.column_stack([S1, b])
+            wv = np.append(wv, w)
+            yprev = np.append(y, 0.0)
+        else:
+            raise RuntimeError(f"folded root {k}: not converged in {max_iter} iterations")
+        roots.append(w)
     return np.sort(np.array(roots)), count[0]

@@ -126,3 +126,32 @@ def test_iterative_folded_solver_on_the_48_orbital_workload():
     roots, n_eff = excited_states_folded_iterative(osys, gs, 3)
     assert np.abs(roots - ref.omega).max() < 1e-9
     assert osys.eps_aibj[osys.mask_S].min() > 2.5 * roots.max()
+
+
+def test_linearised_folded_solver_on_the_48_orbital_workload():
+    """The folded solver that keeps its subspaces across omega updates (first-order model
+    in omega per trial vector) gives the unfolded roots, with fewer applications of A_eff
+    than the plain fixed point in omega."""
+    from oracle.davidson import excited_states
+    from oracle.folded import excited_states_folded_iterative, excited_states_folded_linearised
+    from synth import CONFIGS, make_system
+    s = make_system(CONFIGS["small"])
+    osys = MLCCSystem(s.L, s.fock, s.spec.n_occ, s.level)
+    gs = solve_ground_state(osys)
+    ref = excited_states(osys, gs, 3, res_tol=1e-9)
+    roots, n_lin = excited_states_folded_linearised(osys, gs, 3)
+    assert np.abs(roots - ref.omega).max() < 1e-9
+    _, n_fixed = excited_states_folded_iterative(osys, gs, 3)
+    assert n_lin < n_fixed
+
+
+@pytest.mark.parametrize("name,lev", FOLDABLE)
+def test_linearised_folded_solver_on_the_seven_orbital_partitions(sys7, name, lev):
+    """Same roots as the determinant scan wherever the window holds three roots."""
+    from oracle.folded import excited_states_folded_linearised
+    osys, gs = _setup(sys7, lev)
+    want = excited_states_folded(osys, gs, 3)
+    if want.size < 3:
+        pytest.skip("fewer than three roots below the lowest P_S denominator")
+    roots, _ = excited_states_folded_linearised(osys, gs, 3)
+    assert np.abs(roots - want).max() < 1e-9
