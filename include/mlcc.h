@@ -237,6 +237,25 @@ mlcc_status mlcc_jacobian_prepare(mlcc_system* sys, const double* t1_dev,
    c_dev, sigma_dev [n_vec][vector_len]. precision: mlcc_precision. */
 mlcc_status mlcc_sigma(mlcc_system* sys, int32_t n_vec, const double* c_dev,
                        double* sigma_dev, int32_t precision);
+/* Folded CC2 Jacobian (the CC2 response strategy Sec. 2.1 points to). In the three-level
+   model the doubles rows outside the CCSD block (P_S) have the diagonal doubles block
+   eps_aibj and no coupling to the CCSD-block doubles (P_T), so an eigenpair (omega, c) of
+   A has c_S = (omega - eps_S)^-1 A_S1 c1, and (c1, c_T) is an eigenvector with eigenvalue
+   omega of A_eff(omega) = [[A_11 + A_1S (omega - eps_S)^-1 A_S1, A_1T], [A_T1, A_TT]].
+   mlcc_sigma_eff applies A_eff(omega[k]) to n_vec vectors c_dev [n_vec][vector_len] in the
+   vector layout (only the singles and the P_T doubles of c are read): sigma_dev
+   [n_vec][vector_len] gets the singles and P_T rows, zero on P_S. dsigma_dev (or NULL)
+   [n_vec][n_singles] gets the singles of dA_eff/domega c = -A_1S (omega - eps_S)^-2 A_S1 c1
+   (the P_T rows do not depend on omega). Cost: three Jacobian transformations per vector
+   (two without dsigma), in `precision`. Each omega[k] (host) must lie below the lowest
+   P_S denominator (mlcc_fold_window), else MLCC_E_ARG; MLCC_E_STATE before
+   mlcc_jacobian_prepare. Scratch: three vectors, allocated for the call; synchronises. */
+mlcc_status mlcc_sigma_eff(mlcc_system* sys, int32_t n_vec, const double* omega_host,
+                           const double* c_dev, double* sigma_dev, double* dsigma_dev,
+                           int32_t precision);
+/* The lowest P_S denominator min eps_aibj over P_S (Hartree; 1e300 without P_S pairs):
+   the folded problem is used for omega below it. */
+mlcc_status mlcc_fold_window(const mlcc_system* sys, double* omega_max);
 /* Davidson solve for the lowest opt->n_roots eigenpairs of A at the prepared ground
    state. omega_host [n_roots] (Hartree, ascending); r_dev [n_roots][vector_len]
    (unit 2-norm, largest-magnitude element positive) or NULL; info (host). */

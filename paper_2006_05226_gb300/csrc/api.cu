@@ -411,6 +411,42 @@ mlcc_status mlcc_sigma(mlcc_system* S, int32_t n_vec, const double* c, double* s
   });
 }
 
+mlcc_status mlcc_fold_window(const mlcc_system* S, double* omega_max) {
+  return guard([&] {
+    MLCC_REQUIRE(S && omega_max, "mlcc_fold_window: NULL argument");
+    *omega_max = lowest_ps_denominator(S);
+    return MLCC_OK;
+  });
+}
+
+mlcc_status mlcc_sigma_eff(mlcc_system* S, int32_t n_vec, const double* omega, const double* c,
+                           double* sigma, double* dsigma, int32_t precision) {
+  return guard([&] {
+    MLCC_REQUIRE(S && (n_vec == 0 || (omega && c && sigma)), "mlcc_sigma_eff: NULL argument");
+    MLCC_REQUIRE(n_vec >= 0, "mlcc_sigma_eff: n_vec < 0");
+    MLCC_REQUIRE(precision >= MLCC_FP64 && precision <= MLCC_FP64E, "mlcc_sigma_eff: unknown precision");
+    if (!S->prepared) throw Error(MLCC_E_STATE, "mlcc_sigma_eff: call mlcc_jacobian_prepare first");
+    const double top = lowest_ps_denominator(S);
+    for (int k = 0; k < n_vec; ++k)
+      MLCC_REQUIRE(std::isfinite(omega[k]) && omega[k] < top,
+                   "mlcc_sigma_eff: omega must lie below the lowest P_S denominator");
+    if (n_vec == 0) return MLCC_OK;
+    MLCC_CUDA(cudaSetDevice(S->ctx->device));
+    const int64_t n1 = int64_t(S->nv) * S->no, len = n1 + S->nd;
+    Arena w;
+    w.reserve(size_t(3) * len * 8 + 3 * 256);
+    double* w0 = w.get<double>(len);
+    double* w1 = w.get<double>(len);
+    double* w2 = w.get<double>(len);
+    for (int k = 0; k < n_vec; ++k)
+      sigma_eff_eval(S, c + k * len, omega[k], sigma + k * len, dsigma ? dsigma + k * n1 : nullptr, precision,
+                     w0, w1, w2);
+    if (precision != MLCC_FP64) check_tc_error(S);
+    MLCC_CUDA(cudaStreamSynchronize(S->ctx->stream));   // the scratch is freed on return
+    return MLCC_OK;
+  });
+}
+
 mlcc_status mlcc_excited_states(mlcc_system* S, const mlcc_options* opt, double* omega,
                                 double* r, mlcc_es_info* info) {
   return guard([&] {

@@ -93,6 +93,11 @@ void omega_eval(mlcc_system* S, const double* t1, const double* x2, bool gs_mode
                 const double* tT, double* x2_out, double* om1, double* om2, double* energy);
 void jacobian_prepare(mlcc_system* S, const double* t1, const double* x2);
 void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision);
+// folded CC2 Jacobian: out = A_eff(omega) c (singles and P_T rows; P_S rows zero), dout (if
+// not null) = the singles of dA_eff/domega c; w0, w1, w2: scratch vectors of vector_len
+void sigma_eff_eval(mlcc_system* S, const double* c, double omega, double* out, double* dout, int precision,
+                    double* w0, double* w1, double* w2);
+double lowest_ps_denominator(const mlcc_system* S);
 // c1 (tangent mode only): the singles trial vector; the tangent of g~_acbd is then formed
 // from the cached g~_Kcbd instead of from the Cholesky vectors.
 void ccsd_block(mlcc_system* S, Mode mode, const Dual& Lai, const Dual& Lac, const Dual& Lki,

@@ -31,7 +31,7 @@ EXPORTS = ["mlcc_default_options", "mlcc_ctx_create", "mlcc_ctx_destroy", "mlcc_
            "mlcc_sigma", "mlcc_excited_states", "mlcc_solve", "mlcc_launch_count",
            "mlcc_fock_t1_noalloc", "mlcc_gemm", "mlcc_solve_device", "mlcc_vector_len",
            "mlcc_solve_footprint", "mlcc_server_create", "mlcc_server_destroy", "mlcc_submit",
-           "mlcc_poll", "mlcc_cancel", "mlcc_server_stats"]
+           "mlcc_poll", "mlcc_cancel", "mlcc_server_stats", "mlcc_sigma_eff", "mlcc_fold_window"]
 
 
 class mlcc_problem(ctypes.Structure):
@@ -126,6 +126,8 @@ def load():
         "mlcc_solve_device": (c_int, [P, POINTER(mlcc_problem), P, P, POINTER(mlcc_options),
                                       POINTER(mlcc_gs_info), D, POINTER(mlcc_es_info), P]),
         "mlcc_vector_len": (c_int64, [POINTER(mlcc_problem)]),
+        "mlcc_sigma_eff": (c_int, [P, c_int32, D, P, P, P, c_int32]),
+        "mlcc_fold_window": (c_int, [P, D]),
         "mlcc_solve_footprint": (c_int, [POINTER(mlcc_problem), POINTER(mlcc_options), POINTER(c_int64)]),
         "mlcc_server_create": (c_int, [c_int, c_int32, c_int64, POINTER(c_void_p)]),
         "mlcc_server_destroy": (None, [P]),
@@ -303,6 +305,24 @@ class System:
         self.ctx.after()
         _check(st)
         return t1, x2[: self.dims.n_doubles], info
+
+    def sigma_eff(self, c, omega, precision=MLCC_FP64, derivative=False):
+        """mlcc_sigma_eff: A_eff(omega_k) c_k (singles and P_T rows) and, if derivative,
+        the singles of dA_eff/domega c_k. c: [n_vec, vector_len]; omega: n_vec floats."""
+        c = c.reshape(-1, self.dims.vector_len)
+        n_vec = c.shape[0]
+        w = (c_double * max(1, n_vec))(*[float(x) for x in np.atleast_1d(omega)])
+        out = self._new(n_vec, self.dims.vector_len)
+        dout = self._new(n_vec, self.dims.n_singles) if derivative else None
+        self.ctx.before(c, out)
+        _check(load().mlcc_sigma_eff(self.handle, n_vec, w, _ptr(c), _ptr(out), _ptr(dout), precision))
+        self.ctx.after()
+        return (out, dout) if derivative else out
+
+    def fold_window(self):
+        w = c_double(0.0)
+        _check(load().mlcc_fold_window(self.handle, byref(w)))
+        return w.value
 
     def jacobian_prepare(self, t1, x2):
         self.ctx.before(t1, x2)

@@ -4,6 +4,7 @@ concurrently on their own streams. Each request's result in the mix equals the s
 run alone (mlcc_solve on one context), in binary64 and on the mixed path; the requests
 overlapped; the footprint the server admits by bounds the device memory one solve takes;
 over-budget requests are rejected and queued ones can be cancelled.
+Collected after the other GPU tests, so that a failure here cannot hide their results.
 """
 import threading
 
