@@ -15,6 +15,8 @@ paper-shaped workloads); synthetic seeded inputs (synth/), larger than L2 (L is 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|bf16|bf16x3|bf16x6|fp64e]
                   [--refine fp64|fp64e] [--impl ours|reference]
 
+--workload three_level runs the same step on the 560-orbital three-level workload (60 occ /
+500 vir, 2500 Cholesky vectors, CCSD-active 20/140 inside CC2-active 40/300, CCS rest).
 --workload serving replays the serving mix instead (synth.serving_request_spec: occupied
 20-80, virtual 150-600, N_J = 5 (occ + vir), active fraction 0.1-0.3, CCS/CCSD or MLCC2,
 4 roots) with exponential arrival gaps at --rate requests/s through the serving loop
@@ -178,8 +180,8 @@ def cpu_sample_oracle(system, seconds_hint=30.0):
     t0 = time.perf_counter()
     sigma_mlcc2_paper(o, t1, x2, c1, c2)
     dt = time.perf_counter() - t0
-    desc = ("one sigma-vector of the same 340-orbital system by the oracle's explicit MLCC2 "
-            "Jacobian formula (Appendix A; CCSD-block terms not included), FP64 numpy")
+    desc = (f"one sigma-vector of the same {system.spec.n_mo}-orbital system by the oracle's explicit "
+            "MLCC2 Jacobian formula (Appendix A; CCSD-block terms not included), FP64 numpy")
     return 1.0 / dt, cores, desc, dt
 
 
@@ -222,7 +224,8 @@ def config_dict(args, prec):
                         f"CC2-active {s.s_occ}/{s.s_vir}, {s.n_roots} roots",
             "n_mo": s.n_mo, "n_occ": s.n_occ, "n_chol": s.n_chol, "ccsd_active": [s.t_occ, s.t_vir],
             "cc2_active": [s.s_occ, s.s_vir], "n_roots": s.n_roots, "precision": prec,
-            "l2": "inputs larger than L2 (L^J_pq is 1.39 GB)", "parallelism": f"replicas{args.gpus}"}
+            "l2": f"inputs larger than L2 (L^J_pq is {s.n_chol * s.n_mo ** 2 * 8 / 1e9:.2f} GB)",
+            "parallelism": f"replicas{args.gpus}"}
 
 
 def _make_system(spec):
@@ -335,7 +338,9 @@ def run_serving(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="mid", choices=["mid", "serving"])
+    ap.add_argument("--workload", default="mid", choices=["mid", "three_level", "serving"],
+                    help="mid: 340 orbitals (the benchmark); three_level: 560 orbitals, CCSD 20/140 inside "
+                         "CC2 40/300, CCS rest; serving: the request mix")
     ap.add_argument("--requests", type=int, default=8, help="serving: number of requests")
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent slots")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: arrivals per second")
@@ -352,6 +357,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
+    global WORKLOAD
+    if args.workload != "serving":
+        WORKLOAD = args.workload
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "serving":
