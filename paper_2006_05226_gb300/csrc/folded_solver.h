@@ -1,0 +1,340 @@
+// Eigensolver of the folded CC2 Jacobian A_eff(omega) (c1, c_T) = omega (c1, c_T) with
+// subspaces kept across omega updates. Plain C++ (header only, no CUDA): the vector space
+// and the operator are a template parameter, so the same control logic runs on device
+// vectors in the library and on host vectors with a dense operator in the host tests.
+//
+// Each trial vector b stores A_eff(w_b) b and dA_eff/domega (w_b) b at the omega w_b it was
+// applied at; the projected problem at omega uses the first-order model
+//   A_eff(omega) b ~ A_eff(w_b) b + (omega - w_b) dA_eff/domega (w_b) b.
+// Stage 1 (all roots): every vector is applied at one omega_0 (the lowest diagonal element
+// of the guesses); the k-th eigenvalue of the projected model is made self-consistent in
+// omega for each root; new directions are the preconditioned residuals; it stops when
+// every model residual is below stage1_tol.
+// Stage 2 (each root): a subspace of its own, started from the stage-1 Ritz vector applied
+// at omega_k; the Ritz pair of the projected model that overlaps most with the previous one
+// is made self-consistent; its preconditioned residual, applied at the current omega,
+// extends the subspace. When the model residual is below res_tol, the root is converged if
+// every vector was applied within exact_dw of omega (the model error is second order in
+// omega - w_b); otherwise the subspace restarts from the Ritz vector applied exactly at
+// omega.
+#pragma once
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <functional>
+#include <vector>
+
+#include "small_eig.h"
+
+namespace mlcc {
+namespace fold {
+
+struct Options {
+  int n_roots = 3;
+  double res_tol = 1e-8;     // model residual norm per root
+  double exact_dw = 1e-7;    // |omega - w_b| bound for every subspace vector at convergence
+  double stage1_tol = 1e-3;  // model residual norm that ends stage 1
+  int max_iter = 200;        // iterations per stage (per root in stage 2)
+  int max_sub = 0;           // subspace size limit (0: 8 n_roots, at least 2 n_roots + 4)
+  double omega_max = 1e300;  // the lowest P_S denominator: omega must stay below it
+};
+
+struct Result {
+  std::vector<double> omega;      // ascending
+  std::vector<double> residual;   // model residual norm per root at the end
+  int n_apply = 0;                // applications of A_eff (each with its derivative)
+  int iterations = 0;             // stage 1 plus stage 2 iterations
+  bool converged = false;
+  const char* failure = nullptr;  // why not, when not converged
+};
+
+// Space requirements (Vec is a value type: copyable, movable):
+//   Vec make();                                    zero vector
+//   int n_guess();                                 candidate unit start vectors
+//   void guess(int k, Vec& v, double& diag);       the k-th lowest-diagonal unit vector
+//   double dot(const Vec& x, const Vec& y);
+//   void axpy(double a, const Vec& x, Vec& y);     y += a x
+//   void scale(double a, Vec& x);
+//   void precondition(const Vec& r, double omega, Vec& t);   t = P[(D - omega)^-1 r]
+//   void apply(double omega, const Vec& x, Vec& y, Vec& dy); A_eff x and dA_eff/domega x
+template <class Space>
+class Solver {
+ public:
+  using Vec = typename Space::Vec;
+
+  Solver(Space& sp, const Options& o) : sp_(sp), o_(o) {
+    max_sub_ = o.max_sub > 0 ? o.max_sub : std::max(8 * o.n_roots, 2 * o.n_roots + 4);
+  }
+
+  // vectors (optional): the folded Ritz vectors of the roots, in the order of res.omega
+  Result run(std::vector<Vec>* vectors = nullptr);
+
+ private:
+  struct Basis {
+    std::vector<Vec> V, S0, S1;
+    std::vector<double> w;
+    std::vector<double> G0, G1;   // V^T S0, V^T S1, row-major m x m
+    int m() const { return int(V.size()); }
+  };
+  struct Pair {
+    double omega = 0.0;
+    std::vector<double> y;   // coefficients in the basis
+    Vec x, r;
+    double rnorm = 0.0;
+    bool ok = false;
+  };
+
+  Space& sp_;
+  Options o_;
+  int max_sub_ = 0;
+  int n_apply_ = 0;
+
+  // orthonormalises t against the basis (two Gram-Schmidt passes); false if it vanishes
+  bool orthonormalise(const Basis& B, Vec& t, double drop) {
+    const double n0 = std::sqrt(std::max(0.0, sp_.dot(t, t)));
+    if (!(n0 > 0.0)) return false;
+    for (int pass = 0; pass < 2; ++pass)
+      for (int i = 0; i < B.m(); ++i) sp_.axpy(-sp_.dot(B.V[i], t), B.V[i], t);
+    const double n1 = std::sqrt(std::max(0.0, sp_.dot(t, t)));
+    if (!(n1 > drop * n0)) return false;
+    sp_.scale(1.0 / n1, t);
+    return true;
+  }
+
+  // appends an orthonormal v applied at w, updating the projected matrices
+  void append(Basis& B, Vec v, double w) {
+    Vec y = sp_.make(), dy = sp_.make();
+    sp_.apply(w, v, y, dy);
+    ++n_apply_;
+    const int m = B.m(), m1 = m + 1;
+    std::vector<double> G0(size_t(m1) * m1, 0.0), G1(size_t(m1) * m1, 0.0);
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) {
+        G0[size_t(i) * m1 + j] = B.G0[size_t(i) * m + j];
+        G1[size_t(i) * m1 + j] = B.G1[size_t(i) * m + j];
+      }
+    B.V.push_back(std::move(v));
+    B.S0.push_back(std::move(y));
+    B.S1.push_back(std::move(dy));
+    B.w.push_back(w);
+    for (int i = 0; i < m1; ++i) {
+      G0[size_t(i) * m1 + m] = sp_.dot(B.V[i], B.S0[m]);
+      G1[size_t(i) * m1 + m] = sp_.dot(B.V[i], B.S1[m]);
+      G0[size_t(m) * m1 + i] = sp_.dot(B.V[m], B.S0[i]);
+      G1[size_t(m) * m1 + i] = sp_.dot(B.V[m], B.S1[i]);
+    }
+    B.G0.swap(G0);
+    B.G1.swap(G1);
+  }
+
+  // the self-consistent Ritz pair of the projected first-order model chosen by pick
+  Pair model_pair(const Basis& B, double w,
+                  const std::function<int(const std::vector<std::complex<double>>&,
+                                          const std::vector<std::vector<std::complex<double>>>&)>& pick) {
+    Pair p;
+    const int m = B.m();
+    std::vector<std::complex<double>> lam;
+    std::vector<std::vector<std::complex<double>>> Y;
+    int j = -1;
+    for (int it = 0; it < 100; ++it) {
+      std::vector<double> M(size_t(m) * m);
+      for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b)
+          M[size_t(a) * m + b] = B.G0[size_t(a) * m + b] + B.G1[size_t(a) * m + b] * (w - B.w[b]);
+      if (!eig_nonsym(m, M, lam, &Y, m)) return p;
+      j = pick(lam, Y);
+      if (j < 0) return p;
+      const double lj = lam[j].real();
+      if (!std::isfinite(lj)) return p;
+      const bool done = std::fabs(lj - w) < 1e-14 * std::max(1.0, std::fabs(w));
+      w = lj;
+      if (done) break;
+    }
+    if (!(w < o_.omega_max)) return p;
+    // Ritz pair (the basis is orthonormal, so |x| = |y|)
+    p.y.resize(m);
+    double ny = 0.0;
+    for (int a = 0; a < m; ++a) {
+      p.y[a] = Y[j][a].real();
+      ny += p.y[a] * p.y[a];
+    }
+    ny = std::sqrt(ny);
+    if (!(ny > 0.0)) return p;
+    for (double& v : p.y) v /= ny;
+    p.omega = w;
+    p.x = sp_.make();
+    p.r = sp_.make();
+    for (int a = 0; a < m; ++a) {
+      sp_.axpy(p.y[a], B.V[a], p.x);
+      sp_.axpy(p.y[a], B.S0[a], p.r);
+      sp_.axpy(p.y[a] * (w - B.w[a]), B.S1[a], p.r);
+    }
+    sp_.axpy(-w, p.x, p.r);
+    p.rnorm = std::sqrt(std::max(0.0, sp_.dot(p.r, p.r)));
+    p.ok = std::isfinite(p.rnorm);
+    return p;
+  }
+};
+
+template <class Space>
+Result Solver<Space>::run(std::vector<Vec>* vectors) {
+  Result res;
+  const int nr = o_.n_roots;
+  const int ng = std::min(2 * nr, sp_.n_guess());
+  if (nr < 1 || ng < nr) {
+    res.failure = "fewer start vectors than roots";
+    return res;
+  }
+  // stage 1: every vector applied at omega_0
+  Basis B;
+  double w0 = 0.0;
+  for (int k = 0; k < ng; ++k) {
+    Vec v = sp_.make();
+    double dk = 0.0;
+    sp_.guess(k, v, dk);
+    if (k == 0) w0 = std::min(dk, 0.5 * o_.omega_max);
+    if (orthonormalise(B, v, 1e-10)) append(B, std::move(v), w0);
+  }
+  std::vector<double> om(nr, w0);
+  std::vector<Vec> X(nr);
+  bool stage1_done = false;
+  for (int it = 0; it < o_.max_iter && !stage1_done; ++it) {
+    ++res.iterations;
+    std::vector<Pair> P(nr);
+    double worst = 0.0;
+    for (int k = 0; k < nr; ++k) {
+      P[k] = model_pair(B, om[k], [k](const std::vector<std::complex<double>>& lam,
+                                      const std::vector<std::vector<std::complex<double>>>&) {
+        return k < int(lam.size()) ? k : -1;   // eigenvalues come sorted by real part
+      });
+      if (!P[k].ok) {
+        res.failure = "stage 1: no admissible Ritz pair";
+        return res;
+      }
+      om[k] = P[k].omega;
+      X[k] = P[k].x;
+      worst = std::max(worst, P[k].rnorm);
+    }
+    if (worst < o_.stage1_tol) {
+      stage1_done = true;
+      break;
+    }
+    if (B.m() + nr > max_sub_) {
+      // collapse onto the Ritz vectors, re-applied at omega_0
+      Basis C;
+      for (int k = 0; k < nr; ++k) {
+        Vec v = X[k];
+        if (orthonormalise(C, v, 1e-10)) append(C, std::move(v), w0);
+      }
+      B = std::move(C);
+      continue;
+    }
+    int added = 0;
+    for (int k = 0; k < nr; ++k) {
+      Vec t = sp_.make();
+      sp_.precondition(P[k].r, om[k], t);
+      if (orthonormalise(B, t, 1e-10)) {
+        append(B, std::move(t), w0);
+        ++added;
+      }
+    }
+    if (added == 0) stage1_done = true;   // invariant subspace: the model pairs are final
+  }
+  if (!stage1_done) {
+    res.failure = "stage 1 did not converge";
+    return res;
+  }
+  // stage 2: one root at a time
+  res.omega.assign(nr, 0.0);
+  res.residual.assign(nr, 0.0);
+  if (vectors) vectors->clear();
+  bool all = true;
+  for (int k = 0; k < nr; ++k) {
+    double w = om[k];
+    Basis R;
+    std::vector<double> yprev;
+    auto restart = [&](Vec x, double wr) {
+      R = Basis();
+      const double nx = std::sqrt(std::max(0.0, sp_.dot(x, x)));
+      sp_.scale(1.0 / nx, x);
+      append(R, std::move(x), wr);
+      yprev.assign(1, 1.0);
+    };
+    restart(X[k], w);
+    bool done = false;
+    Pair p;
+    for (int it = 0; it < o_.max_iter; ++it) {
+      ++res.iterations;
+      const std::vector<double> prev = yprev;
+      p = model_pair(R, w, [&prev](const std::vector<std::complex<double>>& lam,
+                                   const std::vector<std::vector<std::complex<double>>>& Y) {
+        // homing: the Ritz vector with the largest overlap with the previous one
+        int best = -1;
+        double bo = -1.0;
+        for (int j = 0; j < int(lam.size()); ++j) {
+          double ov = 0.0, nrm = 0.0;
+          for (size_t a = 0; a < Y[j].size(); ++a) {
+            nrm += std::norm(Y[j][a]);
+            if (a < prev.size()) ov += Y[j][a].real() * prev[a];
+          }
+          const double s = nrm > 0.0 ? std::fabs(ov) / std::sqrt(nrm) : 0.0;
+          if (s > bo) {
+            bo = s;
+            best = j;
+          }
+        }
+        return best;
+      });
+      if (!p.ok) break;
+      w = p.omega;
+      if (p.rnorm < o_.res_tol) {
+        double dw = 0.0;
+        for (double wb : R.w) dw = std::max(dw, std::fabs(w - wb));
+        if (dw < o_.exact_dw) {
+          done = true;
+          break;
+        }
+        restart(p.x, w);
+        continue;
+      }
+      Vec t = sp_.make();
+      sp_.precondition(p.r, w, t);
+      if (R.m() >= max_sub_ || !orthonormalise(R, t, 1e-12)) {
+        restart(p.x, w);
+        continue;
+      }
+      append(R, std::move(t), w);
+      yprev = p.y;
+      yprev.push_back(0.0);
+    }
+    res.omega[k] = w;
+    res.residual[k] = p.ok ? p.rnorm : INFINITY;
+    if (vectors) vectors->push_back(p.ok ? p.x : sp_.make());
+    if (!done) {
+      all = false;
+      if (!res.failure) res.failure = p.ok ? "stage 2 did not converge" : "stage 2: no admissible Ritz pair";
+    }
+  }
+  // ascending order (vectors alongside)
+  std::vector<int> idx(nr);
+  for (int k = 0; k < nr; ++k) idx[k] = k;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return res.omega[a] < res.omega[b]; });
+  std::vector<double> so(nr), sr(nr);
+  for (int k = 0; k < nr; ++k) {
+    so[k] = res.omega[idx[k]];
+    sr[k] = res.residual[idx[k]];
+  }
+  res.omega.swap(so);
+  res.residual.swap(sr);
+  if (vectors) {
+    std::vector<Vec> sv;
+    for (int k = 0; k < nr; ++k) sv.push_back((*vectors)[idx[k]]);
+    vectors->swap(sv);
+  }
+  res.n_apply = n_apply_;
+  res.converged = all;
+  return res;
+}
+
+}  // namespace fold
+}  // namespace mlcc

@@ -1,0 +1,197 @@
+"""The folded CC2 eigensolver's control logic (csrc/folded_solver.h), compiled on its own with
+g++ and run on the host with dense operators of the folded form
+    A_eff(omega) = P + [U diag(1 / (omega - d)) V, 0; 0, 0]     (singles block)
+(no GPU). Checked against the eigenvalues of the unfolded matrix [[P, [U; 0]], [[V, 0], diag d]]
+below min d (the folded roots are exactly those eigenvalues):
+  * synthetic three-level operators with CC2-sized couplings: every root to 1e-9, with fewer
+    applications than the plain fixed point in omega would need;
+  * the 7-orbital test system's fold (P, U, V, d from the oracle's sigma applications) on
+    every partition that has three roots in the window;
+  * a start with fewer start vectors than roots is refused.
+"""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2006_05226_gb300", "csrc")
+
+SHIM = r"""
+#include "folded_solver.h"
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+struct Dense {
+  using Vec = std::vector<double>;
+  int n, n1, ns;
+  const double *P, *U, *V, *d;
+  std::vector<int> order;   // singles by ascending diagonal
+  Vec make() { return Vec(n, 0.0); }
+  int n_guess() { return n1; }
+  void guess(int k, Vec& v, double& dk) {
+    v.assign(n, 0.0);
+    v[order[k]] = 1.0;
+    dk = P[size_t(order[k]) * n + order[k]];
+  }
+  double dot(const Vec& x, const Vec& y) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += x[i] * y[i];
+    return s;
+  }
+  void axpy(double a, const Vec& x, Vec& y) { for (int i = 0; i < n; ++i) y[i] += a * x[i]; }
+  void scale(double a, Vec& x) { for (double& v : x) v *= a; }
+  void precondition(const Vec& r, double w, Vec& t) {
+    t.resize(n);
+    for (int i = 0; i < n; ++i) {
+      double den = P[size_t(i) * n + i] - w;
+      if (std::fabs(den) < 1e-8) den = den < 0 ? -1e-8 : 1e-8;
+      t[i] = r[i] / den;
+    }
+  }
+  void apply(double w, const Vec& x, Vec& y, Vec& dy) {
+    y.assign(n, 0.0);
+    dy.assign(n, 0.0);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) y[i] += P[size_t(i) * n + j] * x[j];
+    std::vector<double> t(ns, 0.0);
+    for (int s = 0; s < ns; ++s)
+      for (int j = 0; j < n1; ++j) t[s] += V[size_t(s) * n1 + j] * x[j];
+    for (int i = 0; i < n1; ++i)
+      for (int s = 0; s < ns; ++s) {
+        const double q = U[size_t(i) * ns + s] * t[s] / (w - d[s]);
+        y[i] += q;
+        dy[i] -= q / (w - d[s]);
+      }
+  }
+};
+
+extern "C" int t_solve(int n, int n1, int ns, const double* P, const double* U, const double* V, const double* d,
+                       int n_roots, double omega_max, double res_tol, double* omega, int* n_apply, double* vecs) {
+  Dense D{n, n1, ns, P, U, V, d, {}};
+  D.order.resize(n1);
+  std::iota(D.order.begin(), D.order.end(), 0);
+  std::stable_sort(D.order.begin(), D.order.end(),
+                   [&](int a, int b) { return P[size_t(a) * n + a] < P[size_t(b) * n + b]; });
+  mlcc::fold::Options o;
+  o.n_roots = n_roots;
+  o.omega_max = omega_max;
+  o.res_tol = res_tol;
+  mlcc::fold::Solver<Dense> s(D, o);
+  std::vector<std::vector<double>> X;
+  const mlcc::fold::Result r = s.run(&X);
+  *n_apply = r.n_apply;
+  if (!r.converged) return 0;
+  for (int k = 0; k < n_roots; ++k) {
+    omega[k] = r.omega[k];
+    for (int i = 0; i < n; ++i) vecs[size_t(k) * n + i] = X[k][i];
+  }
+  return 1;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def lib(tmp_path_factory):
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    d = tmp_path_factory.mktemp("folded_solver")
+    shim = d / "shim.cpp"
+    shim.write_text(SHIM)
+    so = d / "libfolded_test.so"
+    subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", f"-I{CSRC}", str(shim),
+                    os.path.join(CSRC, "small_eig.cpp"), "-o", str(so)], check=True)
+    L = ctypes.CDLL(str(so))
+    D = ctypes.POINTER(ctypes.c_double)
+    L.t_solve.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, D, D, D, D, ctypes.c_int, ctypes.c_double,
+                          ctypes.c_double, D, ctypes.POINTER(ctypes.c_int), D]
+    return L
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _solve(lib, P, U, V, d, n_roots, res_tol=1e-10):
+    P, U, V, d = (np.ascontiguousarray(a, dtype=np.float64) for a in (P, U, V, d))
+    n, n1, ns = P.shape[0], U.shape[0], U.shape[1]
+    w = np.zeros(n_roots)
+    X = np.zeros((n_roots, n))
+    napp = ctypes.c_int(0)
+    top = float(d.min()) if ns else 1e300
+    ok = lib.t_solve(n, n1, ns, _p(P), _p(U), _p(V), _p(d), n_roots, top, res_tol, _p(w), ctypes.byref(napp), _p(X))
+    return bool(ok), w, X, napp.value
+
+
+def _unfolded_roots(P, U, V, d, k):
+    n, n1, ns = P.shape[0], U.shape[0], U.shape[1]
+    A = np.zeros((n + ns, n + ns))
+    A[:n, :n] = P
+    A[:n1, n:] = U
+    A[n:, :n1] = V
+    A[n:, n:] = np.diag(d)
+    w = np.linalg.eigvals(A)
+    w = np.sort(w.real[np.abs(w.imag) < 1e-9])
+    top = d.min() if ns else np.inf
+    return w[(w > 0) & (w < top)][:k]
+
+
+def _synthetic(seed, n1=120, nT=60, nS=3000, cpl=0.004):
+    rng = np.random.default_rng(seed)
+    e = np.concatenate([np.sort(rng.uniform(0.2, 1.5, n1)), np.sort(rng.uniform(0.4, 2.0, nT))])
+    B = 0.01 * rng.standard_normal((n1 + nT, n1 + nT))
+    P = np.diag(e) + 0.5 * (B + B.T) + 0.001 * rng.standard_normal((n1 + nT, n1 + nT))
+    d = rng.uniform(1.0, 3.0, nS)
+    V = cpl * rng.standard_normal((nS, n1))
+    U = 2.0 * V.T + 0.2 * cpl * rng.standard_normal((n1, nS))
+    return P, U, V, d
+
+
+@pytest.mark.parametrize("seed", [0, 2, 3])
+def test_synthetic_three_level_operators(lib, seed):
+    P, U, V, d = _synthetic(seed)
+    want = _unfolded_roots(P, U, V, d, 4)
+    ok, w, X, napp = _solve(lib, P, U, V, d, 4)
+    assert ok
+    assert np.abs(w - want).max() < 1e-9
+    # each vector solves A_eff(w) x = w x
+    n1 = U.shape[0]
+    for k in range(4):
+        x = X[k]
+        y = P @ x
+        y[:n1] += U @ ((V @ x[:n1]) / (w[k] - d))
+        assert np.linalg.norm(y - w[k] * x) < 1e-8 * np.linalg.norm(x)
+    assert napp < 250
+
+
+def test_the_seven_orbital_fold(lib):
+    from oracle.folded import excited_states_folded, fold_parts
+    from oracle.mlcc import MLCCSystem, solve_ground_state
+    from test_oracle_pins import PARTITIONS
+    from tiny_systems import tiny
+    t = tiny()
+    tested = 0
+    for name, lev in PARTITIONS:
+        if not any(v >= 1 for v in lev):
+            continue
+        o = MLCCSystem(t.L, t.F, t.k, np.array(lev, dtype=np.int8))
+        gs = solve_ground_state(o)
+        want = excited_states_folded(o, gs, 3)
+        if want.size < 3:
+            continue
+        P, U, V, d = fold_parts(o, gs)
+        ok, w, _, _ = _solve(lib, P, U, V, d, 3)
+        assert ok, name
+        assert np.abs(w - want).max() < 1e-9, name
+        tested += 1
+    assert tested >= 2
+
+
+def test_too_few_start_vectors(lib):
+    P, U, V, d = _synthetic(0, n1=3, nT=2, nS=10)
+    ok, _, _, napp = _solve(lib, P, U, V, d, 4)   # 3 singles, 4 roots
+    assert not ok and napp == 0
