@@ -256,6 +256,22 @@ mlcc_status mlcc_sigma_eff(mlcc_system* sys, int32_t n_vec, const double* omega_
 /* The lowest P_S denominator min eps_aibj over P_S (Hartree; 1e300 without P_S pairs):
    the folded problem is used for omega below it. */
 mlcc_status mlcc_fold_window(const mlcc_system* sys, double* omega_max);
+/* Lowest opt->n_roots excitation energies below the lowest P_S denominator from the folded
+   CC2 Jacobian (mlcc_sigma_eff), by a Davidson-type solver whose subspaces hold only
+   singles and CCSD-block doubles (n_vir n_occ + (t_vir t_occ)^2 elements per vector) and are
+   kept across omega updates: each trial vector b keeps A_eff(w_b) b and dA_eff/domega b at
+   the omega w_b it was applied at, and the projected problem uses the first-order model in
+   omega - w_b. Stage 1 finds all roots roughly with one omega; stage 2 refines each root in
+   its own subspace, restarting from the Ritz vector applied exactly at omega until every
+   vector of the subspace was applied within 1e-7 Ha of it and the model residual is below
+   opt->es_res_tol. opt->precision (MLCC_FP64 or MLCC_FP64E) is the sigma precision;
+   opt->max_es_iter bounds each stage; opt->max_subspace the subspace (0: 8 n_roots).
+   omega_host [n_roots] ascending; r_dev [n_roots][vector_len] or NULL: the unfolded
+   eigenvectors (c1, c_S(omega) + c_T), unit 2-norm, largest-magnitude element positive.
+   info->n_sigma counts Jacobian transformations (three per application). Needs
+   2 n_roots <= n_vir n_occ. MLCC_E_ES_NOCONV if a root does not converge. */
+mlcc_status mlcc_excited_states_folded(mlcc_system* sys, const mlcc_options* opt,
+                                       double* omega_host, double* r_dev, mlcc_es_info* info);
 /* Davidson solve for the lowest opt->n_roots eigenpairs of A at the prepared ground
    state. omega_host [n_roots] (Hartree, ascending); r_dev [n_roots][vector_len]
    (unit 2-norm, largest-magnitude element positive) or NULL; info (host). */

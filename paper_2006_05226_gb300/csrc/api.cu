@@ -447,6 +447,18 @@ mlcc_status mlcc_sigma_eff(mlcc_system* S, int32_t n_vec, const double* omega, c
   });
 }
 
+mlcc_status mlcc_excited_states_folded(mlcc_system* S, const mlcc_options* opt, double* omega,
+                                       double* r, mlcc_es_info* info) {
+  return guard([&] {
+    MLCC_REQUIRE(S && opt && omega, "mlcc_excited_states_folded: NULL argument");
+    MLCC_REQUIRE(opt->precision == MLCC_FP64 || opt->precision == MLCC_FP64E,
+                 "mlcc_excited_states_folded: precision must be MLCC_FP64 or MLCC_FP64E");
+    MLCC_REQUIRE(opt->max_es_iter >= 1, "mlcc_excited_states_folded: bad options");
+    MLCC_CUDA(cudaSetDevice(S->ctx->device));
+    return excited_states_folded(S, opt, omega, r, info);
+  });
+}
+
 mlcc_status mlcc_excited_states(mlcc_system* S, const mlcc_options* opt, double* omega,
                                 double* r, mlcc_es_info* info) {
   return guard([&] {

@@ -98,6 +98,9 @@ void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision);
 void sigma_eff_eval(mlcc_system* S, const double* c, double omega, double* out, double* dout, int precision,
                     double* w0, double* w1, double* w2);
 double lowest_ps_denominator(const mlcc_system* S);
+// lowest roots of the folded CC2 Jacobian (folded_solve.cu); MLCC_E_ES_NOCONV if not converged
+mlcc_status excited_states_folded(mlcc_system* S, const mlcc_options* opt, double* omega_host, double* r_out,
+                                  mlcc_es_info* info);
 // c1 (tangent mode only): the singles trial vector; the tangent of g~_acbd is then formed
 // from the cached g~_Kcbd instead of from the Cholesky vectors.
 void ccsd_block(mlcc_system* S, Mode mode, const Dual& Lai, const Dual& Lac, const Dual& Lki,

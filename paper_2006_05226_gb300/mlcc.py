@@ -31,7 +31,8 @@ EXPORTS = ["mlcc_default_options", "mlcc_ctx_create", "mlcc_ctx_destroy", "mlcc_
            "mlcc_sigma", "mlcc_excited_states", "mlcc_solve", "mlcc_launch_count",
            "mlcc_fock_t1_noalloc", "mlcc_gemm", "mlcc_solve_device", "mlcc_vector_len",
            "mlcc_solve_footprint", "mlcc_server_create", "mlcc_server_destroy", "mlcc_submit",
-           "mlcc_poll", "mlcc_cancel", "mlcc_server_stats", "mlcc_sigma_eff", "mlcc_fold_window"]
+           "mlcc_poll", "mlcc_cancel", "mlcc_server_stats", "mlcc_sigma_eff", "mlcc_fold_window",
+           "mlcc_excited_states_folded"]
 
 
 class mlcc_problem(ctypes.Structure):
@@ -128,6 +129,7 @@ def load():
         "mlcc_vector_len": (c_int64, [POINTER(mlcc_problem)]),
         "mlcc_sigma_eff": (c_int, [P, c_int32, D, P, P, P, c_int32]),
         "mlcc_fold_window": (c_int, [P, D]),
+        "mlcc_excited_states_folded": (c_int, [P, POINTER(mlcc_options), D, P, POINTER(mlcc_es_info)]),
         "mlcc_solve_footprint": (c_int, [POINTER(mlcc_problem), POINTER(mlcc_options), POINTER(c_int64)]),
         "mlcc_server_create": (c_int, [c_int, c_int32, c_int64, POINTER(c_void_p)]),
         "mlcc_server_destroy": (None, [P]),
@@ -318,6 +320,18 @@ class System:
         _check(load().mlcc_sigma_eff(self.handle, n_vec, w, _ptr(c), _ptr(out), _ptr(dout), precision))
         self.ctx.after()
         return (out, dout) if derivative else out
+
+    def excited_states_folded(self, opts=None, want_vectors=True):
+        """mlcc_excited_states_folded: (omega array, unfolded vectors or None, mlcc_es_info)."""
+        opts = opts or default_options()
+        w = (c_double * opts.n_roots)()
+        R = self._new(opts.n_roots, self.dims.vector_len) if want_vectors else None
+        info = mlcc_es_info()
+        self.ctx.before()
+        st = load().mlcc_excited_states_folded(self.handle, byref(opts), w, _ptr(R), byref(info))
+        self.ctx.after()
+        _check(st)
+        return np.array(w[:]), R, info
 
     def fold_window(self):
         w = c_double(0.0)

@@ -3,7 +3,8 @@ oracle's sigma_eff / sigma_eff_domega (oracle/folded.py, pinned to the dense fol
 Jacobian), element by element at the oracle's ground state, for several omega below the
 lowest P_S denominator: singles and P_T rows of A_eff(omega) c, zero P_S rows, and the
 singles of dA_eff/domega c. Also the window itself (min eps_aibj over P_S) and the
-argument checks.
+argument checks; and the folded eigensolver (mlcc_excited_states_folded) against the
+oracle's unfolded Davidson roots and, through the oracle's sigma, its unfolded vectors.
 Collected after the other GPU tests, so that a failure here cannot hide their results.
 """
 import numpy as np
@@ -86,3 +87,33 @@ def test_sigma_eff_argument_checks(ctx):
         g.sigma_eff(c, [top])                   # on the lowest pole
     assert e.value.status == mlcc.MLCC_E_ARG
     assert float(_host(g.sigma_eff(c, [0.5 * top])).max()) == 0.0   # linear: zero in, zero out
+
+
+@pytest.mark.parametrize("case", ["small", "tiny:three_level"])
+def test_folded_eigensolver(ctx, case):
+    from oracle.davidson import excited_states
+    from oracle.folded import excited_states_folded
+    from oracle.mlcc import sigma
+    from paper_2006_05226_gb300 import mlcc
+    L, F, no, lev = _inputs(case)
+    g, o, lay = _make(ctx, L, F, no, lev)
+    gs = solve_ground_state(o)
+    g.jacobian_prepare(_dev(lay.t1(gs.t1)), _dev(lay.x2(gs.x2)))
+    if case == "small":
+        want = excited_states(o, gs, 3, res_tol=1e-9).omega
+    else:
+        want = excited_states_folded(o, gs, 3)
+        if want.size < 3:
+            pytest.skip("fewer than three roots below the lowest P_S denominator")
+    w, R, info = g.excited_states_folded(mlcc.default_options(n_roots=3, es_res_tol=1e-9))
+    assert info.converged and info.n_sigma > 0
+    assert np.abs(w - want).max() < 1e-8
+    R = _host(R)
+    n1 = o.nv * o.no
+    for k in range(3):
+        assert abs(np.linalg.norm(R[k]) - 1.0) < 1e-12
+        c1 = lay.t1_back(R[k][:n1], (o.nv, o.no))
+        c2 = lay.x2_back(R[k][n1:], o.doubles_shape())
+        s1, s2 = sigma(o, gs.t1, gs.x2, c1, c2)
+        res = np.sqrt(np.sum((s1 - w[k] * c1) ** 2) + np.sum((s2 - w[k] * c2) ** 2))
+        assert res < 1e-6
