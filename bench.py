@@ -225,7 +225,8 @@ def config_dict(args, prec):
             "n_mo": s.n_mo, "n_occ": s.n_occ, "n_chol": s.n_chol, "ccsd_active": [s.t_occ, s.t_vir],
             "cc2_active": [s.s_occ, s.s_vir], "n_roots": s.n_roots, "precision": prec,
             "l2": f"inputs larger than L2 (L^J_pq is {s.n_chol * s.n_mo ** 2 * 8 / 1e9:.2f} GB)",
-            "parallelism": f"replicas{args.gpus}"}
+            "parallelism": f"replicas{args.gpus}",
+            "excited_state_solver": getattr(args, "solver", "davidson")}
 
 
 def _make_system(spec):
@@ -356,6 +357,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--solver", default="davidson", choices=["davidson", "folded"],
+                    help="excited states: Davidson on the full Jacobian, or the folded CC2 Jacobian "
+                         "(sigma in the --refine precision)")
     args = ap.parse_args()
     global WORKLOAD
     if args.workload != "serving":
@@ -392,10 +396,15 @@ def main():
     L_dev = torch.as_tensor(system.L, device=f"cuda:{local}")
     F_dev = torch.as_tensor(system.fock, device=f"cuda:{local}")
 
+    fold_opts = mlcc.default_options(n_roots=spec.n_roots, precision=refine, es_res_tol=1e-8)
+
     def step():
         g = mlcc.System(ctx, L_dev, F_dev, spec.n_occ, system.level)
         t1, x2, gi = g.ground_state(opts)
-        w, _, ei = g.excited_states(opts, want_vectors=False)
+        if args.solver == "folded":
+            w, _, ei = g.excited_states_folded(fold_opts, want_vectors=False)
+        else:
+            w, _, ei = g.excited_states(opts, want_vectors=False)
         g.close()
         return ei.n_sigma, ei.n_sigma_lowp, w, gi
 
