@@ -47,22 +47,6 @@ __global__ void k_diag(const double* F, int n, double* eps) {
 }
 }  // namespace
 
-template <class F>
-static mlcc_status guard(F&& f) {
-  try {
-    return f();
-  } catch (const Error& e) {
-    set_last_error(e.what());
-    return e.status;
-  } catch (const std::exception& e) {
-    set_last_error(e.what());
-    return MLCC_E_CUDA;
-  } catch (...) {
-    set_last_error("unknown error");
-    return MLCC_E_CUDA;
-  }
-}
-
 static void setup_system(mlcc_system* S, const mlcc_problem* P, const double* chol, const double* fock) {
   cudaStream_t s = S->ctx->stream;
   const int n = P->n_mo, no = P->n_occ, nj = P->n_chol;

@@ -40,6 +40,24 @@ void count_launch();
     if (!(cond)) throw ::mlcc::Error(MLCC_E_ARG, std::string(msg));  \
   } while (0)
 
+// Runs an entry point's body; every mlcc::Error and std::exception becomes a status code
+// with its message in mlcc_last_error(), so no exception crosses the C ABI.
+template <class F>
+mlcc_status guard(F&& f) {
+  try {
+    return f();
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.status;
+  } catch (const std::exception& e) {
+    set_last_error(e.what());
+    return MLCC_E_CUDA;
+  } catch (...) {
+    set_last_error("unknown error");
+    return MLCC_E_CUDA;
+  }
+}
+
 // ---------------------------------------------------------------------------------
 // Device arena: one cudaMalloc, bump allocation with marks. Allocations are 256-byte
 // aligned so every TMA / vector access starts on an aligned boundary.

@@ -70,28 +70,12 @@ int64_t footprint(const sizes::Dims& d, const mlcc_options& o) {
   return int64_t(system + std::max(inputs, after));
 }
 
-template <class F>
-mlcc_status guarded(F&& f) {
-  try {
-    return f();
-  } catch (const Error& e) {
-    set_last_error(e.what());
-    return e.status;
-  } catch (const std::exception& e) {
-    set_last_error(e.what());
-    return MLCC_E_CUDA;
-  } catch (...) {
-    set_last_error("unknown error");
-    return MLCC_E_CUDA;
-  }
-}
-
 }  // namespace
 
 extern "C" {
 
 mlcc_status mlcc_solve_footprint(const mlcc_problem* prob, const mlcc_options* opt, int64_t* bytes) {
-  return guarded([&] {
+  return guard([&] {
     MLCC_REQUIRE(prob && opt && bytes, "mlcc_solve_footprint: NULL argument");
     sizes::Dims d;
     MLCC_REQUIRE(sizes::dims_from_levels(prob->n_mo, prob->n_occ, prob->n_chol, prob->level, &d),
@@ -102,7 +86,7 @@ mlcc_status mlcc_solve_footprint(const mlcc_problem* prob, const mlcc_options* o
 }
 
 mlcc_status mlcc_server_create(int device, int32_t n_slots, int64_t hbm_budget_bytes, mlcc_server** out) {
-  return guarded([&] {
+  return guard([&] {
     MLCC_REQUIRE(out != nullptr, "mlcc_server_create: out is NULL");
     *out = nullptr;
     MLCC_REQUIRE(n_slots >= 1 && n_slots <= 64, "mlcc_server_create: n_slots must be in [1, 64]");
@@ -153,7 +137,7 @@ void mlcc_server_destroy(mlcc_server* srv) {
 
 mlcc_status mlcc_submit(mlcc_server* srv, const mlcc_problem* prob, const double* chol_host,
                         const double* fock_host, const mlcc_options* opt, uint64_t* ticket) {
-  return guarded([&] {
+  return guard([&] {
     MLCC_REQUIRE(srv && prob && chol_host && fock_host && opt && ticket, "mlcc_submit: NULL argument");
     *ticket = 0;
     sizes::Dims d;
@@ -179,7 +163,7 @@ mlcc_status mlcc_submit(mlcc_server* srv, const mlcc_problem* prob, const double
 
 mlcc_status mlcc_poll(mlcc_server* srv, uint64_t ticket, int64_t wait_ms, mlcc_request_result* res,
                       double* omega_host) {
-  return guarded([&] {
+  return guard([&] {
     MLCC_REQUIRE(srv && res, "mlcc_poll: NULL argument");
     serve::Outcome o;
     void* payload = nullptr;
@@ -206,7 +190,7 @@ mlcc_status mlcc_poll(mlcc_server* srv, uint64_t ticket, int64_t wait_ms, mlcc_r
 }
 
 mlcc_status mlcc_cancel(mlcc_server* srv, uint64_t ticket) {
-  return guarded([&] {
+  return guard([&] {
     MLCC_REQUIRE(srv != nullptr, "mlcc_cancel: NULL server");
     const int32_t st = srv->sched->cancel(ticket);
     MLCC_REQUIRE(st != serve::kArg, "mlcc_cancel: unknown ticket");
@@ -216,7 +200,7 @@ mlcc_status mlcc_cancel(mlcc_server* srv, uint64_t ticket) {
 }
 
 mlcc_status mlcc_server_stats(mlcc_server* srv, mlcc_server_info* info) {
-  return guarded([&] {
+  return guard([&] {
     MLCC_REQUIRE(srv && info, "mlcc_server_stats: NULL argument");
     const serve::Stats s = srv->sched->stats();
     *info = mlcc_server_info{};
