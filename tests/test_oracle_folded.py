@@ -155,3 +155,29 @@ def test_linearised_folded_solver_on_the_seven_orbital_partitions(sys7, name, le
         pytest.skip("fewer than three roots below the lowest P_S denominator")
     roots, _ = excited_states_folded_linearised(osys, gs, 3)
     assert np.abs(roots - want).max() < 1e-9
+
+
+@pytest.mark.parametrize("name,lev", FOLDABLE)
+def test_sigma_eff_domega_is_the_omega_derivative(sys7, name, lev):
+    """dA_eff/domega c from sigma_eff_domega equals the central difference of sigma_eff in
+    omega (singles; the P_T rows do not depend on omega), and equals
+    -A_1S diag((omega - eps_S)^-2) A_S1 c1 built from the dense Jacobian."""
+    from oracle.folded import sigma_eff_domega
+    osys, gs = _setup(sys7, lev)
+    A, one, S, T, dS = _blocks(osys, gs)
+    rng = np.random.default_rng(5)
+    c1 = rng.standard_normal((osys.nv, osys.no))
+    cT = rng.standard_normal(osys.doubles_shape())
+    cT = cT + cT.transpose(2, 3, 0, 1)
+    top = dS.min() if dS.size else 1.0
+    for omega in (0.0, 0.3 * top, -0.2):
+        d1 = sigma_eff_domega(osys, gs, c1, omega)
+        h = 1e-4
+        p1, p2 = sigma_eff(osys, gs, c1, cT, omega + h)
+        m1, m2 = sigma_eff(osys, gs, c1, cT, omega - h)
+        fd = (p1 - m1) / (2 * h)
+        assert np.abs(d1 - fd).max() < 1e-6 * max(1.0, np.abs(d1).max())
+        assert np.abs(p2 - m2).max() < 1e-12
+        if S.size:
+            ref = -A[np.ix_(one, S)] @ (((omega - dS) ** -2) * (A[np.ix_(S, one)] @ c1.ravel()))
+            assert np.abs(d1.ravel() - ref).max() < 1e-10 * max(1.0, np.abs(ref).max())
