@@ -246,8 +246,10 @@ mlcc_status mlcc_sigma(mlcc_system* sys, int32_t n_vec, const double* c_dev,
    vector layout (only the singles and the P_T doubles of c are read): sigma_dev
    [n_vec][vector_len] gets the singles and P_T rows, zero on P_S. dsigma_dev (or NULL)
    [n_vec][n_singles] gets the singles of dA_eff/domega c = -A_1S (omega - eps_S)^-2 A_S1 c1
-   (the P_T rows do not depend on omega). Cost: three Jacobian transformations per vector
-   (two without dsigma), in `precision`. Each omega[k] (host) must lie below the lowest
+   (the P_T rows do not depend on omega). Cost per vector: three partial Jacobian
+   transformations (two without dsigma), each with one Cholesky-rank GEMM: the P_S rows of
+   sigma(c1, 0), the singles and P_T rows of sigma(c1, c_S + c_T), and the
+   doubles-to-singles part of sigma(0, x_S); in `precision`. Each omega[k] (host) must lie below the lowest
    P_S denominator (mlcc_fold_window), else MLCC_E_ARG; MLCC_E_STATE before
    mlcc_jacobian_prepare. Scratch: three vectors, allocated for the call; synchronises. */
 mlcc_status mlcc_sigma_eff(mlcc_system* sys, int32_t n_vec, const double* omega_host,
@@ -268,7 +270,7 @@ mlcc_status mlcc_fold_window(const mlcc_system* sys, double* omega_max);
    opt->max_es_iter bounds each stage; opt->max_subspace the subspace (0: 8 n_roots).
    omega_host [n_roots] ascending; r_dev [n_roots][vector_len] or NULL: the unfolded
    eigenvectors (c1, c_S(omega) + c_T), unit 2-norm, largest-magnitude element positive.
-   info->n_sigma counts Jacobian transformations (three per application). Needs
+   info->n_sigma counts partial Jacobian transformations (three per application). Needs
    2 n_roots <= n_vir n_occ. MLCC_E_ES_NOCONV if a root does not converge. */
 mlcc_status mlcc_excited_states_folded(mlcc_system* sys, const mlcc_options* opt,
                                        double* omega_host, double* r_dev, mlcc_es_info* info);

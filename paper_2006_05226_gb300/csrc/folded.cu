@@ -4,10 +4,12 @@
 // part is c_S(omega) = (omega - eps_S)^-1 A_S1 c1 and (c1, c_T) solves
 //   A_eff(omega) (c1, c_T) = omega (c1, c_T),
 //   A_eff(omega) = [[A_11 + A_1S (omega - eps_S)^-1 A_S1, A_1T], [A_T1, A_TT]].
-// sigma_eff applies A_eff(omega) with two Jacobian transformations: sigma(c1, 0) gives
-// A_S1 c1 on the P_S rows; sigma(c1, c_S(omega) + c_T) gives the singles and P_T rows. The
+// sigma_eff applies A_eff(omega) with two partial Jacobian transformations: sigma(c1, 0)
+// without its doubles-to-singles and CCSD parts gives A_S1 c1 on the P_S rows;
+// sigma(c1, c_S(omega) + c_T) without its P_S rows gives the singles and P_T rows. The
 // omega-derivative dA_eff/domega (c1, c_T) = (-A_1S (omega - eps_S)^-2 A_S1 c1, 0) is the
-// singles part of sigma(0, x_S) with x_S = -(A_S1 c1) / (omega - eps_S)^2.
+// singles part of sigma(0, x_S) with x_S = -(A_S1 c1) / (omega - eps_S)^2, of which only
+// the doubles-to-singles part is evaluated. Each part runs one Cholesky-rank GEMM.
 #include "system.cuh"
 
 #include <algorithm>
@@ -85,13 +87,13 @@ void sigma_eff_eval(mlcc_system* S, const double* c, double omega, double* out, 
   // w0 = (c1, 0); w1 = sigma(c1, 0)
   MLCC_CUDA(cudaMemcpyAsync(w0, c, size_t(n1) * 8, cudaMemcpyDeviceToDevice, s));
   if (nd) MLCC_CUDA(cudaMemsetAsync(w0 + n1, 0, size_t(nd) * 8, s));
-  sigma_eval(S, w0, w1, precision);
+  sigma_eval(S, w0, w1, precision, SIGMA_CC2_DOUBLES);   // only its P_S rows are read
   // w0 doubles = c_S(omega) + c_T; w2 doubles = derivative direction x_S
   if (nd) {
     k_fold_doubles<<<nblk(nd), 256, 0, s>>>(w1 + n1, c + n1, S->eps, no, sv, so, tv, to, omega, w0 + n1, w2 + n1);
     MLCC_CHECK_LAUNCH();
   }
-  sigma_eval(S, w0, out, precision);
+  sigma_eval(S, w0, out, precision, SIGMA_DOUBLES_TO_SINGLES | SIGMA_CCSD_ROWS);
   if (nd) {
     k_keep_T<<<nblk(nd), 256, 0, s>>>(out + n1, sv, so, tv, to);
     MLCC_CHECK_LAUNCH();
@@ -99,7 +101,7 @@ void sigma_eff_eval(mlcc_system* S, const double* c, double omega, double* out, 
   if (dout) {
     // (0, x_S): its singles are A_1S x_S
     MLCC_CUDA(cudaMemsetAsync(w2, 0, size_t(n1) * 8, s));
-    sigma_eval(S, w2, w1, precision);
+    sigma_eval(S, w2, w1, precision, SIGMA_DOUBLES_TO_SINGLES);
     MLCC_CUDA(cudaMemcpyAsync(dout, w1, size_t(n1) * 8, cudaMemcpyDeviceToDevice, s));
   }
 }

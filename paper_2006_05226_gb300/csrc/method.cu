@@ -618,7 +618,7 @@ static void jacobian_intermediates(mlcc_system* S) {
 // intermediates X and Y, the doubles-to-singles terms, the CC2 doubles
 // (L~_bC c_Cj - c_bK L~_Kj) L~_ai symmetrised plus eps c, and the CCSD rows as the tangent
 // of the MLCCSD doubles residual.
-void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision) {
+void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision, unsigned parts) {
   if (!S->prepared) throw Error(MLCC_E_STATE, "mlcc_sigma: call mlcc_jacobian_prepare first");
   cudaStream_t s = stm(S);
   if (precision != MLCC_FP64 && S->opcache) {
@@ -675,35 +675,39 @@ void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision) {
       k_to_fv<<<nblk(dS), 256, 0, s>>>(dF, so, sv, dfv);
       MLCC_CHECK_LAUNCH();
       phase.mark("sigma_doubles_to_singles");
-      // doubles -> singles
-      double* uc = S->ws.get<double>(size_t(S->nd));
-      make_u(S, c2, uc);
-      double* Zc = S->ws.get<double>(size_t(nj) * dS);
-      rank_gemm(S, precision, false, S->Lov, uc, Zc, 1.0, 0.0);
-      double* tmp = S->ws.get<double>(size_t(dS));
-      gemm1(S, dS, 1, dS, 1.0, S->u, dS, false, dfv, 1, false, 0.0, tmp, 1);
-      gemm1(S, dS, 1, dS, 1.0, uc, dS, false, S->Fov, 1, false, 1.0, tmp, 1);
-      k_scatter_add_ai<<<nblk(dS), 256, 0, s>>>(tmp, sv, so, no, 1.0, s1);
-      MLCC_CHECK_LAUNCH();
-      // (u(c)^{bc}_{ij} Lt^K_jc) Lt^K_Ab  and  - (u(c)^{ab}_{jk} Lt^K_kb) Lt^K_jI
-      bgemm(S, nv, so, sv, 1.0, Lvv, n, nn, false, Zc, so, dS, false, 1.0, s1, no, 0, true);
-      bgemm(S, sv, no, so, -1.0, Zc, so, dS, false, Loo, n, nn, false, 1.0, s1, no, 0, true);
-      phase.mark("sigma_cc2_doubles");
-      // CC2 doubles on P_S
-      double* V = S->ws.get<double>(size_t(nj) * dS);
-      {
-        int64_t dims[3] = {nj, sv, so}, ss[3] = {vo, no, 1}, ds[3] = {dS, so, 1};
-        permute_f64(3, dims, dvo, ss, V, ds, 1.0, 0.0, s);
+      if (parts & SIGMA_DOUBLES_TO_SINGLES) {
+        // doubles -> singles
+        double* uc = S->ws.get<double>(size_t(S->nd));
+        make_u(S, c2, uc);
+        double* Zc = S->ws.get<double>(size_t(nj) * dS);
+        rank_gemm(S, precision, false, S->Lov, uc, Zc, 1.0, 0.0);
+        double* tmp = S->ws.get<double>(size_t(dS));
+        gemm1(S, dS, 1, dS, 1.0, S->u, dS, false, dfv, 1, false, 0.0, tmp, 1);
+        gemm1(S, dS, 1, dS, 1.0, uc, dS, false, S->Fov, 1, false, 1.0, tmp, 1);
+        k_scatter_add_ai<<<nblk(dS), 256, 0, s>>>(tmp, sv, so, no, 1.0, s1);
+        MLCC_CHECK_LAUNCH();
+        // (u(c)^{bc}_{ij} Lt^K_jc) Lt^K_Ab  and  - (u(c)^{ab}_{jk} Lt^K_kb) Lt^K_jI
+        bgemm(S, nv, so, sv, 1.0, Lvv, n, nn, false, Zc, so, dS, false, 1.0, s1, no, 0, true);
+        bgemm(S, sv, no, so, -1.0, Zc, so, dS, false, Loo, n, nn, false, 1.0, s1, no, 0, true);
       }
-      double* W = S->ws.get<double>(size_t(S->nd));
-      rank_gemm(S, precision, true, S->Lai, V, W, 1.0, 0.0);
-      dim3 blk(32, 8), grd(unsigned((dS + 31) / 32), unsigned((dS + 31) / 32));
-      k_sigma2_cc2<<<grd, blk, 0, s>>>(W, c2, S->eps, no, sv, so, tv, to, s2);
-      MLCC_CHECK_LAUNCH();
+      phase.mark("sigma_cc2_doubles");
+      if (parts & SIGMA_CC2_DOUBLES) {
+        // CC2 doubles on P_S
+        double* V = S->ws.get<double>(size_t(nj) * dS);
+        {
+          int64_t dims[3] = {nj, sv, so}, ss[3] = {vo, no, 1}, ds[3] = {dS, so, 1};
+          permute_f64(3, dims, dvo, ss, V, ds, 1.0, 0.0, s);
+        }
+        double* W = S->ws.get<double>(size_t(S->nd));
+        rank_gemm(S, precision, true, S->Lai, V, W, 1.0, 0.0);
+        dim3 blk(32, 8), grd(unsigned((dS + 31) / 32), unsigned((dS + 31) / 32));
+        k_sigma2_cc2<<<grd, blk, 0, s>>>(W, c2, S->eps, no, sv, so, tv, to, s2);
+        MLCC_CHECK_LAUNCH();
+      }
     }
     phase.mark("sigma_ccsd_rows");
     // CCSD rows: tangent of the CCSD residual around the cached values
-    if (to > 0 && tv > 0) {
+    if ((parts & SIGMA_CCSD_ROWS) && to > 0 && tv > 0) {
       Scope sb(S->ws);
       const int64_t oo = int64_t(no) * no;
       Dual Lai, Lac, Lki, Lkc, Fvv, Foo, t;

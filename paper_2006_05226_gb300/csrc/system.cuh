@@ -92,7 +92,15 @@ void make_u(mlcc_system* S, const double* x2, double* u);
 void omega_eval(mlcc_system* S, const double* t1, const double* x2, bool gs_mode,
                 const double* tT, double* x2_out, double* om1, double* om2, double* energy);
 void jacobian_prepare(mlcc_system* S, const double* t1, const double* x2);
-void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision);
+// parts of sigma_eval: the singles terms driven by c1 always run; the others can be left
+// out when their rows are not needed (the rows they write are then left as they were)
+enum SigmaParts : unsigned {
+  SIGMA_DOUBLES_TO_SINGLES = 1u,   // singles terms driven by c2
+  SIGMA_CC2_DOUBLES = 2u,          // the P_S rows (and zero P_T rows before the CCSD part)
+  SIGMA_CCSD_ROWS = 4u,            // the P_T rows
+  SIGMA_ALL = 7u
+};
+void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision, unsigned parts = SIGMA_ALL);
 // folded CC2 Jacobian: out = A_eff(omega) c (singles and P_T rows; P_S rows zero), dout (if
 // not null) = the singles of dA_eff/domega c; w0, w1, w2: scratch vectors of vector_len
 void sigma_eff_eval(mlcc_system* S, const double* c, double omega, double* out, double* dout, int precision,
