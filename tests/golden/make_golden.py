@@ -3,6 +3,7 @@
   python tests/golden/make_golden.py small    # seconds
   python tests/golden/make_golden.py mid      # the oracle ground state of the 340-orbital
                                               # workload: tens of minutes on 8 cores
+  python tests/golden/make_golden.py three_level   # 560 orbitals, CCS / CC2 / CCSD levels
 
 For each workload: the reference energy E_HF = sum_I (h_II + F_II) of the reduced space,
 the MLCC ground-state correlation energy (Eq. mlcc_energy at Omega = 0, DIIS quasi-Newton

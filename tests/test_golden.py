@@ -4,8 +4,9 @@ the oracle alone) still match what the oracle and the generator produce (no GPU)
     generator's stream and draw order are unchanged;
   * the oracle's reference energy, ground-state correlation energy and lowest excitation
     energies of that workload equal the stored ones;
-  * the stored files are complete and internally consistent (the 340-orbital file, used by
-    the full-size GPU test, holds a converged ground state of the stated workload).
+  * the stored files are complete and internally consistent (the 340- and 560-orbital
+    files, used by the full-size GPU tests, hold converged ground states of the stated
+    workloads).
 """
 import json
 import os
@@ -50,7 +51,7 @@ def test_oracle_reproduces_the_stored_small_workload():
     assert np.abs(es.omega - np.array(g["omega"])).max() < 1e-9
 
 
-@pytest.mark.parametrize("name", ["small", "mid"])
+@pytest.mark.parametrize("name", ["small", "mid", "three_level"])
 def test_stored_files_describe_their_workload(name):
     from synth import CONFIGS
     g = _load(name)
