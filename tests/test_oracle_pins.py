@@ -238,3 +238,27 @@ def test_limits_reduce_between_models(sys7):
     ga = solve_ground_state(o)
     gb = solve_ground_state(o2)
     assert ga.converged and gb.converged
+
+
+@pytest.mark.parametrize("name,lev", PARTITIONS)
+def test_invariant_under_relabelling_the_orbitals(sys7, name, lev):
+    """The equations do not depend on the order in which the caller lists the orbitals of
+    each level (Sec. 2.1 defines the levels as sets): permuting the occupied and the
+    virtual orbitals, with their levels, leaves the correlation energy, the reference
+    energy and the whole spectrum of the Jacobian unchanged."""
+    t = sys7
+    lev = np.array(lev, dtype=np.int8)
+    o = MLCCSystem(t.L, t.F, t.k, lev)
+    g = solve_ground_state(o)
+    rng = np.random.default_rng(3)
+    n, k = t.F.shape[0], t.k
+    p = np.concatenate([rng.permutation(k), k + rng.permutation(n - k)])
+    o2 = MLCCSystem(t.L[:, p][:, :, p], t.F[np.ix_(p, p)], k, lev[p])
+    g2 = solve_ground_state(o2)
+    assert abs(g.energy - g2.energy) < 1e-12
+    assert abs(hf_energy(o) - hf_energy(o2)) < 1e-12
+    # the whole Jacobian spectrum (a relabelling is a similarity transformation of A)
+    w = np.linalg.eigvals(_dense_jacobian(o, g))
+    w2 = np.linalg.eigvals(_dense_jacobian(o2, g2))
+    key = lambda z: np.lexsort((np.round(z.imag, 8), np.round(z.real, 8)))
+    assert np.abs(w[key(w)] - w2[key(w2)]).max() < 1e-9
