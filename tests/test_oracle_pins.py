@@ -228,7 +228,9 @@ def test_dressing_leaves_ov_block_and_integral_symmetry(sys7):
 
 def test_limits_reduce_between_models(sys7):
     """CCS/CCSD with the CC2 level equal to the CCSD level is MLCCSD; an empty CCSD
-    level gives MLCC2 (Sec. 2.1): the three-level code must reproduce both."""
+    level gives MLCC2 (Sec. 2.1): the three-level code must reproduce both, and a CCSD
+    level that spans only occupied (or only virtual) orbitals must give the MLCC2 energy
+    and Jacobian spectrum."""
     lev_a = np.array([0, 2, 2, 2, 2, 0, 0], dtype=np.int8)
     o = MLCCSystem(sys7.L, sys7.F, sys7.k, lev_a)
     assert not o.mask_S.any()
@@ -238,6 +240,16 @@ def test_limits_reduce_between_models(sys7):
     ga = solve_ground_state(o)
     gb = solve_ground_state(o2)
     assert ga.converged and gb.converged
+    # a CCSD level with occupied orbitals only (or virtual orbitals only) holds no doubles
+    # with all four indices CCSD-active: the model is MLCC2 on the same CC2 set
+    for lev_c in ([2, 1, 1, 1, 1, 1, 0], [1, 1, 2, 2, 1, 1, 0]):
+        oc = MLCCSystem(sys7.L, sys7.F, sys7.k, np.array(lev_c, dtype=np.int8))
+        assert not oc.mask_T.any()
+        gc = solve_ground_state(oc)
+        assert abs(gc.energy - gb.energy) < 1e-12
+        wc = np.sort_complex(np.linalg.eigvals(_dense_jacobian(oc, gc)))
+        wb = np.sort_complex(np.linalg.eigvals(_dense_jacobian(o2, gb)))
+        assert np.abs(wc - wb).max() < 1e-9
 
 
 @pytest.mark.parametrize("name,lev", PARTITIONS)
