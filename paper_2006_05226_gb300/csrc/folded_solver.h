@@ -13,10 +13,13 @@
 // Stage 2 (each root): a subspace of its own, started from the stage-1 Ritz vector applied
 // at omega_k; the Ritz pair of the projected model that overlaps most with the previous one
 // is made self-consistent; its preconditioned residual, applied at the current omega,
-// extends the subspace. When the model residual is below res_tol, the root is converged if
-// every vector was applied within exact_dw of omega (the model error is second order in
-// omega - w_b); otherwise the subspace restarts from the Ritz vector applied exactly at
-// omega.
+// extends the subspace. Once the model residual is below refresh_tol, omega is known to
+// about the square of the residual: vectors applied farther than exact_dw from it are
+// dropped and the rest of the Ritz vector is applied exactly at omega, so the model is exact
+// (its error is second order in omega - w_b) for the remaining convergence to res_tol. A
+// subspace that reaches max_sub collapses onto combinations of its vectors: exact in stage 1
+// (one omega); in stage 2 they carry the distance of their sources, and count as inexact.
+
 #pragma once
 #include <algorithm>
 #include <cmath>
@@ -34,6 +37,8 @@ struct Options {
   double res_tol = 1e-8;     // model residual norm per root
   double exact_dw = 1e-7;    // |omega - w_b| bound for every subspace vector at convergence
   double stage1_tol = 1e-3;  // model residual norm that ends stage 1
+  double refresh_tol = 1e-5; // stage 2: below this model residual an inexact subspace
+                             // restarts from the Ritz vector applied exactly at omega
   int max_iter = 200;        // iterations per stage (per root in stage 2)
   int max_sub = 0;           // subspace size limit (0: 8 n_roots, at least 2 n_roots + 4)
   double omega_max = 1e300;  // the lowest P_S denominator: omega must stay below it
@@ -72,7 +77,9 @@ class Solver {
  private:
   struct Basis {
     std::vector<Vec> V, S0, S1;
-    std::vector<double> w;
+    std::vector<double> w;        // the omega S0 and S1 refer to
+    std::vector<double> d;        // 0 if applied exactly at w, else a bound on the distance
+                                  // of the first-order combination it came from
     std::vector<double> G0, G1;   // V^T S0, V^T S1, row-major m x m
     int m() const { return int(V.size()); }
   };
@@ -117,6 +124,7 @@ class Solver {
     B.S0.push_back(std::move(y));
     B.S1.push_back(std::move(dy));
     B.w.push_back(w);
+    B.d.push_back(0.0);
     for (int i = 0; i < m1; ++i) {
       G0[size_t(i) * m1 + m] = sp_.dot(B.V[i], B.S0[m]);
       G1[size_t(i) * m1 + m] = sp_.dot(B.V[i], B.S1[m]);
@@ -125,6 +133,78 @@ class Solver {
     }
     B.G0.swap(G0);
     B.G1.swap(G1);
+  }
+
+  // a basis of the combinations C (coefficients in B) of B's vectors, all referred to w by
+  // the first-order model: v = sum c_b V_b, S0 = sum c_b (S0_b + (w - w_b) S1_b),
+  // S1 = sum c_b S1_b; orthonormalised with the same operations on S0 and S1. Exact when
+  // every w_b equals w; no applications of the operator
+  Basis combine(const Basis& B, const std::vector<std::vector<double>>& C, double w) {
+    Basis N;
+    for (const auto& c : C) {
+      Vec v = sp_.make(), s0 = sp_.make(), s1 = sp_.make();
+      double dist = 0.0;
+      for (int b = 0; b < B.m() && b < int(c.size()); ++b) {
+        if (c[b] == 0.0) continue;
+        dist = std::max(dist, std::fabs(w - B.w[b]) + B.d[b]);
+        sp_.axpy(c[b], B.V[b], v);
+        sp_.axpy(c[b], B.S0[b], s0);
+        if (w != B.w[b]) sp_.axpy(c[b] * (w - B.w[b]), B.S1[b], s0);
+        sp_.axpy(c[b], B.S1[b], s1);
+      }
+      const double n0 = std::sqrt(std::max(0.0, sp_.dot(v, v)));
+      if (!(n0 > 0.0)) continue;
+      for (int pass = 0; pass < 2; ++pass)
+        for (int i = 0; i < N.m(); ++i) {
+          const double a = sp_.dot(N.V[i], v);
+          sp_.axpy(-a, N.V[i], v);
+          sp_.axpy(-a, N.S0[i], s0);
+          sp_.axpy(-a, N.S1[i], s1);
+        }
+      const double n1 = std::sqrt(std::max(0.0, sp_.dot(v, v)));
+      if (!(n1 > 1e-8 * n0)) continue;
+      sp_.scale(1.0 / n1, v);
+      sp_.scale(1.0 / n1, s0);
+      sp_.scale(1.0 / n1, s1);
+      N.V.push_back(std::move(v));
+      N.S0.push_back(std::move(s0));
+      N.S1.push_back(std::move(s1));
+      N.w.push_back(w);
+      N.d.push_back(dist);   // conservative: the orthonormalisation mixes earlier ones in
+    }
+    double dmax = 0.0;
+    for (double x : N.d) dmax = std::max(dmax, x);
+    for (double& x : N.d) x = dmax;
+    const int m = N.m();
+    N.G0.assign(size_t(m) * m, 0.0);
+    N.G1.assign(size_t(m) * m, 0.0);
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) {
+        N.G0[size_t(i) * m + j] = sp_.dot(N.V[i], N.S0[j]);
+        N.G1[size_t(i) * m + j] = sp_.dot(N.V[i], N.S1[j]);
+      }
+    return N;
+  }
+
+  // real parts of the eigenvectors of the projected model at w, ordered by eig_nonsym
+  // (ascending real part); empty on failure
+  std::vector<std::vector<double>> model_vectors(const Basis& B, double w, std::vector<double>* re) {
+    const int m = B.m();
+    std::vector<double> M(size_t(m) * m);
+    for (int a = 0; a < m; ++a)
+      for (int b = 0; b < m; ++b)
+        M[size_t(a) * m + b] = B.G0[size_t(a) * m + b] + B.G1[size_t(a) * m + b] * (w - B.w[b]);
+    std::vector<std::complex<double>> lam;
+    std::vector<std::vector<std::complex<double>>> Y;
+    std::vector<std::vector<double>> out;
+    if (!eig_nonsym(m, M, lam, &Y, m)) return out;
+    for (int j = 0; j < m; ++j) {
+      std::vector<double> y(m);
+      for (int a = 0; a < m; ++a) y[a] = Y[j][a].real();
+      out.push_back(std::move(y));
+      if (re) re->push_back(lam[j].real());
+    }
+    return out;
   }
 
   // the self-consistent Ritz pair of the projected first-order model chosen by pick
@@ -183,6 +263,7 @@ Result Solver<Space>::run(std::vector<Vec>* vectors) {
   const int ng = std::min(2 * nr, sp_.n_guess());
   if (nr < 1 || ng < nr) {
     res.failure = "fewer start vectors than roots";
+    res.n_apply = n_apply_;
     return res;
   }
   // stage 1: every vector applied at omega_0
@@ -209,6 +290,7 @@ Result Solver<Space>::run(std::vector<Vec>* vectors) {
       });
       if (!P[k].ok) {
         res.failure = "stage 1: no admissible Ritz pair";
+        res.n_apply = n_apply_;
         return res;
       }
       om[k] = P[k].omega;
@@ -220,13 +302,13 @@ Result Solver<Space>::run(std::vector<Vec>* vectors) {
       break;
     }
     if (B.m() + nr > max_sub_) {
-      // collapse onto the Ritz vectors, re-applied at omega_0
-      Basis C;
-      for (int k = 0; k < nr; ++k) {
-        Vec v = X[k];
-        if (orthonormalise(C, v, 1e-10)) append(C, std::move(v), w0);
-      }
-      B = std::move(C);
+      // collapse onto the roots' Ritz vectors and the next model eigenvectors (2 n_roots
+      // in all); every vector was applied at omega_0, so the combinations are exact
+      std::vector<std::vector<double>> C;
+      for (int k = 0; k < nr; ++k) C.push_back(P[k].y);
+      std::vector<std::vector<double>> extra = model_vectors(B, om[nr - 1], nullptr);
+      for (int j = nr; j < int(extra.size()) && int(C.size()) < 2 * nr; ++j) C.push_back(extra[j]);
+      B = combine(B, C, w0);
       continue;
     }
     int added = 0;
@@ -242,6 +324,7 @@ Result Solver<Space>::run(std::vector<Vec>* vectors) {
   }
   if (!stage1_done) {
     res.failure = "stage 1 did not converge";
+    res.n_apply = n_apply_;
     return res;
   }
   // stage 2: one root at a time
@@ -287,19 +370,60 @@ Result Solver<Space>::run(std::vector<Vec>* vectors) {
       });
       if (!p.ok) break;
       w = p.omega;
-      if (p.rnorm < o_.res_tol) {
+      if (p.rnorm < std::max(o_.res_tol, o_.refresh_tol)) {
         double dw = 0.0;
-        for (double wb : R.w) dw = std::max(dw, std::fabs(w - wb));
-        if (dw < o_.exact_dw) {
+        for (int b = 0; b < R.m(); ++b) dw = std::max(dw, std::fabs(w - R.w[b]) + R.d[b]);
+        if (dw >= o_.exact_dw) {
+          // omega is now known to about the square of the residual: refer the subspace to
+          // it exactly, so that the rest of the convergence uses an exact model. Vectors
+          // applied within exact_dw of omega stay; the rest of the Ritz vector is applied
+          // exactly at omega
+          std::vector<std::vector<double>> C;
+          for (int b = 0; b < R.m(); ++b)
+            if (std::fabs(w - R.w[b]) + R.d[b] < o_.exact_dw) {
+              std::vector<double> e(R.m(), 0.0);
+              e[b] = 1.0;
+              C.push_back(std::move(e));
+            }
+          Basis K = combine(R, C, w);
+          Vec t = p.x;
+          if (orthonormalise(K, t, 1e-10)) append(K, std::move(t), w);
+          if (K.m() == 0) {
+            restart(p.x, w);
+            continue;
+          }
+          R = std::move(K);
+          yprev.assign(R.m(), 0.0);
+          for (int b = 0; b < R.m(); ++b) yprev[b] = sp_.dot(R.V[b], p.x);
+          continue;
+        }
+        if (p.rnorm < o_.res_tol) {
           done = true;
           break;
         }
-        restart(p.x, w);
+      }
+      if (R.m() >= max_sub_) {
+        // thick restart: the Ritz vector and the three model eigenvectors whose values lie
+        // nearest omega, referred to omega by the first-order model (no applications)
+        std::vector<double> re;
+        std::vector<std::vector<double>> ev = model_vectors(R, w, &re);
+        std::vector<int> idx(ev.size());
+        for (size_t j = 0; j < idx.size(); ++j) idx[j] = int(j);
+        std::stable_sort(idx.begin(), idx.end(),
+                         [&](int a, int b) { return std::fabs(re[a] - w) < std::fabs(re[b] - w); });
+        std::vector<std::vector<double>> C{p.y};
+        for (int j : idx) {
+          if (C.size() >= 4) break;
+          C.push_back(ev[j]);
+        }
+        R = combine(R, C, w);
+        yprev.assign(R.m(), 0.0);
+        yprev[0] = 1.0;
         continue;
       }
       Vec t = sp_.make();
       sp_.precondition(p.r, w, t);
-      if (R.m() >= max_sub_ || !orthonormalise(R, t, 1e-12)) {
+      if (!orthonormalise(R, t, 1e-12)) {
         restart(p.x, w);
         continue;
       }

@@ -168,6 +168,23 @@ def test_synthetic_three_level_operators(lib, seed):
     assert napp < 250
 
 
+def test_larger_diagonally_dominant_operator(lib):
+    """400 singles, 100 CCSD-block doubles, 2000 folded pairs, weak couplings (the regime of
+    CC Jacobians): six roots exact to 1e-10, within a bound on the applications."""
+    rng = np.random.default_rng(21)
+    n1, nT, nS = 400, 100, 2000
+    e = np.concatenate([np.sort(rng.uniform(0.2, 1.5, n1)), np.sort(rng.uniform(0.4, 2.0, nT))])
+    B = 0.002 * rng.standard_normal((n1 + nT, n1 + nT))
+    P = np.diag(e) + 0.5 * (B + B.T)
+    d = rng.uniform(1.0, 3.0, nS)
+    V = 0.004 * rng.standard_normal((nS, n1))
+    U = 2.0 * V.T
+    ok, w, _, napp = _solve(lib, P, U, V, d, 6)
+    assert ok
+    assert np.abs(w - _unfolded_roots(P, U, V, d, 6)).max() < 1e-10
+    assert napp < 400
+
+
 def test_the_seven_orbital_fold(lib):
     from oracle.folded import excited_states_folded, fold_parts
     from oracle.mlcc import MLCCSystem, solve_ground_state
