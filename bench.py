@@ -337,6 +337,52 @@ def run_serving(args):
     return 0
 
 
+def run_probe(args):
+    """--probe: the Jacobian transformation of one synthetic system, for kernel profiling.
+
+    The system has the Cholesky-rank GEMM shapes of the benchmark workload scaled down so
+    that the device holds a few GB (--occ, --vir, --chol, --ccsd-occ, --ccsd-vir). The
+    Jacobian is prepared at seeded small amplitudes (no ground-state solve) and --nsigma
+    sigma-vectors in --precision run inside a cudaProfilerStart/Stop range (capture with
+    ncu --profile-from-start off). Prints one line; no JSON, not a bench value."""
+    import numpy as np
+    import torch
+    from paper_2006_05226_gb300 import mlcc
+    from synth.generator import SystemSpec, default_scale, make_system
+    precs = {"fp64": mlcc.MLCC_FP64, "bf16": mlcc.MLCC_BF16, "bf16x3": mlcc.MLCC_BF16X3,
+             "bf16x6": mlcc.MLCC_BF16X6, "fp64e": mlcc.MLCC_FP64E}
+    prec = precs[args.precision]
+    tau = args.chol / 5.0
+    spec = SystemSpec("probe", args.occ, args.vir, args.chol, tau, args.occ, args.vir, args.ccsd_occ,
+                      args.ccsd_vir, 4, 0, default_scale(tau))
+    s = make_system(spec, rhf_tol=1e-8)
+    ctx = mlcc.Context(0)
+    g = mlcc.System(ctx, torch.as_tensor(s.L, device="cuda"), torch.as_tensor(s.fock, device="cuda"),
+                    args.occ, s.level)
+    d = g.dims
+    rng = np.random.default_rng(0)
+    t1 = torch.as_tensor(0.01 * rng.standard_normal(d.n_singles), device="cuda")
+    m = d.s_vir * d.s_occ
+    x2 = 0.01 * rng.standard_normal((m, m))
+    x2 = torch.as_tensor((x2 + x2.T).ravel(), device="cuda")
+    g.jacobian_prepare(t1, x2)
+    c = rng.standard_normal(d.vector_len)
+    c2 = c[d.n_singles:].reshape(m, m)
+    c[d.n_singles:] = (c2 + c2.T).ravel()
+    c = torch.as_tensor(c, device="cuda").reshape(1, -1)
+    g.sigma(c, precision=prec)      # warm: operand caches, kernel attributes
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStart()
+    for _ in range(args.nsigma):
+        g.sigma(c, precision=prec)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    g.close()
+    ctx.close()
+    print(f"probe ok: vector_len {d.vector_len}, precision {args.precision}, {args.nsigma} sigma")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="mid", choices=["mid", "three_level", "serving"],
@@ -360,7 +406,17 @@ def main():
     ap.add_argument("--solver", default="davidson", choices=["davidson", "folded"],
                     help="excited states: Davidson on the full Jacobian, or the folded CC2 Jacobian "
                          "(sigma in the --refine precision)")
+    ap.add_argument("--probe", action="store_true",
+                    help="profiling probe: sigma-vectors of one scaled-down system (see run_probe)")
+    ap.add_argument("--occ", type=int, default=40, help="probe: occupied orbitals")
+    ap.add_argument("--vir", type=int, default=150, help="probe: virtual orbitals")
+    ap.add_argument("--chol", type=int, default=1500, help="probe: Cholesky vectors")
+    ap.add_argument("--ccsd-occ", type=int, default=10, help="probe: CCSD-active occupied")
+    ap.add_argument("--ccsd-vir", type=int, default=60, help="probe: CCSD-active virtual")
+    ap.add_argument("--nsigma", type=int, default=1, help="probe: sigma-vectors in the profiled range")
     args = ap.parse_args()
+    if args.probe:
+        return run_probe(args)
     global WORKLOAD
     if args.workload != "serving":
         WORKLOAD = args.workload

@@ -62,6 +62,9 @@ typedef enum {
   MLCC_E_ES_NOCONV = -4,    /* excited states not converged in max_es_iter       */
   MLCC_E_COMPLEX_ROOT = -5, /* a wanted Ritz value has a non-zero imaginary part */
   MLCC_E_NAN = -6,          /* NaN or Inf met in a residual or sigma             */
+  MLCC_E_TIMEOUT = -7,      /* a bounded wait inside a tensor-core kernel expired
+                               (about 2 s); the kernel stopped, freed its tensor
+                               memory and left the context usable                */
   MLCC_E_CUDA = -8,         /* a CUDA runtime call failed                        */
   MLCC_E_STATE = -9,        /* call order violated (e.g. sigma before prepare)   */
   MLCC_E_REJECTED = -10,    /* serving: footprint above the server's budget      */
@@ -271,7 +274,9 @@ mlcc_status mlcc_fold_window(const mlcc_system* sys, double* omega_max);
    omega_host [n_roots] ascending; r_dev [n_roots][vector_len] or NULL: the unfolded
    eigenvectors (c1, c_S(omega) + c_T), unit 2-norm, largest-magnitude element positive.
    info->n_sigma counts partial Jacobian transformations (three per application). Needs
-   2 n_roots <= n_vir n_occ. MLCC_E_ES_NOCONV if a root does not converge. */
+   2 n_roots <= n_vir n_occ. MLCC_E_ES_NOCONV if a root does not converge (or two roots
+   settle on the same eigenpair); MLCC_E_COMPLEX_ROOT (info->complex_pair = 1) if a wanted
+   eigenvalue is one of a complex pair, whose real part is then reported. */
 mlcc_status mlcc_excited_states_folded(mlcc_system* sys, const mlcc_options* opt,
                                        double* omega_host, double* r_dev, mlcc_es_info* info);
 /* Davidson solve for the lowest opt->n_roots eigenpairs of A at the prepared ground
@@ -382,9 +387,10 @@ mlcc_status mlcc_server_stats(mlcc_server* srv, mlcc_server_info* info);
    (a cudaStream_t, NULL for the default stream); the call does not synchronise.
    Scratch: a static device array of 2 * MLCC_NOALLOC_MAX_CHOL doubles (512 KiB), held by
    every device that loads the library until the process exits; n_chol above the limit
-   returns MLCC_E_ARG. The first call on a device looks up the array's address with that
-   device current (make that first call before any stream capture). All calls share the
-   array, so calls whose work overlaps on the device race; order them on one stream. */
+   returns MLCC_E_ARG. Each call looks up the array's address on the current device (the
+   first call on a device also loads the library's device code there: make that first call
+   before any stream capture). All calls share the array, so calls whose work overlaps on
+   the device race; order them on one stream. */
 #define MLCC_NOALLOC_MAX_CHOL 32768
 mlcc_status mlcc_fock_t1_noalloc(int32_t n_mo, int32_t n_occ, int32_t n_chol,
                                  const double* chol_dev, const double* fock_dev,

@@ -501,7 +501,7 @@ mlcc_status mlcc_gemm(mlcc_ctx* ctx, int32_t trans_a, int32_t trans_b, int64_t M
     int h = 0;
     MLCC_CUDA(cudaMemcpyAsync(&h, err, 4, cudaMemcpyDeviceToHost, s));
     MLCC_CUDA(cudaStreamSynchronize(s));
-    if (h != 0) throw Error(MLCC_E_CUDA, "mlcc_gemm: a tensor-core pipeline wait timed out");
+    if (h != 0) throw Error(MLCC_E_TIMEOUT, "mlcc_gemm: a tensor-core pipeline wait timed out");
     return MLCC_OK;
   });
 }

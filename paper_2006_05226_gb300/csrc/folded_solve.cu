@@ -114,28 +114,65 @@ __global__ void k_absmax_final(const double* x, const double* pv, const long lon
   out[0] = x[bi];
 }
 
-// a folded vector in device memory, ordered on the context stream
+// Device storage of the folded vectors: slabs of 16 vectors taken with cudaMalloc as the
+// solver needs them and reused through a free list, so that the vector operations of the
+// solve allocate and free nothing (cudaFree synchronises the device); the slabs are
+// released together when the solve ends. Slots are reused in stream order (all work of a
+// solve is on one stream), so a slot released while kernels still read it is only
+// overwritten after them.
+struct VecPool {
+  int64_t n = 0;
+  std::vector<double*> slabs, free_slots;
+  explicit VecPool(int64_t n_) : n(std::max<int64_t>(n_, 1)) {}
+  VecPool(const VecPool&) = delete;
+  VecPool& operator=(const VecPool&) = delete;
+  double* acquire() {
+    if (free_slots.empty()) {
+      constexpr int kSlab = 16;
+      // each slot starts on a 256-byte boundary
+      const int64_t stride = (n + 31) / 32 * 32;
+      double* p = nullptr;
+      MLCC_CUDA(cudaMalloc(&p, size_t(stride) * kSlab * 8));
+      slabs.push_back(p);
+      for (int k = kSlab - 1; k >= 0; --k) free_slots.push_back(p + k * stride);
+    }
+    double* p = free_slots.back();
+    free_slots.pop_back();
+    return p;
+  }
+  void release(double* p) { free_slots.push_back(p); }
+  ~VecPool() {
+    for (double* p : slabs) cudaFree(p);
+  }
+};
+
+// a folded vector in device memory (a pool slot), ordered on the context stream
 struct DVec {
   double* p = nullptr;
   int64_t n = 0;
   cudaStream_t s = nullptr;
+  VecPool* pool = nullptr;
   DVec() = default;
-  DVec(int64_t n_, cudaStream_t s_) : n(n_), s(s_) {
-    MLCC_CUDA(cudaMalloc(&p, size_t(std::max<int64_t>(n, 1)) * 8));
+  DVec(VecPool* pool_, cudaStream_t s_) : n(pool_->n), s(s_), pool(pool_) {
+    p = pool->acquire();
     MLCC_CUDA(cudaMemsetAsync(p, 0, size_t(n) * 8, s));
   }
-  DVec(const DVec& o) : DVec(o.n, o.s) {
-    if (n) MLCC_CUDA(cudaMemcpyAsync(p, o.p, size_t(n) * 8, cudaMemcpyDeviceToDevice, s));
+  DVec(const DVec& o) : n(o.n), s(o.s), pool(o.pool) {
+    if (pool) {
+      p = pool->acquire();
+      MLCC_CUDA(cudaMemcpyAsync(p, o.p, size_t(n) * 8, cudaMemcpyDeviceToDevice, s));
+    }
   }
-  DVec(DVec&& o) noexcept : p(o.p), n(o.n), s(o.s) { o.p = nullptr; }
+  DVec(DVec&& o) noexcept : p(o.p), n(o.n), s(o.s), pool(o.pool) { o.p = nullptr; }
   DVec& operator=(DVec o) noexcept {
     std::swap(p, o.p);
     std::swap(n, o.n);
     std::swap(s, o.s);
+    std::swap(pool, o.pool);
     return *this;
   }
   ~DVec() {
-    if (p) cudaFree(p);
+    if (p && pool) pool->release(p);
   }
 };
 
@@ -149,8 +186,11 @@ struct DeviceSpace {
   std::vector<int64_t> order;   // singles by ascending eps_a - eps_i
   Arena work;                   // five full vectors, the derivative singles, a scalar
   double *cf, *of, *w0, *w1, *w2, *dsing, *scal;
+  VecPool pool;                 // the folded vectors
 
-  DeviceSpace(mlcc_system* sys, int prec) : S(sys), precision(prec), s(sys->ctx->stream) {
+  DeviceSpace(mlcc_system* sys, int prec)
+      : S(sys), precision(prec), s(sys->ctx->stream),
+        pool(int64_t(sys->nv) * sys->no + int64_t(sys->tv) * sys->to * sys->tv * sys->to) {
     const int no = S->no, nv = S->nv;
     n1 = int64_t(nv) * no;
     tl = int64_t(S->tv) * S->to * S->tv * S->to;
@@ -171,7 +211,7 @@ struct DeviceSpace {
     dsing = work.get<double>(size_t(std::max<int64_t>(n1, 1)));
     scal = work.get<double>(1);
   }
-  Vec make() { return DVec(nf, s); }
+  Vec make() { return DVec(&pool, s); }
   int n_guess() { return int(std::min<int64_t>(n1, 1 << 20)); }
   void guess(int k, Vec& v, double& diag) {
     v = make();
@@ -280,9 +320,10 @@ mlcc_status excited_states_folded(mlcc_system* S, const mlcc_options* opt, doubl
     for (double r : res.residual) mr = std::max(mr, r);
     info->max_residual = have ? mr : INFINITY;
   }
+  if (info) info->complex_pair = res.complex_pair ? 1 : 0;
   if (!res.converged) {
     set_last_error(std::string("mlcc_excited_states_folded: ") + (res.failure ? res.failure : "not converged"));
-    return MLCC_E_ES_NOCONV;
+    return res.complex_pair ? MLCC_E_COMPLEX_ROOT : MLCC_E_ES_NOCONV;
   }
   return MLCC_OK;
 }

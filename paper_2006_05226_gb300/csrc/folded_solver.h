@@ -6,19 +6,25 @@
 // Each trial vector b stores A_eff(w_b) b and dA_eff/domega (w_b) b at the omega w_b it was
 // applied at; the projected problem at omega uses the first-order model
 //   A_eff(omega) b ~ A_eff(w_b) b + (omega - w_b) dA_eff/domega (w_b) b.
+// With a column b referred to w_b, the projected model is the linear pencil
+// (G0 - G1 W) y + omega G1 y, so its self-consistent pairs are the eigenpairs of
+// (I - G1)^-1 (G0 - G1 W): one small eigensolve gives them all.
 // Stage 1 (all roots): every vector is applied at one omega_0 (the lowest diagonal element
-// of the guesses); the k-th eigenvalue of the projected model is made self-consistent in
-// omega for each root; new directions are the preconditioned residuals; it stops when
-// every model residual is below stage1_tol.
+// of the guesses); the k-th self-consistent eigenvalue of the model is the k-th root;
+// new directions are the preconditioned residuals; it stops when every model residual is
+// below stage1_tol.
 // Stage 2 (each root): a subspace of its own, started from the stage-1 Ritz vector applied
 // at omega_k; the Ritz pair of the projected model that overlaps most with the previous one
-// is made self-consistent; its preconditioned residual, applied at the current omega,
+// is taken; its preconditioned residual, applied at the current omega,
 // extends the subspace. Once the model residual is below refresh_tol, omega is known to
 // about the square of the residual: vectors applied farther than exact_dw from it are
 // dropped and the rest of the Ritz vector is applied exactly at omega, so the model is exact
 // (its error is second order in omega - w_b) for the remaining convergence to res_tol. A
 // subspace that reaches max_sub collapses onto combinations of its vectors: exact in stage 1
 // (one omega); in stage 2 they carry the distance of their sources, and count as inexact.
+// A wanted eigenvalue with a non-zero imaginary part (a complex pair of the non-symmetric
+// Jacobian) is reported as such (Result::complex_pair) instead of being refined, and two
+// roots that settled on the same eigenpair make the solve fail.
 
 #pragma once
 #include <algorithm>
@@ -50,6 +56,7 @@ struct Result {
   int n_apply = 0;                // applications of A_eff (each with its derivative)
   int iterations = 0;             // stage 1 plus stage 2 iterations
   bool converged = false;
+  bool complex_pair = false;      // a wanted eigenvalue is complex (its real part reported)
   const char* failure = nullptr;  // why not, when not converged
 };
 
@@ -68,7 +75,10 @@ class Solver {
   using Vec = typename Space::Vec;
 
   Solver(Space& sp, const Options& o) : sp_(sp), o_(o) {
-    max_sub_ = o.max_sub > 0 ? o.max_sub : std::max(8 * o.n_roots, 2 * o.n_roots + 4);
+    // stage 1 collapses to 2 n_roots vectors and then adds n_roots, stage 2 restarts on 4:
+    // a limit below 3 n_roots (or 2 n_roots + 4) would collapse without progress
+    max_sub_ = o.max_sub > 0 ? o.max_sub : 8 * o.n_roots;
+    max_sub_ = std::max(max_sub_, std::max(3 * o.n_roots, 2 * o.n_roots + 4));
   }
 
   // vectors (optional): the folded Ritz vectors of the roots, in the order of res.omega
@@ -88,6 +98,7 @@ class Solver {
     std::vector<double> y;   // coefficients in the basis
     Vec x, r;
     double rnorm = 0.0;
+    double imag = 0.0;       // imaginary part of the model eigenvalue (0 for a real pair)
     bool ok = false;
   };
 
@@ -186,17 +197,39 @@ class Solver {
     return N;
   }
 
-  // real parts of the eigenvectors of the projected model at w, ordered by eig_nonsym
-  // (ascending real part); empty on failure
-  std::vector<std::vector<double>> model_vectors(const Basis& B, double w, std::vector<double>* re) {
+  // The first-order model of the projected operator is the linear pencil
+  //   A(omega) y = (G0 - G1 W) y + omega G1 y,   W = diag(w_b),
+  // so its self-consistent pairs A(omega) y = omega y are the eigenpairs of
+  //   M = (I - G1)^-1 (G0 - G1 W),
+  // found in one small eigensolve (no fixed-point iteration in omega, which can stall on a
+  // spurious point where only the real part of a complex pair equals omega). Returns M,
+  // or an empty matrix if I - G1 is singular.
+  std::vector<double> pencil(const Basis& B) {
     const int m = B.m();
-    std::vector<double> M(size_t(m) * m);
+    std::vector<double> IG(size_t(m) * m), R(size_t(m) * m), M(size_t(m) * m);
     for (int a = 0; a < m; ++a)
-      for (int b = 0; b < m; ++b)
-        M[size_t(a) * m + b] = B.G0[size_t(a) * m + b] + B.G1[size_t(a) * m + b] * (w - B.w[b]);
+      for (int b = 0; b < m; ++b) {
+        IG[size_t(a) * m + b] = (a == b ? 1.0 : 0.0) - B.G1[size_t(a) * m + b];
+        R[size_t(a) * m + b] = B.G0[size_t(a) * m + b] - B.G1[size_t(a) * m + b] * B.w[b];
+      }
+    std::vector<double> col(m), x;
+    for (int b = 0; b < m; ++b) {
+      for (int a = 0; a < m; ++a) col[a] = R[size_t(a) * m + b];
+      if (!solve_linear(m, IG, col, x)) return {};
+      for (int a = 0; a < m; ++a) M[size_t(a) * m + b] = x[a];
+    }
+    return M;
+  }
+
+  // real parts of the model's eigenvectors, ordered by eig_nonsym (ascending real part);
+  // empty on failure
+  std::vector<std::vector<double>> model_vectors(const Basis& B, std::vector<double>* re) {
+    const int m = B.m();
+    std::vector<std::vector<double>> out;
+    const std::vector<double> M = pencil(B);
+    if (M.empty()) return out;
     std::vector<std::complex<double>> lam;
     std::vector<std::vector<std::complex<double>>> Y;
-    std::vector<std::vector<double>> out;
     if (!eig_nonsym(m, M, lam, &Y, m)) return out;
     for (int j = 0; j < m; ++j) {
       std::vector<double> y(m);
@@ -207,30 +240,22 @@ class Solver {
     return out;
   }
 
-  // the self-consistent Ritz pair of the projected first-order model chosen by pick
-  Pair model_pair(const Basis& B, double w,
+  // the model pair chosen by pick among the self-consistent pairs of the pencil
+  Pair model_pair(const Basis& B,
                   const std::function<int(const std::vector<std::complex<double>>&,
                                           const std::vector<std::vector<std::complex<double>>>&)>& pick) {
     Pair p;
     const int m = B.m();
+    const std::vector<double> M = pencil(B);
+    if (M.empty()) return p;
     std::vector<std::complex<double>> lam;
     std::vector<std::vector<std::complex<double>>> Y;
-    int j = -1;
-    for (int it = 0; it < 100; ++it) {
-      std::vector<double> M(size_t(m) * m);
-      for (int a = 0; a < m; ++a)
-        for (int b = 0; b < m; ++b)
-          M[size_t(a) * m + b] = B.G0[size_t(a) * m + b] + B.G1[size_t(a) * m + b] * (w - B.w[b]);
-      if (!eig_nonsym(m, M, lam, &Y, m)) return p;
-      j = pick(lam, Y);
-      if (j < 0) return p;
-      const double lj = lam[j].real();
-      if (!std::isfinite(lj)) return p;
-      const bool done = std::fabs(lj - w) < 1e-14 * std::max(1.0, std::fabs(w));
-      w = lj;
-      if (done) break;
-    }
-    if (!(w < o_.omega_max)) return p;
+    if (!eig_nonsym(m, M, lam, &Y, m)) return p;
+    const int j = pick(lam, Y);
+    if (j < 0) return p;
+    const double w = lam[j].real();
+    if (!std::isfinite(w) || !(w < o_.omega_max)) return p;
+    p.imag = lam[j].imag();
     // Ritz pair (the basis is orthonormal, so |x| = |y|)
     p.y.resize(m);
     double ny = 0.0;
@@ -284,7 +309,7 @@ Result Solver<Space>::run(std::vector<Vec>* vectors) {
     std::vector<Pair> P(nr);
     double worst = 0.0;
     for (int k = 0; k < nr; ++k) {
-      P[k] = model_pair(B, om[k], [k](const std::vector<std::complex<double>>& lam,
+      P[k] = model_pair(B, [k](const std::vector<std::complex<double>>& lam,
                                       const std::vector<std::vector<std::complex<double>>>&) {
         return k < int(lam.size()) ? k : -1;   // eigenvalues come sorted by real part
       });
@@ -306,7 +331,7 @@ Result Solver<Space>::run(std::vector<Vec>* vectors) {
       // in all); every vector was applied at omega_0, so the combinations are exact
       std::vector<std::vector<double>> C;
       for (int k = 0; k < nr; ++k) C.push_back(P[k].y);
-      std::vector<std::vector<double>> extra = model_vectors(B, om[nr - 1], nullptr);
+      std::vector<std::vector<double>> extra = model_vectors(B, nullptr);
       for (int j = nr; j < int(extra.size()) && int(C.size()) < 2 * nr; ++j) C.push_back(extra[j]);
       B = combine(B, C, w0);
       continue;
@@ -330,7 +355,7 @@ Result Solver<Space>::run(std::vector<Vec>* vectors) {
   // stage 2: one root at a time
   res.omega.assign(nr, 0.0);
   res.residual.assign(nr, 0.0);
-  if (vectors) vectors->clear();
+  std::vector<Vec> xs;   // the roots' folded Ritz vectors
   bool all = true;
   for (int k = 0; k < nr; ++k) {
     double w = om[k];
@@ -344,12 +369,13 @@ Result Solver<Space>::run(std::vector<Vec>* vectors) {
       yprev.assign(1, 1.0);
     };
     restart(X[k], w);
-    bool done = false;
+    bool done = false, cplx = false;
+    int n_complex = 0;   // consecutive iterations whose chosen model eigenvalue is complex
     Pair p;
     for (int it = 0; it < o_.max_iter; ++it) {
       ++res.iterations;
       const std::vector<double> prev = yprev;
-      p = model_pair(R, w, [&prev](const std::vector<std::complex<double>>& lam,
+      p = model_pair(R, [&prev](const std::vector<std::complex<double>>& lam,
                                    const std::vector<std::vector<std::complex<double>>>& Y) {
         // homing: the Ritz vector with the largest overlap with the previous one
         int best = -1;
@@ -370,10 +396,23 @@ Result Solver<Space>::run(std::vector<Vec>* vectors) {
       });
       if (!p.ok) break;
       w = p.omega;
+      // a complex pair of the Jacobian: its real part is a fixed point of the model but no
+      // real eigenvector exists there, so the residual cannot fall below |Im|
+      n_complex = std::fabs(p.imag) > std::max(o_.res_tol, 1e-6 * std::fabs(w)) ? n_complex + 1 : 0;
+      if (n_complex >= 3) {
+        cplx = true;
+        break;
+      }
       if (p.rnorm < std::max(o_.res_tol, o_.refresh_tol)) {
         double dw = 0.0;
         for (int b = 0; b < R.m(); ++b) dw = std::max(dw, std::fabs(w - R.w[b]) + R.d[b]);
-        if (dw >= o_.exact_dw) {
+        // the first-order model errs by about (omega - w_b)^2 |d2A/domega2|; refer the subspace
+        // to omega only when that could matter at the present residual (|omega - w_b| above
+        // 0.1 sqrt(|r|)), and exactly (within exact_dw) before accepting convergence, so the
+        // subspace is not rebuilt at every small move of omega
+        const double allow = p.rnorm < o_.res_tol ? o_.exact_dw
+                                                  : std::max(o_.exact_dw, 0.1 * std::sqrt(p.rnorm));
+        if (dw >= allow) {
           // omega is now known to about the square of the residual: refer the subspace to
           // it exactly, so that the rest of the convergence uses an exact model. Vectors
           // applied within exact_dw of omega stay; the rest of the Ritz vector is applied
@@ -406,7 +445,7 @@ Result Solver<Space>::run(std::vector<Vec>* vectors) {
         // thick restart: the Ritz vector and the three model eigenvectors whose values lie
         // nearest omega, referred to omega by the first-order model (no applications)
         std::vector<double> re;
-        std::vector<std::vector<double>> ev = model_vectors(R, w, &re);
+        std::vector<std::vector<double>> ev = model_vectors(R, &re);
         std::vector<int> idx(ev.size());
         for (size_t j = 0; j < idx.size(); ++j) idx[j] = int(j);
         std::stable_sort(idx.begin(), idx.end(),
@@ -433,11 +472,31 @@ Result Solver<Space>::run(std::vector<Vec>* vectors) {
     }
     res.omega[k] = w;
     res.residual[k] = p.ok ? p.rnorm : INFINITY;
-    if (vectors) vectors->push_back(p.ok ? p.x : sp_.make());
-    if (!done) {
+    xs.push_back(p.ok ? p.x : sp_.make());
+    if (cplx) {
+      all = false;
+      res.complex_pair = true;
+      if (!res.failure) res.failure = "a wanted eigenvalue is complex (a complex pair of the Jacobian)";
+    } else if (!done) {
       all = false;
       if (!res.failure) res.failure = p.ok ? "stage 2 did not converge" : "stage 2: no admissible Ritz pair";
     }
+  }
+  // two roots that settled on the same eigenpair (equal omega, parallel vectors) would
+  // hide a root: refuse them
+  if (all) {
+    for (int a = 0; a < nr && all; ++a)
+      for (int b = a + 1; b < nr && all; ++b) {
+        if (std::fabs(res.omega[a] - res.omega[b]) > 1e-6 * std::max(1.0, std::fabs(res.omega[a]))) continue;
+        const Vec& xa = xs[a];
+        const Vec& xb = xs[b];
+        const double na = sp_.dot(xa, xa), nb = sp_.dot(xb, xb);
+        const double c = na > 0.0 && nb > 0.0 ? std::fabs(sp_.dot(xa, xb)) / std::sqrt(na * nb) : 1.0;
+        if (c > 0.99) {
+          all = false;
+          res.failure = "two roots settled on the same eigenpair";
+        }
+      }
   }
   // ascending order (vectors alongside)
   std::vector<int> idx(nr);
@@ -451,9 +510,8 @@ Result Solver<Space>::run(std::vector<Vec>* vectors) {
   res.omega.swap(so);
   res.residual.swap(sr);
   if (vectors) {
-    std::vector<Vec> sv;
-    for (int k = 0; k < nr; ++k) sv.push_back((*vectors)[idx[k]]);
-    vectors->swap(sv);
+    vectors->clear();
+    for (int k = 0; k < nr; ++k) vectors->push_back(std::move(xs[idx[k]]));
   }
   res.n_apply = n_apply_;
   res.converged = all;

@@ -8,8 +8,6 @@
 // device, which a caller interleaving its own work on other streams may not accept.
 #include "internal.cuh"
 
-#include <mutex>
-
 namespace mlcc {
 
 namespace {
@@ -17,21 +15,13 @@ constexpr int kMaxChol = MLCC_NOALLOC_MAX_CHOL;
 // [0, kMaxChol): D_J = sum_I L^J_II;  [kMaxChol, 2 kMaxChol): the same for Lt^J
 static __device__ __align__(256) double g_noalloc_scratch[2 * kMaxChol];
 
-// per-device address of the scratch array, looked up once with that device current
-std::mutex g_mu;
-double* g_addr[64] = {nullptr};
-
+// Address of the scratch array on the current device. It is looked up on every call (a
+// cheap query) rather than cached, so it stays valid after the caller resets the device
+// or makes another context current.
 double* scratch_for_current_device() {
-  int dev = 0;
-  MLCC_CUDA(cudaGetDevice(&dev));
-  MLCC_REQUIRE(dev >= 0 && dev < 64, "mlcc_fock_t1_noalloc: device index out of range");
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    MLCC_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_addr[dev] = static_cast<double*>(p);
-  }
-  return g_addr[dev];
+  void* p = nullptr;
+  MLCC_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+  return static_cast<double*>(p);
 }
 
 inline int blocks_for(int64_t n) {

@@ -863,7 +863,7 @@ void check_tc_error(mlcc_system* S) {
   MLCC_CUDA(cudaStreamSynchronize(S->ctx->stream));
   if (h != 0) {
     MLCC_CUDA(cudaMemsetAsync(S->tc_err, 0, 4, S->ctx->stream));
-    throw Error(MLCC_E_CUDA, "tensor-core GEMM: a pipeline wait timed out (code " + std::to_string(h) + ")");
+    throw Error(MLCC_E_TIMEOUT, "tensor-core GEMM: a pipeline wait timed out (code " + std::to_string(h) + ")");
   }
 }
 

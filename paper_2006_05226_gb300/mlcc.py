@@ -16,12 +16,24 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmlcc.so")
 
+# enum values of include/mlcc.h (tests/test_library.py checks them against the header)
 MLCC_FP64, MLCC_BF16, MLCC_BF16X3, MLCC_BF16X6, MLCC_FP64E = 0, 1, 2, 3, 4
-STATUS = {0: "MLCC_OK", -1: "MLCC_E_ARG", -2: "MLCC_E_OOM", -3: "MLCC_E_GS_NOCONV",
-          -4: "MLCC_E_ES_NOCONV", -5: "MLCC_E_COMPLEX_ROOT", -6: "MLCC_E_NAN",
-          -8: "MLCC_E_CUDA", -9: "MLCC_E_STATE", -10: "MLCC_E_REJECTED", -11: "MLCC_E_CANCELLED",
-          1: "MLCC_PENDING"}
-MLCC_PENDING, MLCC_E_REJECTED, MLCC_E_CANCELLED = 1, -10, -11
+MLCC_LEVEL_CCS, MLCC_LEVEL_CC2, MLCC_LEVEL_CCSD = 0, 1, 2
+MLCC_OK = 0
+MLCC_E_ARG = -1
+MLCC_E_OOM = -2
+MLCC_E_GS_NOCONV = -3
+MLCC_E_ES_NOCONV = -4
+MLCC_E_COMPLEX_ROOT = -5
+MLCC_E_NAN = -6
+MLCC_E_TIMEOUT = -7
+MLCC_E_CUDA = -8
+MLCC_E_STATE = -9
+MLCC_E_REJECTED = -10
+MLCC_E_CANCELLED = -11
+MLCC_PENDING = 1
+STATUS = {v: k for k, v in dict(globals()).items()
+          if k.startswith("MLCC_") and (k.startswith("MLCC_E_") or k in ("MLCC_OK", "MLCC_PENDING"))}
 
 # every symbol include/mlcc.h declares
 EXPORTS = ["mlcc_default_options", "mlcc_ctx_create", "mlcc_ctx_destroy", "mlcc_ctx_stream",

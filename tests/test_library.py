@@ -122,3 +122,38 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in text.replace("oracle-", ""), f
+
+
+def _header_enums():
+    """name -> value of every enumerator in include/mlcc.h (the enums use explicit or
+    implicit consecutive values)."""
+    src = open(os.path.join(ROOT, "include", "mlcc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for body in re.findall(r"typedef\s+enum\s*\{(.*?)\}", src, flags=re.S):
+        nxt = 0
+        for item in body.split(","):
+            item = item.strip()
+            if not item:
+                continue
+            if "=" in item:
+                name, val = (x.strip() for x in item.split("="))
+                nxt = int(val, 0)
+            else:
+                name = item
+            out[name] = nxt
+            nxt += 1
+    return out
+
+
+def test_every_header_enum_has_a_binding_constant():
+    from paper_2006_05226_gb300 import mlcc
+    enums = _header_enums()
+    assert "MLCC_E_STATE" in enums and "MLCC_PENDING" in enums and len(enums) >= 20
+    for name, val in enums.items():
+        assert hasattr(mlcc, name), f"binding lacks {name}"
+        assert getattr(mlcc, name) == val, (name, getattr(mlcc, name), val)
+    # the status table names every status code the header declares
+    for name, val in enums.items():
+        if name.startswith("MLCC_E_") or name in ("MLCC_OK", "MLCC_PENDING"):
+            assert mlcc.STATUS[val] == name
