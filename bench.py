@@ -272,7 +272,7 @@ def run_serving(args):
     seq_w = []
     t0 = time.perf_counter()
     for sy, (Lp, Fp) in zip(systems, host):
-        _, w, _, _ = mlcc.solve(ctx, Lp.numpy(), Fp.numpy(), sy.spec.n_occ, sy.level, opts_for(sy.spec, prec))
+        w = mlcc.solve(ctx, Lp.numpy(), Fp.numpy(), sy.spec.n_occ, sy.level, opts_for(sy.spec, prec)).omega
         seq_w.append(w)
     seq_s = time.perf_counter() - t0
     # plain binary64, one at a time, on the first fp64_sample requests (accuracy and speed)
@@ -280,8 +280,8 @@ def run_serving(args):
     for k in range(min(args.fp64_sample, len(systems))):
         sy, (Lp, Fp) = systems[k], host[k]
         t1 = time.perf_counter()
-        _, w64, _, _ = mlcc.solve(ctx, Lp.numpy(), Fp.numpy(), sy.spec.n_occ, sy.level,
-                                  opts_for(sy.spec, mlcc.MLCC_FP64))
+        w64 = mlcc.solve(ctx, Lp.numpy(), Fp.numpy(), sy.spec.n_occ, sy.level,
+                         opts_for(sy.spec, mlcc.MLCC_FP64)).omega
         fp64_s.append(time.perf_counter() - t1)
         errs.append(float(np.max(np.abs(np.asarray(seq_w[k]) - w64))))
     ctx.close()
@@ -550,7 +550,8 @@ def main():
             host_mem = "pageable"
         barrier(world)
         t0 = time.perf_counter()
-        gi, w2, ei, t1h = mlcc.solve(ctx, Lh, Fh, spec.n_occ, system.level, opts)
+        sol = mlcc.solve(ctx, Lh, Fh, spec.n_occ, system.level, opts, t1=True)
+        ei, w2, t1h = sol.es, sol.omega, sol.t1
         dt = time.perf_counter() - t0
         dt = allreduce_max(dt, world)
         e_val = allreduce_sum(float(ei.n_sigma), world) / dt

@@ -30,8 +30,12 @@
  *    equation built from P_T amplitudes only; every other CC2-active doubles element
  *    obeys the CC2 equation g~ + eps x = 0 (Appendix A, Eq. mlcc2_omega2); singles and
  *    energy use all doubles. No CCSD level gives MLCC2, CCSD = CC2 gives CCS/CCSD.
- *  - F must be diagonal inside the occupied-occupied and virtual-virtual blocks of the
- *    CC2-active orbitals (semicanonical basis, Sec. 2.1); otherwise MLCC_E_ARG.
+ *  - Semicanonical basis (Sec. 2.1-2.2): inside each level's occupied-occupied and
+ *    virtual-virtual block the system diagonalises F and rotates the Cholesky vectors
+ *    with it (an orbital rotation inside a level leaves the model unchanged). Couplings
+ *    of F between levels are kept and enter through F~. With F already diagonal inside
+ *    every level block nothing is rotated. Amplitudes and vectors refer to the system's
+ *    orbitals: mlcc_orbital_order / mlcc_orbitals give them in terms of the caller's.
  *
  * Memory and errors
  * -----------------
@@ -163,8 +167,14 @@ typedef struct {
    gs_energy_tol 1e-12, es_res_tol 1e-8, es_omega_tol 1e-11, lowp_res_tol 1e-4,
    refine_precision FP64. */
 void mlcc_default_options(mlcc_options* opt);
-/* Creates a context on CUDA device `device` with its own non-blocking stream. */
+/* Creates a context on CUDA device `device` with its own non-blocking stream and no
+   device-memory budget of its own (a solve may use what the device has). */
 mlcc_status mlcc_ctx_create(int device, mlcc_ctx** out);
+/* As mlcc_ctx_create, with a device-memory budget: the systems of this context together
+   (their workspace, mlcc_system_info) and each whole solve (mlcc_solve_footprint) may hold
+   at most hbm_budget_bytes; a system or solve that would exceed it returns MLCC_E_OOM
+   before allocating. hbm_budget_bytes <= 0: no budget. */
+mlcc_status mlcc_ctx_create_budget(int device, int64_t hbm_budget_bytes, mlcc_ctx** out);
 void mlcc_ctx_destroy(mlcc_ctx* ctx);
 /* The cudaStream_t (as void*) that every entry point of this context launches on. */
 void* mlcc_ctx_stream(mlcc_ctx* ctx);
@@ -210,8 +220,13 @@ mlcc_status mlcc_system_create(mlcc_ctx* ctx, const mlcc_problem* prob,
                                mlcc_system** out);
 void mlcc_system_destroy(mlcc_system* sys);
 mlcc_status mlcc_system_info(const mlcc_system* sys, mlcc_dims* dims);
-/* perm_host[k] = caller index of internal orbital k, k < n_mo. */
+/* perm_host[k] = caller index of internal orbital k, k < n_mo (before the semicanonical
+   rotation inside each level). */
 mlcc_status mlcc_orbital_order(const mlcc_system* sys, int32_t* perm_host);
+/* The system's orbitals in the caller's: orbital k of the system is
+   sum_p c_host[p * n_mo + k] (caller orbital p), [n_mo][n_mo]. A permutation matrix (from
+   mlcc_orbital_order) when no level block needed the semicanonical rotation. */
+mlcc_status mlcc_orbitals(const mlcc_system* sys, double* c_host);
 
 /* ---- steps of the hot path (device buffers, internal order, no host sync) ------- */
 /* T1-dressing (Sec. 2.1 "Cholesky vectors in the X1 basis", Appendix A):
@@ -285,21 +300,39 @@ mlcc_status mlcc_excited_states_folded(mlcc_system* sys, const mlcc_options* opt
 mlcc_status mlcc_excited_states(mlcc_system* sys, const mlcc_options* opt,
                                 double* omega_host, double* r_dev, mlcc_es_info* info);
 
-/* ---- whole solve from host memory ------------------------------------------------ */
-/* Copies chol_host / fock_host to the device, runs ground state and excited states and
-   returns energies (host). t1_host [n_vir][n_occ] may be NULL. */
+/* ---- whole solve ------------------------------------------------------------------- */
+/* What a whole solve returns (Sec. 2.1: the converged ground state, the energy and the lowest
+   eigenpairs of the Jacobian). gs and es are filled by the call. The arrays are the
+   caller's, NULL where not wanted; omega is required. For mlcc_solve every array is host
+   memory; for mlcc_solve_device t1, x2 and r are device memory on the context's device and
+   the others host memory. Amplitudes and vectors are in the system's orbital order and
+   basis (see Conventions); perm and orbitals relate it to the caller's. */
+typedef struct {
+  mlcc_gs_info gs;
+  mlcc_es_info es;
+  double* omega;      /* [n_roots] excitation energies, Hartree, ascending                  */
+  double* residual;   /* [n_roots] |A R_k - w_k R_k|_2 at the last evaluation, in its
+                         precision (binary64-class after a refinement sweep)               */
+  double* t1;         /* [n_vir][n_occ] converged singles amplitudes                      */
+  double* x2;         /* [n_doubles] converged doubles on the CC2-active pairs, the layout
+                         under Conventions (the analytic CC2 doubles outside the CCSD block) */
+  double* r;          /* [n_roots][vector_len] right eigenvectors, unit 2-norm, largest-
+                         magnitude element positive                                        */
+  int32_t* perm;      /* [n_mo] as mlcc_orbital_order                                      */
+  double* orbitals;   /* [n_mo][n_mo] as mlcc_orbitals                                     */
+} mlcc_result;
+
+/* Copies chol_host / fock_host to the device, builds the system, runs the ground state and
+   the excited states, fills *res and frees everything it allocated. On MLCC_E_GS_NOCONV
+   or MLCC_E_ES_NOCONV (and MLCC_E_COMPLEX_ROOT) the outputs hold the last iterate. */
 mlcc_status mlcc_solve(mlcc_ctx* ctx, const mlcc_problem* prob, const double* chol_host,
-                       const double* fock_host, const mlcc_options* opt,
-                       mlcc_gs_info* gs, double* omega_host, mlcc_es_info* es,
-                       double* t1_host);
+                       const double* fock_host, const mlcc_options* opt, mlcc_result* res);
 
 /* As mlcc_solve, with chol_dev / fock_dev on the context's device (borrowed for the call;
    the caller keeps ownership). The system copies them, so they may be reused after the
    call returns. */
 mlcc_status mlcc_solve_device(mlcc_ctx* ctx, const mlcc_problem* prob, const double* chol_dev,
-                              const double* fock_dev, const mlcc_options* opt,
-                              mlcc_gs_info* gs, double* omega_host, mlcc_es_info* es,
-                              double* t1_host);
+                              const double* fock_dev, const mlcc_options* opt, mlcc_result* res);
 
 /* Length of a Davidson vector of the problem, n_vir n_occ + (s_vir s_occ)^2 (the layout
    under "Conventions"), from the sizes and levels alone; -1 if they are invalid. */

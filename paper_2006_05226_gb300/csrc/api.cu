@@ -2,6 +2,7 @@
 // (orbital re-ordering, recovery of the one-electron matrix of Sec. 2.3) and the
 // exception-to-status boundary.
 #include "system.cuh"
+#include "small_eig.h"
 
 #include <algorithm>
 #include <cmath>
@@ -15,7 +16,22 @@ int64_t launch_count();
 mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out, double* x2_out,
                          mlcc_gs_info* info);
 mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omega_host,
-                           double* r_out, mlcc_es_info* info);
+                           double* r_out, mlcc_es_info* info, double* residual_host = nullptr);
+
+// the Davidson solve behind mlcc_excited_states and mlcc_solve, with their argument checks
+static mlcc_status excited_states_checked(mlcc_system* S, const mlcc_options* opt, double* omega, double* r,
+                                          mlcc_es_info* info, double* residual) {
+  MLCC_REQUIRE(S && opt && omega, "mlcc_excited_states: NULL argument");
+  MLCC_REQUIRE(opt->precision >= MLCC_FP64 && opt->precision <= MLCC_FP64E,
+               "mlcc_excited_states: unknown precision");
+  MLCC_REQUIRE(opt->refine_precision == MLCC_FP64 || opt->refine_precision == MLCC_FP64E,
+               "mlcc_excited_states: refine_precision must be MLCC_FP64 or MLCC_FP64E");
+  MLCC_CUDA(cudaSetDevice(S->ctx->device));
+  const mlcc_status st = excited_states(S, opt, omega, r, info, residual);
+  if (st == MLCC_E_ES_NOCONV) set_last_error("excited states did not converge");
+  if (st == MLCC_E_COMPLEX_ROOT) set_last_error("a wanted Ritz value is complex");
+  return st;
+}
 
 namespace {
 __global__ void k_reorder(const double* src, const int* perm, int n, int64_t batch, double* dst) {
@@ -75,6 +91,14 @@ static void setup_system(mlcc_system* S, const mlcc_problem* P, const double* ch
   const int64_t nn = int64_t(n) * n, dS = S->dS;
   // persistent buffers
   const sizes::Dims dims = sys_dims(S);
+  {
+    const int64_t need = int64_t(sizes::persist_bytes(dims) + sizes::ws_bytes(dims));
+    mlcc_ctx* c = S->ctx;
+    if (c->budget > 0 && c->held.load() + need > c->budget)
+      throw Error(MLCC_E_OOM, "mlcc_system_create: the system needs " + std::to_string(need) +
+                                  " bytes; the context's budget leaves " +
+                                  std::to_string(c->budget - c->held.load()));
+  }
   S->persist.reserve(sizes::persist_bytes(dims));
   S->L = S->persist.get<double>(size_t(nj) * nn);
   S->Lt = S->persist.get<double>(size_t(nj) * nn);
@@ -109,7 +133,7 @@ static void setup_system(mlcc_system* S, const mlcc_problem* P, const double* ch
     k_reorder<<<int(std::min<int64_t>((nn + 255) / 256, 16384)), 256, 0, s>>>(fock, dperm, n, 1, S->ht);
     MLCC_CHECK_LAUNCH();
   }
-  // checks: symmetric L and F, semicanonical CC2-active blocks
+  // checks: symmetric L and F
   unsigned long long* asym = S->ws.get<unsigned long long>(1);
   MLCC_CUDA(cudaMemsetAsync(asym, 0, 8, s));
   k_asym<<<1024, 256, 0, s>>>(S->L, n, nj, asym);
@@ -130,16 +154,84 @@ static void setup_system(mlcc_system* S, const mlcc_problem* P, const double* ch
       if (!std::isfinite(a)) throw Error(MLCC_E_NAN, "Fock matrix has NaN or Inf");
       if (std::fabs(a - b) > 1e-10 * std::max(1.0, fmax)) throw Error(MLCC_E_ARG, "Fock matrix is not symmetric");
     }
-  auto check_block = [&](int lo, int hi) {
-    for (int p = lo; p < hi; ++p)
-      for (int q = lo; q < hi; ++q)
-        if (p != q && std::fabs(Fh[size_t(p) * n + q]) > 1e-10 * std::max(1.0, fmax))
-          throw Error(MLCC_E_ARG, "Fock matrix is not diagonal in the CC2-active occupied-occupied or "
-                                  "virtual-virtual block (semicanonical basis required, Sec. 2.1)");
-  };
-  if (S->nd > 0 && S->nd != int64_t(S->tv) * S->to * S->tv * S->to) {
-    check_block(0, S->so);
-    check_block(no, no + S->sv);
+  // Semicanonical basis (Sec. 2.1-2.2): the CC2 doubles equations use only the orbital
+  // energies, so the Fock matrix must be diagonal inside each level's occupied and virtual
+  // blocks. Blocks that are not are diagonalised here, and the Cholesky vectors and F are
+  // rotated with them (an orbital rotation inside a level leaves the model unchanged);
+  // couplings between levels stay and enter through F~.
+  {
+    const int bounds[7] = {0, S->to, S->so, no, no + S->tv, no + S->sv, n};
+    std::vector<double> U;
+    for (int b = 0; b < 6; ++b) {
+      const int lo = bounds[b], hi = bounds[b + 1], m = hi - lo;
+      if (m < 2) continue;
+      double off = 0.0;
+      for (int p = lo; p < hi; ++p)
+        for (int q = lo; q < hi; ++q)
+          if (p != q) off = std::max(off, std::fabs(Fh[size_t(p) * n + q]));
+      if (off <= 1e-12 * std::max(1.0, fmax)) continue;
+      std::vector<double> blk(size_t(m) * m), wb, Vb;
+      for (int p = 0; p < m; ++p)
+        for (int q = 0; q < m; ++q) blk[size_t(p) * m + q] = 0.5 * (Fh[size_t(lo + p) * n + lo + q] + Fh[size_t(lo + q) * n + lo + p]);
+      if (!eig_sym(m, blk, wb, Vb)) throw Error(MLCC_E_ARG, "semicanonicalisation: eigensolver failed");
+      for (int k = 0; k < m; ++k) {   // sign: largest-magnitude component positive
+        int big = 0;
+        for (int p = 1; p < m; ++p)
+          if (std::fabs(Vb[size_t(p) * m + k]) > std::fabs(Vb[size_t(big) * m + k])) big = p;
+        if (Vb[size_t(big) * m + k] < 0.0)
+          for (int p = 0; p < m; ++p) Vb[size_t(p) * m + k] = -Vb[size_t(p) * m + k];
+      }
+      if (U.empty()) {
+        U.assign(size_t(nn), 0.0);
+        for (int p = 0; p < n; ++p) U[size_t(p) * n + p] = 1.0;
+      }
+      for (int p = 0; p < m; ++p)
+        for (int q = 0; q < m; ++q) U[size_t(lo + p) * n + lo + q] = Vb[size_t(p) * m + q];
+    }
+    if (!U.empty()) {
+      // F <- U^T F U on the host; L^J <- U^T L^J U on the device (binary64), through Lt
+      std::vector<double> T(size_t(nn), 0.0), F2(size_t(nn), 0.0);
+      for (int p = 0; p < n; ++p)
+        for (int r = 0; r < n; ++r) {
+          const double f = Fh[size_t(p) * n + r];
+          if (f == 0.0) continue;
+          for (int q = 0; q < n; ++q) T[size_t(p) * n + q] += f * U[size_t(r) * n + q];
+        }
+      for (int r = 0; r < n; ++r)
+        for (int p = 0; p < n; ++p) {
+          const double u = U[size_t(r) * n + p];
+          if (u == 0.0) continue;
+          for (int q = 0; q < n; ++q) F2[size_t(p) * n + q] += u * T[size_t(r) * n + q];
+        }
+      for (int p = 0; p < n; ++p)   // exact zeros inside the rotated blocks, symmetric
+        for (int q = 0; q < p; ++q) F2[size_t(p) * n + q] = F2[size_t(q) * n + p] = 0.5 * (F2[size_t(p) * n + q] + F2[size_t(q) * n + p]);
+      for (int b = 0; b < 6; ++b)
+        for (int p = bounds[b]; p < bounds[b + 1]; ++p)
+          for (int q = bounds[b]; q < bounds[b + 1]; ++q)
+            if (p != q) F2[size_t(p) * n + q] = 0.0;
+      Fh.swap(F2);
+      Scope sc(S->ws);
+      double* dU = S->ws.get<double>(size_t(nn));
+      copy_h2d(dU, U.data(), nn, s);
+      copy_h2d(S->ht, Fh.data(), nn, s);
+      Gemm g1;   // Lt[J] = L[J] U
+      g1.M = g1.N = g1.K = n;
+      g1.A = S->L; g1.lda = n; g1.sA = nn;
+      g1.B = dU; g1.ldb = n; g1.sB = 0;
+      g1.C = S->Lt; g1.ldc = n; g1.sC = nn;
+      g1.batch = nj;
+      gemm_f64(g1, S->ws, s, S->ctx->sm_count);
+      Gemm g2;   // L[J] = U^T Lt[J]
+      g2.ta = true;
+      g2.M = g2.N = g2.K = n;
+      g2.A = dU; g2.lda = n; g2.sA = 0;
+      g2.B = S->Lt; g2.ldb = n; g2.sB = nn;
+      g2.C = S->L; g2.ldc = n; g2.sC = nn;
+      g2.batch = nj;
+      gemm_f64(g2, S->ws, s, S->ctx->sm_count);
+      MLCC_CUDA(cudaStreamSynchronize(s));
+      S->rot.swap(U);
+    }
   }
   S->eps_host.resize(n);
   for (int p = 0; p < n; ++p) S->eps_host[p] = Fh[size_t(p) * n + p];
@@ -168,8 +260,7 @@ using namespace mlcc;
 // once the system holds its own copies
 static mlcc_status solve_from_device(mlcc_ctx* ctx, const mlcc_problem* prob, const double* dL,
                                      const double* dF, std::function<void()> inputs_done,
-                                     const mlcc_options* opt, mlcc_gs_info* gs, double* omega,
-                                     mlcc_es_info* es, double* t1_host);
+                                     const mlcc_options* opt, mlcc_result* res, bool host_out);
 
 extern "C" {
 
@@ -194,7 +285,9 @@ void mlcc_default_options(mlcc_options* o) {
 
 const char* mlcc_last_error(void) { return last_error_cstr(); }
 
-mlcc_status mlcc_ctx_create(int device, mlcc_ctx** out) {
+mlcc_status mlcc_ctx_create(int device, mlcc_ctx** out) { return mlcc_ctx_create_budget(device, 0, out); }
+
+mlcc_status mlcc_ctx_create_budget(int device, int64_t hbm_budget_bytes, mlcc_ctx** out) {
   return guard([&] {
     MLCC_REQUIRE(out != nullptr, "mlcc_ctx_create: out is NULL");
     *out = nullptr;
@@ -204,6 +297,7 @@ mlcc_status mlcc_ctx_create(int device, mlcc_ctx** out) {
     MLCC_CUDA(cudaSetDevice(device));
     auto* c = new mlcc_ctx();
     c->device = device;
+    c->budget = std::max<int64_t>(hbm_budget_bytes, 0);
     MLCC_CUDA(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device));
     MLCC_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
     *out = c;
@@ -274,6 +368,7 @@ mlcc_status mlcc_system_create(mlcc_ctx* ctx, const mlcc_problem* prob, const do
       delete S;
       throw;
     }
+    ctx->held += S->workspace_bytes;
     *out = S;
     return MLCC_OK;
   });
@@ -281,6 +376,7 @@ mlcc_status mlcc_system_create(mlcc_ctx* ctx, const mlcc_problem* prob, const do
 
 void mlcc_system_destroy(mlcc_system* sys) {
   if (!sys) return;
+  sys->ctx->held -= sys->workspace_bytes;
   cudaSetDevice(sys->ctx->device);
   cudaStreamSynchronize(sys->ctx->stream);
   ccsd_cache_free(sys);
@@ -309,6 +405,21 @@ mlcc_status mlcc_orbital_order(const mlcc_system* S, int32_t* perm) {
   return guard([&] {
     MLCC_REQUIRE(S && perm, "mlcc_orbital_order: NULL argument");
     std::copy(S->perm.begin(), S->perm.end(), perm);
+    return MLCC_OK;
+  });
+}
+
+mlcc_status mlcc_orbitals(const mlcc_system* S, double* c) {
+  return guard([&] {
+    MLCC_REQUIRE(S && c, "mlcc_orbitals: NULL argument");
+    const int n = S->n;
+    std::fill(c, c + size_t(n) * n, 0.0);
+    // system orbital k = sum_k' rot[k'][k] (re-ordered orbital k'), re-ordered k' = caller perm[k']
+    for (int kp = 0; kp < n; ++kp)
+      for (int k = 0; k < n; ++k) {
+        const double u = S->rot.empty() ? (kp == k ? 1.0 : 0.0) : S->rot[size_t(kp) * n + k];
+        if (u != 0.0) c[size_t(S->perm[kp]) * n + k] = u;
+      }
     return MLCC_OK;
   });
 }
@@ -445,18 +556,7 @@ mlcc_status mlcc_excited_states_folded(mlcc_system* S, const mlcc_options* opt, 
 
 mlcc_status mlcc_excited_states(mlcc_system* S, const mlcc_options* opt, double* omega,
                                 double* r, mlcc_es_info* info) {
-  return guard([&] {
-    MLCC_REQUIRE(S && opt && omega, "mlcc_excited_states: NULL argument");
-    MLCC_REQUIRE(opt->precision >= MLCC_FP64 && opt->precision <= MLCC_FP64E,
-                 "mlcc_excited_states: unknown precision");
-    MLCC_REQUIRE(opt->refine_precision == MLCC_FP64 || opt->refine_precision == MLCC_FP64E,
-                 "mlcc_excited_states: refine_precision must be MLCC_FP64 or MLCC_FP64E");
-    MLCC_CUDA(cudaSetDevice(S->ctx->device));
-    mlcc_status st = excited_states(S, opt, omega, r, info);
-    if (st == MLCC_E_ES_NOCONV) set_last_error("excited states did not converge");
-    if (st == MLCC_E_COMPLEX_ROOT) set_last_error("a wanted Ritz value is complex");
-    return st;
-  });
+  return guard([&] { return excited_states_checked(S, opt, omega, r, info, nullptr); });
 }
 
 mlcc_status mlcc_gemm(mlcc_ctx* ctx, int32_t trans_a, int32_t trans_b, int64_t M, int64_t N, int64_t K,
@@ -506,13 +606,24 @@ mlcc_status mlcc_gemm(mlcc_ctx* ctx, int32_t trans_a, int32_t trans_b, int64_t M
   });
 }
 
+// a whole solve must fit the context's budget next to the systems it already holds
+static void check_solve_budget(mlcc_ctx* ctx, const mlcc_problem* prob, const mlcc_options* opt) {
+  if (ctx->budget <= 0) return;
+  int64_t fp = 0;
+  const mlcc_status st = mlcc_solve_footprint(prob, opt, &fp);
+  if (st != MLCC_OK) throw Error(st, mlcc_last_error());
+  if (ctx->held.load() + fp > ctx->budget)
+    throw Error(MLCC_E_OOM, "mlcc_solve: the solve holds up to " + std::to_string(fp) +
+                                " bytes; the context's budget leaves " + std::to_string(ctx->budget - ctx->held.load()));
+}
+
 mlcc_status mlcc_solve(mlcc_ctx* ctx, const mlcc_problem* prob, const double* chol_host,
-                       const double* fock_host, const mlcc_options* opt, mlcc_gs_info* gs,
-                       double* omega, mlcc_es_info* es, double* t1_host) {
+                       const double* fock_host, const mlcc_options* opt, mlcc_result* res) {
   return guard([&] {
-    MLCC_REQUIRE(ctx && prob && chol_host && fock_host && opt && omega, "mlcc_solve: NULL argument");
+    MLCC_REQUIRE(ctx && prob && chol_host && fock_host && opt && res && res->omega, "mlcc_solve: NULL argument");
     MLCC_REQUIRE(prob->n_mo > 0 && prob->n_chol > 0, "mlcc_solve: sizes must be positive");
     MLCC_CUDA(cudaSetDevice(ctx->device));
+    check_solve_budget(ctx, prob, opt);
     const int64_t nn = int64_t(prob->n_mo) * prob->n_mo;
     double *dL = nullptr, *dF = nullptr;
     struct Free {
@@ -528,17 +639,17 @@ mlcc_status mlcc_solve(mlcc_ctx* ctx, const mlcc_problem* prob, const double* ch
       cudaFree(dL); dL = nullptr;
       cudaFree(dF); dF = nullptr;
     };
-    return solve_from_device(ctx, prob, dL, dF, release, opt, gs, omega, es, t1_host);
+    return solve_from_device(ctx, prob, dL, dF, release, opt, res, true);
   });
 }
 
 mlcc_status mlcc_solve_device(mlcc_ctx* ctx, const mlcc_problem* prob, const double* chol_dev,
-                              const double* fock_dev, const mlcc_options* opt, mlcc_gs_info* gs,
-                              double* omega, mlcc_es_info* es, double* t1_host) {
+                              const double* fock_dev, const mlcc_options* opt, mlcc_result* res) {
   return guard([&] {
-    MLCC_REQUIRE(ctx && prob && chol_dev && fock_dev && opt && omega, "mlcc_solve_device: NULL argument");
+    MLCC_REQUIRE(ctx && prob && chol_dev && fock_dev && opt && res && res->omega, "mlcc_solve_device: NULL argument");
     MLCC_CUDA(cudaSetDevice(ctx->device));
-    return solve_from_device(ctx, prob, chol_dev, fock_dev, nullptr, opt, gs, omega, es, t1_host);
+    check_solve_budget(ctx, prob, opt);
+    return solve_from_device(ctx, prob, chol_dev, fock_dev, nullptr, opt, res, false);
   });
 }
 
@@ -552,26 +663,52 @@ int64_t mlcc_vector_len(const mlcc_problem* prob) {
 
 static mlcc_status solve_from_device(mlcc_ctx* ctx, const mlcc_problem* prob, const double* dL,
                                      const double* dF, std::function<void()> inputs_done,
-                                     const mlcc_options* opt, mlcc_gs_info* gs, double* omega,
-                                     mlcc_es_info* es, double* t1_host) {
+                                     const mlcc_options* opt, mlcc_result* res, bool host_out) {
   mlcc_system* S = nullptr;
   mlcc_status st = mlcc_system_create(ctx, prob, dL, dF, &S);
   if (st != MLCC_OK) return st;
   struct Sys { mlcc_system* s; ~Sys() { mlcc_system_destroy(s); } } sg{S};
   if (inputs_done) inputs_done();
+  if (res->perm) std::copy(S->perm.begin(), S->perm.end(), res->perm);
+  if (res->orbitals) {
+    st = mlcc_orbitals(S, res->orbitals);
+    if (st != MLCC_OK) return st;
+  }
+  const int64_t n1 = int64_t(S->nv) * S->no, dim = n1 + S->nd;
   double *t1 = nullptr, *x2 = nullptr;
-  MLCC_CUDA(cudaMalloc(&t1, size_t(S->nv) * S->no * 8 + 8));
+  MLCC_CUDA(cudaMalloc(&t1, size_t(n1) * 8 + 8));
   struct Free1 { double* a; ~Free1() { cudaFree(a); } } f1{t1};
   MLCC_CUDA(cudaMalloc(&x2, size_t(S->nd) * 8 + 8));
   struct Free2 { double* a; ~Free2() { cudaFree(a); } } f2{x2};
   mlcc_gs_info gi{};
-  st = mlcc_ground_state(S, opt, t1, x2, &gi);
-  if (gs) *gs = gi;
-  if (st != MLCC_OK) return st;
-  if (t1_host) copy_d2h(t1_host, t1, int64_t(S->nv) * S->no, ctx->stream);
+  const mlcc_status gst = mlcc_ground_state(S, opt, t1, x2, &gi);
+  res->gs = gi;
+  auto out = [&](double* dst, const double* src, int64_t count) {
+    if (!dst || count <= 0) return;
+    if (host_out) copy_d2h(dst, src, count, ctx->stream);
+    else MLCC_CUDA(cudaMemcpyAsync(dst, src, size_t(count) * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+  };
+  out(res->t1, t1, n1);
+  out(res->x2, x2, S->nd);
+  if (gst != MLCC_OK) {
+    MLCC_CUDA(cudaStreamSynchronize(ctx->stream));
+    return gst;
+  }
+  // eigenvectors into the caller's device buffer directly, or through a device copy
+  double* rdev = nullptr;
+  struct Free3 { double* a; ~Free3() { if (a) cudaFree(a); } } f3{nullptr};
+  if (res->r) {
+    if (host_out) {
+      MLCC_CUDA(cudaMalloc(&rdev, size_t(opt->n_roots) * dim * 8));
+      f3.a = rdev;
+    } else {
+      rdev = res->r;
+    }
+  }
   mlcc_es_info ei{};
-  st = mlcc_excited_states(S, opt, omega, nullptr, &ei);
-  if (es) *es = ei;
+  st = excited_states_checked(S, opt, res->omega, rdev, &ei, res->residual);
+  res->es = ei;
+  if (res->r && host_out) copy_d2h(res->r, rdev, int64_t(opt->n_roots) * dim, ctx->stream);
+  MLCC_CUDA(cudaStreamSynchronize(ctx->stream));
   return st;
 }
-

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <string>
 #include <vector>
+#include <atomic>
 #include <map>
 #include <stdexcept>
 
@@ -106,6 +107,8 @@ struct mlcc_ctx {
   cudaStream_t stream = nullptr;
   mlcc::KernelTimer timer;
   int sm_count = 0;
+  int64_t budget = 0;                 // device-memory budget of the context (0: none)
+  std::atomic<int64_t> held{0};       // workspace bytes of the context's live systems
 };
 
 namespace mlcc {

@@ -115,8 +115,11 @@ mlcc_status mlcc_server_create(int device, int32_t n_slots, int64_t hbm_budget_b
     mlcc_server* raw = srv.get();
     auto run = [raw](int slot, void* payload) -> int32_t {
       auto* j = static_cast<Job*>(payload);
-      const mlcc_status st = mlcc_solve(raw->ctx[slot], &j->prob, j->chol, j->fock, &j->opt, &j->gs,
-                                        j->omega.data(), &j->es, nullptr);
+      mlcc_result r{};
+      r.omega = j->omega.data();
+      const mlcc_status st = mlcc_solve(raw->ctx[slot], &j->prob, j->chol, j->fock, &j->opt, &r);
+      j->gs = r.gs;
+      j->es = r.es;
       if (st != MLCC_OK) j->error = mlcc_last_error();
       return st;
     };

@@ -5,11 +5,18 @@
 // the complex single-shift QR iteration with Wilkinson shifts and deflation (Golub and
 // Van Loan, Matrix Computations, Sec. 7.4-7.5). Eigenvectors: inverse iteration on the
 // original matrix with a complex LU factorisation with partial pivoting.
+//
+// Symmetric eigenpairs (the orbital rotations that make the Fock matrix diagonal inside
+// each level): Householder tridiagonalisation with the reflections accumulated, then the
+// implicit QL iteration on the tridiagonal matrix with a shift from its leading 2 x 2 block
+// (Golub and Van Loan, Sec. 8.3; Wilkinson and Reinsch's QL variant).
 #include "small_eig.h"
 
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <cstdint>
+#include <limits>
 #include <vector>
 
 namespace mlcc {
@@ -208,6 +215,121 @@ bool eig_nonsym(int n, const std::vector<double>& A, std::vector<cplx>& w,
       vecs->push_back(x);
     }
   }
+  return true;
+}
+
+bool eig_sym(int n, const std::vector<double>& A0, std::vector<double>& w, std::vector<double>& V) {
+  if (n < 1 || int64_t(A0.size()) < int64_t(n) * n) return false;
+  std::vector<double> a(A0.begin(), A0.begin() + size_t(n) * n);
+  V.assign(size_t(n) * n, 0.0);
+  for (int i = 0; i < n; ++i) V[size_t(i) * n + i] = 1.0;
+  // 1. tridiagonalisation: column k below the subdiagonal is annihilated by the reflection
+  //    H = I - beta v v^T acting on rows and columns k+1..n-1
+  std::vector<double> v(n), p(n), q(n);
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;   // length of the reflected part
+    double alpha = 0.0;
+    for (int i = 0; i < m; ++i) alpha += a[size_t(k + 1 + i) * n + k] * a[size_t(k + 1 + i) * n + k];
+    alpha = std::sqrt(alpha);
+    if (alpha == 0.0) continue;
+    const double x0 = a[size_t(k + 1) * n + k];
+    const double sub = x0 >= 0.0 ? -alpha : alpha;   // the new subdiagonal element
+    for (int i = 0; i < m; ++i) v[i] = a[size_t(k + 1 + i) * n + k];
+    v[0] -= sub;
+    double vv = 0.0;
+    for (int i = 0; i < m; ++i) vv += v[i] * v[i];
+    if (vv == 0.0) continue;
+    const double beta = 2.0 / vv;
+    // trailing block B <- H B H = B - v q^T - q v^T with p = beta B v, q = p - (beta/2)(v^T p) v
+    for (int i = 0; i < m; ++i) {
+      double sdot = 0.0;
+      const double* row = &a[size_t(k + 1 + i) * n + (k + 1)];
+      for (int j = 0; j < m; ++j) sdot += row[j] * v[j];
+      p[i] = beta * sdot;
+    }
+    double vp = 0.0;
+    for (int i = 0; i < m; ++i) vp += v[i] * p[i];
+    const double K = 0.5 * beta * vp;
+    for (int i = 0; i < m; ++i) q[i] = p[i] - K * v[i];
+    for (int i = 0; i < m; ++i) {
+      double* row = &a[size_t(k + 1 + i) * n + (k + 1)];
+      for (int j = 0; j < m; ++j) row[j] -= v[i] * q[j] + q[i] * v[j];
+    }
+    a[size_t(k + 1) * n + k] = a[size_t(k) * n + k + 1] = sub;
+    for (int i = 1; i < m; ++i) a[size_t(k + 1 + i) * n + k] = a[size_t(k) * n + k + 1 + i] = 0.0;
+    // accumulate: V <- V H on columns k+1..n-1
+    for (int r = 0; r < n; ++r) {
+      double* row = &V[size_t(r) * n + (k + 1)];
+      double sdot = 0.0;
+      for (int j = 0; j < m; ++j) sdot += row[j] * v[j];
+      sdot *= beta;
+      for (int j = 0; j < m; ++j) row[j] -= sdot * v[j];
+    }
+  }
+  std::vector<double> d(n), e(n, 0.0);
+  for (int i = 0; i < n; ++i) d[i] = a[size_t(i) * n + i];
+  for (int i = 0; i + 1 < n; ++i) e[i] = a[size_t(i + 1) * n + i];   // couples d[i] and d[i+1]
+  // 2. implicit QL: deflate from the top; each sweep chases the bulge from the bottom of
+  //    the unreduced block [l, m] up to l with plane rotations, applied to V's columns
+  const double eps = std::numeric_limits<double>::epsilon();
+  for (int l = 0; l < n; ++l) {
+    int iter = 0;
+    while (true) {
+      int m = l;
+      for (; m + 1 < n; ++m) {
+        const double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
+        if (std::fabs(e[m]) <= eps * dd) break;
+      }
+      if (m == l) break;
+      if (++iter > 80) return false;
+      double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+      double r = std::hypot(g, 1.0);
+      g = d[m] - d[l] + e[l] / (g + (g >= 0.0 ? r : -r));
+      double s = 1.0, c = 1.0, pp = 0.0;
+      bool early = false;
+      for (int i = m - 1; i >= l; --i) {
+        const double f = s * e[i], b = c * e[i];
+        r = std::hypot(f, g);
+        e[i + 1] = r;
+        if (r == 0.0) {
+          d[i + 1] -= pp;
+          e[m] = 0.0;
+          early = true;
+          break;
+        }
+        s = f / r;
+        c = g / r;
+        g = d[i + 1] - pp;
+        r = (d[i] - g) * s + 2.0 * c * b;
+        pp = s * r;
+        d[i + 1] = g + pp;
+        g = c * r - b;
+        for (int k = 0; k < n; ++k) {
+          double* row = &V[size_t(k) * n];
+          const double t = row[i + 1];
+          row[i + 1] = s * row[i] + c * t;
+          row[i] = c * row[i] - s * t;
+        }
+      }
+      if (early) continue;
+      d[l] -= pp;
+      e[l] = g;
+      e[m] = 0.0;
+    }
+  }
+  // 3. ascending order
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return d[x] < d[y]; });
+  w.resize(n);
+  std::vector<double> Vs(size_t(n) * n);
+  for (int k = 0; k < n; ++k) {
+    w[k] = d[idx[k]];
+    for (int r = 0; r < n; ++r) Vs[size_t(r) * n + k] = V[size_t(r) * n + idx[k]];
+  }
+  V.swap(Vs);
+  for (double x : w)
+    if (!std::isfinite(x)) return false;
   return true;
 }
 

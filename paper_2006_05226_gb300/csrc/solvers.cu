@@ -523,7 +523,7 @@ static void ritz_body(DavState& D, const std::vector<double>& Yt, int nr, const 
 }
 
 mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omega_host,
-                           double* r_out, mlcc_es_info* info) {
+                           double* r_out, mlcc_es_info* info, double* residual_host) {
   if (!S->prepared) throw Error(MLCC_E_STATE, "mlcc_excited_states: no prepared ground state");
   cudaStream_t s = S->ctx->stream;
   const int no = S->no, nv = S->nv, nreq = opt->n_roots;
@@ -776,6 +776,8 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
     }
   }
   for (int k = 0; k < nreq; ++k) omega_host[k] = w[k];
+  if (residual_host)
+    for (int k = 0; k < nreq; ++k) residual_host[k] = rn[k];
   if (r_out) MLCC_CUDA(cudaMemcpyAsync(r_out, X, size_t(nreq) * dim * 8, cudaMemcpyDeviceToDevice, s));
   MLCC_CUDA(cudaStreamSynchronize(s));
   if (info) {

@@ -37,6 +37,10 @@ struct mlcc_system {
   int64_t dS = 0;          // sv * so
   int64_t nd = 0;          // dS * dS
   std::vector<int32_t> perm;   // internal -> caller orbital
+  // semicanonical rotation inside each level's occupied and virtual blocks (internal order):
+  // the system's orbital k is sum_k' rot[k' * n + k] (re-ordered input orbital k'); empty
+  // when the input Fock matrix was already diagonal inside every level block
+  std::vector<double> rot;
   std::vector<double> eps_host;
   // persistent device buffers
   double* L = nullptr;     // [nj][n][n] internal order

@@ -36,7 +36,7 @@ STATUS = {v: k for k, v in dict(globals()).items()
           if k.startswith("MLCC_") and (k.startswith("MLCC_E_") or k in ("MLCC_OK", "MLCC_PENDING"))}
 
 # every symbol include/mlcc.h declares
-EXPORTS = ["mlcc_default_options", "mlcc_ctx_create", "mlcc_ctx_destroy", "mlcc_ctx_stream",
+EXPORTS = ["mlcc_default_options", "mlcc_ctx_create", "mlcc_ctx_create_budget", "mlcc_orbitals", "mlcc_ctx_destroy", "mlcc_ctx_stream",
            "mlcc_last_error", "mlcc_kernel_timing", "mlcc_kernel_time", "mlcc_system_create",
            "mlcc_system_destroy", "mlcc_system_info", "mlcc_orbital_order", "mlcc_t1_transform",
            "mlcc_fock_t1", "mlcc_omega", "mlcc_ground_state", "mlcc_jacobian_prepare",
@@ -91,6 +91,12 @@ class mlcc_server_info(ctypes.Structure):
                 ("cancelled", c_int64), ("retried", c_int64)]
 
 
+class mlcc_result(ctypes.Structure):
+    _fields_ = [("gs", mlcc_gs_info), ("es", mlcc_es_info), ("omega", POINTER(c_double)),
+                ("residual", POINTER(c_double)), ("t1", c_void_p), ("x2", c_void_p), ("r", c_void_p),
+                ("perm", POINTER(c_int32)), ("orbitals", POINTER(c_double))]
+
+
 class MLCCError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -114,6 +120,8 @@ def load():
     sig = {
         "mlcc_default_options": (None, [POINTER(mlcc_options)]),
         "mlcc_ctx_create": (c_int, [c_int, POINTER(c_void_p)]),
+        "mlcc_ctx_create_budget": (c_int, [c_int, c_int64, POINTER(c_void_p)]),
+        "mlcc_orbitals": (c_int, [P, D]),
         "mlcc_ctx_destroy": (None, [P]),
         "mlcc_ctx_stream": (c_void_p, [P]),
         "mlcc_last_error": (c_char_p, []),
@@ -134,10 +142,9 @@ def load():
         "mlcc_jacobian_prepare": (c_int, [P, P, P]),
         "mlcc_sigma": (c_int, [P, c_int32, P, P, c_int32]),
         "mlcc_excited_states": (c_int, [P, POINTER(mlcc_options), D, P, POINTER(mlcc_es_info)]),
-        "mlcc_solve": (c_int, [P, POINTER(mlcc_problem), P, P, POINTER(mlcc_options),
-                               POINTER(mlcc_gs_info), D, POINTER(mlcc_es_info), P]),
+        "mlcc_solve": (c_int, [P, POINTER(mlcc_problem), P, P, POINTER(mlcc_options), POINTER(mlcc_result)]),
         "mlcc_solve_device": (c_int, [P, POINTER(mlcc_problem), P, P, POINTER(mlcc_options),
-                                      POINTER(mlcc_gs_info), D, POINTER(mlcc_es_info), P]),
+                                      POINTER(mlcc_result)]),
         "mlcc_vector_len": (c_int64, [POINTER(mlcc_problem)]),
         "mlcc_sigma_eff": (c_int, [P, c_int32, D, P, P, P, c_int32]),
         "mlcc_fold_window": (c_int, [P, D]),
@@ -190,13 +197,14 @@ def _ptr(t):
 
 
 class Context:
-    """mlcc_ctx: one device, one stream."""
+    """mlcc_ctx: one device, one stream; budget_bytes > 0 caps the device memory its systems
+    and whole solves may hold (mlcc_ctx_create_budget)."""
 
-    def __init__(self, device=0):
+    def __init__(self, device=0, budget_bytes=0):
         import torch
         self._torch = torch
         h = c_void_p()
-        _check(load().mlcc_ctx_create(device, byref(h)))
+        _check(load().mlcc_ctx_create_budget(device, int(budget_bytes), byref(h)))
         self.handle = h
         self.device = device
         self.stream = torch.cuda.ExternalStream(load().mlcc_ctx_stream(h), device=f"cuda:{device}")
@@ -281,6 +289,12 @@ class System:
         self.n, self.no = fock.shape[0], n_occ
         self.nv = self.n - n_occ
         self.n_chol = chol.shape[0]
+
+    def orbitals(self):
+        """mlcc_orbitals: [n, n] with column k the system's orbital k in the caller's orbitals."""
+        c = np.zeros((self.n, self.n))
+        _check(load().mlcc_orbitals(self.handle, c.ctypes.data_as(POINTER(c_double))))
+        return c
 
     def _new(self, *shape):
         return self.ctx._torch.empty(*shape, dtype=self.ctx._torch.float64,
@@ -386,23 +400,62 @@ class System:
             pass
 
 
-def solve(ctx, chol_host, fock_host, n_occ, level, opts=None):
-    """mlcc_solve from host arrays (copies them to the device inside the call)."""
+class Solution:
+    """What a whole solve returned: gs (mlcc_gs_info), es (mlcc_es_info), omega and residual
+    (numpy, per root), and t1, x2, r, perm, orbitals where asked for (else None): numpy
+    arrays from solve(), torch device tensors (t1, x2, r) from solve_device()."""
+
+    def __init__(self, **kw):
+        self.__dict__.update(kw)
+
+
+def _dims_of(n_mo, n_occ, level):
+    lev = np.asarray(level)
+    so = int(np.sum(lev[:n_occ] >= MLCC_LEVEL_CC2))
+    sv = int(np.sum(lev[n_occ:] >= MLCC_LEVEL_CC2))
+    n1 = (n_mo - n_occ) * n_occ
+    return n1, (so * sv) ** 2
+
+
+def _solve(entry, ctx, chol, fock, n_occ, level, opts, t1, x2, vectors, orbitals, alloc):
+    opts = opts or default_options()
+    n_mo = fock.shape[0]
+    prob, lev = _problem(n_mo, n_occ, chol.shape[0], level)
+    n1, nd = _dims_of(n_mo, n_occ, lev)
+    w = np.zeros(opts.n_roots)
+    rs = np.zeros(opts.n_roots)
+    out = {"t1": alloc(n1) if t1 else None, "x2": alloc(max(nd, 1)) if x2 else None,
+           "r": alloc(opts.n_roots * (n1 + nd)) if vectors else None}
+    perm = np.zeros(n_mo, dtype=np.int32)
+    orb = np.zeros((n_mo, n_mo)) if orbitals else None
+    res = mlcc_result()
+    res.omega = w.ctypes.data_as(POINTER(c_double))
+    res.residual = rs.ctypes.data_as(POINTER(c_double))
+    addr = (lambda a: None if a is None else (a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr()))
+    res.t1, res.x2, res.r = addr(out["t1"]), addr(out["x2"]), addr(out["r"])
+    res.perm = perm.ctypes.data_as(POINTER(c_int32))
+    res.orbitals = orb.ctypes.data_as(POINTER(c_double)) if orb is not None else None
+    st = entry(res, prob)
+    _check(st)
+    if out["x2"] is not None:
+        out["x2"] = out["x2"][:nd]
+    if out["r"] is not None:
+        out["r"] = out["r"].reshape(opts.n_roots, n1 + nd)
+    return Solution(gs=res.gs, es=res.es, omega=w, residual=rs, perm=perm.astype(np.int64),
+                    orbitals=orb, **out)
+
+
+def solve(ctx, chol_host, fock_host, n_occ, level, opts=None, t1=False, x2=False, vectors=False,
+          orbitals=False):
+    """mlcc_solve from host arrays (copies them to the device inside the call). t1, x2,
+    vectors, orbitals: also return those (host numpy arrays)."""
     chol_host = np.ascontiguousarray(chol_host, dtype=np.float64)
     fock_host = np.ascontiguousarray(fock_host, dtype=np.float64)
-    level = np.ascontiguousarray(np.asarray(level, dtype=np.int8))
-    opts = opts or default_options()
-    prob = mlcc_problem(fock_host.shape[0], n_occ, chol_host.shape[0],
-                        level.ctypes.data_as(POINTER(c_int8)))
-    gs, es = mlcc_gs_info(), mlcc_es_info()
-    w = (c_double * opts.n_roots)()
-    nv = fock_host.shape[0] - n_occ
-    t1 = np.zeros(nv * n_occ)
-    st = load().mlcc_solve(ctx.handle, byref(prob), c_void_p(chol_host.ctypes.data),
-                           c_void_p(fock_host.ctypes.data), byref(opts), byref(gs), w, byref(es),
-                           c_void_p(t1.ctypes.data))
-    _check(st)
-    return gs, np.array(w[:]), es, t1
+    o = opts or default_options()
+    return _solve(lambda res, prob: load().mlcc_solve(ctx.handle, byref(prob), c_void_p(chol_host.ctypes.data),
+                                                      c_void_p(fock_host.ctypes.data), byref(o), byref(res)),
+                  ctx, chol_host, fock_host, n_occ, level, o, t1, x2, vectors, orbitals,
+                  lambda n: np.zeros(n))
 
 
 def _problem(n_mo, n_occ, n_chol, level):
@@ -411,18 +464,21 @@ def _problem(n_mo, n_occ, n_chol, level):
     return mlcc_problem(n_mo, n_occ, n_chol, level.ctypes.data_as(POINTER(c_int8))), level
 
 
-def solve_device(ctx, chol, fock, n_occ, level, opts=None):
-    """mlcc_solve_device on float64 CUDA tensors (borrowed for the call)."""
-    opts = opts or default_options()
-    prob, lev = _problem(fock.shape[0], n_occ, chol.shape[0], level)
-    gs, es = mlcc_gs_info(), mlcc_es_info()
-    w = (c_double * opts.n_roots)()
-    ctx.before()
-    st = load().mlcc_solve_device(ctx.handle, byref(prob), _ptr(chol), _ptr(fock), byref(opts),
-                                  byref(gs), w, byref(es), None)
-    ctx.after()
-    _check(st)
-    return gs, np.array(w[:]), es
+def solve_device(ctx, chol, fock, n_occ, level, opts=None, t1=False, x2=False, vectors=False,
+                 orbitals=False):
+    """mlcc_solve_device on float64 CUDA tensors (borrowed for the call); t1, x2 and the
+    vectors come back as device tensors."""
+    o = opts or default_options()
+    torch = ctx._torch
+
+    def entry(res, prob):
+        ctx.before()
+        st = load().mlcc_solve_device(ctx.handle, byref(prob), _ptr(chol), _ptr(fock), byref(o), byref(res))
+        ctx.after()
+        return st
+
+    return _solve(entry, ctx, chol, fock, n_occ, level, o, t1, x2, vectors, orbitals,
+                  lambda n: torch.zeros(n, dtype=torch.float64, device=f"cuda:{ctx.device}"))
 
 
 def vector_len(n_mo, n_occ, n_chol, level):

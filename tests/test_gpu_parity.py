@@ -187,10 +187,10 @@ def test_solve_from_host_memory(ctx, small):
     o = MLCCSystem(small.L, small.fock, small.spec.n_occ, small.level)
     gs = solve_ground_state(o)
     ref = oracle_es(o, gs, 3, res_tol=1e-9)
-    info, w, es, t1 = mlcc.solve(ctx, small.L, small.fock, small.spec.n_occ, small.level,
-                                 mlcc.default_options(n_roots=3))
-    assert abs(info.e_corr - gs.energy) < E_TOL
-    assert np.abs(w - ref.omega).max() < E_TOL
+    sol = mlcc.solve(ctx, small.L, small.fock, small.spec.n_occ, small.level,
+                     mlcc.default_options(n_roots=3))
+    assert abs(sol.gs.e_corr - gs.energy) < E_TOL
+    assert np.abs(sol.omega - ref.omega).max() < E_TOL
 
 
 def test_invalid_inputs_are_rejected(ctx, sys7):
@@ -205,10 +205,15 @@ def test_invalid_inputs_are_rejected(ctx, sys7):
         mlcc.System(ctx, _dev(Lb), _dev(F), 2, np.ones(7, np.int8))
     assert e.value.status == -1
     Fb = F.copy()
-    Fb[3, 4] = Fb[4, 3] = 1e-3
+    Fb[3, 4] += 1e-3                                # not symmetric
     with pytest.raises(mlcc.MLCCError) as e:
         mlcc.System(ctx, _dev(L), _dev(Fb), 2, np.ones(7, np.int8))
     assert e.value.status == -1
+    Fb = F.copy()
+    Fb[3, 3] = np.nan
+    with pytest.raises(mlcc.MLCCError) as e:
+        mlcc.System(ctx, _dev(L), _dev(Fb), 2, np.ones(7, np.int8))
+    assert e.value.status == mlcc.MLCC_E_NAN
     g = mlcc.System(ctx, _dev(L), _dev(F), 2, np.ones(7, np.int8))
     with pytest.raises(mlcc.MLCCError) as e:
         g.sigma(torch.zeros(1, g.dims.vector_len, dtype=torch.float64, device="cuda"))

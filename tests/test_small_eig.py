@@ -113,3 +113,72 @@ def test_eig_davidson_like_subspace(lib, n, seed):
     A = np.diag(d) + 0.02 * rng.standard_normal((n, n))
     w, V = _eig(lib, A, 4)
     _check_spectrum(A, w, V)
+
+
+SYM_SHIM = r"""
+#include "small_eig.h"
+#include <vector>
+extern "C" int t_eig_sym(int n, const double* A, double* w, double* V) {
+  std::vector<double> a(A, A + n * n), ww, vv;
+  if (!mlcc::eig_sym(n, a, ww, vv)) return 0;
+  for (int i = 0; i < n; ++i) w[i] = ww[i];
+  for (int i = 0; i < n * n; ++i) V[i] = vv[i];
+  return 1;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def symlib(tmp_path_factory):
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    d = tmp_path_factory.mktemp("eig_sym")
+    (d / "shim.cpp").write_text(SYM_SHIM)
+    so = d / "libeig_sym_test.so"
+    subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", f"-I{CSRC}", str(d / "shim.cpp"),
+                    os.path.join(CSRC, "small_eig.cpp"), "-o", str(so)], check=True)
+    L = ctypes.CDLL(str(so))
+    P = ctypes.POINTER(ctypes.c_double)
+    L.t_eig_sym.argtypes = [ctypes.c_int, P, P, P]
+    return L
+
+
+def _eig_sym(lib, A):
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    w, V = np.zeros(n), np.zeros((n, n))
+    ok = lib.t_eig_sym(n, _p(A), _p(w), _p(V))
+    return bool(ok), w, V
+
+
+@pytest.mark.parametrize("n,seed", [(1, 0), (2, 1), (3, 2), (17, 3), (64, 4), (201, 5)])
+def test_eig_sym_random(symlib, n, seed):
+    """Eigenvalues against LAPACK (numpy.linalg.eigvalsh); A V = V diag(w) and V^T V = I."""
+    rng = np.random.default_rng(seed)
+    B = rng.standard_normal((n, n))
+    A = B + B.T
+    ok, w, V = _eig_sym(symlib, A)
+    assert ok
+    scale = max(1.0, np.abs(A).max())
+    assert np.abs(w - np.linalg.eigvalsh(A)).max() < 1e-12 * scale * n
+    assert np.all(np.diff(w) >= 0)
+    assert np.abs(A @ V - V * w).max() < 1e-11 * scale * n
+    assert np.abs(V.T @ V - np.eye(n)).max() < 1e-12 * n
+
+
+def test_eig_sym_degenerate_and_structured(symlib):
+    """Repeated eigenvalues (a rotated diagonal with a threefold level), a diagonal matrix (no
+    reflections needed) and a tridiagonal one with tiny off-diagonals."""
+    rng = np.random.default_rng(9)
+    Q, _ = np.linalg.qr(rng.standard_normal((12, 12)))
+    lam = np.array([1.0, 1.0, 1.0, -2.0, 0.5, 0.5, 3.0, 4.0, -1.0, 0.0, 2.0, 2.0])
+    A = Q @ np.diag(lam) @ Q.T
+    ok, w, V = _eig_sym(symlib, A)
+    assert ok and np.abs(w - np.sort(lam)).max() < 1e-13
+    assert np.abs(A @ V - V * w).max() < 1e-13 and np.abs(V.T @ V - np.eye(12)).max() < 1e-13
+    D = np.diag([3.0, -1.0, 2.0, 0.0])
+    ok, w, V = _eig_sym(symlib, D)
+    assert ok and np.array_equal(w, [-1.0, 0.0, 2.0, 3.0]) and np.abs(np.abs(V) - np.abs(V).round()).max() == 0.0
+    T = np.diag(np.arange(6.0)) + np.diag(np.full(5, 1e-9), 1) + np.diag(np.full(5, 1e-9), -1)
+    ok, w, V = _eig_sym(symlib, T)
+    assert ok and np.abs(w - np.linalg.eigvalsh(T)).max() < 1e-14

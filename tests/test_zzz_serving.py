@@ -51,8 +51,8 @@ def test_each_result_in_the_mix_equals_the_solve_alone(problems, mixed):
     ctx = mlcc.Context(0)
     alone = []
     for L, F, no, lev in problems:
-        gs, w, es, _ = mlcc.solve(ctx, L, F, no, lev, opts)
-        alone.append((gs.e_corr, w))
+        sol = mlcc.solve(ctx, L, F, no, lev, opts)
+        alone.append((sol.gs.e_corr, sol.omega))
     ctx.close()
     srv = mlcc.Server(0, n_slots=3)
     order = [0, 1, 2, 0, 2, 1]                      # more requests than slots
@@ -129,8 +129,9 @@ def test_problem_queries(problems):
         sv = int(np.sum(lev[no:] >= 1))
         assert mlcc.vector_len(n, no, nj, lev) == (n - no) * no + (so * sv) ** 2
         ctx = mlcc.Context(0)
-        gs_h, w_h, _, _ = mlcc.solve(ctx, L, F, no, lev, _opts(False))
-        gs_d, w_d, _ = mlcc.solve_device(ctx, torch.as_tensor(L, device="cuda"), torch.as_tensor(F, device="cuda"),
-                                         no, lev, _opts(False))
+        h = mlcc.solve(ctx, L, F, no, lev, _opts(False))
+        d = mlcc.solve_device(ctx, torch.as_tensor(L, device="cuda"), torch.as_tensor(F, device="cuda"),
+                              no, lev, _opts(False))
+        gs_h, w_h, gs_d, w_d = h.gs, h.omega, d.gs, d.omega
         ctx.close()
         assert gs_d.e_corr == gs_h.e_corr and np.array_equal(w_d, w_h)
