@@ -404,6 +404,42 @@ mlcc_status mlcc_poll(mlcc_server* srv, uint64_t ticket, int64_t wait_ms, mlcc_r
 mlcc_status mlcc_cancel(mlcc_server* srv, uint64_t ticket);
 mlcc_status mlcc_server_stats(mlcc_server* srv, mlcc_server_info* info);
 
+/* ---- active-space selection: correlated natural transition orbitals ----------------- */
+/* CNTOs (Sec. 2.2, Eqs. M, N, approx_double_1, approx_double_2, select_CNTOs): from the
+   lowest n_states CCS excitation vectors R_ai (unit 2-norm) and energies omega, the
+   approximate doubles
+     R_aibj = -gbar_aibj / ((1 + delta_{ai,bj}) (eps_a + eps_b - eps_i - eps_j - omega)),
+     gbar_aibj = P^{ab}_{ij} (sum_{cJ} R_ci L^J_bj L^J_ac - sum_{kJ} R_bk L^J_kj L^J_ai),
+   then M_ij = sum_a R_ai R_aj + 1/2 sum_abk (1 + delta_{ai,bk} delta_ij) R_aibk R_ajbk and
+   N_ab = sum_i R_ai R_bi + 1/2 sum_ijc (1 + delta_{ai,cj} delta_ab) R_aicj R_bicj summed over
+   the states, and their eigenpairs: the eigenvectors of M (N) rotate the occupied
+   (virtual) orbitals, and those of the largest eigenvalues are the active ones.
+   Inputs: canonical orbitals (fock_dev diagonal, else MLCC_E_ARG) in the caller's order
+   (occupied first), chol_dev [n_chol][n_mo][n_mo] symmetric, both device memory on the
+   context's device. All outputs are host memory owned by the caller. The doubles are
+   built and contracted in blocks of rows, so their (n_vir n_occ)^2 size is never held at
+   once. precision: mlcc_precision of the large contractions (MLCC_FP64, MLCC_FP64E or a
+   split-bfloat16 one); the CCS states are solved in binary64. Synchronises. */
+typedef struct {
+  double* omega;         /* [n_states] CCS excitation energies, Hartree; required          */
+  double* m;             /* [n_occ][n_occ] M summed over the states, or NULL               */
+  double* n;             /* [n_vir][n_vir] N summed over the states, or NULL               */
+  double* occ_values;    /* [n_occ] eigenvalues of M, descending; required                 */
+  double* occ_vectors;   /* [n_occ][n_occ] row-major, column k the eigenvector of
+                            occ_values[k] (largest-magnitude component positive), or NULL */
+  double* vir_values;    /* [n_vir] eigenvalues of N, descending; required                 */
+  double* vir_vectors;   /* [n_vir][n_vir] as occ_vectors, or NULL                         */
+  int32_t n_occ_active;  /* in: n_o^a, the active occupied CNTOs                          */
+  int32_t n_vir_active;  /* in: n_v^a, or <= 0 for Eq. select_CNTOs, n_v^a = (N_v / N_o)
+                            n_o^a rounded to the nearest integer; out: the value used      */
+  int32_t block_rows;    /* in: rows (pairs ai) of the doubles built at once; 0: about
+                            128 MiB of doubles per block                                   */
+  int32_t reserved;      /* zero                                                           */
+} mlcc_cnto_result;
+mlcc_status mlcc_cnto(mlcc_ctx* ctx, int32_t n_mo, int32_t n_occ, int32_t n_chol,
+                      const double* chol_dev, const double* fock_dev, int32_t n_states,
+                      int32_t precision, mlcc_cnto_result* res);
+
 /* ---- allocation-free variant ------------------------------------------------------ */
 /* The paper has no counterpart to this entry point; it exists for callers that cannot let
    a library allocate device memory: a program that reserves the device memory for its own

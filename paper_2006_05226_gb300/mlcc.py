@@ -36,7 +36,7 @@ STATUS = {v: k for k, v in dict(globals()).items()
           if k.startswith("MLCC_") and (k.startswith("MLCC_E_") or k in ("MLCC_OK", "MLCC_PENDING"))}
 
 # every symbol include/mlcc.h declares
-EXPORTS = ["mlcc_default_options", "mlcc_ctx_create", "mlcc_ctx_create_budget", "mlcc_orbitals", "mlcc_ctx_destroy", "mlcc_ctx_stream",
+EXPORTS = ["mlcc_default_options", "mlcc_cnto", "mlcc_ctx_create", "mlcc_ctx_create_budget", "mlcc_orbitals", "mlcc_ctx_destroy", "mlcc_ctx_stream",
            "mlcc_last_error", "mlcc_kernel_timing", "mlcc_kernel_time", "mlcc_system_create",
            "mlcc_system_destroy", "mlcc_system_info", "mlcc_orbital_order", "mlcc_t1_transform",
            "mlcc_fock_t1", "mlcc_omega", "mlcc_ground_state", "mlcc_jacobian_prepare",
@@ -97,6 +97,14 @@ class mlcc_result(ctypes.Structure):
                 ("perm", POINTER(c_int32)), ("orbitals", POINTER(c_double))]
 
 
+class mlcc_cnto_result(ctypes.Structure):
+    _fields_ = [("omega", POINTER(c_double)), ("m", POINTER(c_double)), ("n", POINTER(c_double)),
+                ("occ_values", POINTER(c_double)), ("occ_vectors", POINTER(c_double)),
+                ("vir_values", POINTER(c_double)), ("vir_vectors", POINTER(c_double)),
+                ("n_occ_active", c_int32), ("n_vir_active", c_int32), ("block_rows", c_int32),
+                ("reserved", c_int32)]
+
+
 class MLCCError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -122,6 +130,7 @@ def load():
         "mlcc_ctx_create": (c_int, [c_int, POINTER(c_void_p)]),
         "mlcc_ctx_create_budget": (c_int, [c_int, c_int64, POINTER(c_void_p)]),
         "mlcc_orbitals": (c_int, [P, D]),
+        "mlcc_cnto": (c_int, [P, c_int32, c_int32, c_int32, P, P, c_int32, c_int32, POINTER(mlcc_cnto_result)]),
         "mlcc_ctx_destroy": (None, [P]),
         "mlcc_ctx_stream": (c_void_p, [P]),
         "mlcc_last_error": (c_char_p, []),
@@ -479,6 +488,26 @@ def solve_device(ctx, chol, fock, n_occ, level, opts=None, t1=False, x2=False, v
 
     return _solve(entry, ctx, chol, fock, n_occ, level, o, t1, x2, vectors, orbitals,
                   lambda n: torch.zeros(n, dtype=torch.float64, device=f"cuda:{ctx.device}"))
+
+
+def cnto(ctx, chol, fock, n_occ, n_states, n_occ_active, n_vir_active=0, precision=MLCC_FP64, block_rows=0):
+    """mlcc_cnto on float64 CUDA tensors (canonical orbitals): a Solution with omega, m, n,
+    occ_values, occ_vectors, vir_values, vir_vectors (numpy) and the active counts."""
+    n_mo = fock.shape[0]
+    nv = n_mo - n_occ
+    out = {"omega": np.zeros(n_states), "m": np.zeros((n_occ, n_occ)), "n": np.zeros((nv, nv)),
+           "occ_values": np.zeros(n_occ), "occ_vectors": np.zeros((n_occ, n_occ)),
+           "vir_values": np.zeros(nv), "vir_vectors": np.zeros((nv, nv))}
+    res = mlcc_cnto_result()
+    for k, a in out.items():
+        setattr(res, k, a.ctypes.data_as(POINTER(c_double)))
+    res.n_occ_active, res.n_vir_active, res.block_rows = n_occ_active, n_vir_active, block_rows
+    ctx.before()
+    st = load().mlcc_cnto(ctx.handle, n_mo, n_occ, chol.shape[0], _ptr(chol), _ptr(fock), n_states, precision,
+                          byref(res))
+    ctx.after()
+    _check(st)
+    return Solution(n_occ_active=res.n_occ_active, n_vir_active=res.n_vir_active, **out)
 
 
 def vector_len(n_mo, n_occ, n_chol, level):

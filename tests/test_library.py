@@ -65,7 +65,7 @@ def test_struct_layouts_match_the_header_compiled_with_gcc(lib, tmp_path):
     if shutil.which("gcc") is None:
         pytest.skip("gcc not available")
     structs = [mlcc.mlcc_problem, mlcc.mlcc_dims, mlcc.mlcc_options, mlcc.mlcc_gs_info, mlcc.mlcc_es_info,
-               mlcc.mlcc_request_result, mlcc.mlcc_server_info, mlcc.mlcc_result]
+               mlcc.mlcc_request_result, mlcc.mlcc_server_info, mlcc.mlcc_result, mlcc.mlcc_cnto_result]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mlcc.h"', 'int main(void) {', 'printf("{");']
     for st in structs:
         n = st.__name__
