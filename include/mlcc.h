@@ -255,6 +255,19 @@ mlcc_status mlcc_jacobian_prepare(mlcc_system* sys, const double* t1_dev,
    c_dev, sigma_dev [n_vec][vector_len]. precision: mlcc_precision. */
 mlcc_status mlcc_sigma(mlcc_system* sys, int32_t n_vec, const double* c_dev,
                        double* sigma_dev, int32_t precision);
+/* Jacobian transformation split over the Cholesky index (Sec. 2.4: every integral is a sum
+   over J, g_pqrs = sum_J L^J_pq L^J_rs, and so is every heavy term of sigma). Writes the part
+   of sigma = A c that sums over the Cholesky vectors J in [j_begin, j_end) and, when
+   with_rest is non-zero, adds the terms that do not sum over J (those built from F~, the
+   MLCC2 intermediates X and Y, the cached CCSD value tensors and the orbital energies).
+   Ranks whose ranges tile [0, n_chol), exactly one of them with with_rest, obtain
+   mlcc_sigma's result by one sum (an all-reduce) of their outputs per sigma batch. Here
+   each rank holds the whole prepared system and the work is what is split. Layout,
+   precisions and errors as mlcc_sigma; j_begin == j_end is allowed (the rest terms alone, or
+   zero). In a split-bfloat16 precision the cached bfloat16 operands are not used inside a
+   range: each call converts its operands. */
+mlcc_status mlcc_sigma_partial(mlcc_system* sys, int32_t j_begin, int32_t j_end, int32_t with_rest,
+                               int32_t n_vec, const double* c_dev, double* sigma_dev, int32_t precision);
 /* Folded CC2 Jacobian (the CC2 response strategy Sec. 2.1 points to). In the three-level
    model the doubles rows outside the CCSD block (P_S) have the diagonal doubles block
    eps_aibj and no coupling to the CCSD-block doubles (P_T), so an eigenpair (omega, c) of

@@ -506,6 +506,57 @@ mlcc_status mlcc_sigma(mlcc_system* S, int32_t n_vec, const double* c, double* s
   });
 }
 
+// Restricts a prepared system to the Cholesky vectors [j0, j1) for the duration of a
+// sharded Jacobian transformation: the J-indexed buffers are offset, nj shrinks, and the
+// converted-operand caches (which cover every J) are bypassed.
+namespace {
+struct JWindow {
+  mlcc_system* S;
+  int nj;
+  double *Lt, *Lai, *Lov, *Z;
+  OperandCache* oc;
+  JWindow(mlcc_system* s, int j0, int j1) : S(s), nj(s->nj), Lt(s->Lt), Lai(s->Lai), Lov(s->Lov), Z(s->Z), oc(s->opcache) {
+    const int64_t nn = int64_t(S->n) * S->n;
+    S->Lt += int64_t(j0) * nn;
+    S->Lai += int64_t(j0) * S->dS;
+    S->Lov += int64_t(j0) * S->dS;
+    S->Z += int64_t(j0) * S->dS;
+    S->nj = j1 - j0;
+    S->jwin = true;
+    S->jwin0 = j0;
+    S->opcache = nullptr;
+  }
+  ~JWindow() {
+    S->Lt = Lt; S->Lai = Lai; S->Lov = Lov; S->Z = Z;
+    S->nj = nj;
+    S->jwin = false;
+    S->jwin0 = 0;
+    S->opcache = oc;
+  }
+};
+}  // namespace
+
+mlcc_status mlcc_sigma_partial(mlcc_system* S, int32_t j_begin, int32_t j_end, int32_t with_rest,
+                               int32_t n_vec, const double* c, double* sigma, int32_t precision) {
+  return guard([&] {
+    MLCC_REQUIRE(S && c && sigma, "mlcc_sigma_partial: NULL argument");
+    MLCC_REQUIRE(n_vec >= 0, "mlcc_sigma_partial: n_vec < 0");
+    MLCC_REQUIRE(0 <= j_begin && j_begin <= j_end && j_end <= S->nj,
+                 "mlcc_sigma_partial: need 0 <= j_begin <= j_end <= n_chol");
+    MLCC_REQUIRE(precision >= MLCC_FP64 && precision <= MLCC_FP64E, "mlcc_sigma_partial: unknown precision");
+    if (!S->prepared) throw Error(MLCC_E_STATE, "mlcc_sigma_partial: call mlcc_jacobian_prepare first");
+    MLCC_CUDA(cudaSetDevice(S->ctx->device));
+    const int64_t len = int64_t(S->nv) * S->no + S->nd;
+    {
+      JWindow w(S, j_begin, j_end);
+      const unsigned parts = SIGMA_ALL | (with_rest ? 0u : unsigned(SIGMA_J_ONLY));
+      for (int k = 0; k < n_vec; ++k) sigma_eval(S, c + k * len, sigma + k * len, precision, parts);
+    }
+    if (precision != MLCC_FP64) check_tc_error(S);
+    return MLCC_OK;
+  });
+}
+
 mlcc_status mlcc_fold_window(const mlcc_system* S, double* omega_max) {
   return guard([&] {
     MLCC_REQUIRE(S && omega_max, "mlcc_fold_window: NULL argument");

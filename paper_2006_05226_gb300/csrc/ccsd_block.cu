@@ -49,9 +49,13 @@ struct Eval {
     }
     return x;
   }
-  // input tensor: value from the caller (Value) or from the cache; tangent from the caller
-  Dual input(const Dual& in) {
+  // input tensor: value from the caller (Value) or from the cache; tangent from the caller.
+  // j_indexed: the leading index is the Cholesky index; inside a J window the cached value
+  // (over every J) is read from the window's first vector on
+  Dual input(const Dual& in, bool j_indexed = false) {
     Dual x = make(in.v.p ? in.v.d : in.d.d);
+    if (mode == Mode::Tangent && j_indexed && S->jwin)
+      x.v.p += int64_t(S->jwin0) * (count(x.v.d) / std::max<int64_t>(x.v.d[0], 1));
     cudaStream_t s = S->ctx->stream;
     if (mode == Mode::Value) {
       MLCC_CUDA(cudaMemcpyAsync(x.v.p, in.v.p, size_t(x.v.size()) * 8, cudaMemcpyDeviceToDevice, s));
@@ -84,6 +88,16 @@ struct Eval {
       else axpby(C.d.p, C.d.p, C.d.size(), 0.0, beta, s);
     }
   }
+  // a value tensor whose tangent is never formed (Tangent mode: the cached value only)
+  Dual value_only(const std::vector<int64_t>& dims) {
+    if (mode == Mode::Value) return make(dims);
+    if (slot >= S->ccsd->slots.size()) throw Error(MLCC_E_STATE, "CCSD cache out of sync");
+    Dual x;
+    x.v.d = dims;
+    x.d.d = dims;
+    x.v.p = S->ccsd->slots[slot++];
+    return x;
+  }
   // C = alpha perm(A) + beta C (linear)
   void perm(const char* spec, double alpha, const Dual& A, double beta, Dual& C) {
     cudaStream_t s = S->ctx->stream;
@@ -92,11 +106,50 @@ struct Eval {
   }
 };
 
+// Tangent of the ladder term sum_cd g~_acbd t^{cd}_{ij} along a trial vector (c1, dt):
+//   sum_cd g~_acbd dt_cidj  -  sum_K (c_aK X_Kbij + c_bK X_Kaji),
+// the second part from d g~_acbd = - c_aK g~_Kcbd - c_bK g~_Kdac and the symmetry of t,
+// with X_Kbij = sum_cd g~_Kcbd t_cidj built once at the ground state. The first part is one
+// GEMM of [(ab)][(cd)] x [(cd)][(ij)] with the cached g~ as its constant operand (2 v^4 o^2
+// flop): the O(o^2 v^4) contraction of the CCSD rows, timed as the "ladder" family.
+void ladder_tangent(mlcc_system* S, const DT& dt, const double* c1, DT& om_d) {
+  cudaStream_t s = S->ctx->stream;
+  const int64_t o = S->to, v = S->tv, no = S->no;
+  const CCSDCache& C = *S->ccsd;
+  Scope sc(S->ws);
+  DT W;
+  W.d = {v, v, o, o};
+  W.p = S->ws.get<double>(size_t(v * v * o * o));
+  if (dt.p) {
+    DT dcd;
+    dcd.d = {v, v, o, o};
+    dcd.p = S->ws.get<double>(size_t(v * v * o * o));
+    eperm("cidj->cdij", 1.0, dt, 0.0, dcd, s);
+    Gemm g;
+    g.M = v * v; g.N = o * o; g.K = v * v;
+    g.A = C.G2.p; g.lda = v * v; g.a_const = true;
+    g.B = dcd.p; g.ldb = o * o;
+    g.C = W.p; g.ldc = o * o;
+    timed(S, "ladder", 2.0 * double(v * v) * double(v * v) * double(o * o),
+          [&] { gemm_f64(g, S->ws, s, S->ctx->sm_count); });
+    eperm("abij->aibj", 1.0, W, 1.0, om_d, s);
+  }
+  // Y[a][(b i j)] = sum_K c_aK X[K][(b i j)]; c1 rows are the CCSD virtuals, stride no
+  Gemm gy;
+  gy.M = v; gy.N = v * o * o; gy.K = no;
+  gy.A = c1; gy.lda = no;
+  gy.B = C.X.p; gy.ldb = v * o * o;
+  gy.C = W.p; gy.ldc = v * o * o;
+  gemm_f64(gy, S->ws, s, S->ctx->sm_count);
+  eperm("abij->aibj", -1.0, W, 1.0, om_d, s);
+  eperm("baji->aibj", -1.0, W, 1.0, om_d, s);
+}
+
 }  // namespace
 
 void ccsd_block(mlcc_system* S, Mode mode, const Dual& Lai_in, const Dual& Lac_in,
                 const Dual& Lki_in, const Dual& Lkc_in, const Dual& Fvv_in, const Dual& Foo_in,
-                const Dual& t_in, double* om_out, bool cache_values, const double* c1) {
+                const Dual& t_in, double* om_out, bool cache_values, const double* c1, bool rest) {
   if (mode == Mode::Value && cache_values) {
     ccsd_cache_free(S);
     S->ccsd = new CCSDCache();
@@ -105,29 +158,18 @@ void ccsd_block(mlcc_system* S, Mode mode, const Dual& Lai_in, const Dual& Lac_i
   }
   Eval E{S, mode, cache_values};
   cudaStream_t s = S->ctx->stream;
-  Dual Lai = E.input(Lai_in), Lac = E.input(Lac_in), Lki = E.input(Lki_in);
-  Dual Lkc = E.input(Lkc_in);   // in tangent mode the ov block has no tangent (NULL)
+  Dual Lai = E.input(Lai_in, true), Lac = E.input(Lac_in, true), Lki = E.input(Lki_in, true);
+  Dual Lkc = E.input(Lkc_in, true);   // in tangent mode the ov block has no tangent (NULL)
   Dual Fvv = E.input(Fvv_in), Foo = E.input(Foo_in), t = E.input(t_in);
   const int64_t o = S->to, v = S->tv;
   const std::vector<int64_t> vovo = {v, o, v, o};
 
-  // X1-basis integrals over the CCSD-active orbitals, g~_pqrs = Lt^J_pq Lt^J_rs
-  Dual g_acbd = E.make({v, v, v, v});
-  if (mode == Mode::Tangent && c1) {
-    // d g~_acbd = - c_aK g~_Kcbd - c_bK g~_Kdac  (d Lt_ac = - c_aK Lt_Kc, Appendix A's route
-    // through an intermediate built once at the ground state instead of N_J v^4 work)
-    DT cb;
-    cb.p = const_cast<double*>(c1);
-    cb.d = {v, int64_t(S->no)};
-    DT T1;
-    T1.d = {v, v, v, v};
-    T1.p = S->ws.get<double>(size_t(v * v * v * v));
-    einsum("aK,Kcbd->acbd", -1.0, cb, S->ccsd->G, 0.0, T1, S->ws, s, S->ctx->sm_count);
-    eperm("acbd->acbd", 1.0, T1, 0.0, g_acbd.d, s);
-    eperm("bdac->acbd", 1.0, T1, 1.0, g_acbd.d, s);
-  } else {
-    E.ein("Jac,Jbd->acbd", 1.0, Lac, Lac, 0.0, g_acbd);
-  }
+  // X1-basis integrals over the CCSD-active orbitals, g~_pqrs = Lt^J_pq Lt^J_rs. The
+  // tangent of g~_acbd is not formed: the ladder term, its only use, has its own tangent
+  // (ladder_tangent, through the intermediates cached below)
+  if (mode == Mode::Tangent && !c1) throw Error(MLCC_E_STATE, "CCSD tangent without the trial singles");
+  Dual g_acbd = E.value_only({v, v, v, v});
+  if (mode == Mode::Value) E.ein("Jac,Jbd->acbd", 1.0, Lac, Lac, 0.0, g_acbd);
   if (mode == Mode::Value && cache_values) {
     // g~_Kcbd for the tangent above
     const int64_t no = S->no, nj = S->nj, n = S->n, nn = n * n;
@@ -139,6 +181,13 @@ void ccsd_block(mlcc_system* S, Mode mode, const Dual& Lai_in, const Dual& Lac_i
     S->ccsd->G.d = {no, v, v, v};
     S->ccsd->G.p = S->ccsd->arena.get<double>(size_t(no * v * v * v));
     einsum("JKc,Jbd->Kcbd", 1.0, LKc, Lac.v, 0.0, S->ccsd->G, S->ws, s, S->ctx->sm_count);
+    // the ladder tangent's operands: g~ as [(ab)][(cd)], X_Kbij = sum_cd g~_Kcbd t_cidj
+    S->ccsd->G2.d = {v, v, v, v};
+    S->ccsd->G2.p = S->ccsd->arena.get<double>(size_t(v * v * v * v));
+    eperm("acbd->abcd", 1.0, g_acbd.v, 0.0, S->ccsd->G2, s);
+    S->ccsd->X.d = {no, v, o, o};
+    S->ccsd->X.p = S->ccsd->arena.get<double>(size_t(no * v * o * o));
+    einsum("Kcbd,cidj->Kbij", 1.0, S->ccsd->G, t.v, 0.0, S->ccsd->X, S->ws, s, S->ctx->sm_count);
   }
   Dual g_kilj = E.make({o, o, o, o});
   E.ein("Jki,Jlj->kilj", 1.0, Lki, Lki, 0.0, g_kilj);
@@ -160,7 +209,8 @@ void ccsd_block(mlcc_system* S, Mode mode, const Dual& Lai_in, const Dual& Lac_i
   // first line: g~_aibj + g~_acbd t^{cd}_{ij} + t^{ab}_{kl} (g~_kilj + t^{cd}_{ij} g~_kcld)
   Dual om = E.make(vovo);
   E.ein("Jai,Jbj->aibj", 1.0, Lai, Lai, 0.0, om);
-  E.ein("acbd,cidj->aibj", 1.0, g_acbd, t, 1.0, om);
+  if (mode == Mode::Value) E.ein("acbd,cidj->aibj", 1.0, g_acbd, t, 1.0, om);
+  else if (rest) ladder_tangent(S, t.d, c1, om.d);   // built from the cached values over all J
   Dual X = E.make({o, o, o, o});
   E.perm("kilj->kilj", 1.0, g_kilj, 0.0, X);
   E.ein("cidj,kcld->kilj", 1.0, t, g_kcld, 1.0, X);

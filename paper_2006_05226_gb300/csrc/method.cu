@@ -100,7 +100,7 @@ __global__ void k_omega2_cc2(const double* g, const double* x2, const double* ep
 // sigma on P_S: W_(ai)(bj) + W_(bj)(ai) + eps c; P_T rows 0. 32 x 32 tiles through shared
 // memory so that both the direct and the transposed read are coalesced.
 __global__ void k_sigma2_cc2(const double* W, const double* c, const double* eps, int no, int sv,
-                             int so, int tv, int to, double* s2) {
+                             int so, int tv, int to, double eps_scale, double* s2) {
   __shared__ double tile[32][33];
   const int64_t dS = int64_t(sv) * so;
   const int64_t r0 = int64_t(blockIdx.y) * 32, c0 = int64_t(blockIdx.x) * 32;
@@ -118,7 +118,7 @@ __global__ void k_sigma2_cc2(const double* W, const double* c, const double* eps
     const int64_t t = row * dS + col;
     s2[t] = in_T(a, i, b, j, tv, to)
                 ? 0.0
-                : W[t] + tile[threadIdx.x][y] + eps4(eps, no, a, i, b, j) * c[t];
+                : W[t] + tile[threadIdx.x][y] + eps_scale * eps4(eps, no, a, i, b, j) * c[t];
   }
 }
 // om1[a*no + i] += alpha * tmp[a*so + i]
@@ -344,7 +344,7 @@ void rank_gemm_f64(mlcc_system* S, bool outer, const double* A, const double* B,
 
 static void rank_gemm(mlcc_system* S, int precision, bool outer, const double* A, const double* B,
                       double* C, double alpha, double beta) {
-  if (is_split_precision(precision)) {
+  if (is_split_precision(precision) && !S->jwin) {   // the cached pieces cover every J
     if (S->lowp_prec != precision) lowp_prepare(S, precision);
     rank_gemm_lowp(S, outer, A, B, C, alpha, beta, precision, false);
   } else {
@@ -627,6 +627,8 @@ void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision, u
     operand_cache_set_ranges(S->opcache, r);
   }
   LowpScope lowp(precision == MLCC_FP64 ? 0 : precision, S->tc_err, S->opcache);
+  // rest: the terms that do not sum over the Cholesky vectors (all but SIGMA_J_ONLY)
+  const bool rest = !(parts & SIGMA_J_ONLY);
   const int n = S->n, no = S->no, nv = S->nv, nj = S->nj, so = S->so, sv = S->sv;
   const int to = S->to, tv = S->tv;
   const int64_t nn = int64_t(n) * n, dS = S->dS, vo = int64_t(nv) * no;
@@ -657,14 +659,20 @@ void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision, u
     k_trace_occ<<<(nj + warps - 1) / warps, 32 * warps, 0, s>>>(Q, nj, no, no, dJ);
     MLCC_CHECK_LAUNCH();
     // CCS: s1 = F~_AB c_BI - c_AJ F~_JI + 2 d_J Lt^J_AI - (Lt^J_AB c_BJ) Lt^J_JI
-    gemm1(S, nv, no, nv, 1.0, S->Ft + int64_t(no) * n + no, n, false, c1, no, false, 0.0, s1, no);
-    gemm1(S, nv, no, no, -1.0, c1, no, false, S->Ft, n, false, 1.0, s1, no);
+    if (rest) {
+      gemm1(S, nv, no, nv, 1.0, S->Ft + int64_t(no) * n + no, n, false, c1, no, false, 0.0, s1, no);
+      gemm1(S, nv, no, no, -1.0, c1, no, false, S->Ft, n, false, 1.0, s1, no);
+    } else {
+      fill(s1, vo, 0.0, s);
+    }
     sum_over_J(S, dJ, S->Lt, no, 0, nv, no, 2.0, s1, no);
     bgemm(S, nv, no, no, -1.0, Xc, no, vo, false, Loo, n, nn, false, 1.0, s1, no, 0, true);
     if (dS > 0) {
       // MLCC2 singles: - c_AJ X_Ji - Y_aB c_BI
-      gemm1(S, nv, so, no, -1.0, c1, no, false, S->Xji, so, false, 1.0, s1, no);
-      gemm1(S, sv, no, nv, -1.0, S->Yab, nv, false, c1, no, false, 1.0, s1, no);
+      if (rest) {
+        gemm1(S, nv, so, no, -1.0, c1, no, false, S->Xji, so, false, 1.0, s1, no);
+        gemm1(S, sv, no, nv, -1.0, S->Yab, nv, false, c1, no, false, 1.0, s1, no);
+      }
       // tangent of F~_kc (k, c active): 2 d_J Lt^J_kc - (Lt^J_kB c_BJ) Lt^J_Jc
       double* dF = S->ws.get<double>(size_t(so) * sv);
       fill(dF, int64_t(so) * sv, 0.0, s);
@@ -683,7 +691,7 @@ void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision, u
         rank_gemm(S, precision, false, S->Lov, uc, Zc, 1.0, 0.0);
         double* tmp = S->ws.get<double>(size_t(dS));
         gemm1(S, dS, 1, dS, 1.0, S->u, dS, false, dfv, 1, false, 0.0, tmp, 1);
-        gemm1(S, dS, 1, dS, 1.0, uc, dS, false, S->Fov, 1, false, 1.0, tmp, 1);
+        if (rest) gemm1(S, dS, 1, dS, 1.0, uc, dS, false, S->Fov, 1, false, 1.0, tmp, 1);
         k_scatter_add_ai<<<nblk(dS), 256, 0, s>>>(tmp, sv, so, no, 1.0, s1);
         MLCC_CHECK_LAUNCH();
         // (u(c)^{bc}_{ij} Lt^K_jc) Lt^K_Ab  and  - (u(c)^{ab}_{jk} Lt^K_kb) Lt^K_jI
@@ -701,7 +709,7 @@ void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision, u
         double* W = S->ws.get<double>(size_t(S->nd));
         rank_gemm(S, precision, true, S->Lai, V, W, 1.0, 0.0);
         dim3 blk(32, 8), grd(unsigned((dS + 31) / 32), unsigned((dS + 31) / 32));
-        k_sigma2_cc2<<<grd, blk, 0, s>>>(W, c2, S->eps, no, sv, so, tv, to, s2);
+        k_sigma2_cc2<<<grd, blk, 0, s>>>(W, c2, S->eps, no, sv, so, tv, to, rest ? 1.0 : 0.0, s2);
         MLCC_CHECK_LAUNCH();
       }
     }
@@ -730,7 +738,8 @@ void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision, u
       Fvv.d.p = S->ws.get<double>(size_t(tv) * tv);
       double* D = S->ws.get<double>(size_t(nj));
       trace_occ(S, S->Lt, D);
-      gemm1(S, tv, tv, no, -1.0, c1, no, false, S->ht + no, n, false, 0.0, Fvv.d.p, tv);
+      if (rest) gemm1(S, tv, tv, no, -1.0, c1, no, false, S->ht + no, n, false, 0.0, Fvv.d.p, tv);
+      else fill(Fvv.d.p, int64_t(tv) * tv, 0.0, s);
       {
         Gemm g;  // + 2 sum_J D_J dLac^J  (M = 1 over the flattened tv*tv block)
         g.M = 1; g.N = int64_t(tv) * tv; g.K = nj;
@@ -744,7 +753,8 @@ void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision, u
       //   with dh~_kj = h~_kA c_Aj and dLt^J_kI = Q^J[k][I]
       Foo.d.d = {to, to};
       Foo.d.p = S->ws.get<double>(size_t(to) * to);
-      gemm1(S, to, to, nv, 1.0, S->ht + no, n, false, c1, no, false, 0.0, Foo.d.p, to);
+      if (rest) gemm1(S, to, to, nv, 1.0, S->ht + no, n, false, c1, no, false, 0.0, Foo.d.p, to);
+      else fill(Foo.d.p, int64_t(to) * to, 0.0, s);
       {
         Gemm g;
         g.M = 1; g.N = int64_t(to) * to; g.K = nj;
@@ -757,11 +767,12 @@ void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision, u
       bgemm(S, to, to, no, -1.0, Loo, n, nn, false, Q, no, oo, false, 1.0, Foo.d.p, to, 0, true);
       t.d.d = {tv, to, tv, to};
       t.d.p = S->ws.get<double>(size_t(tv) * to * tv * to);
-      take_tbox(S, c2, t.d);
+      if (rest) take_tbox(S, c2, t.d);
+      else fill(t.d.p, t.d.size(), 0.0, s);   // the trial doubles enter only with the cached values
       Lkc.d.d = {nj, to, tv};   // zero tangent (occupied-virtual block is unchanged)
       const int64_t tl = int64_t(tv) * to * tv * to;
       double* omT = S->ws.get<double>(size_t(tl));
-      ccsd_block(S, Mode::Tangent, Lai, Lac, Lki, Lkc, Fvv, Foo, t, omT, false, c1);
+      ccsd_block(S, Mode::Tangent, Lai, Lac, Lki, Lkc, Fvv, Foo, t, omT, false, c1, rest);
       put_tbox(S, omT, s2);
     }
   }

@@ -68,8 +68,11 @@ inline size_t ws_bytes(const Dims& d) {
 inline size_t ccsd_cache_bytes(const Dims& d) {
   if (d.to <= 0 || d.tv <= 0) return 0;
   const int64_t o = d.to, v = d.tv;
-  const int64_t need = d.nj * (v * o + v * v + o * o + o * v) + v * v + o * o + v * v * v * v +
-                       14 * (v * o * v * o) + 4 * (o * o * o * o) + 4 * v * v + 4 * o * o + d.no * v * v * v;
+  // inputs, the value tensors of one residual, g~_Kcbd, and the ladder operands of the
+  // tangent: g~ as [(ab)][(cd)] and X_Kbij
+  const int64_t need = d.nj * (v * o + v * v + o * o + o * v) + v * v + o * o + 2 * v * v * v * v +
+                       14 * (v * o * v * o) + 4 * (o * o * o * o) + 4 * v * v + 4 * o * o + d.no * v * v * v +
+                       d.no * v * o * o;
   return size_t(need) * 8 + 64 * 256;
 }
 
@@ -94,13 +97,13 @@ inline size_t davidson_bytes(int64_t dim, int max_subspace, int n_roots) {
 }
 
 // Allowance for the converted copies of constant GEMM operands (the dressed Cholesky
-// vectors, Lai, Lov, Z and u) that a system caches while sigma runs on the tensor cores:
+// vectors, Lai, Lov, Z, u and the ladder's g~_(ab)(cd)) that a system caches while sigma runs on the tensor cores:
 // `bytes_per_element` summed over the precisions in use (2 per bfloat16 piece; 16 plus
 // exponents for the 8 integer digits of the binary64 emulation). An estimate, not a bound
 // the cache enforces.
 inline size_t operand_cache_allowance(const Dims& d, int bytes_per_element) {
   if (bytes_per_element <= 0) return 0;
-  const int64_t elems = d.nj * d.nn() + 3 * d.nj * d.dS + d.nd;
+  const int64_t elems = d.nj * d.nn() + 3 * d.nj * d.dS + d.nd + d.tv * d.tv * d.tv * d.tv;
   return size_t(elems) * size_t(bytes_per_element);
 }
 

@@ -22,6 +22,8 @@ struct CCSDCache {
   Arena arena;
   std::vector<double*> slots;
   DT G;   // g~_Kcbd = Lt^J_Kc Lt^J_bd, K over all occupied orbitals, c, b, d CCSD-active
+  DT G2;  // g~_acbd as a [(ab)][(cd)] matrix: the constant operand of the ladder tangent
+  DT X;   // X_Kbij = sum_cd g~_Kcbd t_cidj, for the dressing part of the ladder tangent
   const char* arena_base() const { return arena.base(); }
   size_t arena_size() const { return arena.capacity(); }
 };
@@ -69,6 +71,10 @@ struct mlcc_system {
   int lowp_prec = -1;
   int* tc_err = nullptr;
   mlcc::OperandCache* opcache = nullptr;   // bfloat16 pieces of Jacobian-constant operands
+  // J window of a sharded Jacobian transformation (mlcc_sigma_partial): while set, nj, Lt,
+  // Lai, Lov and Z describe the Cholesky vectors [jwin0, jwin0 + nj) only
+  bool jwin = false;
+  int jwin0 = 0;
   mlcc::Arena persist;     // the buffers above
   mlcc::Arena ws;          // scratch
   int64_t workspace_bytes = 0;
@@ -102,7 +108,12 @@ enum SigmaParts : unsigned {
   SIGMA_DOUBLES_TO_SINGLES = 1u,   // singles terms driven by c2
   SIGMA_CC2_DOUBLES = 2u,          // the P_S rows (and zero P_T rows before the CCSD part)
   SIGMA_CCSD_ROWS = 4u,            // the P_T rows
-  SIGMA_ALL = 7u
+  SIGMA_ALL = 7u,
+  // with this bit only the terms that sum over the Cholesky vectors run (over the system's
+  // current J window); the terms built from F~, X, Y, the cached CCSD value tensors, the
+  // orbital energies and the trial doubles alone are left out (a J-sharded evaluation adds
+  // them on one rank)
+  SIGMA_J_ONLY = 8u
 };
 void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision, unsigned parts = SIGMA_ALL);
 // folded CC2 Jacobian: out = A_eff(omega) c (singles and P_T rows; P_S rows zero), dout (if
@@ -117,7 +128,7 @@ mlcc_status excited_states_folded(mlcc_system* S, const mlcc_options* opt, doubl
 // from the cached g~_Kcbd instead of from the Cholesky vectors.
 void ccsd_block(mlcc_system* S, Mode mode, const Dual& Lai, const Dual& Lac, const Dual& Lki,
                 const Dual& Lkc, const Dual& Fvv, const Dual& Foo, const Dual& t, double* om_out,
-                bool cache_values, const double* c1);
+                bool cache_values, const double* c1, bool rest = true);
 void ccsd_cache_free(mlcc_system* S);
 void rank_gemm_lowp(mlcc_system* S, bool outer, const double* A, const double* B, double* C,
                     double alpha, double beta, int precision, bool b_is_u_source);

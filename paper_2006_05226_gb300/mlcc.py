@@ -36,7 +36,7 @@ STATUS = {v: k for k, v in dict(globals()).items()
           if k.startswith("MLCC_") and (k.startswith("MLCC_E_") or k in ("MLCC_OK", "MLCC_PENDING"))}
 
 # every symbol include/mlcc.h declares
-EXPORTS = ["mlcc_default_options", "mlcc_cnto", "mlcc_ctx_create", "mlcc_ctx_create_budget", "mlcc_orbitals", "mlcc_ctx_destroy", "mlcc_ctx_stream",
+EXPORTS = ["mlcc_default_options", "mlcc_sigma_partial", "mlcc_cnto", "mlcc_ctx_create", "mlcc_ctx_create_budget", "mlcc_orbitals", "mlcc_ctx_destroy", "mlcc_ctx_stream",
            "mlcc_last_error", "mlcc_kernel_timing", "mlcc_kernel_time", "mlcc_system_create",
            "mlcc_system_destroy", "mlcc_system_info", "mlcc_orbital_order", "mlcc_t1_transform",
            "mlcc_fock_t1", "mlcc_omega", "mlcc_ground_state", "mlcc_jacobian_prepare",
@@ -150,6 +150,7 @@ def load():
         "mlcc_ground_state": (c_int, [P, POINTER(mlcc_options), P, P, POINTER(mlcc_gs_info)]),
         "mlcc_jacobian_prepare": (c_int, [P, P, P]),
         "mlcc_sigma": (c_int, [P, c_int32, P, P, c_int32]),
+        "mlcc_sigma_partial": (c_int, [P, c_int32, c_int32, c_int32, c_int32, P, P, c_int32]),
         "mlcc_excited_states": (c_int, [P, POINTER(mlcc_options), D, P, POINTER(mlcc_es_info)]),
         "mlcc_solve": (c_int, [P, POINTER(mlcc_problem), P, P, POINTER(mlcc_options), POINTER(mlcc_result)]),
         "mlcc_solve_device": (c_int, [P, POINTER(mlcc_problem), P, P, POINTER(mlcc_options),
@@ -386,6 +387,24 @@ class System:
         self.ctx.after()
         return out
 
+    def sigma_partial(self, c, j_begin, j_end, with_rest, precision=MLCC_FP64):
+        """mlcc_sigma_partial: the part of sigma over the Cholesky vectors [j_begin, j_end),
+        plus the terms that do not sum over them when with_rest."""
+        c = c.reshape(-1, self.dims.vector_len)
+        out = self._new(c.shape[0], self.dims.vector_len)
+        self.ctx.before(c, out)
+        _check(load().mlcc_sigma_partial(self.handle, int(j_begin), int(j_end), int(bool(with_rest)), c.shape[0],
+                                         _ptr(c), _ptr(out), precision))
+        self.ctx.after()
+        return out
+
+    def sigma_sharded(self, c, rank, world, precision=MLCC_FP64, group=None):
+        """sigma split over `world` ranks by Cholesky index (shard_range), summed with one
+        torch.distributed all-reduce: on the device under NCCL, through host memory under
+        gloo. Rank 0 adds the terms that do not sum over J."""
+        return sharded_sum(lambda j0, j1, rest: self.sigma_partial(c, j0, j1, rest, precision),
+                           self.n_chol, rank, world, group)
+
     def excited_states(self, opts=None, want_vectors=True):
         opts = opts or default_options()
         w = (c_double * opts.n_roots)()
@@ -508,6 +527,33 @@ def cnto(ctx, chol, fock, n_occ, n_states, n_occ_active, n_vir_active=0, precisi
     ctx.after()
     _check(st)
     return Solution(n_occ_active=res.n_occ_active, n_vir_active=res.n_vir_active, **out)
+
+
+def shard_range(n_chol, rank, world):
+    """[j_begin, j_end) of Cholesky vectors for one of `world` ranks: contiguous, in rank
+    order, sizes differing by at most one (the first n_chol % world ranks take one more)."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("need 0 <= rank < world")
+    q, r = divmod(int(n_chol), int(world))
+    j0 = rank * q + min(rank, r)
+    return j0, j0 + q + (1 if rank < r else 0)
+
+
+def sharded_sum(partial, n_chol, rank, world, group=None):
+    """The sum over ranks of partial(j_begin, j_end, with_rest) (a torch tensor) for this
+    rank's shard_range, with_rest on rank 0 only: one torch.distributed all-reduce, on the
+    device under NCCL and through host memory under gloo."""
+    j0, j1 = shard_range(n_chol, rank, world)
+    part = partial(j0, j1, rank == 0)
+    if world == 1:
+        return part
+    import torch.distributed as dist
+    if dist.get_backend(group) == "nccl" or part.device.type == "cpu":
+        dist.all_reduce(part, group=group)
+        return part
+    host = part.cpu()
+    dist.all_reduce(host, group=group)
+    return host.to(part.device)
 
 
 def vector_len(n_mo, n_occ, n_chol, level):
