@@ -8,15 +8,16 @@ the Jacobian intermediates, and the Davidson solve for the lowest roots with sig
 (and, on the mixed path, the binary64 refinement). value = sigma-vectors evaluated in the
 Davidson solves of all ranks / max over ranks of the timed wall time (CUDA events).
 
-Workload: 340 orbitals (40 occupied, 300 virtual), 1500 Cholesky vectors, CCSD-active
-10 occupied / 60 virtual, CC2-active the rest, 4 roots (the second configuration of the
-paper-shaped workloads); synthetic seeded inputs (synth/), larger than L2 (L is 1.39 GB).
+Workload (default): the three-level system, 560 orbitals (60 occupied, 500 virtual), 2500
+Cholesky vectors, CCSD-active 20 occupied / 140 virtual inside CC2-active 40 / 300, CCS the
+rest, 4 roots: the largest of the paper-shaped workloads that one GPU holds (the 1350-orbital
+MLCC2 workload needs more device memory than a GB300 has, by mlcc_solve_footprint; the line
+states both figures). Synthetic seeded inputs (synth/), larger than L2 (L is 6.3 GB).
+--workload mid runs the 340-orbital, 1500-vector two-level system (CCSD 10/60, CC2 the rest).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|bf16|bf16x3|bf16x6|fp64e]
                   [--refine fp64|fp64e] [--impl ours|reference]
 
---workload three_level runs the same step on the 560-orbital three-level workload (60 occ /
-500 vir, 2500 Cholesky vectors, CCSD-active 20/140 inside CC2-active 40/300, CCS rest).
 --workload serving replays the serving mix instead (synth.serving_request_spec: occupied
 20-80, virtual 150-600, N_J = 5 (occ + vir), active fraction 0.1-0.3, CCS/CCSD or MLCC2,
 4 roots) with exponential arrival gaps at --rate requests/s through the serving loop
@@ -40,7 +41,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Davidson sigma-vectors/s"
 UNIT = "sigma-vectors/s"
-WORKLOAD = "mid"
+WORKLOAD = "three_level"
 # FP64 DFMA peak of the GB300 SM: 152 SMs x 2 FP64 FMA/clock x 2 flop x 2.070 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
@@ -162,14 +163,16 @@ def rank_spec(rank):
     return replace(CONFIGS[WORKLOAD], seed=CONFIGS[WORKLOAD].seed + rank)
 
 
-def cpu_sample_oracle(system, seconds_hint=30.0):
-    """The oracle, as it stands, on the host cores: one Jacobian transformation of the
-    same system by its explicit real-arithmetic MLCC2 formula (Appendix A), at seeded
-    random amplitudes. Returns (sigma-vectors/s, cores, description)."""
+def cpu_sample_oracle(system, n_chol=None):
+    """The oracle, as it stands, on the host cores: one Jacobian transformation of the same
+    system by its explicit real-arithmetic MLCC2 formula (Appendix A; the CCSD-block terms
+    are not in it), at seeded random amplitudes, with the first n_chol Cholesky vectors
+    (all by default). Returns (sigma-vectors/s, cores, description, seconds)."""
     import numpy as np
     from oracle.mlcc import MLCCSystem, sigma_mlcc2_paper
     cores = len(os.sched_getaffinity(0))
-    o = MLCCSystem(system.L, system.fock, system.spec.n_occ, system.level)
+    nj = system.L.shape[0] if n_chol is None else int(n_chol)
+    o = MLCCSystem(system.L[:nj], system.fock, system.spec.n_occ, system.level)
     rng = np.random.default_rng(0)
     t1 = 0.01 * rng.standard_normal((o.nv, o.no))
     x2 = 0.01 * rng.standard_normal(o.doubles_shape())
@@ -180,8 +183,9 @@ def cpu_sample_oracle(system, seconds_hint=30.0):
     t0 = time.perf_counter()
     sigma_mlcc2_paper(o, t1, x2, c1, c2)
     dt = time.perf_counter() - t0
-    desc = (f"one sigma-vector of the same {system.spec.n_mo}-orbital system by the oracle's explicit "
-            "MLCC2 Jacobian formula (Appendix A; CCSD-block terms not included), FP64 numpy")
+    desc = (f"one sigma-vector of the same {system.spec.n_mo}-orbital system ({nj} of its {system.L.shape[0]} "
+            "Cholesky vectors) by the oracle's explicit MLCC2 Jacobian formula (Appendix A; CCSD-block terms not "
+            "included), FP64 numpy")
     return 1.0 / dt, cores, desc, dt
 
 
@@ -192,36 +196,81 @@ def set_blas_threads():
 
 
 def run_reference(args):
+    """--impl reference: the oracle's Jacobian transformation on the host cores, on this
+    workload. A whole sigma takes tens of seconds here, so each step times one sigma of the
+    same system with its first quarter of the Cholesky vectors, and the time is scaled to a
+    whole sigma by the ratio of one whole sigma to one such sigma, both measured in the
+    warm-up (the sigma cost is not proportional to the vector count, hence the measured
+    ratio). Rank 0 alone runs it."""
     rank, world, local = dist_env()
     if rank != 0:
         return 0
     set_blas_threads()
     from synth import CONFIGS, make_system
     system = make_system(CONFIGS[WORKLOAD])
-    for _ in range(args.warmup):
-        cpu_sample_oracle(system)
+    nj = system.L.shape[0]
+    sub = max(1, nj // 4)
+    _, cores, desc_full, t_full = cpu_sample_oracle(system)
+    _, _, _, t_sub = cpu_sample_oracle(system, sub)
+    ratio = t_full / t_sub
+    for _ in range(max(0, args.warmup - 1)):
+        cpu_sample_oracle(system, sub)
     times = []
-    cores, desc = None, None
     for _ in range(args.steps):
-        v, cores, desc, dt = cpu_sample_oracle(system)
-        times.append(dt)
+        _, cores, _, dt = cpu_sample_oracle(system, sub)
+        times.append(dt * ratio)
     value = args.steps / sum(times)
+    sample = (f"per step one sigma-vector of the same {system.spec.n_mo}-orbital system with its first {sub} of {nj} "
+              f"Cholesky vectors by the oracle's explicit MLCC2 Jacobian formula (Appendix A; CCSD-block terms not "
+              f"included), FP64 numpy, its time scaled by {ratio:.3f} = (one whole sigma, {t_full:.2f} s) / "
+              f"(one such sigma, {t_sub:.2f} s), both measured in the warm-up")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(args, "fp64"),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
+def workload_label(s):
+    """What the workload is, with its sizes and levels."""
+    cc2_all = s.s_occ == s.n_occ and s.s_vir == s.n_vir
+    if s.t_occ and s.t_vir and not cc2_all:
+        kind = (f"three-level MLCCSD: CCSD-active {s.t_occ}/{s.t_vir} inside CC2-active {s.s_occ}/{s.s_vir}, "
+                f"CCS the rest")
+    elif s.t_occ and s.t_vir:
+        kind = f"MLCCSD, two levels: CCSD-active {s.t_occ}/{s.t_vir}, CC2 the rest"
+    elif cc2_all:
+        kind = "CC2 (every orbital CC2-active)"
+    else:
+        kind = f"MLCC2: CC2-active {s.s_occ}/{s.s_vir}, CCS the rest"
+    return (f"{kind}; {s.n_mo} orbitals ({s.n_occ} occ / {s.n_vir} vir), {s.n_chol} Cholesky vectors, "
+            f"{s.n_roots} roots")
+
+
+def larger_workload_excluded(opts_mixed):
+    """The larger paper-shaped workload and why it is not the bench's: its device footprint."""
+    from paper_2006_05226_gb300 import mlcc
+    from synth import CONFIGS
+    from synth.generator import level_map
+    s = CONFIGS["mlcc2_large"]
+    lev = level_map(s.n_occ, s.n_vir, s.s_occ, s.s_vir, s.t_occ, s.t_vir)
+    fp = mlcc.solve_footprint(s.n_mo, s.n_occ, s.n_chol, lev, opts_mixed)
+    try:
+        import torch
+        total = int(torch.cuda.get_device_properties(0).total_memory)
+    except Exception:
+        total = None
+    return {"workload": workload_label(s), "footprint_bytes": fp, "device_bytes": total,
+            "fits": bool(total is not None and fp <= total)}
+
+
 def config_dict(args, prec):
     from synth import CONFIGS
     s = CONFIGS[WORKLOAD]
-    return {"workload": f"MLCCSD three-level: {s.n_mo} orbitals ({s.n_occ} occ / {s.n_vir} vir), "
-                        f"{s.n_chol} Cholesky vectors, CCSD-active {s.t_occ}/{s.t_vir}, "
-                        f"CC2-active {s.s_occ}/{s.s_vir}, {s.n_roots} roots",
+    return {"workload": workload_label(s),
             "n_mo": s.n_mo, "n_occ": s.n_occ, "n_chol": s.n_chol, "ccsd_active": [s.t_occ, s.t_vir],
             "cc2_active": [s.s_occ, s.s_vir], "n_roots": s.n_roots, "precision": prec,
             "l2": f"inputs larger than L2 (L^J_pq is {s.n_chol * s.n_mo ** 2 * 8 / 1e9:.2f} GB)",
@@ -253,11 +302,12 @@ def run_serving(args):
     prec, refine = precs[args.precision], precs[args.refine]
     split = prec in (mlcc.MLCC_BF16, mlcc.MLCC_BF16X3, mlcc.MLCC_BF16X6)
 
-    def opts_for(spec, p):
+    def opts_for(spec, p, graph=1):
         sp = p in (mlcc.MLCC_BF16, mlcc.MLCC_BF16X3, mlcc.MLCC_BF16X6)
         return mlcc.default_options(n_roots=spec.n_roots, precision=p, gs_precision=p, refine_fp64=1,
                                     lowp_res_tol=1e-5, refine_precision=refine,
-                                    gs_tol=1e-9 if sp else 1e-11, gs_energy_tol=1e-10 if sp else 1e-12)
+                                    gs_tol=1e-9 if sp else 1e-11, gs_energy_tol=1e-10 if sp else 1e-12,
+                                    sigma_graph=graph if args.sigma_graph else 0)
 
     # pinned host copies: the server borrows them until each result is polled
     host = []
@@ -281,7 +331,7 @@ def run_serving(args):
         sy, (Lp, Fp) = systems[k], host[k]
         t1 = time.perf_counter()
         w64 = mlcc.solve(ctx, Lp.numpy(), Fp.numpy(), sy.spec.n_occ, sy.level,
-                         opts_for(sy.spec, mlcc.MLCC_FP64)).omega
+                         opts_for(sy.spec, mlcc.MLCC_FP64, graph=0)).omega
         fp64_s.append(time.perf_counter() - t1)
         errs.append(float(np.max(np.abs(np.asarray(seq_w[k]) - w64))))
     ctx.close()
@@ -323,6 +373,7 @@ def run_serving(args):
                                    f"active fraction 0.1-0.3, CCS/CCSD or MLCC2, 4 roots), Poisson arrivals "
                                    f"at {args.rate} req/s", "requests": n, "slots": args.slots,
                        "rate_per_s": args.rate, "budget_bytes": int(info.budget_bytes),
+                       "sigma_graph": bool(args.sigma_graph),
                        "parallelism": f"replicas{world}"},
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "status": status, "peak_running": int(info.peak_running), "peak_admitted_bytes": int(info.peak_bytes),
@@ -385,13 +436,15 @@ def run_probe(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="mid", choices=["mid", "three_level", "serving"],
-                    help="mid: 340 orbitals (the benchmark); three_level: 560 orbitals, CCSD 20/140 inside "
-                         "CC2 40/300, CCS rest; serving: the request mix")
+    ap.add_argument("--workload", default="three_level", choices=["mid", "three_level", "serving"],
+                    help="three_level (default): 560 orbitals, CCSD 20/140 inside CC2 40/300, CCS rest; "
+                         "mid: 340 orbitals, CCSD 10/60, CC2 the rest; serving: the request mix")
     ap.add_argument("--requests", type=int, default=8, help="serving: number of requests")
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent slots")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: arrivals per second")
     ap.add_argument("--fp64-sample", type=int, default=1, help="serving: requests also solved in binary64")
+    ap.add_argument("--sigma-graph", type=int, default=1,
+                    help="serving: replay each request's Jacobian transformation from a CUDA graph (1) or not (0)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
@@ -499,7 +552,8 @@ def main():
     elapsed = ev0.elapsed_time(ev1) / 1e3
     step_s = [a.elapsed_time(b) / 1e3 for a, b in zip(step_ev[:-1], step_ev[1:])]
     launches = mlcc.launch_count() - launches0
-    fams = {f: ctx.kernel_time(f) for f in ("rank_gemm_tc", "rank_gemm_f64e", "rank_gemm_f64")}
+    fams = {f: ctx.kernel_time(f) for f in ("rank_gemm_tc", "rank_gemm_f64e", "rank_gemm_f64",
+                                            "ladder_tc", "ladder_f64e", "ladder_f64")}
     phases = {f: ctx.kernel_time(f) for f in ("gs_omega", "jacobian_prepare", "sigma", "sigma_singles",
                                               "sigma_doubles_to_singles", "sigma_cc2_doubles",
                                               "sigma_ccsd_rows", "dav_update_G", "dav_ritz",
@@ -565,11 +619,16 @@ def main():
     pieces = {mlcc.MLCC_BF16: 1, mlcc.MLCC_BF16X3: 3, mlcc.MLCC_BF16X6: 6}
     # tensor-core products per algorithmic flop: split-bf16 pieces, or the 36 digit
     # products of the binary64 emulation
-    ops = {"rank_gemm_tc": pieces.get(prec, 3), "rank_gemm_f64e": 36, "rank_gemm_f64": None}
+    ops = {"rank_gemm_tc": pieces.get(prec, 3), "rank_gemm_f64e": 36, "rank_gemm_f64": None,
+           "ladder_tc": pieces.get(prec, 3), "ladder_f64e": 36, "ladder_f64": None}
     kernels = {"rank_gemm_tc": "k_tc_gemm: Cholesky-rank doubles GEMMs, split bf16 (tcgen05, fp32 accumulate)",
                "rank_gemm_f64e": "k_tc_gemm (emulation mode) + k_emu_reduce: Cholesky-rank GEMMs "
                                  "in binary64 from exact bf16 integer digits",
-               "rank_gemm_f64": "k_dgemm: Cholesky-rank GEMMs on the binary64 FMA units"}
+               "rank_gemm_f64": "k_dgemm: Cholesky-rank GEMMs on the binary64 FMA units",
+               "ladder_tc": "k_tc_gemm: the CCSD-row ladder sum_cd g~_acbd c_cidj, [(ab)][(cd)] x [(cd)][(ij)], "
+                            "split bf16 (tcgen05, fp32 accumulate)",
+               "ladder_f64e": "k_tc_gemm (emulation mode) + k_emu_reduce: the CCSD-row ladder in binary64",
+               "ladder_f64": "k_dgemm: the CCSD-row ladder on the binary64 FMA units"}
     families = {}
     for f, (n, ms, fl) in fams.items():
         if n == 0:
@@ -622,7 +681,13 @@ def main():
             "omega": [float(x) for x in omegas], "e_corr": gs.e_corr,
             "max_abs_omega_err_vs_fp64_gpu_Ha": err_fp64, "fp64_gpu_solve": fp64_solve,
             "roofline": roof, "clocks": clk, "gpu_launches": int(launches), "e2e": e2e,
-            "breakdown": breakdown}
+            "breakdown": breakdown,
+            "precision_notes": "split-bf16 phases (ground state, Davidson sigma) then a binary64-class refinement "
+                               f"({args.refine}); in the split phase the Davidson vector arithmetic (dot products, "
+                               "Gram-Schmidt, Ritz vectors) runs in binary32 and the small subspace eigenproblem "
+                               "on the host in binary64; omega and e_corr are those of the refined solve"}
+    if WORKLOAD == "three_level":
+        line["config"]["larger_workload_excluded"] = larger_workload_excluded(opts)
     if world == 1 and not args.no_cpu_baseline:
         set_blas_threads()
         v, cores, desc, dt = cpu_sample_oracle(system)

@@ -141,7 +141,13 @@ typedef struct {
   int32_t refine_precision; /* precision of the refinement after a low-precision phase
                              (ground-state polish and Davidson sweeps): MLCC_FP64 or
                              MLCC_FP64E                                                 */
-  int32_t reserved;       /* zero                                                     */
+  int32_t sigma_graph;    /* non-zero: the Davidson solver captures the Jacobian
+                             transformation of each precision in a CUDA graph (after one
+                             eager evaluation that fills the operand caches) and replays it
+                             for every trial vector, the vector staged through fixed
+                             buffers; it saves the launches of the many small kernels of a
+                             small system. Results are bitwise those of the eager path.
+                             Not used while kernel timing is enabled. Default 0          */
 } mlcc_options;
 
 typedef struct {
@@ -185,7 +191,8 @@ const char* mlcc_last_error(void);
    GEMMs in MLCC_FP64E) and "rank_gemm_f64" (the same GEMMs on the binary64 FMA units);
    and phases of the solvers: "gs_omega" (one ground-state residual), "jacobian_prepare",
    "sigma" (one Jacobian transformation; inside it "sigma_singles", "sigma_doubles_to_singles",
-   "sigma_cc2_doubles", "sigma_ccsd_rows"), "dav_update_G" (subspace matrix), "dav_ritz"
+   "sigma_cc2_doubles", "sigma_ccsd_rows", and inside the last the ladder GEMM of the CCSD
+   rows, sum_cd g~_acbd c_cidj: "ladder_tc", "ladder_f64e" or "ladder_f64" by precision), "dav_update_G" (subspace matrix), "dav_ritz"
    (Ritz vectors and residuals), "dav_orthonormalise" (Gram-Schmidt of new directions).
    Phases contain the GEMM families launched inside them.
    mlcc_kernel_time returns launches, summed milliseconds and summed algorithmic flops
@@ -263,8 +270,8 @@ mlcc_status mlcc_sigma(mlcc_system* sys, int32_t n_vec, const double* c_dev,
    Ranks whose ranges tile [0, n_chol), exactly one of them with with_rest, obtain
    mlcc_sigma's result by one sum (an all-reduce) of their outputs per sigma batch. Here
    each rank holds the whole prepared system and the work is what is split. Layout,
-   precisions and errors as mlcc_sigma; j_begin == j_end is allowed (the rest terms alone, or
-   zero). In a split-bfloat16 precision the cached bfloat16 operands are not used inside a
+   precisions and errors as mlcc_sigma; the range must not be empty (0 <= j_begin < j_end <=
+   n_chol, else MLCC_E_ARG), so there are at most n_chol ranks. In a split-bfloat16 precision the cached bfloat16 operands are not used inside a
    range: each call converts its operands. */
 mlcc_status mlcc_sigma_partial(mlcc_system* sys, int32_t j_begin, int32_t j_end, int32_t with_rest,
                                int32_t n_vec, const double* c_dev, double* sigma_dev, int32_t precision);
@@ -452,6 +459,35 @@ typedef struct {
 mlcc_status mlcc_cnto(mlcc_ctx* ctx, int32_t n_mo, int32_t n_occ, int32_t n_chol,
                       const double* chol_dev, const double* fock_dev, int32_t n_states,
                       int32_t precision, mlcc_cnto_result* res);
+
+/* ---- Cholesky vectors: MO-screened decomposition and MO vectors ---------------------- */
+/* Sec. 2.4. The AO integral matrix g has rows and columns indexed by AO pairs (ab):
+   g[(ab)][(cd)] = (ab|cd), symmetric positive semi-definite, row-major [n_pairs][n_pairs]
+   device memory. The decomposition takes, one at a time, the pair K with the largest
+   screened diagonal w[K] D[K] (D the diagonal updated by the vectors so far) and stops when
+   that value is below tau (Eq. standard_cholesky; w = 1 without screening); each new vector
+   is L[:, J] = (g[:, K] - L[:, :J] L[K, :J]^T) / sqrt(D[K]).
+
+   mlcc_mo_screening: w_dev [n_ao * n_ao], w[(ab)] = nu_a nu_b with nu_a = max_p C[a][p]^2
+   over the active MO coefficients c_active_dev [n_ao][n_active] (Eqs. mo_screening and
+   cd_screening). No synchronisation. */
+mlcc_status mlcc_mo_screening(mlcc_ctx* ctx, int32_t n_ao, int32_t n_active, const double* c_active_dev,
+                              double* w_dev);
+/* The decomposition: w_dev [n_pairs] or NULL (unscreened); l_dev [n_pairs][max_vectors]
+   (column J is vector J); pivots_host [max_vectors] the basis pairs in order; diag_dev
+   [n_pairs] or NULL: the final D; *n_vectors the vectors made (at most max_vectors).
+   Synchronises (the host reads each step's largest diagonal to decide the stop). */
+mlcc_status mlcc_cholesky_decompose(mlcc_ctx* ctx, int64_t n_pairs, const double* g_dev, const double* w_dev,
+                                    double tau, int32_t max_vectors, int32_t* pivots_host, double* l_dev,
+                                    double* diag_dev, int32_t* n_vectors);
+/* Algorithm 1: MO Cholesky vectors from the basis, L^J_pq = sum_K X_pqK [Q^-T]_KJ with
+   X_pqK = sum_ab C_ap C_bq (ab|K) and S = g[B, B] = Q Q^T. g_dev as above with n_pairs =
+   n_ao^2; pivots_host [n_vectors]; c_dev [n_ao][n_mo]; lmo_dev [n_vectors][n_mo][n_mo] (the
+   layout of mlcc_problem's Cholesky vectors). MLCC_E_ARG if S is not positive definite.
+   Synchronises. */
+mlcc_status mlcc_cholesky_mo_vectors(mlcc_ctx* ctx, int32_t n_ao, int32_t n_mo, const double* g_dev,
+                                     const int32_t* pivots_host, int32_t n_vectors, const double* c_dev,
+                                     double* lmo_dev);
 
 /* ---- allocation-free variant ------------------------------------------------------ */
 /* The paper has no counterpart to this entry point; it exists for callers that cannot let

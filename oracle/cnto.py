@@ -26,7 +26,7 @@ from .davidson import excited_states
 from .mlcc import MLCCSystem, solve_ground_state
 
 
-def ccs_states(L, F, no, n_states, res_tol=1e-10):
+def ccs_states(L, F, no, n_states, res_tol=1e-11):
     """(omega [n_states], R [n_states, N_v, N_o]) of the CCS Jacobian, R unit 2-norm."""
     n = F.shape[0]
     sys = MLCCSystem(L, F, no, np.zeros(n, dtype=np.int8))

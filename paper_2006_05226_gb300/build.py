@@ -9,7 +9,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libmlcc.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["linalg_f64.cu", "method.cu", "ccsd_block.cu", "solvers.cu", "api.cu", "tc_gemm.cu",
-           "tc_emu.cu", "vec32.cu", "noalloc.cu", "serve.cu", "folded.cu", "folded_solve.cu", "cnto.cu", "small_eig.cpp", "scheduler.cpp"]
+           "tc_emu.cu", "vec32.cu", "noalloc.cu", "serve.cu", "folded.cu", "folded_solve.cu", "cnto.cu", "cholesky.cu", "small_eig.cpp", "scheduler.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

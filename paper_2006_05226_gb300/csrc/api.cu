@@ -379,6 +379,7 @@ void mlcc_system_destroy(mlcc_system* sys) {
   sys->ctx->held -= sys->workspace_bytes;
   cudaSetDevice(sys->ctx->device);
   cudaStreamSynchronize(sys->ctx->stream);
+  sigma_graphs_free(sys);
   ccsd_cache_free(sys);
   operand_cache_free(sys->opcache);
   delete sys;
@@ -429,6 +430,7 @@ mlcc_status mlcc_t1_transform(mlcc_system* S, const double* t1, double* lt) {
     MLCC_REQUIRE(S && t1 && lt, "mlcc_t1_transform: NULL argument");
     MLCC_CUDA(cudaSetDevice(S->ctx->device));
     S->prepared = false;
+    sigma_graphs_free(S);
     operand_cache_clear(S->opcache);
     dress(S, t1, lt, nullptr);
     return MLCC_OK;
@@ -440,6 +442,7 @@ mlcc_status mlcc_fock_t1(mlcc_system* S, const double* t1, double* f) {
     MLCC_REQUIRE(S && t1 && f, "mlcc_fock_t1: NULL argument");
     MLCC_CUDA(cudaSetDevice(S->ctx->device));
     S->prepared = false;
+    sigma_graphs_free(S);
     operand_cache_clear(S->opcache);
     dress(S, t1, S->Lt, S->ht);
     build_fock(S, S->ht, S->Lt, f);
@@ -541,8 +544,8 @@ mlcc_status mlcc_sigma_partial(mlcc_system* S, int32_t j_begin, int32_t j_end, i
   return guard([&] {
     MLCC_REQUIRE(S && c && sigma, "mlcc_sigma_partial: NULL argument");
     MLCC_REQUIRE(n_vec >= 0, "mlcc_sigma_partial: n_vec < 0");
-    MLCC_REQUIRE(0 <= j_begin && j_begin <= j_end && j_end <= S->nj,
-                 "mlcc_sigma_partial: need 0 <= j_begin <= j_end <= n_chol");
+    MLCC_REQUIRE(0 <= j_begin && j_begin < j_end && j_end <= S->nj,
+                 "mlcc_sigma_partial: need 0 <= j_begin < j_end <= n_chol");
     MLCC_REQUIRE(precision >= MLCC_FP64 && precision <= MLCC_FP64E, "mlcc_sigma_partial: unknown precision");
     if (!S->prepared) throw Error(MLCC_E_STATE, "mlcc_sigma_partial: call mlcc_jacobian_prepare first");
     MLCC_CUDA(cudaSetDevice(S->ctx->device));

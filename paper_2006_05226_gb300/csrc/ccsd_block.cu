@@ -111,7 +111,8 @@ struct Eval {
 // the second part from d g~_acbd = - c_aK g~_Kcbd - c_bK g~_Kdac and the symmetry of t,
 // with X_Kbij = sum_cd g~_Kcbd t_cidj built once at the ground state. The first part is one
 // GEMM of [(ab)][(cd)] x [(cd)][(ij)] with the cached g~ as its constant operand (2 v^4 o^2
-// flop): the O(o^2 v^4) contraction of the CCSD rows, timed as the "ladder" family.
+// flop): the O(o^2 v^4) contraction of the CCSD rows, timed as the "ladder_tc" (split
+// bfloat16), "ladder_f64e" or "ladder_f64" family by the precision it runs in.
 void ladder_tangent(mlcc_system* S, const DT& dt, const double* c1, DT& om_d) {
   cudaStream_t s = S->ctx->stream;
   const int64_t o = S->to, v = S->tv, no = S->no;
@@ -130,8 +131,9 @@ void ladder_tangent(mlcc_system* S, const DT& dt, const double* c1, DT& om_d) {
     g.A = C.G2.p; g.lda = v * v; g.a_const = true;
     g.B = dcd.p; g.ldb = o * o;
     g.C = W.p; g.ldc = o * o;
-    timed(S, "ladder", 2.0 * double(v * v) * double(v * v) * double(o * o),
-          [&] { gemm_f64(g, S->ws, s, S->ctx->sm_count); });
+    const int lp = lowp_precision();   // the precision this GEMM runs in
+    timed(S, lp == 0 ? "ladder_f64" : (lp == MLCC_FP64E ? "ladder_f64e" : "ladder_tc"),
+          2.0 * double(v * v) * double(v * v) * double(o * o), [&] { gemm_f64(g, S->ws, s, S->ctx->sm_count); });
     eperm("abij->aibj", 1.0, W, 1.0, om_d, s);
   }
   // Y[a][(b i j)] = sum_K c_aK X[K][(b i j)]; c1 rows are the CCSD virtuals, stride no

@@ -102,7 +102,7 @@ mlcc_status cnto_build(mlcc_ctx* ctx, int n, int no, int nj, const double* chol,
   mlcc_options opt;
   mlcc_default_options(&opt);
   opt.n_roots = n_states;
-  opt.es_res_tol = 1e-9;
+  opt.es_res_tol = 1e-11;
   Arena work;
   const int64_t rows = res->block_rows > 0
                            ? std::min<int64_t>(d, res->block_rows)

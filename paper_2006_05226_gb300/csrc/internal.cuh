@@ -31,6 +31,7 @@ void set_last_error(const std::string& msg);
   } while (0)
 // every kernel launch is followed by MLCC_CHECK_LAUNCH(), which also counts it
 void count_launch();
+void count_launches(int64_t n);   // kernels of a replayed CUDA graph
 #define MLCC_CHECK_LAUNCH()          \
   do {                               \
     ::mlcc::count_launch();          \

@@ -422,6 +422,7 @@ void omega_eval(mlcc_system* S, const double* t1, const double* x2, bool gs_mode
   const int n = S->n, no = S->no, nv = S->nv, nj = S->nj, so = S->so, sv = S->sv;
   const int64_t nn = int64_t(n) * n, dS = S->dS;
   S->prepared = false;
+  sigma_graphs_free(S);
   operand_cache_clear(S->opcache);
   Scope sc(S->ws);
   dress(S, t1, S->Lt, S->ht);
@@ -511,6 +512,7 @@ void jacobian_prepare(mlcc_system* S, const double* t1, const double* x2) {
   const int64_t dS = S->dS;
   S->prepared = false;
   S->lowp_prec = -1;
+  sigma_graphs_free(S);   // their kernels point into the caches cleared here
   operand_cache_clear(S->opcache);
   ccsd_cache_free(S);
   Scope sc(S->ws);

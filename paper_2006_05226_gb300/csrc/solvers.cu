@@ -13,11 +13,16 @@
 #include <cstdlib>
 
 namespace mlcc {
+int64_t launch_count();
 
 namespace {
 inline int nblk(int64_t n) { return int(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 16384))); }
 
-// quasi-Newton step on (t1, tT): p = x - Omega / eps, e = Omega / eps
+// quasi-Newton step on (t1, tT): p = x - Omega / eps, e = Omega / eps. The CCSD-block part
+// is taken on the symmetric (admissible) amplitudes: x and Omega are averaged with their
+// (ai) <-> (bj) transposes. Without that, the rounding of a split-precision phase leaves an
+// antisymmetric part in tT on which the residual has no eps-diagonal term, so the
+// quasi-Newton step cannot remove it and the refinement stalls on it.
 __global__ void k_qn(const double* t1, const double* tT, const double* om1, const double* omT,
                      const double* eps, int no, int nv, int tv, int to, double* p, double* e) {
   const int64_t n1 = int64_t(nv) * no, nt = int64_t(tv) * to * tv * to, total = n1 + nt;
@@ -35,8 +40,9 @@ __global__ void k_qn(const double* t1, const double* tT, const double* om1, cons
       const int b = int(t % tv); t /= tv;
       const int i = int(t % to);
       const int a = int(t / to);
-      x = tT[k - n1];
-      om = omT[k - n1];
+      const int64_t kt = ((int64_t(b) * to + j) * tv + a) * to + i;   // (bj, ai)
+      x = 0.5 * (tT[k - n1] + tT[kt]);
+      om = 0.5 * (omT[k - n1] + omT[kt]);
       den = eps[no + a] - eps[i] + eps[no + b] - eps[j];
     }
     e[k] = om / den;
@@ -200,6 +206,8 @@ mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out
   int phase_prec = opt->gs_precision;
   const double lowp_switch = std::max(opt->gs_tol, 1e-7);
   std::vector<double> lowp_norms;   // residual norms of the low-precision phase
+  std::vector<double> phase_norms;  // residual norms since the last DIIS (re)start, binary64-class
+  int diis_restarts = 0;
   for (it = 1; it <= opt->max_gs_iter; ++it) {
     {
       LowpScope lowp(phase_prec, S->tc_err);
@@ -238,6 +246,7 @@ mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out
       }
       phase_prec = opt->refine_precision;   // the next iterations refine these amplitudes
       order.clear();            // the low-precision residuals do not belong in DIIS
+      phase_norms.clear();
       std::fill(Bm.begin(), Bm.end(), 0.0);
       e_old = e;
       continue;                 // re-evaluate the residual in binary64 before stepping
@@ -247,6 +256,21 @@ mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out
       break;
     }
     e_old = e;
+    // DIIS stagnation: when the binary64-class residual has not halved over four iterations,
+    // the extrapolation space has stopped helping (typically after a precision switch, where
+    // the history holds only the slow error directions); restart it from the newest pair
+    if (!split_phase) {
+      phase_norms.push_back(norm);
+      const size_t q = phase_norms.size();
+      if (q >= 5 && order.size() > 1 &&
+          norm > 0.5 * *std::min_element(phase_norms.end() - 5, phase_norms.end() - 1)) {
+        order.clear();
+        std::fill(Bm.begin(), Bm.end(), 0.0);
+        phase_norms.clear();
+        ++diis_restarts;
+        if (verbose()) std::fprintf(stderr, "[mlcc] GS it %3d DIIS restart\n", it);
+      }
+    }
     k_qn<<<nblk(len), 256, 0, s>>>(t1, tT, om1, omT, S->eps, no, nv, tv, to, pn, en);
     MLCC_CHECK_LAUNCH();
     // ring buffer of (p, e)
@@ -267,6 +291,9 @@ mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out
       Bm[size_t(slot) * dd + k] = dh[k];
       Bm[size_t(k) * dd + slot] = dh[k];
     }
+    // entries whose error is 1e4 times the newest one's carry no information for the
+    // extrapolation and only spoil the conditioning of its equations: drop them
+    while (order.size() > 2 && Bm[size_t(order.front()) * dd + order.front()] > 1e8 * dh[slot]) order.erase(order.begin());
     const int m = int(order.size());
     std::vector<double> coef(dd, 0.0);
     bool ok = false;
@@ -401,24 +428,93 @@ void vcopy(DavState& D, void* dst, const void* src, int64_t count) {
 }
 }  // namespace
 
+// Captured Jacobian transformations: sigma_eval(in -> out) in one precision as a CUDA graph.
+// A graph's kernels read their scratch from S->ws above the mark it was captured at, so it is
+// replayed only while the workspace mark is at or below that one (nothing live there).
+struct SigmaGraphs {
+  struct Entry {
+    int prec;
+    const double* in;
+    double* out;
+    size_t mark;
+    int64_t kernels;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Entry> entries;
+  std::vector<int> warmed;   // precisions evaluated eagerly since the last prepare
+  ~SigmaGraphs() {
+    for (auto& e : entries) cudaGraphExecDestroy(e.exec);
+  }
+};
+
+void sigma_graphs_free(mlcc_system* S) {
+  delete S->graphs;
+  S->graphs = nullptr;
+}
+
+// sigma of `in` into `out`: eagerly, or through a graph captured on the second call of a
+// precision (the first, eager one fills the operand caches, so the capture allocates nothing)
+static void sigma_one(mlcc_system* S, const double* in, double* out, int prec, bool graph) {
+  cudaStream_t s = S->ctx->stream;
+  if (!graph || S->ctx->timer.enabled) {
+    timed(S, "sigma", 0.0, [&] { sigma_eval(S, in, out, prec); });
+    return;
+  }
+  if (!S->graphs) S->graphs = new SigmaGraphs();
+  SigmaGraphs& G = *S->graphs;
+  for (auto& e : G.entries)
+    if (e.prec == prec && e.in == in && e.out == out && S->ws.mark() <= e.mark) {
+      MLCC_CUDA(cudaGraphLaunch(e.exec, s));
+      count_launches(e.kernels);
+      return;
+    }
+  if (std::find(G.warmed.begin(), G.warmed.end(), prec) == G.warmed.end()) {
+    sigma_eval(S, in, out, prec);
+    G.warmed.push_back(prec);
+    return;
+  }
+  SigmaGraphs::Entry e{prec, in, out, S->ws.mark(), 0, nullptr};
+  const int64_t l0 = launch_count();
+  cudaGraph_t g = nullptr;
+  MLCC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  try {
+    sigma_eval(S, in, out, prec);
+  } catch (...) {
+    cudaStreamEndCapture(s, &g);
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    throw;
+  }
+  MLCC_CUDA(cudaStreamEndCapture(s, &g));
+  e.kernels = launch_count() - l0;
+  const cudaError_t st = cudaGraphInstantiate(&e.exec, g, 0);
+  cudaGraphDestroy(g);
+  MLCC_CUDA(st);
+  G.entries.push_back(e);
+  MLCC_CUDA(cudaGraphLaunch(e.exec, s));
+}
+
 static void sigma_batch(mlcc_system* S, const double* C, double* Sg, int nvec, int64_t dim, int prec) {
   for (int k = 0; k < nvec; ++k)
     timed(S, "sigma", 0.0, [&] { sigma_eval(S, C + int64_t(k) * dim, Sg + int64_t(k) * dim, prec); });
   if (prec != MLCC_FP64) check_tc_error(S);
 }
-// sigma-vectors of the stored vectors [k0, k0 + nvec); binary32 storage goes through the
-// binary64 buffers tc (trial vector) and ts (sigma-vector)
-static void sigma_stored(DavState& D, int k0, int nvec, int prec, double* tc, double* ts) {
+// sigma-vectors of the stored vectors [k0, k0 + nvec); binary32 storage, and every storage
+// when sigma runs through a graph, goes through the binary64 buffers tc (trial vector) and
+// ts (sigma-vector)
+static void sigma_stored(DavState& D, int k0, int nvec, int prec, double* tc, double* ts, bool graph) {
   mlcc_system* S = D.S;
-  if (!D.f32()) {
+  if (!D.f32() && !graph) {
     sigma_batch(S, static_cast<const double*>(D.B(k0)), static_cast<double*>(D.Sg(k0)), nvec, D.dim, prec);
     return;
   }
   cudaStream_t s = S->ctx->stream;
   for (int k = 0; k < nvec; ++k) {
-    cvt_f2d(static_cast<const float*>(D.B(k0 + k)), tc, D.dim, s);
-    timed(S, "sigma", 0.0, [&] { sigma_eval(S, tc, ts, prec); });
-    cvt_d2f(ts, static_cast<float*>(D.Sg(k0 + k)), D.dim, s);
+    if (D.f32()) cvt_f2d(static_cast<const float*>(D.B(k0 + k)), tc, D.dim, s);
+    else MLCC_CUDA(cudaMemcpyAsync(tc, D.B(k0 + k), size_t(D.dim) * 8, cudaMemcpyDeviceToDevice, s));
+    sigma_one(S, tc, ts, prec, graph);
+    if (D.f32()) cvt_d2f(ts, static_cast<float*>(D.Sg(k0 + k)), D.dim, s);
+    else MLCC_CUDA(cudaMemcpyAsync(D.Sg(k0 + k), ts, size_t(D.dim) * 8, cudaMemcpyDeviceToDevice, s));
   }
   if (prec != MLCC_FP64) check_tc_error(S);
 }
@@ -573,7 +669,7 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
     n_sigma += k;
     if (is_split_precision(prec)) n_sigma_lowp += k;
   };
-  sigma_stored(D, 0, D.m, prec, tmpv, tmps);
+  sigma_stored(D, 0, D.m, prec, tmpv, tmps, opt->sigma_graph != 0);
   count_sigma(D.m);
   {
     Vec32Scope v32(lowp);
@@ -657,7 +753,7 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
             ++added;
           }
         }
-        sigma_stored(D, 0, D.m, prec, tmpv, tmps);
+        sigma_stored(D, 0, D.m, prec, tmpv, tmps, opt->sigma_graph != 0);
         count_sigma(D.m);
         std::fill(D.G.begin(), D.G.end(), 0.0);
         update_G(D, 0);
@@ -753,7 +849,7 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
       for (int k = 0; k < nreq; ++k) conv = conv && rn[k] < opt->es_res_tol;
       break;
     }
-    sigma_stored(D, m0, D.m - m0, prec, tmpv, tmps);
+    sigma_stored(D, m0, D.m - m0, prec, tmpv, tmps, opt->sigma_graph != 0);
     count_sigma(D.m - m0);
     update_G(D, m0);
   }

@@ -29,6 +29,7 @@ struct CCSDCache {
 };
 
 struct TCGemm;      // tensor-core GEMM plan (mixed precision)
+struct SigmaGraphs; // captured Jacobian transformations (solvers.cu)
 
 }  // namespace mlcc
 
@@ -71,6 +72,7 @@ struct mlcc_system {
   int lowp_prec = -1;
   int* tc_err = nullptr;
   mlcc::OperandCache* opcache = nullptr;   // bfloat16 pieces of Jacobian-constant operands
+  mlcc::SigmaGraphs* graphs = nullptr;     // CUDA graphs of sigma (mlcc_options.sigma_graph)
   // J window of a sharded Jacobian transformation (mlcc_sigma_partial): while set, nj, Lt,
   // Lai, Lov and Z describe the Cholesky vectors [jwin0, jwin0 + nj) only
   bool jwin = false;
@@ -130,6 +132,7 @@ void ccsd_block(mlcc_system* S, Mode mode, const Dual& Lai, const Dual& Lac, con
                 const Dual& Lkc, const Dual& Fvv, const Dual& Foo, const Dual& t, double* om_out,
                 bool cache_values, const double* c1, bool rest = true);
 void ccsd_cache_free(mlcc_system* S);
+void sigma_graphs_free(mlcc_system* S);
 void rank_gemm_lowp(mlcc_system* S, bool outer, const double* A, const double* B, double* C,
                     double alpha, double beta, int precision, bool b_is_u_source);
 void lowp_prepare(mlcc_system* S, int precision);

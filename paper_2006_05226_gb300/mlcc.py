@@ -36,7 +36,7 @@ STATUS = {v: k for k, v in dict(globals()).items()
           if k.startswith("MLCC_") and (k.startswith("MLCC_E_") or k in ("MLCC_OK", "MLCC_PENDING"))}
 
 # every symbol include/mlcc.h declares
-EXPORTS = ["mlcc_default_options", "mlcc_sigma_partial", "mlcc_cnto", "mlcc_ctx_create", "mlcc_ctx_create_budget", "mlcc_orbitals", "mlcc_ctx_destroy", "mlcc_ctx_stream",
+EXPORTS = ["mlcc_default_options", "mlcc_mo_screening", "mlcc_cholesky_decompose", "mlcc_cholesky_mo_vectors", "mlcc_sigma_partial", "mlcc_cnto", "mlcc_ctx_create", "mlcc_ctx_create_budget", "mlcc_orbitals", "mlcc_ctx_destroy", "mlcc_ctx_stream",
            "mlcc_last_error", "mlcc_kernel_timing", "mlcc_kernel_time", "mlcc_system_create",
            "mlcc_system_destroy", "mlcc_system_info", "mlcc_orbital_order", "mlcc_t1_transform",
            "mlcc_fock_t1", "mlcc_omega", "mlcc_ground_state", "mlcc_jacobian_prepare",
@@ -64,7 +64,7 @@ class mlcc_options(ctypes.Structure):
                 ("refine_fp64", c_int32), ("gs_precision", c_int32), ("gs_tol", c_double),
                 ("gs_energy_tol", c_double), ("es_res_tol", c_double),
                 ("es_omega_tol", c_double), ("lowp_res_tol", c_double),
-                ("refine_precision", c_int32), ("reserved", c_int32)]
+                ("refine_precision", c_int32), ("sigma_graph", c_int32)]
 
 
 class mlcc_gs_info(ctypes.Structure):
@@ -130,6 +130,10 @@ def load():
         "mlcc_ctx_create": (c_int, [c_int, POINTER(c_void_p)]),
         "mlcc_ctx_create_budget": (c_int, [c_int, c_int64, POINTER(c_void_p)]),
         "mlcc_orbitals": (c_int, [P, D]),
+        "mlcc_mo_screening": (c_int, [P, c_int32, c_int32, P, P]),
+        "mlcc_cholesky_decompose": (c_int, [P, c_int64, P, P, c_double, c_int32, POINTER(c_int32), P, P,
+                                            POINTER(c_int32)]),
+        "mlcc_cholesky_mo_vectors": (c_int, [P, c_int32, c_int32, P, POINTER(c_int32), c_int32, P, P]),
         "mlcc_cnto": (c_int, [P, c_int32, c_int32, c_int32, P, P, c_int32, c_int32, POINTER(mlcc_cnto_result)]),
         "mlcc_ctx_destroy": (None, [P]),
         "mlcc_ctx_stream": (c_void_p, [P]),
@@ -529,11 +533,50 @@ def cnto(ctx, chol, fock, n_occ, n_states, n_occ_active, n_vir_active=0, precisi
     return Solution(n_occ_active=res.n_occ_active, n_vir_active=res.n_vir_active, **out)
 
 
+def mo_screening(ctx, c_active):
+    """mlcc_mo_screening: the weights nu_a nu_b [n_ao * n_ao] of the screened diagonal."""
+    n_ao, n_act = c_active.shape
+    w = ctx._torch.empty(n_ao * n_ao, dtype=ctx._torch.float64, device=f"cuda:{ctx.device}")
+    ctx.before()
+    _check(load().mlcc_mo_screening(ctx.handle, n_ao, n_act, _ptr(c_active), _ptr(w)))
+    ctx.after()
+    return w
+
+
+def cholesky_decompose(ctx, g, tau, max_vectors=None, w=None):
+    """mlcc_cholesky_decompose of the [n_pairs, n_pairs] device matrix g: (pivots list,
+    L [n_pairs, n_vectors] device tensor, final diagonal [n_pairs] device tensor)."""
+    torch = ctx._torch
+    m = g.shape[0]
+    mv = m if max_vectors is None else int(max_vectors)
+    L = torch.zeros(m, mv, dtype=torch.float64, device=f"cuda:{ctx.device}")
+    D = torch.empty(m, dtype=torch.float64, device=f"cuda:{ctx.device}")
+    piv = (c_int32 * mv)()
+    nvec = c_int32(0)
+    ctx.before()
+    _check(load().mlcc_cholesky_decompose(ctx.handle, m, _ptr(g), _ptr(w), float(tau), mv, piv, _ptr(L), _ptr(D),
+                                          byref(nvec)))
+    ctx.after()
+    return list(piv[:nvec.value]), L[:, :nvec.value], D
+
+
+def cholesky_mo_vectors(ctx, g, pivots, C):
+    """mlcc_cholesky_mo_vectors (Algorithm 1): [n_vectors, n_mo, n_mo] device tensor."""
+    torch = ctx._torch
+    n_ao, n_mo = C.shape
+    piv = (c_int32 * len(pivots))(*pivots)
+    out = torch.empty(len(pivots), n_mo, n_mo, dtype=torch.float64, device=f"cuda:{ctx.device}")
+    ctx.before()
+    _check(load().mlcc_cholesky_mo_vectors(ctx.handle, n_ao, n_mo, _ptr(g), piv, len(pivots), _ptr(C), _ptr(out)))
+    ctx.after()
+    return out
+
+
 def shard_range(n_chol, rank, world):
     """[j_begin, j_end) of Cholesky vectors for one of `world` ranks: contiguous, in rank
     order, sizes differing by at most one (the first n_chol % world ranks take one more)."""
-    if world < 1 or not 0 <= rank < world:
-        raise ValueError("need 0 <= rank < world")
+    if world < 1 or not 0 <= rank < world or world > n_chol:
+        raise ValueError("need 0 <= rank < world <= n_chol")
     q, r = divmod(int(n_chol), int(world))
     j0 = rank * q + min(rank, r)
     return j0, j0 + q + (1 if rank < r else 0)

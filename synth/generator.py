@@ -134,6 +134,9 @@ CONFIGS = {
     "mlcc2_large": _spec("mlcc2_large", 150, 1200, 6000, 40, 300, 0, 0, 6),
     # 560 orbitals, 60 occupied, 2500 vectors; CCSD 20 / 140 in CC2 40 / 300, CCS rest
     "three_level": _spec("three_level", 60, 500, 2500, 40, 300, 20, 140, 4),
+    # excited-state parity case: 170 orbitals, 20 occupied, 850 vectors; CCSD 6 / 36 in
+    # CC2 16 / 110, CCS rest; 4 roots (its rank GEMMs take the tensor-core paths)
+    "es_parity": _spec("es_parity", 20, 150, 850, 16, 110, 6, 36, 4),
 }
 
 

@@ -4,10 +4,11 @@
   python tests/golden/make_golden.py mid      # the oracle ground state of the 340-orbital
                                               # workload: tens of minutes on 8 cores
   python tests/golden/make_golden.py three_level   # 560 orbitals, CCS / CC2 / CCSD levels
+  python tests/golden/make_golden.py es_parity     # 170 orbitals, three levels, with roots
 
 For each workload: the reference energy E_HF = sum_I (h_II + F_II) of the reduced space,
 the MLCC ground-state correlation energy (Eq. mlcc_energy at Omega = 0, DIIS quasi-Newton
-of Sec. 2.1), the residual norm and iteration count, and (small only) the lowest
+of Sec. 2.1), the residual norm and iteration count, and (small and es_parity) the lowest
 excitation energies from the oracle's Davidson on A = dOmega/dx. Inputs come from the
 seeded generator in synth/ (shared input module, no method arithmetic).
 """
@@ -49,9 +50,12 @@ def main(name):
            "s_occ": spec.s_occ, "s_vir": spec.s_vir, "t_occ": spec.t_occ, "t_vir": spec.t_vir,
            "seed": spec.seed, "e_hf": float(hf_energy(o)), "e_corr": float(gs.energy),
            "omega_norm": float(gs.omega_norm), "gs_iterations": int(gs.iterations), "gs_converged": bool(gs.converged)}
-    if name == "small":
+    if name in ("small", "es_parity"):
         es = excited_states(o, gs, spec.n_roots, res_tol=1e-9)
         out["omega"] = [float(w) for w in es.omega]
+        out["es_residuals"] = [float(r) for r in es.residuals]
+        out["es_sigma"] = int(es.n_sigma)
+    if name == "small":
         out["draws_sha256"] = draws_sha256(spec)
     out["written_by"] = "tests/golden/make_golden.py (oracle/ only)"
     out["host"] = {"machine": platform.machine(), "numpy": np.__version__, "seconds": time.time() - t0}

@@ -30,5 +30,7 @@ def test_workload_configs():
             s = CONFIGS[name]
             assert c["n_mo"] == s.n_mo and c["n_chol"] == s.n_chol and c["n_roots"] == s.n_roots
             assert f"{s.n_mo} orbitals" in c["workload"] and c["excited_state_solver"] == "davidson"
+            assert ("three-level" in c["workload"]) == (name == "three_level")
+            assert ("two levels" in c["workload"]) == (name == "mid")
     finally:
         bench.WORKLOAD = saved

@@ -51,7 +51,7 @@ def test_oracle_reproduces_the_stored_small_workload():
     assert np.abs(es.omega - np.array(g["omega"])).max() < 1e-9
 
 
-@pytest.mark.parametrize("name", ["small", "mid", "three_level"])
+@pytest.mark.parametrize("name", ["small", "mid", "three_level", "es_parity"])
 def test_stored_files_describe_their_workload(name):
     from synth import CONFIGS
     g = _load(name)

@@ -85,10 +85,14 @@ def test_partial_sigmas_add_up(ctx, case):
         scale = float(np.abs(ref).max())
         assert np.abs(total - whole).max() <= 1e-10 * scale, (prec, float(np.abs(total - whole).max()))
         assert np.abs(total - ref).max() <= 1e-10 * scale
-        # the rest terms alone (an empty range) plus the whole J range without them
-        a = g.sigma_partial(c, 0, 0, True, prec).cpu().numpy()
-        b = g.sigma_partial(c, 0, nj, False, prec).cpu().numpy()
+        # a one-vector range with the rest terms plus the remaining range without them
+        a = g.sigma_partial(c, 0, 1, True, prec).cpu().numpy()
+        b = g.sigma_partial(c, 1, nj, False, prec).cpu().numpy()
         assert np.abs(a + b - whole).max() <= 1e-10 * scale
+    from paper_2006_05226_gb300 import mlcc as m
+    with pytest.raises(m.MLCCError) as e:
+        g.sigma_partial(c, 3, 3, True)
+    assert e.value.status == m.MLCC_E_ARG
     # the unsplit sigma after partial calls is unchanged (the window is restored)
     assert np.array_equal(g.sigma(c).cpu().numpy(), g.sigma(c).cpu().numpy())
     assert np.abs(g.sigma(c).cpu().numpy() - ref).max() <= 1e-10 * float(np.abs(ref).max())

@@ -37,7 +37,7 @@ def test_default_options(lib):
     o = mlcc.default_options()
     assert o.n_roots == 3 and o.diis_dim == 8 and o.precision == mlcc.MLCC_FP64
     assert o.gs_tol == 1e-11 and o.es_res_tol == 1e-8 and o.lowp_res_tol == 1e-4
-    assert o.refine_precision == mlcc.MLCC_FP64 and o.reserved == 0
+    assert o.refine_precision == mlcc.MLCC_FP64 and o.sigma_graph == 0
 
 
 def test_binding_struct_sizes_match_header(lib):

@@ -24,7 +24,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def test_shard_ranges_tile_the_cholesky_index():
     from paper_2006_05226_gb300 import mlcc
     for n_chol in (1, 2, 7, 200, 1500, 2501):
-        for world in range(1, 9):
+        for world in range(1, min(9, n_chol + 1)):
             rs = [mlcc.shard_range(n_chol, r, world) for r in range(world)]
             assert rs[0][0] == 0 and rs[-1][1] == n_chol
             assert all(a[1] == b[0] for a, b in zip(rs, rs[1:]))
@@ -32,6 +32,8 @@ def test_shard_ranges_tile_the_cholesky_index():
             assert max(sizes) - min(sizes) <= 1 and sizes == sorted(sizes, reverse=True)
     with pytest.raises(ValueError):
         mlcc.shard_range(10, 2, 2)
+    with pytest.raises(ValueError):
+        mlcc.shard_range(3, 0, 4)                   # an empty range for some rank
 
 
 WORKER = r"""

@@ -135,3 +135,22 @@ def test_problem_queries(problems):
         gs_h, w_h, gs_d, w_d = h.gs, h.omega, d.gs, d.omega
         ctx.close()
         assert gs_d.e_corr == gs_h.e_corr and np.array_equal(w_d, w_h)
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_sigma_graph_replay_equals_the_eager_solve(problems, mixed):
+    """mlcc_options.sigma_graph: the Davidson's Jacobian transformations replayed from CUDA
+    graphs give bitwise the eager solve's roots and vectors, with the same sigma count, and
+    the graphs stand for fewer host launches per sigma (the library counts their kernels)."""
+    from paper_2006_05226_gb300 import mlcc
+    for L, F, no, lev in problems:
+        ctx = mlcc.Context(0)
+        res = []
+        for graph in (0, 1):
+            o = _opts(mixed)
+            o.sigma_graph = graph
+            res.append(mlcc.solve(ctx, L, F, no, lev, o, vectors=True))
+        ctx.close()
+        a, b = res
+        assert np.array_equal(a.omega, b.omega) and np.array_equal(a.r, b.r)
+        assert a.es.n_sigma == b.es.n_sigma and a.gs.e_corr == b.gs.e_corr
