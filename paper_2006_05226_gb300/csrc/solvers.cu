@@ -206,8 +206,6 @@ mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out
   int phase_prec = opt->gs_precision;
   const double lowp_switch = std::max(opt->gs_tol, 1e-7);
   std::vector<double> lowp_norms;   // residual norms of the low-precision phase
-  std::vector<double> phase_norms;  // residual norms since the last DIIS (re)start, binary64-class
-  int diis_restarts = 0;
   for (it = 1; it <= opt->max_gs_iter; ++it) {
     {
       LowpScope lowp(phase_prec, S->tc_err);
@@ -246,7 +244,6 @@ mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out
       }
       phase_prec = opt->refine_precision;   // the next iterations refine these amplitudes
       order.clear();            // the low-precision residuals do not belong in DIIS
-      phase_norms.clear();
       std::fill(Bm.begin(), Bm.end(), 0.0);
       e_old = e;
       continue;                 // re-evaluate the residual in binary64 before stepping
@@ -256,21 +253,6 @@ mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out
       break;
     }
     e_old = e;
-    // DIIS stagnation: when the binary64-class residual has not halved over four iterations,
-    // the extrapolation space has stopped helping (typically after a precision switch, where
-    // the history holds only the slow error directions); restart it from the newest pair
-    if (!split_phase) {
-      phase_norms.push_back(norm);
-      const size_t q = phase_norms.size();
-      if (q >= 5 && order.size() > 1 &&
-          norm > 0.5 * *std::min_element(phase_norms.end() - 5, phase_norms.end() - 1)) {
-        order.clear();
-        std::fill(Bm.begin(), Bm.end(), 0.0);
-        phase_norms.clear();
-        ++diis_restarts;
-        if (verbose()) std::fprintf(stderr, "[mlcc] GS it %3d DIIS restart\n", it);
-      }
-    }
     k_qn<<<nblk(len), 256, 0, s>>>(t1, tT, om1, omT, S->eps, no, nv, tv, to, pn, en);
     MLCC_CHECK_LAUNCH();
     // ring buffer of (p, e)
@@ -291,9 +273,6 @@ mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out
       Bm[size_t(slot) * dd + k] = dh[k];
       Bm[size_t(k) * dd + slot] = dh[k];
     }
-    // entries whose error is 1e4 times the newest one's carry no information for the
-    // extrapolation and only spoil the conditioning of its equations: drop them
-    while (order.size() > 2 && Bm[size_t(order.front()) * dd + order.front()] > 1e8 * dh[slot]) order.erase(order.begin());
     const int m = int(order.size());
     std::vector<double> coef(dd, 0.0);
     bool ok = false;
@@ -434,6 +413,7 @@ void vcopy(DavState& D, void* dst, const void* src, int64_t count) {
 struct SigmaGraphs {
   struct Entry {
     int prec;
+    bool v32;           // captured with binary32 vector arithmetic on (Vec32Scope)
     const double* in;
     double* out;
     size_t mark;
@@ -441,7 +421,7 @@ struct SigmaGraphs {
     cudaGraphExec_t exec;
   };
   std::vector<Entry> entries;
-  std::vector<int> warmed;   // precisions evaluated eagerly since the last prepare
+  std::vector<int> warmed;   // (precision, binary32 state) evaluated eagerly since the last prepare
   ~SigmaGraphs() {
     for (auto& e : entries) cudaGraphExecDestroy(e.exec);
   }
@@ -453,7 +433,9 @@ void sigma_graphs_free(mlcc_system* S) {
 }
 
 // sigma of `in` into `out`: eagerly, or through a graph captured on the second call of a
-// precision (the first, eager one fills the operand caches, so the capture allocates nothing)
+// precision and binary32 vector-arithmetic state (the first, eager one fills the operand
+// caches, so the capture allocates nothing; the state decides the arithmetic of the skinny
+// GEMMs inside sigma, so each state has a graph of its own)
 static void sigma_one(mlcc_system* S, const double* in, double* out, int prec, bool graph) {
   cudaStream_t s = S->ctx->stream;
   if (!graph || S->ctx->timer.enabled) {
@@ -462,18 +444,20 @@ static void sigma_one(mlcc_system* S, const double* in, double* out, int prec, b
   }
   if (!S->graphs) S->graphs = new SigmaGraphs();
   SigmaGraphs& G = *S->graphs;
+  const bool v32 = vec32_active();
   for (auto& e : G.entries)
-    if (e.prec == prec && e.in == in && e.out == out && S->ws.mark() <= e.mark) {
+    if (e.prec == prec && e.v32 == v32 && e.in == in && e.out == out && S->ws.mark() <= e.mark) {
       MLCC_CUDA(cudaGraphLaunch(e.exec, s));
       count_launches(e.kernels);
       return;
     }
-  if (std::find(G.warmed.begin(), G.warmed.end(), prec) == G.warmed.end()) {
+  const int key = 2 * prec + (v32 ? 1 : 0);
+  if (std::find(G.warmed.begin(), G.warmed.end(), key) == G.warmed.end()) {
     sigma_eval(S, in, out, prec);
-    G.warmed.push_back(prec);
+    G.warmed.push_back(key);
     return;
   }
-  SigmaGraphs::Entry e{prec, in, out, S->ws.mark(), 0, nullptr};
+  SigmaGraphs::Entry e{prec, v32, in, out, S->ws.mark(), 0, nullptr};
   const int64_t l0 = launch_count();
   cudaGraph_t g = nullptr;
   MLCC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
