@@ -325,6 +325,13 @@ def run_serving(args):
         w = mlcc.solve(ctx, Lp.numpy(), Fp.numpy(), sy.spec.n_occ, sy.level, opts_for(sy.spec, prec)).omega
         seq_w.append(w)
     seq_s = time.perf_counter() - t0
+    # the same, with the Jacobian transformations evaluated eagerly (no CUDA graphs)
+    seq_nog_s = None
+    if args.sigma_graph:
+        t0 = time.perf_counter()
+        for sy, (Lp, Fp) in zip(systems, host):
+            mlcc.solve(ctx, Lp.numpy(), Fp.numpy(), sy.spec.n_occ, sy.level, opts_for(sy.spec, prec, graph=0))
+        seq_nog_s = time.perf_counter() - t0
     # plain binary64, one at a time, on the first fp64_sample requests (accuracy and speed)
     fp64_s, errs = [], []
     for k in range(min(args.fp64_sample, len(systems))):
@@ -378,6 +385,7 @@ def run_serving(args):
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "status": status, "peak_running": int(info.peak_running), "peak_admitted_bytes": int(info.peak_bytes),
             "one_at_a_time_mixed_solves_per_s": n / seq_s,
+            "one_at_a_time_mixed_solves_per_s_without_sigma_graphs": (n / seq_nog_s) if seq_nog_s else None,
             "fp64_one_at_a_time": {"requests": len(fp64_s), "mean_seconds": float(np.mean(fp64_s)) if fp64_s else None,
                                    "solves_per_s": len(fp64_s) / sum(fp64_s) if fp64_s else None,
                                    "max_abs_omega_err_Ha": max(errs) if errs else None},

@@ -6,7 +6,8 @@
 // One CTA computes a 128 x 256 tile: TMA (cp.async.bulk.tensor, 128-byte swizzle) fills a
 // 4-stage shared-memory ring; one elected thread issues tcgen05.mma (kind::f16, M = 128,
 // N = 256, K = 16) into a 256-column TMEM accumulator and releases stages with
-// tcgen05.commit; four epilogue warps read the accumulator with tcgen05.ld and write C.
+// tcgen05.commit; four epilogue warps read the accumulator with tcgen05.ld and write C
+// through a shared-memory transpose (coalesced row segments).
 // Every mbarrier wait is bounded: on timeout the thread records an error flag and the CTA
 // winds down (freeing its TMEM) instead of spinning.
 //
@@ -198,14 +199,16 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       }
     }
   } else {
-    // epilogue: warps 2..5 own TMEM lanes 32*(warp % 4) .. +31, one output row per thread
+    // epilogue: warps 2..5 own TMEM lanes 32*(warp % 4) .. +31. Each 32 x 32 block of the
+    // accumulator goes through shared memory (lane = row when read from TMEM, lane = column
+    // when stored), so that every warp store writes 32 consecutive doubles of one row
     const int q = warp & 3;
     const bool ok = mbar_wait(accb, 0, p.err, 3);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok && nkb > 0) {
-      const int64_t row = m0 + 32 * q + lane;
+      float* stg = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256) + q * EMU_STAGE_FLOATS;
+      const int64_t rbase = m0 + 32 * q;
       double* const part = p.partial ? p.partial + int64_t(blockIdx.z) * p.M * p.N : nullptr;
-      double* crow = part ? part + row * p.N : p.C + row * p.ldc;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         uint32_t r[32];
@@ -220,30 +223,30 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
               "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (row < p.M) {
-          int64_t cb = 0, cc = n0 + c0;
-          if (p.nb > 0) {
-            cb = cc / p.nb;
-            cc -= cb * p.nb;
-          }
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int64_t col = n0 + c0 + j;
-            if (col < p.N) {
-              if (part) {
-                crow[col] = double(__uint_as_float(r[j]));
-              } else {
-                double* cp = p.nb > 0 ? p.C + cb * p.sCb + row * p.ldc + cc : crow + col;
-                const double v = p.alpha * double(__uint_as_float(r[j]));
-                *cp = (p.beta == 0.0) ? v : v + p.beta * *cp;
-              }
-            }
-            if (p.nb > 0 && ++cc == p.nb) {
-              cc = 0;
-              ++cb;
+        for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = __uint_as_float(r[j]);
+        __syncwarp();
+        const int64_t col = n0 + c0 + lane;
+        if (col < p.N) {
+          // batched output columns: column col of the product is column cc of batch cb
+          int64_t cb = 0, cc = col;
+          if (p.nb > 0) {
+            cb = col / p.nb;
+            cc = col - cb * p.nb;
+          }
+          for (int i = 0; i < 32; ++i) {
+            const int64_t row = rbase + i;
+            if (row >= p.M) break;
+            const double v = double(stg[i * 33 + lane]);
+            if (part) {
+              part[row * p.N + col] = v;
+            } else {
+              double* cp = p.nb > 0 ? p.C + cb * p.sCb + row * p.ldc + cc : p.C + row * p.ldc + col;
+              *cp = (p.beta == 0.0) ? p.alpha * v : p.alpha * v + p.beta * *cp;
             }
           }
         }
+        __syncwarp();
       }
     }
   }
@@ -547,7 +550,7 @@ static void ensure_smem_attr() {
   static std::once_flag once;
   static cudaError_t e = cudaSuccess;
   std::call_once(once, [] {
-    e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES_EMU);
   });
   MLCC_CUDA(e);
 }
@@ -625,7 +628,7 @@ void tc_gemm_split(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t M, in
   dim3 grid = m_fast ? dim3(unsigned(tm), unsigned(tn), unsigned(splits))
                      : dim3(unsigned(tn), unsigned(tm), unsigned(splits));
   MLCC_REQUIRE((m_fast ? tn : tm) < 65536 && splits < 65536, "tc_gemm: grid too large");
-  k_tc_gemm<<<grid, THREADS, SMEM_BYTES, s>>>(ma, mb, p);
+  k_tc_gemm<<<grid, THREADS, SMEM_BYTES_EMU, s>>>(ma, mb, p);
   MLCC_CHECK_LAUNCH();
   if (splits > 1) reduce_partials(partial, splits, M, N, C, ldc, alpha, beta, s);
 }

@@ -156,6 +156,102 @@ __global__ void k_dots32_stage2(const double* partial, int nblk, double* out) {
   if (threadIdx.x == 0) out[k] = red[0];
 }
 
+// Binary32 storage with every vector 16-byte aligned and n a multiple of 4: the same block
+// dot products with float4 loads (four elements per load instruction, CH + NY loads of 16 B
+// in flight per thread), so that the pass runs at the memory's rate rather than the
+// load-issue rate. partial[(k * NY + j)][blk] as in k_dots_block32.
+template <int NY, int CH>
+__global__ void k_dots_block32_v4(const float* __restrict__ x, int64_t ldx, int nx, const float* __restrict__ y,
+                                  int64_t ldy, int64_t n4, double* partial) {
+  __shared__ double red[CH * NY][256 / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t st = int64_t(gridDim.x) * blockDim.x;
+  for (int k0 = 0; k0 < nx; k0 += CH) {
+    const int kc = min(CH, nx - k0);
+    float acc[CH][NY];
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int j = 0; j < NY; ++j) acc[c][j] = 0.0f;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n4; i += st) {
+      float4 yv[NY];
+#pragma unroll
+      for (int j = 0; j < NY; ++j) yv[j] = __ldg(reinterpret_cast<const float4*>(y + int64_t(j) * ldy) + i);
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        if (c < kc) {
+          const float4 xv = __ldg(reinterpret_cast<const float4*>(x + int64_t(k0 + c) * ldx) + i);
+#pragma unroll
+          for (int j = 0; j < NY; ++j)
+            acc[c][j] = fmaf(xv.x, yv[j].x, fmaf(xv.y, yv[j].y, fmaf(xv.z, yv[j].z, fmaf(xv.w, yv[j].w, acc[c][j]))));
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int j = 0; j < NY; ++j) {
+        double v = f2d(acc[c][j]);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[c * NY + j][warp] = v;
+      }
+    __syncthreads();
+    if (threadIdx.x < kc * NY) {
+      double v = 0.0;
+      for (int w = 0; w < int(blockDim.x / 32); ++w) v += red[threadIdx.x][w];
+      const int c = threadIdx.x / NY, j = threadIdx.x - c * NY;
+      partial[int64_t((k0 + c) * NY + j) * gridDim.x + blockIdx.x] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// the skinny binary32 GEMM with four columns per thread and float4 loads of B (ldb and N
+// multiples of 4, B 16-byte aligned); op(A) (K <= 64) staged in shared memory
+template <int MM, bool TA, typename TC>
+__global__ void k_skinny32_v4(int64_t M, int64_t N4, int64_t K, const double* A, int64_t lda,
+                              const float* __restrict__ B, int64_t ldb, TC* C, int64_t ldc, double alpha,
+                              double beta) {
+  __shared__ float As[MM * 64];
+  for (int t = threadIdx.x; t < MM * 64; t += blockDim.x) {
+    const int m = t / 64, k = t - m * 64;
+    As[t] = (m < M && k < K) ? d2f(TA ? A[int64_t(k) * lda + m] : A[int64_t(m) * lda + k]) : 0.0f;
+  }
+  __syncthreads();
+  const int64_t n4 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (n4 >= N4) return;
+  float4 acc[MM];
+#pragma unroll
+  for (int m = 0; m < MM; ++m) acc[m] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int64_t k = 0; k < K; ++k) {
+    const float4 b = __ldg(reinterpret_cast<const float4*>(B + k * ldb) + n4);
+#pragma unroll
+    for (int m = 0; m < MM; ++m) {
+      const float a = As[m * 64 + k];
+      acc[m].x = fmaf(a, b.x, acc[m].x);
+      acc[m].y = fmaf(a, b.y, acc[m].y);
+      acc[m].z = fmaf(a, b.z, acc[m].z);
+      acc[m].w = fmaf(a, b.w, acc[m].w);
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < MM; ++m)
+    if (m < M) {
+      TC* cp = C + m * ldc + 4 * n4;
+      const float r[4] = {acc[m].x, acc[m].y, acc[m].z, acc[m].w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (sizeof(TC) == 8) {
+          const double v = alpha * f2d(r[q]);
+          st64(cp + q, (beta == 0.0) ? v : v + beta * ld64(cp + q));
+        } else {
+          const float a = float(alpha), bb = float(beta);
+          st32(cp + q, (bb == 0.0f) ? a * r[q] : fmaf(a, r[q], bb * d2f(cp[q])));
+        }
+      }
+    }
+}
+
 // C[m][n] = alpha sum_k op(A)[m][k] B[k][n] + beta C[m][n] for M <= MM, one thread per
 // column n; op(A) (K <= 64) is staged in shared memory as binary32
 template <int MM, bool TA, typename TB, typename TC>
@@ -209,11 +305,33 @@ void launch_skinny32(int64_t M, int64_t N, int64_t K, const double* A, int64_t l
   else k_skinny32<MM, false, TB, TC><<<blocks, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, alpha, beta);
   MLCC_CHECK_LAUNCH();
 }
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+template <int MM, typename TC>
+void launch_skinny32_v4(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, bool ta, const float* B,
+                        int64_t ldb, TC* C, int64_t ldc, double alpha, double beta, cudaStream_t s) {
+  const int64_t N4 = N / 4;
+  const unsigned blocks = unsigned((N4 + 255) / 256);
+  if (ta) k_skinny32_v4<MM, true, TC><<<blocks, 256, 0, s>>>(M, N4, K, A, lda, B, ldb, C, ldc, alpha, beta);
+  else k_skinny32_v4<MM, false, TC><<<blocks, 256, 0, s>>>(M, N4, K, A, lda, B, ldb, C, ldc, alpha, beta);
+  MLCC_CHECK_LAUNCH();
+}
+
 template <typename TB, typename TC>
 bool skinny32_t(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, bool ta, const TB* B, int64_t ldb,
                 TC* C, int64_t ldc, double alpha, double beta, cudaStream_t s) {
   if (M < 1 || M > 16 || K > 64 || K < 0 || N < 1) return false;
   MLCC_REQUIRE((N + 255) / 256 < (int64_t(1) << 31), "skinny32: N too large");
+  if constexpr (sizeof(TB) == 4) {
+    if (N % 4 == 0 && ldb % 4 == 0 && aligned16(B) && K > 0) {
+      const float* Bf = reinterpret_cast<const float*>(B);
+      if (M <= 1) launch_skinny32_v4<1>(M, N, K, A, lda, ta, Bf, ldb, C, ldc, alpha, beta, s);
+      else if (M <= 4) launch_skinny32_v4<4>(M, N, K, A, lda, ta, Bf, ldb, C, ldc, alpha, beta, s);
+      else if (M <= 8) launch_skinny32_v4<8>(M, N, K, A, lda, ta, Bf, ldb, C, ldc, alpha, beta, s);
+      else launch_skinny32_v4<16>(M, N, K, A, lda, ta, Bf, ldb, C, ldc, alpha, beta, s);
+      return true;
+    }
+  }
   if (M <= 1) launch_skinny32<1>(M, N, K, A, lda, ta, B, ldb, C, ldc, alpha, beta, s);
   else if (M <= 4) launch_skinny32<4>(M, N, K, A, lda, ta, B, ldb, C, ldc, alpha, beta, s);
   else if (M <= 8) launch_skinny32<8>(M, N, K, A, lda, ta, B, ldb, C, ldc, alpha, beta, s);
@@ -228,7 +346,16 @@ void dots32_t(const TX* x, int64_t ldx, int nx, const TY* y, int64_t n, double* 
   Scope sc(ws);
   const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, DOT32_BLOCKS)));
   double* partial = ws.get<double>(size_t(nx) * blocks);
-  k_dots32<TX, TY><<<blocks, 256, 0, s>>>(x, ldx, nx, y, n, partial);
+  bool v4 = false;
+  if constexpr (sizeof(TX) == 4 && sizeof(TY) == 4)
+    v4 = n % 4 == 0 && ldx % 4 == 0 && aligned16(x) && aligned16(y);
+  if (v4) {
+    if constexpr (sizeof(TX) == 4 && sizeof(TY) == 4)
+      k_dots_block32_v4<1, DOT32_CHUNK><<<blocks, 256, 0, s>>>(reinterpret_cast<const float*>(x), ldx, nx,
+                                                                reinterpret_cast<const float*>(y), 0, n / 4, partial);
+  } else {
+    k_dots32<TX, TY><<<blocks, 256, 0, s>>>(x, ldx, nx, y, n, partial);
+  }
   MLCC_CHECK_LAUNCH();
   k_dots32_stage2<<<nx, 256, 0, s>>>(partial, blocks, out_dev);
   MLCC_CHECK_LAUNCH();
@@ -242,11 +369,27 @@ void dots_block32_t(const TX* x, int64_t ldx, int nx, const TY* y, int64_t ldy, 
   Scope sc(ws);
   const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, DOT32_BLOCKS)));
   double* partial = ws.get<double>(size_t(nx) * ny * blocks);
-  switch (ny) {
-    case 1: k_dots_block32<1, TX, TY><<<blocks, 256, 0, s>>>(x, ldx, nx, y, ldy, n, partial); break;
-    case 2: k_dots_block32<2, TX, TY><<<blocks, 256, 0, s>>>(x, ldx, nx, y, ldy, n, partial); break;
-    case 3: k_dots_block32<3, TX, TY><<<blocks, 256, 0, s>>>(x, ldx, nx, y, ldy, n, partial); break;
-    default: k_dots_block32<4, TX, TY><<<blocks, 256, 0, s>>>(x, ldx, nx, y, ldy, n, partial); break;
+  bool v4 = false;
+  if constexpr (sizeof(TX) == 4 && sizeof(TY) == 4)
+    v4 = n % 4 == 0 && ldx % 4 == 0 && ldy % 4 == 0 && aligned16(x) && aligned16(y);
+  if (v4) {
+    if constexpr (sizeof(TX) == 4 && sizeof(TY) == 4) {
+      const float* xf = reinterpret_cast<const float*>(x);
+      const float* yf = reinterpret_cast<const float*>(y);
+      switch (ny) {
+        case 1: k_dots_block32_v4<1, 16><<<blocks, 256, 0, s>>>(xf, ldx, nx, yf, ldy, n / 4, partial); break;
+        case 2: k_dots_block32_v4<2, 16><<<blocks, 256, 0, s>>>(xf, ldx, nx, yf, ldy, n / 4, partial); break;
+        case 3: k_dots_block32_v4<3, 8><<<blocks, 256, 0, s>>>(xf, ldx, nx, yf, ldy, n / 4, partial); break;
+        default: k_dots_block32_v4<4, 8><<<blocks, 256, 0, s>>>(xf, ldx, nx, yf, ldy, n / 4, partial); break;
+      }
+    }
+  } else {
+    switch (ny) {
+      case 1: k_dots_block32<1, TX, TY><<<blocks, 256, 0, s>>>(x, ldx, nx, y, ldy, n, partial); break;
+      case 2: k_dots_block32<2, TX, TY><<<blocks, 256, 0, s>>>(x, ldx, nx, y, ldy, n, partial); break;
+      case 3: k_dots_block32<3, TX, TY><<<blocks, 256, 0, s>>>(x, ldx, nx, y, ldy, n, partial); break;
+      default: k_dots_block32<4, TX, TY><<<blocks, 256, 0, s>>>(x, ldx, nx, y, ldy, n, partial); break;
+    }
   }
   MLCC_CHECK_LAUNCH();
   k_dots32_stage2<<<nx * ny, 256, 0, s>>>(partial, blocks, out_dev);
