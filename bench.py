@@ -444,9 +444,10 @@ def run_probe(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="three_level", choices=["mid", "three_level", "serving"],
+    ap.add_argument("--workload", default="three_level", choices=["mid", "three_level", "es_parity", "serving"],
                     help="three_level (default): 560 orbitals, CCSD 20/140 inside CC2 40/300, CCS rest; "
-                         "mid: 340 orbitals, CCSD 10/60, CC2 the rest; serving: the request mix")
+                         "mid: 340 orbitals, CCSD 10/60, CC2 the rest; es_parity: 170 orbitals, CCSD 6/36 "
+                         "inside CC2 16/110, CCS rest (a small case for kernel captures); serving: the request mix")
     ap.add_argument("--requests", type=int, default=8, help="serving: number of requests")
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent slots")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: arrivals per second")

@@ -275,6 +275,21 @@ mlcc_status mlcc_sigma(mlcc_system* sys, int32_t n_vec, const double* c_dev,
    range: each call converts its operands. */
 mlcc_status mlcc_sigma_partial(mlcc_system* sys, int32_t j_begin, int32_t j_end, int32_t with_rest,
                                int32_t n_vec, const double* c_dev, double* sigma_dev, int32_t precision);
+/* Left eigenvectors (the transition moments the paper names as a motivation, Sec. 1, need
+   them beside the right ones): rho = A^T l, the adjoint of mlcc_sigma in the plain inner
+   product of the vector storage on symmetric doubles (the doubles of l must be symmetric;
+   those of rho are symmetrised). Systems without a CCSD level (MLCC2, CC2, CCS and their
+   combinations); MLCC_E_ARG otherwise, MLCC_E_STATE before mlcc_jacobian_prepare. Layout
+   and precisions as mlcc_sigma. */
+mlcc_status mlcc_sigma_left(mlcc_system* sys, int32_t n_vec, const double* l_dev, double* rho_dev,
+                            int32_t precision);
+/* The lowest opt->n_roots left eigenpairs by the Davidson solver of mlcc_excited_states on
+   A^T (same options, the same eigenvalues as the right problem): omega_host [n_roots],
+   l_dev [n_roots][vector_len]. With r_dev (the right eigenvectors of the same roots, e.g.
+   from mlcc_excited_states) each l_k is scaled so that <l_k, r_k> = 1; NULL: unit 2-norm,
+   largest-magnitude element positive. */
+mlcc_status mlcc_excited_states_left(mlcc_system* sys, const mlcc_options* opt, double* omega_host,
+                                     double* l_dev, const double* r_dev, mlcc_es_info* info);
 /* Folded CC2 Jacobian (the CC2 response strategy Sec. 2.1 points to). In the three-level
    model the doubles rows outside the CCSD block (P_S) have the diagonal doubles block
    eps_aibj and no coupling to the CCSD-block doubles (P_T), so an eigenpair (omega, c) of

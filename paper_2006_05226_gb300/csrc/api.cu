@@ -16,18 +16,19 @@ int64_t launch_count();
 mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out, double* x2_out,
                          mlcc_gs_info* info);
 mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omega_host,
-                           double* r_out, mlcc_es_info* info, double* residual_host = nullptr);
+                           double* r_out, mlcc_es_info* info, double* residual_host = nullptr,
+                           bool left = false);
 
 // the Davidson solve behind mlcc_excited_states and mlcc_solve, with their argument checks
 static mlcc_status excited_states_checked(mlcc_system* S, const mlcc_options* opt, double* omega, double* r,
-                                          mlcc_es_info* info, double* residual) {
+                                          mlcc_es_info* info, double* residual, bool left = false) {
   MLCC_REQUIRE(S && opt && omega, "mlcc_excited_states: NULL argument");
   MLCC_REQUIRE(opt->precision >= MLCC_FP64 && opt->precision <= MLCC_FP64E,
                "mlcc_excited_states: unknown precision");
   MLCC_REQUIRE(opt->refine_precision == MLCC_FP64 || opt->refine_precision == MLCC_FP64E,
                "mlcc_excited_states: refine_precision must be MLCC_FP64 or MLCC_FP64E");
   MLCC_CUDA(cudaSetDevice(S->ctx->device));
-  const mlcc_status st = excited_states(S, opt, omega, r, info, residual);
+  const mlcc_status st = excited_states(S, opt, omega, r, info, residual, left);
   if (st == MLCC_E_ES_NOCONV) set_last_error("excited states did not converge");
   if (st == MLCC_E_COMPLEX_ROOT) set_last_error("a wanted Ritz value is complex");
   return st;
@@ -556,6 +557,56 @@ mlcc_status mlcc_sigma_partial(mlcc_system* S, int32_t j_begin, int32_t j_end, i
       for (int k = 0; k < n_vec; ++k) sigma_eval(S, c + k * len, sigma + k * len, precision, parts);
     }
     if (precision != MLCC_FP64) check_tc_error(S);
+    return MLCC_OK;
+  });
+}
+
+namespace {
+// <x_k, y_k> for k < nv vectors of length n (device), to the host
+std::vector<double> pair_dots(mlcc_system* S, const double* x, const double* y, int nv, int64_t n) {
+  std::vector<double> out(size_t(std::max(nv, 0)));
+  Scope sc(S->ws);
+  double* d = S->ws.get<double>(1);
+  for (int k = 0; k < nv; ++k) {
+    dots(x + int64_t(k) * n, 0, 1, y + int64_t(k) * n, n, d, S->ws, S->ctx->stream);
+    copy_d2h(&out[size_t(k)], d, 1, S->ctx->stream);
+  }
+  return out;
+}
+}  // namespace
+
+mlcc_status mlcc_sigma_left(mlcc_system* S, int32_t n_vec, const double* l, double* rho, int32_t precision) {
+  return guard([&] {
+    MLCC_REQUIRE(S && l && rho, "mlcc_sigma_left: NULL argument");
+    MLCC_REQUIRE(n_vec >= 0, "mlcc_sigma_left: n_vec < 0");
+    MLCC_REQUIRE(precision >= MLCC_FP64 && precision <= MLCC_FP64E, "mlcc_sigma_left: unknown precision");
+    MLCC_CUDA(cudaSetDevice(S->ctx->device));
+    const int64_t len = int64_t(S->nv) * S->no + S->nd;
+    for (int k = 0; k < n_vec; ++k) sigma_left_eval(S, l + k * len, rho + k * len, precision);
+    if (precision != MLCC_FP64) check_tc_error(S);
+    return MLCC_OK;
+  });
+}
+
+mlcc_status mlcc_excited_states_left(mlcc_system* S, const mlcc_options* opt, double* omega, double* l_dev,
+                                     const double* r_dev, mlcc_es_info* info) {
+  return guard([&] {
+    MLCC_REQUIRE(S && opt && omega && l_dev, "mlcc_excited_states_left: NULL argument");
+    if (S->to > 0 && S->tv > 0)
+      throw Error(MLCC_E_ARG, "mlcc_excited_states_left: systems with a CCSD level are not supported");
+    const mlcc_status st = excited_states_checked(S, opt, omega, l_dev, info, nullptr, true);
+    if (st != MLCC_OK) return st;
+    if (r_dev) {
+      // biorthonormal pair: <l_k, r_k> = 1
+      const int64_t len = int64_t(S->nv) * S->no + S->nd;
+      const std::vector<double> ov = pair_dots(S, l_dev, r_dev, opt->n_roots, len);
+      for (int k = 0; k < opt->n_roots; ++k) {
+        if (!(std::fabs(ov[size_t(k)]) > 1e-12))
+          throw Error(MLCC_E_ES_NOCONV, "mlcc_excited_states_left: a left vector is orthogonal to its right vector");
+        axpby(l_dev + k * len, l_dev + k * len, len, 0.0, 1.0 / ov[size_t(k)], S->ctx->stream);
+      }
+      MLCC_CUDA(cudaStreamSynchronize(S->ctx->stream));
+    }
     return MLCC_OK;
   });
 }

@@ -466,16 +466,26 @@ struct PP {
   const double* src;
   double* dst;
 };
+// I: the index type. 32-bit unsigned when every element index and offset fits: the digit
+// decomposition of the element index then costs 32-bit divisions instead of 64-bit ones,
+// which otherwise bound the kernel rather than its memory traffic.
+template <typename I>
 __global__ void k_permute(PP p) {
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < p.total;
-       i += int64_t(gridDim.x) * blockDim.x) {
-    int64_t rem = i, so = 0, dof = 0;
+  const I total = I(p.total), st = I(gridDim.x) * I(blockDim.x);
+  I dims[MAXD], ss[MAXD], ds[MAXD];
+  for (int d = 0; d < p.nd; ++d) {
+    dims[d] = I(p.dims[d]);
+    ss[d] = I(p.ss[d]);
+    ds[d] = I(p.ds[d]);
+  }
+  for (I i = I(blockIdx.x) * I(blockDim.x) + I(threadIdx.x); i < total; i += st) {
+    I rem = i, so = 0, dof = 0;
     for (int d = p.nd - 1; d >= 0; --d) {
-      const int64_t q = rem / p.dims[d];
-      const int64_t x = rem - q * p.dims[d];
+      const I q = rem / dims[d];
+      const I x = rem - q * dims[d];
       rem = q;
-      so += x * p.ss[d];
-      dof += x * p.ds[d];
+      so += x * ss[d];
+      dof += x * ds[d];
     }
     const double v = (p.alpha == 0.0) ? 0.0 : p.alpha * p.src[so];
     p.dst[dof] = (p.beta == 0.0) ? v : v + p.beta * p.dst[dof];
@@ -502,7 +512,18 @@ void permute_f64(int nd, const int64_t* dims, const double* src, const int64_t* 
   p.src = src;
   p.dst = dst;
   const int blocks = int(std::min<int64_t>((p.total + 255) / 256, 8192));
-  k_permute<<<blocks, 256, 0, s>>>(p);
+  // 32-bit indices when the element count and the largest source and destination offsets
+  // (plus one grid stride) stay below 2^32
+  int64_t smax = 0, dmax = 0;
+  for (int d = 0; d < nd; ++d) {
+    smax += (dims[d] - 1) * std::abs(src_strides[d]);
+    dmax += (dims[d] - 1) * std::abs(dst_strides[d]);
+  }
+  bool small = p.total + int64_t(blocks) * 256 < (int64_t(1) << 32) && smax < (int64_t(1) << 32) &&
+               dmax < (int64_t(1) << 32);
+  for (int d = 0; d < nd; ++d) small = small && src_strides[d] >= 0 && dst_strides[d] >= 0;
+  if (small) k_permute<uint32_t><<<blocks, 256, 0, s>>>(p);
+  else k_permute<int64_t><<<blocks, 256, 0, s>>>(p);
   MLCC_CHECK_LAUNCH();
 }
 

@@ -564,6 +564,66 @@ __global__ void k_to_fv(const double* F, int so, int sv, double* fv) {
     fv[t] = F[int64_t(k) * sv + b];
   }
 }
+// out[B][J] += alpha sum_K d[K] X^K[J][no + B] for B < nv, J < no (out [nv][no]); threads run
+// along B so that the reads of X are contiguous
+__global__ void k_sum_over_J_ov_tr(const double* d, const double* X, int nj, int n, int no, double alpha,
+                                   double* out) {
+  const int nv = n - no;
+  const int64_t total = int64_t(nv) * no, nn = int64_t(n) * n;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int J = int(t / nv), B = int(t - int64_t(J) * nv);
+    const double* x = X + int64_t(J) * n + no + B;
+    double acc = 0.0;
+    for (int K = 0; K < nj; ++K) acc = fma(d[K], x[K * nn], acc);
+    out[int64_t(B) * no + J] += alpha * acc;
+  }
+}
+// e[K] = sum_{A,I} X^K[no + A][I] l[A][I] (the virtual-occupied block); one block per K
+__global__ void k_vo_dot(const double* X, int n, int no, const double* l, double* e) {
+  __shared__ double red[256];
+  const int K = blockIdx.x, nv = n - no;
+  const double* x = X + int64_t(K) * n * n + int64_t(no) * n;
+  double acc = 0.0;
+  for (int64_t t = threadIdx.x; t < int64_t(nv) * no; t += blockDim.x) {
+    const int A = int(t / no), I = int(t - int64_t(A) * no);
+    acc = fma(x[int64_t(A) * n + I], l[t], acc);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) e[K] = red[0];
+}
+// out[a*so + i] = l[a*no + i] (the CC2-active singles)
+__global__ void k_gather_act(const double* l, int sv, int so, int no, double* out) {
+  const int64_t total = int64_t(sv) * so;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int a = int(t / so), i = int(t - int64_t(a) * so);
+    out[t] = l[int64_t(a) * no + i];
+  }
+}
+// out[k*sv + c] = fv[c*so + k]
+__global__ void k_fv_to_kc(const double* fv, int so, int sv, double* out) {
+  const int64_t total = int64_t(sv) * so;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int k = int(t / sv), c = int(t - int64_t(k) * sv);
+    out[t] = fv[int64_t(c) * so + k];
+  }
+}
+// G[p][q] += alpha x[p] y[q] (p, q < m)
+__global__ void k_outer_add(const double* x, const double* y, int64_t m, double alpha, double* G) {
+  const int64_t total = m * m;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t p = t / m, q = t - p * m;
+    G[t] += alpha * x[p] * y[q];
+  }
+}
 }  // namespace
 
 static void sum_over_J(mlcc_system* S, const double* d, const double* X, int r0, int c0, int rows,
@@ -777,6 +837,103 @@ void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision, u
       ccsd_block(S, Mode::Tangent, Lai, Lac, Lki, Lkc, Fvv, Foo, t, omT, false, c1, rest);
       put_tbox(S, omT, s2);
     }
+  }
+}
+
+// Left transformation rho = A^T l for a system without a CCSD level: the adjoint of the
+// Jacobian transformation above in the plain inner product of the vector storage, on
+// symmetric doubles (the doubles of rho are symmetrised). Each term of sigma_eval has its
+// transpose here, in the same notation (K the Cholesky index; A, B, I, J all virtual /
+// occupied orbitals; a, b, i, j CC2-active ones):
+//   CCS:    F~_vv^T l - l F~_oo^T + 2 sum_K (e_K + gamma_K) Lt^K[J][B]^T
+//           - sum_K Lt^K_vv^T (l Lt^K_oo^T),        e_K = <Lt^K_vo, l>
+//   MLCC2:  the F~_kc tangent through lambda = u l_act (gamma_K = <Lt^K_ov, lambda>, Phi^K),
+//           - l X^T, - Y^T l
+//   doubles -> singles: Psi^K_bj = Lt^K_vv^T l - l Lt^K_oo^T (active), Gamma = Lov^T Psi
+//           + l_act F~_ov^T, the doubles of rho = make_u(Gamma) symmetrised + eps l2
+//   singles -> doubles: M = 2 Lai l2, rho1 += Lt_vv^T M - M Lt_oo^T (active)
+void sigma_left_eval(mlcc_system* S, const double* l, double* rho, int precision) {
+  if (!S->prepared) throw Error(MLCC_E_STATE, "left transformation: call mlcc_jacobian_prepare first");
+  if (S->to > 0 && S->tv > 0)
+    throw Error(MLCC_E_ARG, "left transformation: systems with a CCSD level are not supported");
+  cudaStream_t s = stm(S);
+  if (precision != MLCC_FP64 && S->opcache) {
+    std::vector<std::pair<const char*, size_t>> r = {{S->persist.base(), S->persist.capacity()}};
+    operand_cache_set_ranges(S->opcache, r);
+  }
+  LowpScope lowp(precision == MLCC_FP64 ? 0 : precision, S->tc_err, S->opcache);
+  const int n = S->n, no = S->no, nv = S->nv, nj = S->nj, so = S->so, sv = S->sv;
+  const int64_t nn = int64_t(n) * n, dS = S->dS, vo = int64_t(nv) * no;
+  const double* l1 = l;
+  const double* l2 = l + vo;
+  double* r1 = rho;
+  double* r2 = rho + vo;
+  const double* Lvv = S->Lt + int64_t(no) * n + no;   // Lt^K[no+A][no+B]
+  const double* Lov = S->Lt + no;                     // Lt^K[I][no+A]
+  const double* Loo = S->Lt;                          // Lt^K[I][J]
+  Scope sc(S->ws);
+  // CCS: F~_vv^T l - l F~_oo^T
+  gemm1(S, nv, no, nv, 1.0, S->Ft + int64_t(no) * n + no, n, true, l1, no, false, 0.0, r1, no);
+  gemm1(S, nv, no, no, -1.0, l1, no, false, S->Ft, n, true, 1.0, r1, no);
+  double* e = S->ws.get<double>(size_t(nj));
+  k_vo_dot<<<nj, 256, 0, s>>>(S->Lt, n, no, l1, e);
+  MLCC_CHECK_LAUNCH();
+  double* lact = nullptr;
+  double* lam = nullptr;
+  if (dS > 0) {
+    lact = S->ws.get<double>(size_t(dS));
+    k_gather_act<<<nblk(dS), 256, 0, s>>>(l1, sv, so, no, lact);
+    MLCC_CHECK_LAUNCH();
+    lam = S->ws.get<double>(size_t(dS));
+    gemm1(S, dS, 1, dS, 1.0, S->u, dS, false, lact, 1, false, 0.0, lam, 1);
+    gemm1(S, nj, 1, dS, 1.0, S->Lov, dS, false, lam, 1, false, 1.0, e, 1);   // + gamma_K
+  }
+  k_sum_over_J_ov_tr<<<nblk(vo), 256, 0, s>>>(e, S->Lt, nj, n, no, 2.0, r1);
+  MLCC_CHECK_LAUNCH();
+  {
+    Scope st(S->ws);
+    double* T = S->ws.get<double>(size_t(nj) * vo);
+    bgemm(S, nv, no, no, 1.0, l1, no, 0, false, Loo, n, nn, true, 0.0, T, no, vo, false);
+    bgemm(S, nv, no, nv, -1.0, Lvv, n, nn, true, T, no, vo, false, 1.0, r1, no, 0, true);
+  }
+  if (dS == 0) return;
+  {
+    // the F~_kc tangent: Phi^K[k][J] = sum_c Lam[k][c] Lt^K[J][no+c]
+    Scope st(S->ws);
+    double* Lam = S->ws.get<double>(size_t(so) * sv);
+    k_fv_to_kc<<<nblk(dS), 256, 0, s>>>(lam, so, sv, Lam);
+    MLCC_CHECK_LAUNCH();
+    double* Phi = S->ws.get<double>(size_t(nj) * so * no);
+    bgemm(S, so, no, sv, 1.0, Lam, sv, 0, false, Lov, n, nn, true, 0.0, Phi, no, int64_t(so) * no, false);
+    bgemm(S, nv, no, so, -1.0, Lov, n, nn, true, Phi, no, int64_t(so) * no, false, 1.0, r1, no, 0, true);
+  }
+  // - l X^T, - Y^T l
+  gemm1(S, nv, no, so, -1.0, l1, no, false, S->Xji, so, true, 1.0, r1, no);
+  gemm1(S, nv, no, sv, -1.0, S->Yab, nv, true, l1, no, false, 1.0, r1, no);
+  // doubles <- singles (the transpose of the doubles-to-singles terms)
+  {
+    Scope st(S->ws);
+    double* Psi = S->ws.get<double>(size_t(nj) * dS);
+    bgemm(S, sv, so, nv, 1.0, Lvv, n, nn, true, l1, no, 0, false, 0.0, Psi, so, dS, false);
+    bgemm(S, sv, so, no, -1.0, l1, no, 0, false, Loo, n, nn, true, 1.0, Psi, so, dS, false);
+    double* Gam = S->ws.get<double>(size_t(S->nd));
+    rank_gemm(S, precision, true, S->Lov, Psi, Gam, 1.0, 0.0);
+    k_outer_add<<<nblk(S->nd), 256, 0, s>>>(lact, S->Fov, dS, 1.0, Gam);
+    MLCC_CHECK_LAUNCH();
+    double* G = S->ws.get<double>(size_t(S->nd));
+    make_u(S, Gam, G);
+    axpby(G, G, S->nd, 0.0, 0.5, s);
+    dim3 blk(32, 8), grd(unsigned((dS + 31) / 32), unsigned((dS + 31) / 32));
+    k_sigma2_cc2<<<grd, blk, 0, s>>>(G, l2, S->eps, no, sv, so, 0, 0, 1.0, r2);   // G + G^T + eps l2
+    MLCC_CHECK_LAUNCH();
+  }
+  // singles <- doubles (the transpose of the CC2 doubles rows): M = 2 Lai l2
+  {
+    Scope st(S->ws);
+    double* M = S->ws.get<double>(size_t(nj) * dS);
+    rank_gemm(S, precision, false, S->Lai, l2, M, 2.0, 0.0);
+    bgemm(S, nv, so, sv, 1.0, Lvv, n, nn, true, M, so, dS, false, 1.0, r1, no, 0, true);
+    bgemm(S, sv, no, so, -1.0, M, so, dS, false, Loo, n, nn, true, 1.0, r1, no, 0, true);
   }
 }
 

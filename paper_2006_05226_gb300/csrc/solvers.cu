@@ -338,6 +338,7 @@ struct DavState {
   char* Sp;    // sigma-vectors [maxsub][dim]
   int es = 8;  // bytes per stored element
   int m = 0;
+  bool left = false;   // the operator is A^T (left eigenvectors)
   std::vector<double> G;  // [maxsub][maxsub] host, G[i][j] = B_i . S_j
   void* B(int64_t k) const { return Bp + k * dim * es; }
   void* Sg(int64_t k) const { return Sp + k * dim * es; }
@@ -488,6 +489,19 @@ static void sigma_batch(mlcc_system* S, const double* C, double* Sg, int nvec, i
 // ts (sigma-vector)
 static void sigma_stored(DavState& D, int k0, int nvec, int prec, double* tc, double* ts, bool graph) {
   mlcc_system* S = D.S;
+  if (D.left) {
+    // A^T: eager, through the binary64 buffers
+    cudaStream_t s = S->ctx->stream;
+    for (int k = 0; k < nvec; ++k) {
+      if (D.f32()) cvt_f2d(static_cast<const float*>(D.B(k0 + k)), tc, D.dim, s);
+      else MLCC_CUDA(cudaMemcpyAsync(tc, D.B(k0 + k), size_t(D.dim) * 8, cudaMemcpyDeviceToDevice, s));
+      timed(S, "sigma", 0.0, [&] { sigma_left_eval(S, tc, ts, prec); });
+      if (D.f32()) cvt_d2f(ts, static_cast<float*>(D.Sg(k0 + k)), D.dim, s);
+      else MLCC_CUDA(cudaMemcpyAsync(D.Sg(k0 + k), ts, size_t(D.dim) * 8, cudaMemcpyDeviceToDevice, s));
+    }
+    if (prec != MLCC_FP64) check_tc_error(S);
+    return;
+  }
   if (!D.f32() && !graph) {
     sigma_batch(S, static_cast<const double*>(D.B(k0)), static_cast<double*>(D.Sg(k0)), nvec, D.dim, prec);
     return;
@@ -603,7 +617,7 @@ static void ritz_body(DavState& D, const std::vector<double>& Yt, int nr, const 
 }
 
 mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omega_host,
-                           double* r_out, mlcc_es_info* info, double* residual_host) {
+                           double* r_out, mlcc_es_info* info, double* residual_host, bool left) {
   if (!S->prepared) throw Error(MLCC_E_STATE, "mlcc_excited_states: no prepared ground state");
   cudaStream_t s = S->ctx->stream;
   const int no = S->no, nv = S->nv, nreq = opt->n_roots;
@@ -618,6 +632,7 @@ mlcc_status excited_states(mlcc_system* S, const mlcc_options* opt, double* omeg
   DavState D{S, dim, maxsub, static_cast<char*>(dav.alloc(size_t(maxsub) * dim * 8)),
              static_cast<char*>(dav.alloc(size_t(maxsub) * dim * 8))};
   D.G.assign(size_t(maxsub) * maxsub, 0.0);
+  D.left = left;
   double* X = dav.get<double>(size_t(nr) * dim);
   double* R = dav.get<double>(size_t(nr) * dim);
   char* CB = static_cast<char*>(dav.alloc(size_t(collapse) * dim * 8));   // collapse scratch (stored type)

@@ -118,6 +118,8 @@ enum SigmaParts : unsigned {
   SIGMA_J_ONLY = 8u
 };
 void sigma_eval(mlcc_system* S, const double* c, double* sigma, int precision, unsigned parts = SIGMA_ALL);
+// rho = A^T l (the adjoint on symmetric doubles) for systems without a CCSD level
+void sigma_left_eval(mlcc_system* S, const double* l, double* rho, int precision);
 // folded CC2 Jacobian: out = A_eff(omega) c (singles and P_T rows; P_S rows zero), dout (if
 // not null) = the singles of dA_eff/domega c; w0, w1, w2: scratch vectors of vector_len
 void sigma_eff_eval(mlcc_system* S, const double* c, double omega, double* out, double* dout, int precision,

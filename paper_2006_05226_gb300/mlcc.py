@@ -36,7 +36,7 @@ STATUS = {v: k for k, v in dict(globals()).items()
           if k.startswith("MLCC_") and (k.startswith("MLCC_E_") or k in ("MLCC_OK", "MLCC_PENDING"))}
 
 # every symbol include/mlcc.h declares
-EXPORTS = ["mlcc_default_options", "mlcc_mo_screening", "mlcc_cholesky_decompose", "mlcc_cholesky_mo_vectors", "mlcc_sigma_partial", "mlcc_cnto", "mlcc_ctx_create", "mlcc_ctx_create_budget", "mlcc_orbitals", "mlcc_ctx_destroy", "mlcc_ctx_stream",
+EXPORTS = ["mlcc_default_options", "mlcc_sigma_left", "mlcc_excited_states_left", "mlcc_mo_screening", "mlcc_cholesky_decompose", "mlcc_cholesky_mo_vectors", "mlcc_sigma_partial", "mlcc_cnto", "mlcc_ctx_create", "mlcc_ctx_create_budget", "mlcc_orbitals", "mlcc_ctx_destroy", "mlcc_ctx_stream",
            "mlcc_last_error", "mlcc_kernel_timing", "mlcc_kernel_time", "mlcc_system_create",
            "mlcc_system_destroy", "mlcc_system_info", "mlcc_orbital_order", "mlcc_t1_transform",
            "mlcc_fock_t1", "mlcc_omega", "mlcc_ground_state", "mlcc_jacobian_prepare",
@@ -155,6 +155,8 @@ def load():
         "mlcc_jacobian_prepare": (c_int, [P, P, P]),
         "mlcc_sigma": (c_int, [P, c_int32, P, P, c_int32]),
         "mlcc_sigma_partial": (c_int, [P, c_int32, c_int32, c_int32, c_int32, P, P, c_int32]),
+        "mlcc_sigma_left": (c_int, [P, c_int32, P, P, c_int32]),
+        "mlcc_excited_states_left": (c_int, [P, POINTER(mlcc_options), D, P, P, POINTER(mlcc_es_info)]),
         "mlcc_excited_states": (c_int, [P, POINTER(mlcc_options), D, P, POINTER(mlcc_es_info)]),
         "mlcc_solve": (c_int, [P, POINTER(mlcc_problem), P, P, POINTER(mlcc_options), POINTER(mlcc_result)]),
         "mlcc_solve_device": (c_int, [P, POINTER(mlcc_problem), P, P, POINTER(mlcc_options),
@@ -408,6 +410,28 @@ class System:
         gloo. Rank 0 adds the terms that do not sum over J."""
         return sharded_sum(lambda j0, j1, rest: self.sigma_partial(c, j0, j1, rest, precision),
                            self.n_chol, rank, world, group)
+
+    def sigma_left(self, l, precision=MLCC_FP64):
+        """mlcc_sigma_left: rho = A^T l for [n_vec, vector_len] symmetric-doubles vectors."""
+        l = l.reshape(-1, self.dims.vector_len)
+        out = self._new(l.shape[0], self.dims.vector_len)
+        self.ctx.before(l, out)
+        _check(load().mlcc_sigma_left(self.handle, l.shape[0], _ptr(l), _ptr(out), precision))
+        self.ctx.after()
+        return out
+
+    def excited_states_left(self, opts=None, right=None):
+        """mlcc_excited_states_left: (omega, left vectors [n_roots, vector_len], info); with
+        `right` ([n_roots, vector_len] device tensor) the pairs are made biorthonormal."""
+        opts = opts or default_options()
+        w = (c_double * opts.n_roots)()
+        Lv = self._new(opts.n_roots, self.dims.vector_len)
+        info = mlcc_es_info()
+        self.ctx.before()
+        st = load().mlcc_excited_states_left(self.handle, byref(opts), w, _ptr(Lv), _ptr(right), byref(info))
+        self.ctx.after()
+        _check(st)
+        return np.array(w[:]), Lv, info
 
     def excited_states(self, opts=None, want_vectors=True):
         opts = opts or default_options()
