@@ -291,8 +291,14 @@ def run_serving(args):
     from synth import serving_arrivals, serving_request_spec
     specs = [serving_request_spec(r)[0] for r in range(args.requests)]
     # inputs drawn on the host cores before the first CUDA call (spawned workers)
+    t_start = time.perf_counter()
+
+    def progress(what):
+        print(f"[serving] {time.perf_counter() - t_start:8.1f} s  {what}", file=sys.stderr, flush=True)
+
     with mp.get_context("spawn").Pool(max(1, min(len(specs), len(os.sched_getaffinity(0)) // 4))) as pool:
         systems = pool.map(_make_system, specs)
+    progress(f"{len(systems)} synthetic systems drawn")
     arrivals = serving_arrivals(len(specs), rate=args.rate)
     import torch
     torch.cuda.set_device(local)
@@ -322,9 +328,13 @@ def run_serving(args):
     seq_w = []
     t0 = time.perf_counter()
     for sy, (Lp, Fp) in zip(systems, host):
+        t1 = time.perf_counter()
         w = mlcc.solve(ctx, Lp.numpy(), Fp.numpy(), sy.spec.n_occ, sy.level, opts_for(sy.spec, prec)).omega
         seq_w.append(w)
+        progress(f"{sy.spec.name} ({sy.spec.n_occ} occ / {sy.spec.n_vir} vir, {sy.spec.n_chol} vectors): "
+                 f"{time.perf_counter() - t1:.1f} s")
     seq_s = time.perf_counter() - t0
+    progress(f"one at a time: {seq_s:.1f} s")
     # the same, with the Jacobian transformations evaluated eagerly (no CUDA graphs)
     seq_nog_s = None
     if args.sigma_graph:
@@ -332,6 +342,7 @@ def run_serving(args):
         for sy, (Lp, Fp) in zip(systems, host):
             mlcc.solve(ctx, Lp.numpy(), Fp.numpy(), sy.spec.n_occ, sy.level, opts_for(sy.spec, prec, graph=0))
         seq_nog_s = time.perf_counter() - t0
+        progress(f"one at a time without sigma graphs: {seq_nog_s:.1f} s")
     # plain binary64, one at a time, on the first fp64_sample requests (accuracy and speed)
     fp64_s, errs = [], []
     for k in range(min(args.fp64_sample, len(systems))):
@@ -340,6 +351,7 @@ def run_serving(args):
         w64 = mlcc.solve(ctx, Lp.numpy(), Fp.numpy(), sy.spec.n_occ, sy.level,
                          opts_for(sy.spec, mlcc.MLCC_FP64, graph=0)).omega
         fp64_s.append(time.perf_counter() - t1)
+        progress(f"binary64 solve of request {k}: {fp64_s[-1]:.1f} s")
         errs.append(float(np.max(np.abs(np.asarray(seq_w[k]) - w64))))
     ctx.close()
     # the mix: submissions at the arrival times, results polled as they finish

@@ -131,8 +131,9 @@ typedef struct {
                              sweep with refine_precision sigma on the low-precision
                              Ritz vectors), fewer if es_res_tol is met                  */
   int32_t gs_precision;   /* mlcc_precision of the ground-state iterations; the low-
-                             precision phase ends when |Omega| < 1e-7 or stops halving
-                             over three iterations                                     */
+                             precision phase ends when |Omega| < 1e-7, when it stops
+                             halving over three iterations, or when below 1e-5 one
+                             iteration does not halve it                               */
   double gs_tol;          /* |Omega|_2 threshold                                      */
   double gs_energy_tol;   /* |dE| threshold between iterations                        */
   double es_res_tol;      /* |A R - w R|_2 threshold per root                          */

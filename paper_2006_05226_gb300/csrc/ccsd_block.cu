@@ -7,6 +7,10 @@
 // terms with Y, u and F~ (the first line is symmetric already).
 #include "system.cuh"
 
+#include <cstring>
+#include <map>
+#include <string>
+
 namespace mlcc {
 
 void ccsd_cache_free(mlcc_system* S) {
@@ -15,6 +19,37 @@ void ccsd_cache_free(mlcc_system* S) {
 }
 
 namespace {
+
+// For "Jpq,Jrs->out" (equal operand index patterns, the same contracted indices in the same
+// places): out with the free indices of the first operand exchanged for those of the second
+// at the same places, e.g. "Jai,Jbj->aibj" gives "bjai". False for other specs.
+bool exchange_spec(const char* spec, std::string& swapped) {
+  const char* comma = strchr(spec, ',');
+  const char* arrow = strstr(spec, "->");
+  if (!comma || !arrow || arrow < comma) return false;
+  const std::string a(spec, comma), b(comma + 1, arrow), c(arrow + 2);
+  if (a.size() != b.size()) return false;
+  std::map<char, char> swap;
+  for (size_t k = 0; k < a.size(); ++k) {
+    const bool fa = c.find(a[k]) != std::string::npos, fb = c.find(b[k]) != std::string::npos;
+    if (fa != fb) return false;
+    if (!fa) {
+      if (a[k] != b[k]) return false;   // contracted: the same index in the same place
+      continue;
+    }
+    if (a[k] == b[k]) return false;     // a batch index: not a pair exchange
+    swap[a[k]] = b[k];
+    swap[b[k]] = a[k];
+  }
+  if (swap.empty()) return false;
+  swapped = c;
+  for (char& ch : swapped) {
+    auto it = swap.find(ch);
+    if (it == swap.end()) return false;
+    ch = it->second;
+  }
+  return true;
+}
 
 // Value / tangent evaluator. In Value mode tensors get values (persistently when caching);
 // in Tangent mode values come back from the cache in creation order and tangents are
@@ -70,6 +105,20 @@ struct Eval {
     cudaStream_t s = S->ctx->stream;
     if (mode == Mode::Value) {
       einsum(spec, alpha, A.v, B.v, beta, C.v, S->ws, s, S->ctx->sm_count);
+      return;
+    }
+    std::string swapped;
+    if (&A == &B && A.d.p && exchange_spec(spec, swapped)) {
+      // d(A A) = dA A + A dA, and A dA is dA A with the two operands' index groups
+      // exchanged: one product and a permuted copy instead of two products
+      Scope sc(S->ws);
+      DT T;
+      T.d = C.d.d;
+      T.p = S->ws.get<double>(size_t(T.size()));
+      einsum(spec, alpha, A.d, B.v, 0.0, T, S->ws, s, S->ctx->sm_count);
+      const std::string out = std::string(strchr(spec, '>') + 1);
+      eperm((out + "->" + out).c_str(), 1.0, T, beta, C.d, s);
+      eperm((swapped + "->" + out).c_str(), 1.0, T, 1.0, C.d, s);
       return;
     }
     double b = beta;
@@ -147,7 +196,123 @@ void ladder_tangent(mlcc_system* S, const DT& dt, const double* c1, DT& om_d) {
   eperm("baji->aibj", -1.0, W, 1.0, om_d, s);
 }
 
+// The ladder term of the ground-state residual, sum_cd g~_acbd t_cidj, from the undressed
+// integrals of gs_ladder_build. With the T1 dressing of the virtual rows,
+// L~_ac = L_ac - sum_K t_aK L_Kc (K over every occupied orbital, Sec. 2.1),
+//   sum_cd g~_acbd t_cidj = sum_cd g_acbd t_cidj - sum_K t_aK U_Kbij - sum_L t_bL U_Laji
+//                           + sum_KL t_aK t_bL W_KLij,
+// U_Kbij = sum_cd g_Kcbd t_cidj, W_KLij = sum_cd g_KcLd t_cidj (the third term uses the pair
+// symmetry of g and t). The three contractions over (cd) are one GEMM against the stacked
+// constant operand, 2 (v^2 + n_o v + n_o^2) v^2 o^2 flop, timed as the "gs_ladder_*"
+// family; the rest is O(n_o v^2 o^2).
+void ladder_value(mlcc_system* S, const DT& t, const double* t1, DT& om) {
+  cudaStream_t s = S->ctx->stream;
+  const int sm = S->ctx->sm_count;
+  const int64_t o = S->to, v = S->tv, no = S->no, oo = o * o;
+  const int64_t rows = v * v + no * v + no * no;
+  Scope sc(S->ws);
+  DT tcd;
+  tcd.d = {v, v, o, o};
+  tcd.p = S->ws.get<double>(size_t(v * v * oo));
+  eperm("cidj->cdij", 1.0, t, 0.0, tcd, s);
+  double* W = S->ws.get<double>(size_t(rows * oo));
+  Gemm g;
+  g.M = rows; g.N = oo; g.K = v * v;
+  g.A = S->gsl; g.lda = v * v; g.a_const = true;
+  g.B = tcd.p; g.ldb = oo;
+  g.C = W; g.ldc = oo;
+  const int lp = lowp_precision();
+  timed(S, lp == 0 ? "gs_ladder_f64" : (lp == MLCC_FP64E ? "gs_ladder_f64e" : "gs_ladder_tc"),
+        2.0 * double(rows) * double(v * v) * double(oo), [&] { gemm_f64(g, S->ws, s, sm); });
+  DT Wg;
+  Wg.d = {v, v, o, o};
+  Wg.p = W;
+  eperm("abij->aibj", 1.0, Wg, 1.0, om, s);
+  if (!t1 || no == 0) return;
+  // Y[a][(b i j)] = sum_K t_aK U[K][(b i j)]: om -= Y_abij + Y_baji
+  DT Y;
+  Y.d = {v, v, o, o};
+  Y.p = S->ws.get<double>(size_t(v * v * oo));
+  Gemm gy;
+  gy.M = v; gy.N = v * oo; gy.K = no;
+  gy.A = t1; gy.lda = no;
+  gy.B = W + v * v * oo; gy.ldb = v * oo;
+  gy.C = Y.p; gy.ldc = v * oo;
+  gemm_f64(gy, S->ws, s, sm);
+  eperm("abij->aibj", -1.0, Y, 1.0, om, s);
+  eperm("baji->aibj", -1.0, Y, 1.0, om, s);
+  // Z[a][(L i j)] = sum_K t_aK W[K][(L i j)], Q[a][b][(ij)] = sum_L t_bL Z[a][L][(ij)]: om += Q_abij
+  double* Z = S->ws.get<double>(size_t(v * no * oo));
+  Gemm gz;
+  gz.M = v; gz.N = no * oo; gz.K = no;
+  gz.A = t1; gz.lda = no;
+  gz.B = W + (v * v + no * v) * oo; gz.ldb = no * oo;
+  gz.C = Z; gz.ldc = no * oo;
+  gemm_f64(gz, S->ws, s, sm);
+  DT Q;
+  Q.d = {v, v, o, o};
+  Q.p = S->ws.get<double>(size_t(v * v * oo));
+  Gemm gq;
+  gq.M = v; gq.N = oo; gq.K = no;
+  gq.A = t1; gq.lda = no; gq.sA = 0;
+  gq.B = Z; gq.ldb = oo; gq.sB = no * oo;
+  gq.C = Q.p; gq.ldc = oo; gq.sC = v * oo;
+  gq.batch = v;
+  gemm_f64(gq, S->ws, s, sm);
+  eperm("abij->aibj", 1.0, Q, 1.0, om, s);
+}
+
 }  // namespace
+
+void gs_ladder_free(mlcc_system* S) {
+  if (S->gsl) cudaFree(S->gsl);
+  S->gsl = nullptr;
+  if (S->gsl_cache) operand_cache_free(S->gsl_cache);
+  S->gsl_cache = nullptr;
+}
+
+// rows (ab): g_acbd; rows (Kb): g_Kcbd; rows (KL): g_KcLd; columns (cd); all from the
+// undressed Cholesky vectors, so the operand holds for every iteration of a ground state
+bool gs_ladder_build(mlcc_system* S) {
+  gs_ladder_free(S);
+  if (S->to <= 0 || S->tv <= 0) return false;
+  const int64_t v = S->tv, no = S->no, nj = S->nj, n = S->n, nn = n * n;
+  const int64_t rows = v * v + no * v + no * no;
+  double* p = nullptr;
+  if (cudaMalloc(&p, size_t(rows) * size_t(v * v) * 8) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  S->gsl = p;
+  S->gsl_cache = operand_cache_new();
+  cudaStream_t s = S->ctx->stream;
+  const int sm = S->ctx->sm_count;
+  Scope sc(S->ws);
+  DT Lac, LKc;
+  Lac.d = {nj, v, v};
+  Lac.p = S->ws.get<double>(size_t(nj * v * v));
+  LKc.d = {nj, no, v};
+  LKc.p = S->ws.get<double>(size_t(nj * no * v));
+  {
+    int64_t dims[3] = {nj, v, v}, ss[3] = {nn, n, 1}, ds[3] = {v * v, v, 1};
+    permute_f64(3, dims, S->L + no * n + no, ss, Lac.p, ds, 1.0, 0.0, s);
+  }
+  {
+    int64_t dims[3] = {nj, no, v}, ss[3] = {nn, n, 1}, ds[3] = {no * v, v, 1};
+    permute_f64(3, dims, S->L + no, ss, LKc.p, ds, 1.0, 0.0, s);
+  }
+  DT A1, A2, A3;
+  A1.d = {v, v, v, v};
+  A1.p = p;
+  A2.d = {no, v, v, v};
+  A2.p = p + v * v * v * v;
+  A3.d = {no, no, v, v};
+  A3.p = A2.p + no * v * v * v;
+  einsum("Jac,Jbd->abcd", 1.0, Lac, Lac, 0.0, A1, S->ws, s, sm);
+  einsum("JKc,Jbd->Kbcd", 1.0, LKc, Lac, 0.0, A2, S->ws, s, sm);
+  einsum("JKc,JLd->KLcd", 1.0, LKc, LKc, 0.0, A3, S->ws, s, sm);
+  return true;
+}
 
 void ccsd_block(mlcc_system* S, Mode mode, const Dual& Lai_in, const Dual& Lac_in,
                 const Dual& Lki_in, const Dual& Lkc_in, const Dual& Fvv_in, const Dual& Foo_in,
@@ -170,8 +335,11 @@ void ccsd_block(mlcc_system* S, Mode mode, const Dual& Lai_in, const Dual& Lac_i
   // tangent of g~_acbd is not formed: the ladder term, its only use, has its own tangent
   // (ladder_tangent, through the intermediates cached below)
   if (mode == Mode::Tangent && !c1) throw Error(MLCC_E_STATE, "CCSD tangent without the trial singles");
-  Dual g_acbd = E.value_only({v, v, v, v});
-  if (mode == Mode::Value) E.ein("Jac,Jbd->acbd", 1.0, Lac, Lac, 0.0, g_acbd);
+  // the ground state's residual takes the ladder from the undressed integrals (ladder_value)
+  const bool undressed_ladder = mode == Mode::Value && !cache_values && S->gsl && !S->jwin;
+  Dual g_acbd;
+  if (!undressed_ladder) g_acbd = E.value_only({v, v, v, v});
+  if (mode == Mode::Value && !undressed_ladder) E.ein("Jac,Jbd->acbd", 1.0, Lac, Lac, 0.0, g_acbd);
   if (mode == Mode::Value && cache_values) {
     // g~_Kcbd for the tangent above
     const int64_t no = S->no, nj = S->nj, n = S->n, nn = n * n;
@@ -211,7 +379,8 @@ void ccsd_block(mlcc_system* S, Mode mode, const Dual& Lai_in, const Dual& Lac_i
   // first line: g~_aibj + g~_acbd t^{cd}_{ij} + t^{ab}_{kl} (g~_kilj + t^{cd}_{ij} g~_kcld)
   Dual om = E.make(vovo);
   E.ein("Jai,Jbj->aibj", 1.0, Lai, Lai, 0.0, om);
-  if (mode == Mode::Value) E.ein("acbd,cidj->aibj", 1.0, g_acbd, t, 1.0, om);
+  if (undressed_ladder) ladder_value(S, t.v, c1, om.v);
+  else if (mode == Mode::Value) E.ein("acbd,cidj->aibj", 1.0, g_acbd, t, 1.0, om);
   else if (rest) ladder_tangent(S, t.d, c1, om.d);   // built from the cached values over all J
   Dual X = E.make({o, o, o, o});
   E.perm("kilj->kilj", 1.0, g_kilj, 0.0, X);

@@ -17,6 +17,22 @@ __device__ __forceinline__ float d2f_bits(double x) {
   else if (e > 0) r |= (unsigned(e) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
   return __uint_as_float(r);
 }
+// binary64 -> binary32 rounded to nearest (ties to even); magnitudes below the binary32
+// normal range give 0, values that round beyond it give Inf, NaN stays NaN
+__device__ __forceinline__ float d2f_rn_bits(double x) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const unsigned sign = unsigned(b >> 32) & 0x80000000u;
+  const int ef = int((b >> 52) & 0x7FF);
+  const unsigned long long m = b & ((1ull << 52) - 1);
+  if (ef == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (m ? 0x400000u : 0u));
+  const int e = ef - 896;   // binary32 biased exponent
+  if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
+  if (e <= 0) return __uint_as_float(sign);
+  unsigned r = (unsigned(e) << 23) | unsigned(m >> 29);
+  const unsigned rest = unsigned(m & 0x1FFFFFFFull);
+  if (rest > 0x10000000u || (rest == 0x10000000u && (r & 1u))) ++r;   // a carry may reach Inf
+  return __uint_as_float(sign | r);
+}
 // exact binary32 -> binary64 (binary32 subnormals give 0)
 __device__ __forceinline__ double f2d_bits(float f) {
   const unsigned u = __float_as_uint(f);

@@ -5,6 +5,7 @@
 // bfloat16, or the binary64 emulation), under a Vec32Scope its skinny products and the dot
 // products multiply in binary32 (vec32.cu).
 #include "internal.cuh"
+#include "tc_common.cuh"
 
 #include <algorithm>
 #include <cstring>
@@ -257,12 +258,22 @@ __global__ void k_skinny_m(GP p) {
         for (int m = 0; m < MM; ++m) acc[m] = fma(As[m * 64 + k], b, acc[m]);
       }
     } else {
-      for (int64_t k = 0; k < p.K; ++k) {
+      // K split over blockIdx.y when p.kchunk > 0 (partials reduced afterwards)
+      const int64_t k0 = p.kchunk > 0 ? int64_t(blockIdx.y) * p.kchunk : 0;
+      const int64_t k1 = p.kchunk > 0 ? min(p.K, k0 + p.kchunk) : p.K;
+      for (int64_t k = k0; k < k1; ++k) {
         const double b = p.B[k * p.ldb + n];
 #pragma unroll
         for (int m = 0; m < MM; ++m)
           if (m < p.M) acc[m] = fma(TA ? p.A[k * p.lda + m] : p.A[m * p.lda + k], b, acc[m]);
       }
+    }
+    if (p.partial) {
+      double* part = p.partial + int64_t(blockIdx.y) * p.M * p.N;
+#pragma unroll
+      for (int m = 0; m < MM; ++m)
+        if (m < p.M) part[m * p.N + n] = acc[m];
+      return;
     }
 #pragma unroll
     for (int m = 0; m < MM; ++m)
@@ -322,9 +333,9 @@ __global__ void k_gemv_n1(GP p) {
   }
 }
 template <int MM>
-static void launch_skinny(const GP& p, bool ta, bool tb, cudaStream_t s) {
+static void launch_skinny(const GP& p, bool ta, bool tb, cudaStream_t s, int ksplit = 1) {
   if (!tb) {
-    const unsigned blocks = unsigned((p.N + 255) / 256);
+    const dim3 blocks{unsigned((p.N + 255) / 256), unsigned(ksplit), 1};
     if (ta) k_skinny_m<MM, true, false><<<blocks, 256, 0, s>>>(p);
     else k_skinny_m<MM, false, false><<<blocks, 256, 0, s>>>(p);
   } else {
@@ -397,11 +408,33 @@ void gemm_f64(const Gemm& g, Arena& ws, cudaStream_t s, int sm_count) {
   p.kchunk = 0;
   if (!g.reduce && g.batch == 1 && g.M <= 16 && g.N >= 64) {
     if (g_vec32 && skinny32(g, s)) return;
-    if (g.M <= 1) launch_skinny<1>(p, g.ta, g.tb, s);
-    else if (g.M <= 4) launch_skinny<4>(p, g.ta, g.tb, s);
-    else if (g.M <= 8) launch_skinny<8>(p, g.ta, g.tb, s);
-    else launch_skinny<16>(p, g.ta, g.tb, s);
+    // few column blocks and a long K (beyond what is staged): split K over blockIdx.y
+    int64_t ks = 1;
+    size_t mk = ws.mark();
+    const int64_t nblocks = (g.N + 255) / 256;
+    if (!g.tb && g.K > 64 && nblocks < 2LL * std::max(sm_count, 1)) {
+      ks = std::min<int64_t>({(4LL * std::max(sm_count, 1) + nblocks - 1) / nblocks, g.K / 64, 1024});
+      while (ks > 1 && ks * g.M * g.N * 8 > (int64_t(1) << 30)) ks /= 2;
+      if (ks > 1) {
+        p.kchunk = (g.K + ks - 1) / ks;
+        ks = (g.K + p.kchunk - 1) / p.kchunk;
+        p.partial = ws.get<double>(size_t(ks) * g.M * g.N);
+      } else {
+        ks = 1;
+      }
+    }
+    if (g.M <= 1) launch_skinny<1>(p, g.ta, g.tb, s, int(ks));
+    else if (g.M <= 4) launch_skinny<4>(p, g.ta, g.tb, s, int(ks));
+    else if (g.M <= 8) launch_skinny<8>(p, g.ta, g.tb, s, int(ks));
+    else launch_skinny<16>(p, g.ta, g.tb, s, int(ks));
     MLCC_CHECK_LAUNCH();
+    if (ks > 1) {
+      const int64_t total = g.M * g.N;
+      const int blocks = int(std::min<int64_t>((total + 255) / 256, 4096));
+      k_reduce_partials<<<blocks, 256, 0, s>>>(p.partial, int(ks), g.M, g.N, g.C, g.ldc, g.alpha, g.beta);
+      MLCC_CHECK_LAUNCH();
+    }
+    ws.release(mk);
     return;
   }
   if (!g.reduce && g.batch == 1 && g.N == 1 && g.M >= 64) {
@@ -421,11 +454,12 @@ void gemm_f64(const Gemm& g, Arena& ws, cudaStream_t s, int sm_count) {
     // cap the partial buffer at 1 GiB
     while (gz > 1 && gz * g.M * g.N * 8 > (int64_t(1) << 30)) gz /= 2;
     if (gz > 1) p.partial = ws.get<double>(size_t(gz) * g.M * g.N);
-  } else if (g.batch == 1 && tm * tn < 2LL * std::max(sm_count, 1) && g.K >= 512) {
-    // too few output tiles to fill the GPU: split K over CTAs, reduce the partials
+  } else if (g.batch == 1 && tm * tn < 2LL * std::max(sm_count, 1) && g.K >= 64) {
+    // too few output tiles to fill the GPU: split K over CTAs, reduce the partials (one SM
+    // takes about 0.5 ms for a 64 x 64 x 500 binary64 tile, so even short K is split)
     const int64_t tiles = tm * tn;
     const int64_t want = (4LL * std::max(sm_count, 1) + tiles - 1) / tiles;
-    int64_t splits = std::max<int64_t>(1, std::min<int64_t>(want, g.K / 256));
+    int64_t splits = std::max<int64_t>(1, std::min<int64_t>(want, g.K / 32));
     while (splits > 1 && splits * g.M * g.N * 8 > (int64_t(1) << 30)) splits /= 2;
     if (splits > 1) {
       p.kchunk = ((g.K + splits - 1) / splits + BK - 1) / BK * BK;
@@ -629,35 +663,60 @@ void einsum(const char* spec, double alpha, const DT& A, const DT& B, double bet
   };
   std::string kord = cost(ka) <= cost(kb) ? ka : kb;
   Scope scope(ws);
+  // An operand inside the constant ranges of the current operand cache (the Jacobian's
+  // value tensors while sigma runs) keeps its GEMM-order copy in that cache, so the GEMM
+  // can keep its converted pieces too. Nothing is allocated while the stream captures a
+  // graph: the eager evaluation before the capture has filled the cache.
+  OperandCache* oc = lowp_cache();
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (oc) MLCC_CUDA(cudaStreamIsCapturing(s, &cap));
+  auto operand = [&](const DT& X, const std::string& from, const std::string& to, bool& cst) -> const double* {
+    cst = oc && oc->constant(X.p);
+    const std::string sps = from + "->" + to;
+    DT t;
+    for (char ch : to) t.d.push_back(size[ch]);
+    const size_t count = size_t(t.size());
+    if (cst) {
+      for (auto& e : oc->perms)
+        if (e.src == X.p && e.dims == X.d && e.spec == sps) return e.p;
+      void* mem = nullptr;
+      if (cap == cudaStreamCaptureStatusNone && cudaMalloc(&mem, count * 8) == cudaSuccess) {
+        oc->blocks.push_back(mem);
+        t.p = static_cast<double*>(mem);
+        eperm(sps.c_str(), 1.0, X, 0.0, t, s);
+        oc->perms.push_back({X.p, X.d, sps, t.p});
+        return t.p;
+      }
+      if (cap == cudaStreamCaptureStatusNone) cudaGetLastError();
+      cst = false;
+    }
+    t.p = ws.get<double>(count);
+    eperm(sps.c_str(), 1.0, X, 0.0, t, s);
+    return t.p;
+  };
   Gemm g;
   g.M = M; g.N = N; g.K = K;
   g.batch = nb;
   // A operand
   const double* Ap = A.p;
-  if (sp.a == bat + mi + kord) { g.ta = false; g.lda = K; }
-  else if (sp.a == bat + kord + mi) { g.ta = true; g.lda = M; }
+  if (sp.a == bat + mi + kord) { g.ta = false; g.lda = K; g.a_const = oc && oc->constant(A.p); }
+  else if (sp.a == bat + kord + mi) { g.ta = true; g.lda = M; g.a_const = oc && oc->constant(A.p); }
   else {
-    DT t;
-    t.p = ws.get<double>(size_t(nb * M * K));
-    for (char ch : bat + mi + kord) t.d.push_back(size[ch]);
-    const std::string sps = sp.a + "->" + bat + mi + kord;
-    eperm(sps.c_str(), 1.0, A, 0.0, t, s);
-    Ap = t.p;
+    bool cst = false;
+    Ap = operand(A, sp.a, bat + mi + kord, cst);
+    g.a_const = cst;
     g.ta = false;
     g.lda = K;
   }
   g.A = Ap;
   g.sA = M * K;
   const double* Bp = B.p;
-  if (sp.b == bat + kord + ni) { g.tb = false; g.ldb = N; }
-  else if (sp.b == bat + ni + kord) { g.tb = true; g.ldb = K; }
+  if (sp.b == bat + kord + ni) { g.tb = false; g.ldb = N; g.b_const = oc && oc->constant(B.p); }
+  else if (sp.b == bat + ni + kord) { g.tb = true; g.ldb = K; g.b_const = oc && oc->constant(B.p); }
   else {
-    DT t;
-    t.p = ws.get<double>(size_t(nb * K * N));
-    for (char ch : bat + kord + ni) t.d.push_back(size[ch]);
-    const std::string sps = sp.b + "->" + bat + kord + ni;
-    eperm(sps.c_str(), 1.0, B, 0.0, t, s);
-    Bp = t.p;
+    bool cst = false;
+    Bp = operand(B, sp.b, bat + kord + ni, cst);
+    g.b_const = cst;
     g.tb = false;
     g.ldb = N;
   }

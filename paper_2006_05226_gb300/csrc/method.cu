@@ -54,7 +54,24 @@ __device__ __forceinline__ void split4(int64_t t, int sv, int so, int& a, int& i
   i = int(t % so);
   a = int(t / so);
 }
-// u[a,i,b,j] = 2 x[a,i,b,j] - x[a,j,b,i]
+// u[a,i,b,j] = 2 x[a,i,b,j] - x[a,j,b,i]: block (a, b) of u is 2 X - X^T for the so x so
+// block X at rows a so, columns b so of x; one CTA per block through shared memory (so <= 64)
+__global__ void k_make_u_blocks(const double* x, int sv, int so, double* u) {
+  __shared__ double tile[64][65];
+  const int64_t dS = int64_t(sv) * so;
+  const double* xb = x + (int64_t(blockIdx.y) * so) * dS + int64_t(blockIdx.x) * so;
+  double* ub = u + (int64_t(blockIdx.y) * so) * dS + int64_t(blockIdx.x) * so;
+  for (int t = threadIdx.x; t < so * so; t += blockDim.x) {
+    const int i = t / so, j = t - i * so;
+    tile[i][j] = xb[int64_t(i) * dS + j];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < so * so; t += blockDim.x) {
+    const int i = t / so, j = t - i * so;
+    ub[int64_t(i) * dS + j] = fma(2.0, tile[i][j], -tile[j][i]);
+  }
+}
+// the same for any so, element by element
 __global__ void k_make_u(const double* x, int sv, int so, double* u) {
   const int64_t total = int64_t(sv) * so * sv * so;
   for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
@@ -99,26 +116,32 @@ __global__ void k_omega2_cc2(const double* g, const double* x2, const double* ep
 }
 // sigma on P_S: W_(ai)(bj) + W_(bj)(ai) + eps c; P_T rows 0. 32 x 32 tiles through shared
 // memory so that both the direct and the transposed read are coalesced.
+// The orbital-energy part eps_scale (e_a - e_i + e_b - e_j) is split into a row and a column
+// share taken once per row and per thread: three binary64 operations per element remain
+// (the binary64 pipe, not HBM, bounded the straightforward form on GB300).
 __global__ void k_sigma2_cc2(const double* W, const double* c, const double* eps, int no, int sv,
                              int so, int tv, int to, double eps_scale, double* s2) {
   __shared__ double tile[32][33];
-  const int64_t dS = int64_t(sv) * so;
-  const int64_t r0 = int64_t(blockIdx.y) * 32, c0 = int64_t(blockIdx.x) * 32;
+  const int dS = sv * so;   // dS^2 doubles fit the device: dS < 2^31
+  const int r0 = int(blockIdx.y) * 32, c0 = int(blockIdx.x) * 32;
   // transposed block W[c0.., r0..] -> tile[col][row]
   for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-    const int64_t rr = c0 + y, cc = r0 + threadIdx.x;
-    tile[y][threadIdx.x] = (rr < dS && cc < dS) ? W[rr * dS + cc] : 0.0;
+    const int rr = c0 + y, cc = r0 + threadIdx.x;
+    tile[y][threadIdx.x] = (rr < dS && cc < dS) ? W[int64_t(rr) * dS + cc] : 0.0;
   }
   __syncthreads();
+  const int col = c0 + threadIdx.x;
+  if (col >= dS) return;
+  const int b = col / so, j = col - b * so;
+  const double ec = eps_scale * (eps[no + b] - eps[j]);
+  const bool tcol = b < tv && j < to;
   for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-    const int64_t row = r0 + y, col = c0 + threadIdx.x;
-    if (row >= dS || col >= dS) continue;
-    const int a = int(row / so), i = int(row - int64_t(a) * so);
-    const int b = int(col / so), j = int(col - int64_t(b) * so);
-    const int64_t t = row * dS + col;
-    s2[t] = in_T(a, i, b, j, tv, to)
-                ? 0.0
-                : W[t] + tile[threadIdx.x][y] + eps_scale * eps4(eps, no, a, i, b, j) * c[t];
+    const int row = r0 + y;
+    if (row >= dS) break;
+    const int a = row / so, i = row - a * so;
+    const double er = eps_scale * (eps[no + a] - eps[i]);
+    const int64_t t = int64_t(row) * dS + col;
+    s2[t] = (tcol && a < tv && i < to) ? 0.0 : fma(er + ec, c[t], W[t] + tile[threadIdx.x][y]);
   }
 }
 // om1[a*no + i] += alpha * tmp[a*so + i]
@@ -197,7 +220,11 @@ void gather_ov(mlcc_system* S, const double* X, double* out) {
 }
 void make_u(mlcc_system* S, const double* x2, double* u) {
   if (S->nd == 0) return;
-  k_make_u<<<nblk(S->nd), 256, 0, stm(S)>>>(x2, S->sv, S->so, u);
+  if (S->so <= 64 && S->sv < 65536) {
+    k_make_u_blocks<<<dim3(unsigned(S->sv), unsigned(S->sv), 1), 256, 0, stm(S)>>>(x2, S->sv, S->so, u);
+  } else {
+    k_make_u<<<nblk(S->nd), 256, 0, stm(S)>>>(x2, S->sv, S->so, u);
+  }
   MLCC_CHECK_LAUNCH();
 }
 
@@ -449,7 +476,7 @@ void omega_eval(mlcc_system* S, const double* t1, const double* x2, bool gs_mode
     extract_box(S, S->Lt, S->Ft, xuse, Lai.v, Lac.v, Lki.v, Lkc.v, Fvv.v, Foo.v, t.v);
     const int64_t tl = int64_t(S->tv) * S->to * S->tv * S->to;
     double* omT = gs_mode ? om2 : S->ws.get<double>(size_t(tl));
-    ccsd_block(S, Mode::Value, Lai, Lac, Lki, Lkc, Fvv, Foo, t, omT, false, nullptr);
+    ccsd_block(S, Mode::Value, Lai, Lac, Lki, Lkc, Fvv, Foo, t, omT, false, t1);
     if (!gs_mode) put_tbox(S, omT, om2);
   }
   // singles (Eq. mlcc2_omega_codable) with u from all doubles
@@ -543,15 +570,29 @@ void jacobian_prepare(mlcc_system* S, const double* t1, const double* x2) {
 
 // out[A][I] += alpha * sum_J d[J] X[J][r0 + A][c0 + I] over a rows x cols block
 namespace {
+// out[A][I] += alpha sum_J d[J] X^J[r0 + A][c0 + I]. blockIdx.y takes J in [y jc, (y + 1) jc)
+// and writes its partial sums to part[y][rows * cols]; k_sum_over_J_add adds them in order
 __global__ void k_sum_over_J(const double* d, const double* X, int nj, int n, int r0, int c0,
-                             int rows, int cols, double alpha, double* out, int ldo) {
+                             int rows, int cols, int jc, double* part) {
   const int64_t total = int64_t(rows) * cols, nn = int64_t(n) * n;
+  const int j0 = int(blockIdx.y) * jc, j1 = min(nj, j0 + jc);
   for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
        t += int64_t(gridDim.x) * blockDim.x) {
     const int A = int(t / cols), I = int(t - int64_t(A) * cols);
     const double* x = X + int64_t(r0 + A) * n + c0 + I;
     double acc = 0.0;
-    for (int J = 0; J < nj; ++J) acc = fma(d[J], x[J * nn], acc);
+    for (int J = j0; J < j1; ++J) acc = fma(d[J], x[J * nn], acc);
+    part[int64_t(blockIdx.y) * total + t] = acc;
+  }
+}
+__global__ void k_sum_over_J_add(const double* part, int nch, int rows, int cols, double alpha, double* out,
+                                 int ldo) {
+  const int64_t total = int64_t(rows) * cols;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    double acc = 0.0;
+    for (int c = 0; c < nch; ++c) acc += part[int64_t(c) * total + t];
+    const int A = int(t / cols), I = int(t - int64_t(A) * cols);
     out[int64_t(A) * ldo + I] += alpha * acc;
   }
 }
@@ -629,8 +670,18 @@ __global__ void k_outer_add(const double* x, const double* y, int64_t m, double 
 static void sum_over_J(mlcc_system* S, const double* d, const double* X, int r0, int c0, int rows,
                        int cols, double alpha, double* out, int ldo) {
   if (rows <= 0 || cols <= 0) return;
-  k_sum_over_J<<<nblk(int64_t(rows) * cols), 256, 0, stm(S)>>>(d, X, S->nj, S->n, r0, c0, rows, cols,
-                                                                alpha, out, ldo);
+  // the sum over J runs in chunks on blockIdx.y, enough blocks to fill the GPU
+  const int64_t total = int64_t(rows) * cols;
+  const int64_t eb = std::min<int64_t>((total + 255) / 256, 65535);
+  const int nch = int(std::max<int64_t>(1, std::min<int64_t>({(4LL * smc(S) + eb - 1) / eb, S->nj, 64})));
+  const int jc = (S->nj + nch - 1) / nch;
+  const int ny = (S->nj + jc - 1) / jc;
+  Scope sc(S->ws);
+  double* part = S->ws.get<double>(size_t(ny) * total);
+  k_sum_over_J<<<dim3(unsigned(eb), unsigned(ny), 1), 256, 0, stm(S)>>>(d, X, S->nj, S->n, r0, c0, rows, cols, jc,
+                                                                       part);
+  MLCC_CHECK_LAUNCH();
+  k_sum_over_J_add<<<nblk(total), 256, 0, stm(S)>>>(part, ny, rows, cols, alpha, out, ldo);
   MLCC_CHECK_LAUNCH();
 }
 

@@ -66,7 +66,12 @@ int64_t footprint(const sizes::Dims& d, const mlcc_options& o) {
   int bpe = cache_bytes_per_element(o.precision);
   if (split(o.precision) && o.refine_fp64 > 0) bpe += cache_bytes_per_element(o.refine_precision);
   const size_t cache = round_alloc(sizes::operand_cache_allowance(d, bpe));
-  const size_t after = amps + round_alloc(sizes::ccsd_cache_bytes(d)) + lowp + dav + cache;
+  // the ground state's ladder operand (with its largest converted copy) is gone before the
+  // Jacobian's buffers are made
+  const int gs_bpe = std::max(cache_bytes_per_element(o.gs_precision),
+                              o.refine_fp64 > 0 ? cache_bytes_per_element(o.refine_precision) : 0);
+  const size_t gsl = round_alloc(sizes::gs_ladder_bytes(d, gs_bpe));
+  const size_t after = amps + std::max(gsl, round_alloc(sizes::ccsd_cache_bytes(d)) + lowp + dav + cache);
   return int64_t(system + std::max(inputs, after));
 }
 

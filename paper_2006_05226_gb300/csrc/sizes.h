@@ -76,6 +76,16 @@ inline size_t ccsd_cache_bytes(const Dims& d) {
   return size_t(need) * 8 + 64 * 256;
 }
 
+// The ground state's constant ladder operand [(ab) | (Kb) | (KL)][(cd)] in binary64 and one
+// converted copy of it with `conv_bytes_per_element` (zero without a CCSD level). It lives
+// while the ground state runs.
+inline size_t gs_ladder_bytes(const Dims& d, int conv_bytes_per_element) {
+  if (d.to <= 0 || d.tv <= 0) return 0;
+  const int64_t rows = d.tv * d.tv + d.no * d.tv + d.no * d.no, k = d.tv * d.tv;
+  return size_t(rows) * size_t(k) * 8 + size_t(rows) * size_t(pad64(k)) * size_t(std::max(conv_bytes_per_element, 0)) +
+         size_t(rows) * 4;
+}
+
 // bfloat16 pieces of the constant rank-GEMM operands Lai and Lov in a split precision with
 // `seg` pieces per product (zero without CC2-active pairs).
 inline size_t lowp_bytes(const Dims& d, int seg) {
@@ -101,10 +111,14 @@ inline size_t davidson_bytes(int64_t dim, int max_subspace, int n_roots) {
 // `bytes_per_element` summed over the precisions in use (2 per bfloat16 piece; 16 plus
 // exponents for the 8 integer digits of the binary64 emulation). An estimate, not a bound
 // the cache enforces.
+// Each CCSD-block value tensor that an einsum of the sigma rows reads in another order also
+// keeps that binary64 copy (with its converted pieces) in the cache.
 inline size_t operand_cache_allowance(const Dims& d, int bytes_per_element) {
   if (bytes_per_element <= 0) return 0;
   const int64_t elems = d.nj * d.nn() + 3 * d.nj * d.dS + d.nd + d.tv * d.tv * d.tv * d.tv;
-  return size_t(elems) * size_t(bytes_per_element);
+  const int64_t tb = d.tv + d.to;
+  const int64_t perm = (d.to > 0 && d.tv > 0) ? d.nj * tb * tb + 16 * d.tl() + 4 * d.to * d.to * d.to * d.to : 0;
+  return size_t(elems) * size_t(bytes_per_element) + size_t(perm) * size_t(8 + bytes_per_element);
 }
 
 // cudaMalloc hands out large blocks in 2 MiB pages.

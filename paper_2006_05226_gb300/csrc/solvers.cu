@@ -204,11 +204,23 @@ mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out
   bool conv = false;
   // low-precision phase (gs_precision), then refine_precision when refine_fp64 is set
   int phase_prec = opt->gs_precision;
+  // the ladder term's undressed integrals, built once in the most accurate precision the
+  // iterations use and freed with the ground state
+  struct LadderGuard {
+    mlcc_system* S;
+    ~LadderGuard() { gs_ladder_free(S); }
+  } ladder_guard{S};
+  {
+    const int bprec = (is_split_precision(phase_prec) && opt->refine_fp64) ? opt->refine_precision : phase_prec;
+    LowpScope lowp(bprec, S->tc_err);
+    timed(S, "gs_ladder_build", 0.0, [&] { gs_ladder_build(S); });
+    if (bprec != MLCC_FP64) check_tc_error(S);
+  }
   const double lowp_switch = std::max(opt->gs_tol, 1e-7);
   std::vector<double> lowp_norms;   // residual norms of the low-precision phase
   for (it = 1; it <= opt->max_gs_iter; ++it) {
     {
-      LowpScope lowp(phase_prec, S->tc_err);
+      LowpScope lowp(phase_prec, S->tc_err, S->gsl_cache);
       timed(S, "gs_omega", 0.0, [&] {
         omega_eval(S, t1, nullptr, true, tl ? tT : nullptr, x2, om1, tl ? omT : nullptr, energy);
       });
@@ -236,6 +248,9 @@ mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out
         const double recent = *std::min_element(lowp_norms.end() - 3, lowp_norms.end());
         stalled = recent > 0.5 * before;   // no halving in three iterations: the noise floor
       }
+      // within a decade of the split-precision noise floor (about 1e-6), one iteration that
+      // does not halve the residual already marks it: the binary64-class phase takes over
+      if (q >= 2 && norm < 1e-5 && norm > 0.5 * lowp_norms[q - 2]) stalled = true;
     }
     if (split_phase && (norm < lowp_switch || stalled)) {
       if (!opt->refine_fp64) {
@@ -243,6 +258,7 @@ mlcc_status ground_state(mlcc_system* S, const mlcc_options* opt, double* t1_out
         break;
       }
       phase_prec = opt->refine_precision;   // the next iterations refine these amplitudes
+      operand_cache_clear(S->gsl_cache);    // converted in the split precision: not needed now
       order.clear();            // the low-precision residuals do not belong in DIIS
       std::fill(Bm.begin(), Bm.end(), 0.0);
       e_old = e;

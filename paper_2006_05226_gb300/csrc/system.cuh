@@ -73,6 +73,10 @@ struct mlcc_system {
   int* tc_err = nullptr;
   mlcc::OperandCache* opcache = nullptr;   // bfloat16 pieces of Jacobian-constant operands
   mlcc::SigmaGraphs* graphs = nullptr;     // CUDA graphs of sigma (mlcc_options.sigma_graph)
+  // ground state with a CCSD level: the undressed integrals of the ladder term as one
+  // constant operand [(ab) | (Kb) | (KL)][(cd)] (gs_ladder_build), and its converted copies
+  double* gsl = nullptr;
+  mlcc::OperandCache* gsl_cache = nullptr;
   // J window of a sharded Jacobian transformation (mlcc_sigma_partial): while set, nj, Lt,
   // Lai, Lov and Z describe the Cholesky vectors [jwin0, jwin0 + nj) only
   bool jwin = false;
@@ -128,12 +132,18 @@ double lowest_ps_denominator(const mlcc_system* S);
 // lowest roots of the folded CC2 Jacobian (folded_solve.cu); MLCC_E_ES_NOCONV if not converged
 mlcc_status excited_states_folded(mlcc_system* S, const mlcc_options* opt, double* omega_host, double* r_out,
                                   mlcc_es_info* info);
-// c1 (tangent mode only): the singles trial vector; the tangent of g~_acbd is then formed
-// from the cached g~_Kcbd instead of from the Cholesky vectors.
+// c1: in tangent mode the singles trial vector (the tangent of g~_acbd is then formed from
+// the cached g~_Kcbd instead of from the Cholesky vectors); in value mode the singles
+// amplitudes t1 (or NULL), which the ladder term takes with the operand of gs_ladder_build.
 void ccsd_block(mlcc_system* S, Mode mode, const Dual& Lai, const Dual& Lac, const Dual& Lki,
                 const Dual& Lkc, const Dual& Fvv, const Dual& Foo, const Dual& t, double* om_out,
                 bool cache_values, const double* c1, bool rest = true);
 void ccsd_cache_free(mlcc_system* S);
+// the constant ladder operand of the ground state (S->gsl) from the undressed Cholesky
+// vectors, in the current low-precision routing; false (nothing allocated) without a CCSD
+// level or when the device memory is short
+bool gs_ladder_build(mlcc_system* S);
+void gs_ladder_free(mlcc_system* S);
 void sigma_graphs_free(mlcc_system* S);
 void rank_gemm_lowp(mlcc_system* S, bool outer, const double* A, const double* B, double* C,
                     double alpha, double beta, int precision, bool b_is_u_source);

@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include <string>
 #include <tuple>
 #include <vector>
 
@@ -44,6 +45,14 @@ struct OperandCache {
     __nv_bfloat16* p;
   };
   std::vector<Entry> entries;
+  // binary64 copies of constant einsum operands in GEMM order (source, dims, permutation)
+  struct Perm {
+    const void* src;
+    std::vector<int64_t> dims;
+    std::string spec;
+    double* p;
+  };
+  std::vector<Perm> perms;
   std::vector<void*> blocks;
   std::vector<std::pair<const char*, size_t>> ranges;
   bool constant(const void* p) const {

@@ -3,11 +3,13 @@
 // with A, B bfloat16 and K-major (K contiguous, padded to a multiple of 64), the
 // accumulator fp32 in tensor memory and C binary64.
 //
-// One CTA computes a 128 x 256 tile: TMA (cp.async.bulk.tensor, 128-byte swizzle) fills a
-// 4-stage shared-memory ring; one elected thread issues tcgen05.mma (kind::f16, M = 128,
-// N = 256, K = 16) into a 256-column TMEM accumulator and releases stages with
-// tcgen05.commit; four epilogue warps read the accumulator with tcgen05.ld and write C
-// through a shared-memory transpose (coalesced row segments).
+// A persistent grid of one CTA per SM computes 128 x 256 tiles: TMA (cp.async.bulk.tensor,
+// 128-byte swizzle) fills a 4-stage shared-memory ring; one elected thread issues
+// tcgen05.mma (kind::f16, M = 128, N = 256, K = 16) into one of two 256-column TMEM
+// accumulators and releases stages with tcgen05.commit; four epilogue warps read the other
+// accumulator with tcgen05.ld and write C through a shared-memory transpose (coalesced row
+// segments) while the next tile's MMAs run. Whole waves of tiles run data-parallel, the
+// last one stream-K (K ranges of equal length per CTA, partial tiles combined after).
 // Every mbarrier wait is bounded: on timeout the thread records an error flag and the CTA
 // winds down (freeing its TMEM) instead of spinning.
 //
@@ -21,6 +23,7 @@
 // Batches that share A are flattened along N with a batched output-column mapping.
 #include "system.cuh"
 #include "tc_common.cuh"
+#include "fp_convert.cuh"
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -98,121 +101,215 @@ __host__ __device__ constexpr uint32_t instr_desc() {
   return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
 }
 
+// Persistent schedule: G CTAs, one per SM. Tiles [0, dp_tiles) run data-parallel (CTA c
+// takes tiles c, c + G, ...; dp_tiles is a multiple of G). The remaining tiles run
+// stream-K: their K-block iterations, tile after tile, are cut into G equal ranges, one
+// per CTA, so the last wave has no idle SMs. A tile that two or more CTAs share is written
+// by each of them as an fp32 partial into a slot of its own (2c for the first tile of the
+// range of CTA c, 2c + 1 for its last) and k_tc_sk_fixup adds the partials in CTA order.
+// Each CTA runs its segments through two TMEM accumulators in turn, so the epilogue of one
+// tile overlaps the MMAs of the next.
 struct TcParams {
   int64_t M, N;
-  int kblocks;      // K blocks in total
-  int kb_per;       // K blocks per split (blockIdx.z); == kblocks without split
+  int kblocks;      // K blocks of the product
+  int m_fast;       // 1: consecutive tiles run over M
+  int64_t tm, tn;   // tile rows, tile columns
+  int64_t dp_tiles; // data-parallel tiles
+  int64_t sk_iters; // K-block iterations of the stream-K tiles
   double* C;
   int64_t ldc;
   double alpha, beta;
-  double* partial;  // split-K: [split][M][N] (alpha, beta applied by the reduction)
+  float* slots;     // stream-K partial tiles: [2 G][BM][BN]
   int* err;
-  int m_fast;       // 1: blockIdx.x runs over M tiles
   // batched output columns (nb > 0): column b * nb + c of the product lands at
   // C + b * sCb + row * ldc + c (a batch of products that share A, flattened along N)
   int64_t nb, sCb;
 };
+__host__ __device__ __forceinline__ int64_t sk_begin(const TcParams& p, int64_t c, int64_t G) {
+  return c * p.sk_iters / G;
+}
+__device__ __forceinline__ void tile_origin(const TcParams& p, int64_t tile, int64_t& m0, int64_t& n0) {
+  int64_t mt, nt;
+  if (p.m_fast) {
+    mt = tile % p.tm;
+    nt = tile / p.tm;
+  } else {
+    nt = tile % p.tn;
+    mt = tile / p.tn;
+  }
+  m0 = mt * BM;
+  n0 = nt * BN;
+}
+__device__ __forceinline__ double* out_ptr(const TcParams& p, int64_t row, int64_t col) {
+  if (p.nb > 0) {
+    const int64_t cb = col / p.nb;
+    return p.C + cb * p.sCb + row * p.ldc + (col - cb * p.nb);
+  }
+  return p.C + row * p.ldc + col;
+}
+// one tile's K-block range [kb0, kb1) for this CTA; slot < 0: the whole tile, written to C
+struct TcSeg {
+  int64_t tile;
+  int kb0, kb1, slot;
+};
+// the CTA's segments in order (every role of the CTA walks the same list)
+struct TcWalk {
+  int64_t j, it, it0, it1;
+  __device__ explicit TcWalk(const TcParams& p) {
+    j = blockIdx.x;
+    it0 = sk_begin(p, blockIdx.x, gridDim.x);
+    it1 = sk_begin(p, int64_t(blockIdx.x) + 1, gridDim.x);
+    it = it0;
+  }
+  __device__ bool next(const TcParams& p, TcSeg& sg) {
+    if (j < p.dp_tiles) {
+      sg.tile = j;
+      sg.kb0 = 0;
+      sg.kb1 = p.kblocks;
+      sg.slot = -1;
+      j += gridDim.x;
+      return true;
+    }
+    if (it >= it1) return false;
+    const int64_t t = it / p.kblocks;
+    const int kb0 = int(it - t * p.kblocks);
+    const int64_t rest = it1 - it;
+    const int kb1 = rest < int64_t(p.kblocks - kb0) ? kb0 + int(rest) : p.kblocks;
+    sg.tile = p.dp_tiles + t;
+    sg.kb0 = kb0;
+    sg.kb1 = kb1;
+    sg.slot = (kb0 == 0 && kb1 == p.kblocks) ? -1 : int(2 * blockIdx.x + (it == it0 ? 0 : 1));
+    it += kb1 - kb0;
+    return true;
+  }
+};
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
 
 __global__ void __launch_bounds__(THREADS, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // barriers: full[STAGES], empty[STAGES], acc_full[2], acc_empty[2]; then the TMEM slot
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
-  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), accb = smem_u32(bars + 2 * STAGES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
+  const uint32_t accf0 = smem_u32(bars + 2 * STAGES), acce0 = smem_u32(bars + 2 * STAGES + 2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t mt = p.m_fast ? blockIdx.x : blockIdx.y;
-  const int64_t nt = p.m_fast ? blockIdx.y : blockIdx.x;
-  const int64_t m0 = mt * BM, n0 = nt * BN;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    mbar_init(accb, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf0 + 8 * b, 1);
+      mbar_init(acce0 + 8 * b, 4);   // one arrival per epilogue warp
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)), "r"(BN));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)), "r"(2 * BN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const int kb0 = int(blockIdx.z) * p.kb_per;
-  const int nkb = max(0, min(p.kblocks, kb0 + p.kb_per) - kb0);
 
   if (warp == 0) {
     if (lane == 0) {
-      // TMA producer
-      int issued = 0;
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % STAGES;
-        if (kb >= STAGES) {
-          if (!mbar_wait(empty0 + 8 * s, ((kb / STAGES) - 1) & 1, p.err, 1)) break;
+      // TMA producer over the K blocks of every segment of this CTA
+      TcWalk w(p);
+      TcSeg sg;
+      int it = 0;
+      bool ok = true;
+      while (ok && w.next(p, sg)) {
+        int64_t m0, n0;
+        tile_origin(p, sg.tile, m0, n0);
+        for (int kb = sg.kb0; kb < sg.kb1; ++kb) {
+          const int s = it % STAGES;
+          if (it >= STAGES && !mbar_wait(empty0 + 8 * s, ((it / STAGES) - 1) & 1, p.err, 1)) {
+            ok = false;
+            break;
+          }
+          const uint32_t a_dst = smem_u32(smem + s * STAGE_BYTES);
+          mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+          tma_load_2d(a_dst, &tmA, full0 + 8 * s, kb * BK, int(m0));
+          tma_load_2d(a_dst + A_BYTES, &tmB, full0 + 8 * s, kb * BK, int(n0));
+          ++it;
         }
-        const uint32_t a_dst = smem_u32(smem + s * STAGE_BYTES);
-        const uint32_t b_dst = a_dst + A_BYTES;
-        const int xa = (kb0 + kb) * BK, xb = xa;
-        mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
-        tma_load_2d(a_dst, &tmA, full0 + 8 * s, xa, int(m0));
-        tma_load_2d(b_dst, &tmB, full0 + 8 * s, xb, int(n0));
-        ++issued;
       }
       // drain: the copies this thread issued land before the CTA can exit
-      for (int kb = std::max(0, issued - STAGES); kb < issued; ++kb)
-        mbar_wait(full0 + 8 * (kb % STAGES), (kb / STAGES) & 1, p.err, 4);
+      for (int j = max(0, it - STAGES); j < it; ++j) mbar_wait(full0 + 8 * (j % STAGES), (j / STAGES) & 1, p.err, 4);
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // MMA issuer
+      // MMA issuer: segment u accumulates into TMEM columns (u & 1) * BN
       constexpr uint32_t idesc = instr_desc();
+      TcWalk w(p);
+      TcSeg sg;
+      int it = 0, u = 0;
       bool ok = true;
-      for (int kb = 0; kb < nkb && ok; ++kb) {
-        const int s = kb % STAGES;
-        if (!mbar_wait(full0 + 8 * s, (kb / STAGES) & 1, p.err, 2)) {
+      while (ok && w.next(p, sg)) {
+        const int b = u & 1;
+        // the epilogue has drained segment u - 2 from this accumulator
+        if (u >= 2 && !mbar_wait(acce0 + 8 * b, ((u >> 1) - 1) & 1, p.err, 5)) {
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a_addr = smem_u32(smem + s * STAGE_BYTES);
-        const uint32_t b_addr = a_addr + A_BYTES;
-        const uint64_t ad = smem_desc(a_addr), bd = smem_desc(b_addr);
+        const uint32_t acc_tmem = tmem + uint32_t(b * BN);
+        for (int kb = sg.kb0; kb < sg.kb1; ++kb) {
+          const int s = it % STAGES;
+          if (!mbar_wait(full0 + 8 * s, (it / STAGES) & 1, p.err, 2)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a_addr = smem_u32(smem + s * STAGE_BYTES);
+          const uint64_t ad = smem_desc(a_addr), bd = smem_desc(a_addr + A_BYTES);
 #pragma unroll
-        for (int k = 0; k < BK / 16; ++k) {
-          const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
-          // advance 16 bf16 (32 bytes) along K inside the swizzled 128-byte rows
-          asm volatile(
-              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-              "l"(ad + uint64_t(2 * k)), "l"(bd + uint64_t(2 * k)), "r"(idesc), "r"(acc));
+          for (int k = 0; k < BK / 16; ++k) {
+            const uint32_t acc = (kb > sg.kb0 || k > 0) ? 1u : 0u;
+            // advance 16 bf16 (32 bytes) along K inside the swizzled 128-byte rows
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_tmem),
+                "l"(ad + uint64_t(2 * k)), "l"(bd + uint64_t(2 * k)), "r"(idesc), "r"(acc));
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty0 + 8 * s)
+                       : "memory");
+          ++it;
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty0 + 8 * s)
-                     : "memory");
-      }
-      if (ok) {
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(accb)
-                     : "memory");
+        if (ok)
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(accf0 + 8 * b)
+                       : "memory");
+        ++u;
       }
     }
   } else {
     // epilogue: warps 2..5 own TMEM lanes 32*(warp % 4) .. +31. Each 32 x 32 block of the
     // accumulator goes through shared memory (lane = row when read from TMEM, lane = column
-    // when stored), so that every warp store writes 32 consecutive doubles of one row
+    // when stored), so that every warp store writes 32 consecutive elements of one row
     const int q = warp & 3;
-    const bool ok = mbar_wait(accb, 0, p.err, 3);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok && nkb > 0) {
-      float* stg = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256) + q * EMU_STAGE_FLOATS;
+    float* stg = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256) + q * EMU_STAGE_FLOATS;
+    TcWalk w(p);
+    TcSeg sg;
+    int u = 0;
+    while (w.next(p, sg)) {
+      const int b = u & 1;
+      if (!mbar_wait(accf0 + 8 * b, (u >> 1) & 1, p.err, 3)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      int64_t m0, n0;
+      tile_origin(p, sg.tile, m0, n0);
       const int64_t rbase = m0 + 32 * q;
-      double* const part = p.partial ? p.partial + int64_t(blockIdx.z) * p.M * p.N : nullptr;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         uint32_t r[32];
-        const uint32_t taddr = tmem + (uint32_t(32 * q) << 16) + uint32_t(c0);
+        const uint32_t taddr = tmem + (uint32_t(32 * q) << 16) + uint32_t(b * BN + c0);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
             "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
@@ -226,35 +323,85 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 #pragma unroll
         for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = __uint_as_float(r[j]);
         __syncwarp();
-        const int64_t col = n0 + c0 + lane;
-        if (col < p.N) {
-          // batched output columns: column col of the product is column cc of batch cb
-          int64_t cb = 0, cc = col;
-          if (p.nb > 0) {
-            cb = col / p.nb;
-            cc = col - cb * p.nb;
-          }
-          for (int i = 0; i < 32; ++i) {
-            const int64_t row = rbase + i;
-            if (row >= p.M) break;
-            const double v = double(stg[i * 33 + lane]);
-            if (part) {
-              part[row * p.N + col] = v;
+        if (sg.slot >= 0) {
+          // a share of a stream-K tile: the whole 32 x 32 block into the CTA's slot
+          float* dst = p.slots + (int64_t(sg.slot) * BM + 32 * q) * BN + c0 + lane;
+          for (int i = 0; i < 32; ++i) dst[int64_t(i) * BN] = stg[i * 33 + lane];
+        } else {
+          const int64_t col = n0 + c0 + lane;
+          const int64_t left = p.M - rbase;
+          const int nrow = left <= 0 ? 0 : (left >= 32 ? 32 : int(left));
+          if (col < p.N && nrow > 0) {
+            double* cp = out_ptr(p, rbase, col);   // rows of the column are ldc apart
+            if (p.beta == 0.0) {
+              for (int i = 0; i < nrow; ++i) cp[int64_t(i) * p.ldc] = p.alpha * double(stg[i * 33 + lane]);
             } else {
-              double* cp = p.nb > 0 ? p.C + cb * p.sCb + row * p.ldc + cc : p.C + row * p.ldc + col;
-              *cp = (p.beta == 0.0) ? p.alpha * v : p.alpha * v + p.beta * *cp;
+              // independent loads of C first, so their latencies overlap
+              double cv[32];
+#pragma unroll
+              for (int i = 0; i < 32; ++i) cv[i] = i < nrow ? cp[int64_t(i) * p.ldc] : 0.0;
+#pragma unroll
+              for (int i = 0; i < 32; ++i)
+                if (i < nrow) cp[int64_t(i) * p.ldc] = p.alpha * double(stg[i * 33 + lane]) + p.beta * cv[i];
             }
           }
         }
         __syncwarp();
       }
+      // this warp has read the accumulator: the MMAs of segment u + 2 may overwrite it
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acce0 + 8 * b);
+      ++u;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN));
+  }
+}
+
+// C for the stream-K tiles that several CTAs share: block (r, y) takes rows
+// [y * FIX_ROWS, (y + 1) * FIX_ROWS) of stream-K tile r and adds the CTAs' fp32 partials in
+// CTA order (deterministic), then applies alpha and beta. The CTAs and their slots are
+// found once per block.
+constexpr int FIX_ROWS = 16;
+constexpr int TC_MAX_G = 1024;
+__global__ void __launch_bounds__(256) k_tc_sk_fixup(TcParams p, int G) {
+  __shared__ int sl[TC_MAX_G];
+  __shared__ int ns;
+  const int64_t r = blockIdx.x;
+  if (threadIdx.x == 0) {
+    const int64_t b = r * p.kblocks, e = b + p.kblocks;
+    int64_t c = b * G / p.sk_iters;   // the CTA whose range holds iteration b
+    while (c + 1 < G && sk_begin(p, c + 1, G) <= b) ++c;
+    while (c > 0 && sk_begin(p, c, G) > b) --c;
+    int n = 0;
+    if (sk_begin(p, c + 1, G) < e) {   // else one CTA had the whole tile and wrote C
+      for (int64_t cc = c; cc < G; ++cc) {
+        const int64_t beg = sk_begin(p, cc, G);
+        if (beg >= e) break;
+        sl[n++] = int(2 * cc + (beg / p.kblocks == r ? 0 : 1));
+      }
+    }
+    ns = n;
+  }
+  __syncthreads();
+  const int n = ns;
+  if (n == 0) return;
+  int64_t m0, n0;
+  tile_origin(p, p.dp_tiles + r, m0, n0);
+  const int i0 = int(blockIdx.y) * FIX_ROWS;
+  for (int t = threadIdx.x; t < FIX_ROWS * BN; t += blockDim.x) {
+    const int i = i0 + t / BN, jc = t % BN;
+    const int64_t row = m0 + i, col = n0 + jc;
+    if (row >= p.M || col >= p.N) continue;
+    double v = 0.0;
+    for (int q = 0; q < n; ++q) v += double(p.slots[(int64_t(sl[q]) * BM + i) * BN + jc]);
+    double* cp = out_ptr(p, row, col);
+    *cp = (p.beta == 0.0) ? p.alpha * v : p.alpha * v + p.beta * *cp;
   }
 }
 
@@ -279,10 +426,6 @@ __device__ __forceinline__ void emu_chunk(const EmuParams& p, int z, int& grp, i
   loc0 = (z - p.gstart[grp]) * p.ch;
   nkb = max(0, min(p.ch, (grp + 1) * p.kbp - loc0));
 }
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
 __global__ void __launch_bounds__(THREADS, 1)
 k_tc_gemm_emu(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EmuParams p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -463,14 +606,18 @@ __host__ __device__ inline SplitPattern pattern(int precision) {
   }
   return p;
 }
+// x = x0 + x1 + x2 with bfloat16 pieces of x rounded to binary32 (24 bits: the three
+// 8-bit pieces hold all of it). The rounding and the pieces use integer and binary32
+// operations only: on GB300 the binary64 pipe would bound these conversion kernels.
 __device__ __forceinline__ void split3(double x, __nv_bfloat16 out[3]) {
-  const __nv_bfloat16 h0 = __double2bfloat16(x);
-  const double r1 = x - double(__bfloat162float(h0));
-  const __nv_bfloat16 h1 = __double2bfloat16(r1);
-  const double r2 = r1 - double(__bfloat162float(h1));
+  const float xf = d2f_rn_bits(x);
+  const __nv_bfloat16 h0 = __float2bfloat16_rn(xf);
+  const float r1 = xf - __bfloat162float(h0);   // exact: h0 is within 2^-9 of xf
+  const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(h1);   // exact for the same reason
   out[0] = h0;
   out[1] = h1;
-  out[2] = __double2bfloat16(r2);
+  out[2] = __float2bfloat16_rn(r2);
 }
 struct CvtArgs {
   int64_t rows, K, Kp;   // destination rows, true K, padded K
@@ -595,13 +742,16 @@ void tc_gemm_emu_launch(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t 
   MLCC_CHECK_LAUNCH();
 }
 
-// C = alpha A B^T + beta C for bf16 K-major operands A [M][Kt], B [N][Kt] (Kt = S * Kp).
-// splits > 1 divides K over CTAs; partial must then hold splits * M * N doubles.
-void tc_gemm_split(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t M, int64_t N, int64_t Kt,
-                   double* C, int64_t ldc, double alpha, double beta, int* err, bool m_fast, int splits,
-                   double* partial, cudaStream_t s, int64_t nb = 0, int64_t sCb = 0) {
-  MLCC_REQUIRE(Kt % BK == 0, "tc_gemm: K must be a multiple of 64");
-  MLCC_REQUIRE(M < (int64_t(1) << 31) && N < (int64_t(1) << 31), "tc_gemm: size too large");
+// Bytes of workspace tc_gemm takes for its stream-K partial tiles.
+size_t tc_gemm_ws_bytes(int sm_count) { return size_t(2) * std::max(sm_count, 1) * BM * BN * 4 + 256; }
+
+// C = alpha A B^T + beta C for bf16 K-major operands A [M][Kt], B [N][Kt] (Kt = S * Kp),
+// on a persistent grid of one CTA per SM (the schedule above TcParams).
+void tc_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t M, int64_t N, int64_t Kt,
+             double* C, int64_t ldc, double alpha, double beta, int* err, bool m_fast, int sm_count,
+             Arena& ws, cudaStream_t s, int64_t nb, int64_t sCb) {
+  MLCC_REQUIRE(Kt % BK == 0 && Kt > 0, "tc_gemm: K must be a positive multiple of 64");
+  MLCC_REQUIRE(M > 0 && N > 0 && M < (int64_t(1) << 31) && N < (int64_t(1) << 31), "tc_gemm: bad size");
   ensure_smem_attr();
   CUtensorMap ma, mb;
   make_map(&ma, A, M, Kt, BM);
@@ -610,33 +760,34 @@ void tc_gemm_split(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t M, in
   p.M = M;
   p.N = N;
   p.kblocks = int(Kt / BK);
-  splits = std::max(1, std::min(splits, p.kblocks));
-  p.kb_per = (p.kblocks + splits - 1) / splits;
-  splits = (p.kblocks + p.kb_per - 1) / p.kb_per;
+  p.m_fast = m_fast ? 1 : 0;
+  p.tm = (M + BM - 1) / BM;
+  p.tn = (N + BN - 1) / BN;
+  const int64_t tiles = p.tm * p.tn;
+  int64_t G = std::min(std::max(sm_count, 1), TC_MAX_G);
+  if (tiles >= G) {
+    // whole waves data-parallel; the last full wave and the remainder stream-K
+    p.dp_tiles = tiles % G == 0 ? tiles : (tiles / G - 1) * G;
+  } else {
+    // fewer tiles than SMs: all stream-K, at least 8 K blocks per CTA
+    p.dp_tiles = 0;
+    G = std::max<int64_t>(1, std::min<int64_t>(G, tiles * p.kblocks / 8));
+  }
+  p.sk_iters = (tiles - p.dp_tiles) * p.kblocks;
   p.C = C;
   p.ldc = ldc;
   p.alpha = alpha;
   p.beta = beta;
-  p.partial = splits > 1 ? partial : nullptr;
-  MLCC_REQUIRE(splits == 1 || partial, "tc_gemm: split-K needs a partial buffer");
   p.err = err;
-  p.m_fast = m_fast ? 1 : 0;
   p.nb = nb;
   p.sCb = sCb;
-  MLCC_REQUIRE(nb == 0 || splits == 1, "tc_gemm: batched output columns without split-K");
-  const int64_t tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
-  dim3 grid = m_fast ? dim3(unsigned(tm), unsigned(tn), unsigned(splits))
-                     : dim3(unsigned(tn), unsigned(tm), unsigned(splits));
-  MLCC_REQUIRE((m_fast ? tn : tm) < 65536 && splits < 65536, "tc_gemm: grid too large");
-  k_tc_gemm<<<grid, THREADS, SMEM_BYTES_EMU, s>>>(ma, mb, p);
+  p.slots = p.sk_iters > 0 ? ws.get<float>(size_t(2) * G * BM * BN) : nullptr;
+  k_tc_gemm<<<unsigned(G), THREADS, SMEM_BYTES_EMU, s>>>(ma, mb, p);
   MLCC_CHECK_LAUNCH();
-  if (splits > 1) reduce_partials(partial, splits, M, N, C, ldc, alpha, beta, s);
-}
-
-void tc_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t M, int64_t N, int64_t Kt,
-             double* C, int64_t ldc, double alpha, double beta, int* err, bool m_fast,
-             cudaStream_t s) {
-  tc_gemm_split(A, B, M, N, Kt, C, ldc, alpha, beta, err, m_fast, 1, nullptr, s);
+  if (p.sk_iters > 0) {
+    k_tc_sk_fixup<<<dim3(unsigned(tiles - p.dp_tiles), BM / FIX_ROWS), 256, 0, s>>>(p, int(G));
+    MLCC_CHECK_LAUNCH();
+  }
 }
 
 void cvt_operand(const double* src, int64_t ld, int64_t rows, int64_t K, bool transpose, bool u_mode,
@@ -710,6 +861,7 @@ void operand_cache_clear(OperandCache* c) {
   for (void* b : c->blocks) cudaFree(b);
   c->blocks.clear();
   c->entries.clear();
+  c->perms.clear();
 }
 void operand_cache_free(OperandCache* c) {
   operand_cache_clear(c);
@@ -760,7 +912,7 @@ bool gemm_tc(const Gemm& g, int precision, Arena& ws, cudaStream_t s, int sm_cou
   const int64_t N = flat_n ? g.N * g.batch : g.N;
   const SplitPattern pt = pattern(precision);
   const int64_t Kp = pad64(Ktot), Kt = pt.S * Kp;
-  const size_t need = size_t(M + N) * Kt * 2 + 4 * 256;
+  const size_t need = size_t(M + N) * Kt * 2 + 4 * 256 + tc_gemm_ws_bytes(sm_count);
   if (ws.mark() + need + (size_t(1) << 22) > ws.capacity()) return false;
   Scope sc(ws);
   GOp a{};
@@ -787,17 +939,8 @@ bool gemm_tc(const Gemm& g, int precision, Arena& ws, cudaStream_t s, int sm_cou
   for (int i = 0; i < pt.S; ++i) b.piece[i] = pt.b[i];
   const __nv_bfloat16* Abf = get_operand(a, 0, g.a_const, ws, s);
   const __nv_bfloat16* Bbf = get_operand(b, 1, g.b_const, ws, s);
-  const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
-  const int64_t kblocks = Kt / BK;
-  int64_t splits = 1;
-  if (!flat_n && tiles < 2LL * std::max(sm_count, 1)) {
-    splits = std::min<int64_t>((2LL * std::max(sm_count, 1) + tiles - 1) / tiles, kblocks / 4);
-    splits = std::max<int64_t>(splits, 1);
-    while (splits > 1 && size_t(splits) * M * N * 8 + ws.mark() + (size_t(1) << 20) > ws.capacity()) splits /= 2;
-  }
-  double* partial = splits > 1 ? ws.get<double>(size_t(splits) * M * N) : nullptr;
-  tc_gemm_split(Abf, Bbf, M, N, Kt, g.C, g.ldc, g.alpha, g.beta, err, true, int(splits), partial, s,
-                flat_n ? g.N : 0, flat_n ? g.sC : 0);
+  tc_gemm(Abf, Bbf, M, N, Kt, g.C, g.ldc, g.alpha, g.beta, err, true, sm_count, ws, s, flat_n ? g.N : 0,
+          flat_n ? g.sC : 0);
   return true;
 }
 
@@ -823,7 +966,7 @@ void rank_gemm_lowp(mlcc_system* S, bool outer, const double* A, const double* B
     __nv_bfloat16* Bbf = S->ws.get<__nv_bfloat16>(size_t(dS) * Kt);
     cvt_operand(B, dS, dS, nj, true, false, S->sv, S->so, precision, false, Bbf, s);
     timed(S, "rank_gemm_tc", 2.0 * double(dS) * double(dS) * double(nj),
-          [&] { tc_gemm(Abf, Bbf, dS, dS, Kt, C, dS, alpha, beta, S->tc_err, false, s); });
+          [&] { tc_gemm(Abf, Bbf, dS, dS, Kt, C, dS, alpha, beta, S->tc_err, false, S->ctx->sm_count, S->ws, s, 0, 0); });
   } else {
     const int64_t Kp = pad64(dS), Kt = seg * Kp;
     const __nv_bfloat16* Abf = nullptr;
@@ -840,7 +983,7 @@ void rank_gemm_lowp(mlcc_system* S, bool outer, const double* A, const double* B
     cvt_operand(B, dS, dS, dS, true, false, S->sv, S->so, precision, false, Bbf, s);
     (void)b_is_u_source;
     timed(S, "rank_gemm_tc", 2.0 * double(nj) * double(dS) * double(dS),
-          [&] { tc_gemm(Abf, Bbf, nj, dS, Kt, C, dS, alpha, beta, S->tc_err, true, s); });
+          [&] { tc_gemm(Abf, Bbf, nj, dS, Kt, C, dS, alpha, beta, S->tc_err, true, S->ctx->sm_count, S->ws, s, 0, 0); });
   }
 }
 
