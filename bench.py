@@ -296,8 +296,21 @@ def run_serving(args):
     def progress(what):
         print(f"[serving] {time.perf_counter() - t_start:8.1f} s  {what}", file=sys.stderr, flush=True)
 
-    with mp.get_context("spawn").Pool(max(1, min(len(specs), len(os.sched_getaffinity(0)) // 4))) as pool:
-        systems = pool.map(_make_system, specs)
+    # each worker's BLAS gets its share of the cores (oversubscribed BLAS threads spin)
+    cores = len(os.sched_getaffinity(0))
+    workers = max(1, min(len(specs), cores // 4))
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = str(max(1, cores // workers))
+    try:
+        with mp.get_context("spawn").Pool(workers) as pool:
+            systems = pool.map(_make_system, specs)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
     progress(f"{len(systems)} synthetic systems drawn")
     arrivals = serving_arrivals(len(specs), rate=args.rate)
     import torch

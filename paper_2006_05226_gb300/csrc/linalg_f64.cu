@@ -525,6 +525,38 @@ __global__ void k_permute(PP p) {
     p.dst[dof] = (p.beta == 0.0) ? v : v + p.beta * p.dst[dof];
   }
 }
+// Element index below 2^31 and offsets below 2^32: the index digits come from division by
+// invariant integers (Granlund and Montgomery, 1994: q = (umulhi(m, n) + n) >> l with
+// l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, exact for n < 2^31), and a plain copy
+// (alpha 1, beta 0) does no binary64 arithmetic.
+struct PPF {
+  int nd;
+  uint32_t dims[MAXD], magic[MAXD], shift[MAXD], ss[MAXD], ds[MAXD];
+  uint32_t total;
+  double alpha, beta;
+  const double* src;
+  double* dst;
+};
+template <bool COPY>
+__global__ void k_permute_fast(PPF p) {
+  const uint32_t st = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < p.total; i += st) {
+    uint32_t rem = i, so = 0, dof = 0;
+    for (int d = p.nd - 1; d >= 0; --d) {
+      const uint32_t q = (__umulhi(p.magic[d], rem) + rem) >> p.shift[d];
+      const uint32_t x = rem - q * p.dims[d];
+      rem = q;
+      so += x * p.ss[d];
+      dof += x * p.ds[d];
+    }
+    if (COPY) {
+      p.dst[dof] = p.src[so];
+    } else {
+      const double v = (p.alpha == 0.0) ? 0.0 : p.alpha * p.src[so];
+      p.dst[dof] = (p.beta == 0.0) ? v : v + p.beta * p.dst[dof];
+    }
+  }
+}
 }  // namespace
 
 void permute_f64(int nd, const int64_t* dims, const double* src, const int64_t* src_strides,
@@ -556,7 +588,27 @@ void permute_f64(int nd, const int64_t* dims, const double* src, const int64_t* 
   bool small = p.total + int64_t(blocks) * 256 < (int64_t(1) << 32) && smax < (int64_t(1) << 32) &&
                dmax < (int64_t(1) << 32);
   for (int d = 0; d < nd; ++d) small = small && src_strides[d] >= 0 && dst_strides[d] >= 0;
-  if (small) k_permute<uint32_t><<<blocks, 256, 0, s>>>(p);
+  if (small && p.total + int64_t(blocks) * 256 < (int64_t(1) << 31)) {
+    PPF f;
+    f.nd = nd;
+    for (int d = 0; d < nd; ++d) {
+      const uint64_t dv = uint64_t(dims[d]);
+      uint32_t l = 0;
+      while ((uint64_t(1) << l) < dv) ++l;
+      f.dims[d] = uint32_t(dv);
+      f.magic[d] = uint32_t(((uint64_t(1) << 32) * ((uint64_t(1) << l) - dv)) / dv + 1);
+      f.shift[d] = l;
+      f.ss[d] = uint32_t(src_strides[d]);
+      f.ds[d] = uint32_t(dst_strides[d]);
+    }
+    f.total = uint32_t(p.total);
+    f.alpha = alpha;
+    f.beta = beta;
+    f.src = src;
+    f.dst = dst;
+    if (alpha == 1.0 && beta == 0.0) k_permute_fast<true><<<blocks, 256, 0, s>>>(f);
+    else k_permute_fast<false><<<blocks, 256, 0, s>>>(f);
+  } else if (small) k_permute<uint32_t><<<blocks, 256, 0, s>>>(p);
   else k_permute<int64_t><<<blocks, 256, 0, s>>>(p);
   MLCC_CHECK_LAUNCH();
 }

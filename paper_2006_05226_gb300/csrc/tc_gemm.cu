@@ -9,7 +9,7 @@
 // accumulators and releases stages with tcgen05.commit; four epilogue warps read the other
 // accumulator with tcgen05.ld and write C through a shared-memory transpose (coalesced row
 // segments) while the next tile's MMAs run. Whole waves of tiles run data-parallel, the
-// last one stream-K (K ranges of equal length per CTA, partial tiles combined after).
+// remaining tiles stream-K (K ranges of equal length per CTA, partial tiles combined after).
 // Every mbarrier wait is bounded: on timeout the thread records an error flag and the CTA
 // winds down (freeing its TMEM) instead of spinning.
 //
@@ -103,10 +103,11 @@ __host__ __device__ constexpr uint32_t instr_desc() {
 
 // Persistent schedule: G CTAs, one per SM. Tiles [0, dp_tiles) run data-parallel (CTA c
 // takes tiles c, c + G, ...; dp_tiles is a multiple of G). The remaining tiles run
-// stream-K: their K-block iterations, tile after tile, are cut into G equal ranges, one
-// per CTA, so the last wave has no idle SMs. A tile that two or more CTAs share is written
-// by each of them as an fp32 partial into a slot of its own (2c for the first tile of the
-// range of CTA c, 2c + 1 for its last) and k_tc_sk_fixup adds the partials in CTA order.
+// stream-K: their K-block iterations, tile after tile, are cut into sk_ctas equal ranges,
+// one for each of CTAs 0 .. sk_ctas - 1 after their data-parallel tiles, so no SM idles
+// through a partial last wave. A tile that two or more CTAs share is written by each of
+// them as an fp32 partial into a slot of its own (2c for the first tile of the range of
+// CTA c, 2c + 1 for its last) and k_tc_sk_fixup adds the partials in CTA order.
 // Each CTA runs its segments through two TMEM accumulators in turn, so the epilogue of one
 // tile overlaps the MMAs of the next.
 struct TcParams {
@@ -116,6 +117,7 @@ struct TcParams {
   int64_t tm, tn;   // tile rows, tile columns
   int64_t dp_tiles; // data-parallel tiles
   int64_t sk_iters; // K-block iterations of the stream-K tiles
+  int sk_ctas;      // CTAs that share them
   double* C;
   int64_t ldc;
   double alpha, beta;
@@ -125,8 +127,8 @@ struct TcParams {
   // C + b * sCb + row * ldc + c (a batch of products that share A, flattened along N)
   int64_t nb, sCb;
 };
-__host__ __device__ __forceinline__ int64_t sk_begin(const TcParams& p, int64_t c, int64_t G) {
-  return c * p.sk_iters / G;
+__host__ __device__ __forceinline__ int64_t sk_begin(const TcParams& p, int64_t c) {
+  return c >= p.sk_ctas ? p.sk_iters : c * p.sk_iters / p.sk_ctas;
 }
 __device__ __forceinline__ void tile_origin(const TcParams& p, int64_t tile, int64_t& m0, int64_t& n0) {
   int64_t mt, nt;
@@ -157,8 +159,8 @@ struct TcWalk {
   int64_t j, it, it0, it1;
   __device__ explicit TcWalk(const TcParams& p) {
     j = blockIdx.x;
-    it0 = sk_begin(p, blockIdx.x, gridDim.x);
-    it1 = sk_begin(p, int64_t(blockIdx.x) + 1, gridDim.x);
+    it0 = sk_begin(p, blockIdx.x);
+    it1 = sk_begin(p, int64_t(blockIdx.x) + 1);
     it = it0;
   }
   __device__ bool next(const TcParams& p, TcSeg& sg) {
@@ -369,19 +371,20 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 // found once per block.
 constexpr int FIX_ROWS = 16;
 constexpr int TC_MAX_G = 1024;
-__global__ void __launch_bounds__(256) k_tc_sk_fixup(TcParams p, int G) {
+__global__ void __launch_bounds__(256) k_tc_sk_fixup(TcParams p) {
   __shared__ int sl[TC_MAX_G];
   __shared__ int ns;
   const int64_t r = blockIdx.x;
   if (threadIdx.x == 0) {
     const int64_t b = r * p.kblocks, e = b + p.kblocks;
+    const int64_t G = p.sk_ctas;
     int64_t c = b * G / p.sk_iters;   // the CTA whose range holds iteration b
-    while (c + 1 < G && sk_begin(p, c + 1, G) <= b) ++c;
-    while (c > 0 && sk_begin(p, c, G) > b) --c;
+    while (c + 1 < G && sk_begin(p, c + 1) <= b) ++c;
+    while (c > 0 && sk_begin(p, c) > b) --c;
     int n = 0;
-    if (sk_begin(p, c + 1, G) < e) {   // else one CTA had the whole tile and wrote C
+    if (sk_begin(p, c + 1) < e) {   // else one CTA had the whole tile and wrote C
       for (int64_t cc = c; cc < G; ++cc) {
-        const int64_t beg = sk_begin(p, cc, G);
+        const int64_t beg = sk_begin(p, cc);
         if (beg >= e) break;
         sl[n++] = int(2 * cc + (beg / p.kblocks == r ? 0 : 1));
       }
@@ -764,16 +767,13 @@ void tc_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t M, int64_t 
   p.tm = (M + BM - 1) / BM;
   p.tn = (N + BN - 1) / BN;
   const int64_t tiles = p.tm * p.tn;
-  int64_t G = std::min(std::max(sm_count, 1), TC_MAX_G);
-  if (tiles >= G) {
-    // whole waves data-parallel; the last full wave and the remainder stream-K
-    p.dp_tiles = tiles % G == 0 ? tiles : (tiles / G - 1) * G;
-  } else {
-    // fewer tiles than SMs: all stream-K, at least 8 K blocks per CTA
-    p.dp_tiles = 0;
-    G = std::max<int64_t>(1, std::min<int64_t>(G, tiles * p.kblocks / 8));
-  }
+  const int64_t G = std::min(std::max(sm_count, 1), TC_MAX_G);
+  // whole waves data-parallel, the remainder stream-K over at most G CTAs with at least 8
+  // K blocks each
+  p.dp_tiles = tiles / G * G;
   p.sk_iters = (tiles - p.dp_tiles) * p.kblocks;
+  p.sk_ctas = p.sk_iters > 0 ? int(std::max<int64_t>(1, std::min<int64_t>(G, p.sk_iters / 8))) : 0;
+  const int64_t grid = p.dp_tiles > 0 ? G : p.sk_ctas;
   p.C = C;
   p.ldc = ldc;
   p.alpha = alpha;
@@ -782,10 +782,10 @@ void tc_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t M, int64_t 
   p.nb = nb;
   p.sCb = sCb;
   p.slots = p.sk_iters > 0 ? ws.get<float>(size_t(2) * G * BM * BN) : nullptr;
-  k_tc_gemm<<<unsigned(G), THREADS, SMEM_BYTES_EMU, s>>>(ma, mb, p);
+  k_tc_gemm<<<unsigned(grid), THREADS, SMEM_BYTES_EMU, s>>>(ma, mb, p);
   MLCC_CHECK_LAUNCH();
   if (p.sk_iters > 0) {
-    k_tc_sk_fixup<<<dim3(unsigned(tiles - p.dp_tiles), BM / FIX_ROWS), 256, 0, s>>>(p, int(G));
+    k_tc_sk_fixup<<<dim3(unsigned(tiles - p.dp_tiles), BM / FIX_ROWS), 256, 0, s>>>(p);
     MLCC_CHECK_LAUNCH();
   }
 }

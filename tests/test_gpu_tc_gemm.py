@@ -1,14 +1,14 @@
 """The split-bfloat16 tcgen05 GEMM (k_tc_gemm) and its persistent schedule, through mlcc_gemm.
 
-One CTA per SM runs whole waves of 128 x 256 tiles data-parallel and the rest stream-K: the
-K blocks of the remaining tiles are cut into equal ranges, one per CTA, and a tile that
-several CTAs share is summed from their fp32 partials. Integer operands with |a|, |b| <= 15
-are exact in bfloat16 and every partial sum stays below 2^24, so the product is the exact
+One CTA per SM runs whole waves of 128 x 256 tiles data-parallel and the remaining tiles
+stream-K: their K blocks are cut into equal ranges, one per CTA, and a tile that several
+CTAs share is summed from their fp32 partials. Integer operands with |a|, |b| <= 15 are
+exact in bfloat16 and every partial sum stays below 2^24, so the product is the exact
 integer product whatever the schedule: a K block counted twice, a block left out or a
 partial read from the wrong slot changes the result. The shapes hit each case of the
-schedule on the device's SM count G: tiles a multiple of G (data-parallel only), between
-G and 2G (stream-K only), above 2G with a remainder (both), fewer tiles than SMs with long
-K (several CTAs per tile), and a single tile with one K block.
+schedule on the device's SM count G: tiles a multiple of G (data-parallel only), one wave
+and a remainder, two waves and a small remainder (few tiles shared by many CTAs), fewer
+tiles than SMs with long K (stream-K only), and a single tile with one K block.
 """
 import numpy as np
 import pytest
@@ -37,18 +37,18 @@ def _shape(case, G):
     """(M, N, K) for a schedule case, with ragged edges in M, N and K."""
     if case == "dp_only":        # tiles = G
         return BM * 2 - 5, BN * (G // 2) - 7, 640
-    if case == "sk_only":        # G < tiles < 2G
+    if case == "wave_and_rest":  # G < tiles < 2G
         return BM * 3 - 1, BN * ((4 * G) // 9) - 3, 1000
-    if case == "dp_and_sk":      # tiles = 2G + 5
+    if case == "waves_and_rest":  # tiles = 2G + 5
         return BM * 1 - 9, BN * (2 * G + 5) - 11, 1000
-    if case == "few_tiles":      # 9 tiles, 33 K blocks: several CTAs share each tile
+    if case == "few_tiles":      # 9 tiles, 33 K blocks: stream-K only, several CTAs per tile
         return 300, 520, 2100
     if case == "one_block":      # one tile, one K block
         return 17, 16, 64
     raise ValueError(case)
 
 
-@pytest.mark.parametrize("case", ["dp_only", "sk_only", "dp_and_sk", "few_tiles", "one_block"])
+@pytest.mark.parametrize("case", ["dp_only", "wave_and_rest", "waves_and_rest", "few_tiles", "one_block"])
 @pytest.mark.parametrize("ta,tb", [(False, False), (True, True)])
 def test_integer_product_is_exact_under_every_schedule(ctx, case, ta, tb):
     from paper_2006_05226_gb300 import mlcc
@@ -57,9 +57,9 @@ def test_integer_product_is_exact_under_every_schedule(ctx, case, ta, tb):
     tiles = -(-M // BM) * -(-N // BN)
     if case == "dp_only":
         assert tiles % G == 0
-    elif case == "sk_only":
+    elif case == "wave_and_rest":
         assert G < tiles < 2 * G
-    elif case == "dp_and_sk":
+    elif case == "waves_and_rest":
         assert tiles > 2 * G and tiles % G != 0
     rng = np.random.default_rng(hash((case, ta, tb)) % 2 ** 32)
     A = rng.integers(-15, 16, size=(M, K)).astype(np.float64)
