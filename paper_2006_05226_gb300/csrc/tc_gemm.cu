@@ -102,7 +102,7 @@ __host__ __device__ constexpr uint32_t instr_desc() {
 }
 
 // Persistent schedule: G CTAs, one per SM. Tiles [0, dp_tiles) run data-parallel (CTA c
-// takes tiles c, c + G, ...; dp_tiles is a multiple of G). The remaining tiles run
+// takes tiles c, c + G, ...). The remaining tiles run
 // stream-K: their K-block iterations, tile after tile, are cut into sk_ctas equal ranges,
 // one for each of CTAs 0 .. sk_ctas - 1 after their data-parallel tiles, so no SM idles
 // through a partial last wave. A tile that two or more CTAs share is written by each of
@@ -769,11 +769,14 @@ void tc_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t M, int64_t 
   const int64_t tiles = p.tm * p.tn;
   const int64_t G = std::min(std::max(sm_count, 1), TC_MAX_G);
   // whole waves data-parallel, the remainder stream-K over at most G CTAs with at least 8
-  // K blocks each
+  // K blocks each. A remainder of three quarters of a wave or more runs data-parallel too:
+  // the idle quarter costs less than stream-K's reads, whose K offsets differ between the
+  // CTAs that share an operand tile, so that L2 does not keep them
   p.dp_tiles = tiles / G * G;
+  if (4 * (tiles - p.dp_tiles) >= 3 * G) p.dp_tiles = tiles;
   p.sk_iters = (tiles - p.dp_tiles) * p.kblocks;
   p.sk_ctas = p.sk_iters > 0 ? int(std::max<int64_t>(1, std::min<int64_t>(G, p.sk_iters / 8))) : 0;
-  const int64_t grid = p.dp_tiles > 0 ? G : p.sk_ctas;
+  const int64_t grid = p.dp_tiles > 0 ? std::min(G, p.dp_tiles) : p.sk_ctas;
   p.C = C;
   p.ldc = ldc;
   p.alpha = alpha;

@@ -64,6 +64,7 @@ __global__ void k_dots32(const TX* x, int64_t ldx, int nx, const TY* y, int64_t 
     }
 #pragma unroll
     for (int c = 0; c < DOT32_CHUNK; ++c) {
+      if (c >= kc) continue;   // kc is the same in every thread
       double v = f2d(acc[c]);
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       if (lane == 0) red[c][warp] = v;
@@ -125,11 +126,13 @@ __global__ void k_dots_block32(const TX* x, int64_t ldx, int nx, const TY* y, in
     }
 #pragma unroll
     for (int c = 0; c < DOT32_CHUNK; ++c)
+      if (c < kc) {   // kc is the same in every thread
 #pragma unroll
-      for (int j = 0; j < NY; ++j) {
-        double v = f2d(acc[c][j]);
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[c * NY + j][warp] = v;
+        for (int j = 0; j < NY; ++j) {
+          double v = f2d(acc[c][j]);
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (lane == 0) red[c * NY + j][warp] = v;
+        }
       }
     __syncthreads();
     if (threadIdx.x < kc * NY) {
@@ -187,13 +190,16 @@ __global__ void k_dots_block32_v4(const float* __restrict__ x, int64_t ldx, int 
         }
       }
     }
+    // only the kc x NY accumulators in use (kc is the same in every thread)
 #pragma unroll
     for (int c = 0; c < CH; ++c)
+      if (c < kc) {
 #pragma unroll
-      for (int j = 0; j < NY; ++j) {
-        double v = f2d(acc[c][j]);
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[c * NY + j][warp] = v;
+        for (int j = 0; j < NY; ++j) {
+          double v = f2d(acc[c][j]);
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (lane == 0) red[c * NY + j][warp] = v;
+        }
       }
     __syncthreads();
     if (threadIdx.x < kc * NY) {

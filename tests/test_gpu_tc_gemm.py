@@ -7,8 +7,9 @@ exact in bfloat16 and every partial sum stays below 2^24, so the product is the 
 integer product whatever the schedule: a K block counted twice, a block left out or a
 partial read from the wrong slot changes the result. The shapes hit each case of the
 schedule on the device's SM count G: tiles a multiple of G (data-parallel only), one wave
-and a remainder, two waves and a small remainder (few tiles shared by many CTAs), fewer
-tiles than SMs with long K (stream-K only), and a single tile with one K block.
+and a remainder, two waves and a small remainder (few tiles shared by many CTAs), one wave
+and a remainder of at least three quarters of a wave (data-parallel, last wave partial),
+fewer tiles than SMs with long K (stream-K only), and a single tile with one K block.
 """
 import numpy as np
 import pytest
@@ -41,6 +42,8 @@ def _shape(case, G):
         return BM * 3 - 1, BN * ((4 * G) // 9) - 3, 1000
     if case == "waves_and_rest":  # tiles = 2G + 5
         return BM * 1 - 9, BN * (2 * G + 5) - 11, 1000
+    if case == "wave_and_big_rest":  # tiles = G + 9G/10: the remainder runs data-parallel
+        return BM * 1 - 9, BN * (G + (9 * G) // 10) - 11, 700
     if case == "few_tiles":      # 9 tiles, 33 K blocks: stream-K only, several CTAs per tile
         return 300, 520, 2100
     if case == "one_block":      # one tile, one K block
@@ -48,7 +51,8 @@ def _shape(case, G):
     raise ValueError(case)
 
 
-@pytest.mark.parametrize("case", ["dp_only", "wave_and_rest", "waves_and_rest", "few_tiles", "one_block"])
+@pytest.mark.parametrize("case", ["dp_only", "wave_and_rest", "waves_and_rest", "wave_and_big_rest",
+                                  "few_tiles", "one_block"])
 @pytest.mark.parametrize("ta,tb", [(False, False), (True, True)])
 def test_integer_product_is_exact_under_every_schedule(ctx, case, ta, tb):
     from paper_2006_05226_gb300 import mlcc
@@ -61,6 +65,8 @@ def test_integer_product_is_exact_under_every_schedule(ctx, case, ta, tb):
         assert G < tiles < 2 * G
     elif case == "waves_and_rest":
         assert tiles > 2 * G and tiles % G != 0
+    elif case == "wave_and_big_rest":
+        assert G < tiles < 2 * G and 4 * (tiles - G) >= 3 * G
     rng = np.random.default_rng(hash((case, ta, tb)) % 2 ** 32)
     A = rng.integers(-15, 16, size=(M, K)).astype(np.float64)
     B = rng.integers(-15, 16, size=(K, N)).astype(np.float64)
