@@ -24,6 +24,7 @@
 #include "system.cuh"
 #include "tc_common.cuh"
 #include "fp_convert.cuh"
+#include "tc_schedule.h"
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -101,23 +102,15 @@ __host__ __device__ constexpr uint32_t instr_desc() {
   return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
 }
 
-// Persistent schedule: G CTAs, one per SM. Tiles [0, dp_tiles) run data-parallel (CTA c
-// takes tiles c, c + G, ...). The remaining tiles run
-// stream-K: their K-block iterations, tile after tile, are cut into sk_ctas equal ranges,
-// one for each of CTAs 0 .. sk_ctas - 1 after their data-parallel tiles, so no SM idles
-// through a partial last wave. A tile that two or more CTAs share is written by each of
-// them as an fp32 partial into a slot of its own (2c for the first tile of the range of
-// CTA c, 2c + 1 for its last) and k_tc_sk_fixup adds the partials in CTA order.
-// Each CTA runs its segments through two TMEM accumulators in turn, so the epilogue of one
-// tile overlaps the MMAs of the next.
+// Persistent schedule (tc_schedule.h): whole waves of tiles data-parallel, the remainder
+// stream-K with its shared tiles fixed up by k_tc_sk_fixup. Each CTA runs its segments
+// through two TMEM accumulators in turn, so the epilogue of one tile overlaps the MMAs of
+// the next.
 struct TcParams {
   int64_t M, N;
-  int kblocks;      // K blocks of the product
-  int m_fast;       // 1: consecutive tiles run over M
-  int64_t tm, tn;   // tile rows, tile columns
-  int64_t dp_tiles; // data-parallel tiles
-  int64_t sk_iters; // K-block iterations of the stream-K tiles
-  int sk_ctas;      // CTAs that share them
+  int m_fast;         // 1: consecutive tiles run over M
+  int64_t tm, tn;     // tile rows, tile columns
+  sched::Plan plan;   // tiles, K blocks, data-parallel tiles, stream-K share
   double* C;
   int64_t ldc;
   double alpha, beta;
@@ -127,9 +120,6 @@ struct TcParams {
   // C + b * sCb + row * ldc + c (a batch of products that share A, flattened along N)
   int64_t nb, sCb;
 };
-__host__ __device__ __forceinline__ int64_t sk_begin(const TcParams& p, int64_t c) {
-  return c >= p.sk_ctas ? p.sk_iters : c * p.sk_iters / p.sk_ctas;
-}
 __device__ __forceinline__ void tile_origin(const TcParams& p, int64_t tile, int64_t& m0, int64_t& n0) {
   int64_t mt, nt;
   if (p.m_fast) {
@@ -149,41 +139,11 @@ __device__ __forceinline__ double* out_ptr(const TcParams& p, int64_t row, int64
   }
   return p.C + row * p.ldc + col;
 }
-// one tile's K-block range [kb0, kb1) for this CTA; slot < 0: the whole tile, written to C
-struct TcSeg {
-  int64_t tile;
-  int kb0, kb1, slot;
-};
 // the CTA's segments in order (every role of the CTA walks the same list)
 struct TcWalk {
-  int64_t j, it, it0, it1;
-  __device__ explicit TcWalk(const TcParams& p) {
-    j = blockIdx.x;
-    it0 = sk_begin(p, blockIdx.x);
-    it1 = sk_begin(p, int64_t(blockIdx.x) + 1);
-    it = it0;
-  }
-  __device__ bool next(const TcParams& p, TcSeg& sg) {
-    if (j < p.dp_tiles) {
-      sg.tile = j;
-      sg.kb0 = 0;
-      sg.kb1 = p.kblocks;
-      sg.slot = -1;
-      j += gridDim.x;
-      return true;
-    }
-    if (it >= it1) return false;
-    const int64_t t = it / p.kblocks;
-    const int kb0 = int(it - t * p.kblocks);
-    const int64_t rest = it1 - it;
-    const int kb1 = rest < int64_t(p.kblocks - kb0) ? kb0 + int(rest) : p.kblocks;
-    sg.tile = p.dp_tiles + t;
-    sg.kb0 = kb0;
-    sg.kb1 = kb1;
-    sg.slot = (kb0 == 0 && kb1 == p.kblocks) ? -1 : int(2 * blockIdx.x + (it == it0 ? 0 : 1));
-    it += kb1 - kb0;
-    return true;
-  }
+  sched::Walk w;
+  __device__ explicit TcWalk(const TcParams& p) { w.start(p.plan, blockIdx.x, gridDim.x); }
+  __device__ bool next(const TcParams& p, sched::Seg& sg) { return w.next(p.plan, sg); }
 };
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -225,7 +185,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     if (lane == 0) {
       // TMA producer over the K blocks of every segment of this CTA
       TcWalk w(p);
-      TcSeg sg;
+      sched::Seg sg;
       int it = 0;
       bool ok = true;
       while (ok && w.next(p, sg)) {
@@ -252,7 +212,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       // MMA issuer: segment u accumulates into TMEM columns (u & 1) * BN
       constexpr uint32_t idesc = instr_desc();
       TcWalk w(p);
-      TcSeg sg;
+      sched::Seg sg;
       int it = 0, u = 0;
       bool ok = true;
       while (ok && w.next(p, sg)) {
@@ -299,7 +259,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     const int q = warp & 3;
     float* stg = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256) + q * EMU_STAGE_FLOATS;
     TcWalk w(p);
-    TcSeg sg;
+    sched::Seg sg;
     int u = 0;
     while (w.next(p, sg)) {
       const int b = u & 1;
@@ -375,27 +335,12 @@ __global__ void __launch_bounds__(256) k_tc_sk_fixup(TcParams p) {
   __shared__ int sl[TC_MAX_G];
   __shared__ int ns;
   const int64_t r = blockIdx.x;
-  if (threadIdx.x == 0) {
-    const int64_t b = r * p.kblocks, e = b + p.kblocks;
-    const int64_t G = p.sk_ctas;
-    int64_t c = b * G / p.sk_iters;   // the CTA whose range holds iteration b
-    while (c + 1 < G && sk_begin(p, c + 1) <= b) ++c;
-    while (c > 0 && sk_begin(p, c) > b) --c;
-    int n = 0;
-    if (sk_begin(p, c + 1) < e) {   // else one CTA had the whole tile and wrote C
-      for (int64_t cc = c; cc < G; ++cc) {
-        const int64_t beg = sk_begin(p, cc);
-        if (beg >= e) break;
-        sl[n++] = int(2 * cc + (beg / p.kblocks == r ? 0 : 1));
-      }
-    }
-    ns = n;
-  }
+  if (threadIdx.x == 0) ns = sched::fixup_slots(p.plan, r, sl, TC_MAX_G);
   __syncthreads();
   const int n = ns;
   if (n == 0) return;
   int64_t m0, n0;
-  tile_origin(p, p.dp_tiles + r, m0, n0);
+  tile_origin(p, p.plan.dp_tiles + r, m0, n0);
   const int i0 = int(blockIdx.y) * FIX_ROWS;
   for (int t = threadIdx.x; t < FIX_ROWS * BN; t += blockDim.x) {
     const int i = i0 + t / BN, jc = t % BN;
@@ -762,21 +707,13 @@ void tc_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t M, int64_t 
   TcParams p;
   p.M = M;
   p.N = N;
-  p.kblocks = int(Kt / BK);
   p.m_fast = m_fast ? 1 : 0;
   p.tm = (M + BM - 1) / BM;
   p.tn = (N + BN - 1) / BN;
   const int64_t tiles = p.tm * p.tn;
   const int64_t G = std::min(std::max(sm_count, 1), TC_MAX_G);
-  // whole waves data-parallel, the remainder stream-K over at most G CTAs with at least 8
-  // K blocks each. A remainder of three quarters of a wave or more runs data-parallel too:
-  // the idle quarter costs less than stream-K's reads, whose K offsets differ between the
-  // CTAs that share an operand tile, so that L2 does not keep them
-  p.dp_tiles = tiles / G * G;
-  if (4 * (tiles - p.dp_tiles) >= 3 * G) p.dp_tiles = tiles;
-  p.sk_iters = (tiles - p.dp_tiles) * p.kblocks;
-  p.sk_ctas = p.sk_iters > 0 ? int(std::max<int64_t>(1, std::min<int64_t>(G, p.sk_iters / 8))) : 0;
-  const int64_t grid = p.dp_tiles > 0 ? std::min(G, p.dp_tiles) : p.sk_ctas;
+  p.plan = sched::plan(tiles, Kt / BK, G);
+  const int64_t grid = p.plan.grid;
   p.C = C;
   p.ldc = ldc;
   p.alpha = alpha;
@@ -784,11 +721,11 @@ void tc_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t M, int64_t 
   p.err = err;
   p.nb = nb;
   p.sCb = sCb;
-  p.slots = p.sk_iters > 0 ? ws.get<float>(size_t(2) * G * BM * BN) : nullptr;
+  p.slots = p.plan.sk_iters > 0 ? ws.get<float>(size_t(2) * G * BM * BN) : nullptr;
   k_tc_gemm<<<unsigned(grid), THREADS, SMEM_BYTES_EMU, s>>>(ma, mb, p);
   MLCC_CHECK_LAUNCH();
-  if (p.sk_iters > 0) {
-    k_tc_sk_fixup<<<dim3(unsigned(tiles - p.dp_tiles), BM / FIX_ROWS), 256, 0, s>>>(p);
+  if (p.plan.sk_iters > 0) {
+    k_tc_sk_fixup<<<dim3(unsigned(tiles - p.plan.dp_tiles), BM / FIX_ROWS), 256, 0, s>>>(p);
     MLCC_CHECK_LAUNCH();
   }
 }
