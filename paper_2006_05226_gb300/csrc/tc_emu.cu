@@ -167,7 +167,20 @@ struct EmuRed {
   int64_t ldc;
   int64_t n0;              // first output column of the panel
   int64_t nb, sCb;         // batched output columns (nb > 0): column b nb + c at C + b sCb + c
+  // element index below 2^31: t / Nw and col / nb by division by invariant integers
+  // (Granlund and Montgomery, 1994: q = (umulhi(m, n) + n) >> l, exact for n < 2^31)
+  int small;
+  uint32_t nw_magic, nw_shift, nb_magic, nb_shift;
 };
+__device__ __forceinline__ uint32_t div_inv(uint32_t n, uint32_t magic, uint32_t shift) {
+  return (__umulhi(magic, n) + n) >> shift;
+}
+// x 2^e: a multiplication by the power of two while it is a normal binary64 number (the
+// same correctly rounded result as ldexp), ldexp beyond
+__device__ __forceinline__ double scale_pow2(double x, int e) {
+  if (e >= -1022 && e <= 1023) return x * __longlong_as_double(static_cast<long long>(e + 1023) << 52);
+  return ldexp(x, e);
+}
 // C = alpha 2^(E_m + E_n - 2F + 7 (S - 1)) T + beta C with T = sum_g 2^(7 (S - 1 - g)) G_g,
 // G_g the integer sum of group g's chunks; T is held exactly as hi 2^28 + lo (both exact in
 // binary64 while K <= 2^17) and rounded once.
@@ -175,7 +188,14 @@ __global__ void k_emu_reduce(EmuRed r) {
   const int64_t total = r.M * r.Nw, plane = r.M * r.ldp;
   for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
        t += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t m = t / r.Nw, n = t - m * r.Nw;
+    int64_t m, n;
+    if (r.small) {
+      m = div_inv(uint32_t(t), r.nw_magic, r.nw_shift);
+      n = t - m * r.Nw;
+    } else {
+      m = t / r.Nw;
+      n = t - m * r.Nw;
+    }
     const float* p = r.P + m * r.ldp + n;
     long long hi = 0, lo = 0;
 #pragma unroll
@@ -192,11 +212,11 @@ __global__ void k_emu_reduce(EmuRed r) {
       v = __longlong_as_double(0x7FF8000000000000LL);
     } else {
       v = fma(static_cast<double>(hi), double(1LL << EMU_HI), static_cast<double>(lo));
-      v = ldexp(v, ea + eb - 2 * EMU_F + EMU_BITS * (EMU_S - 1));
+      v = scale_pow2(v, ea + eb - 2 * EMU_F + EMU_BITS * (EMU_S - 1));
     }
     int64_t col = r.n0 + n, cb = 0;
     if (r.nb > 0) {
-      cb = col / r.nb;
+      cb = r.small ? int64_t(div_inv(uint32_t(col), r.nb_magic, r.nb_shift)) : col / r.nb;
       col -= cb * r.nb;
     }
     double* c = r.C + cb * r.sCb + m * r.ldc + col;
@@ -204,6 +224,14 @@ __global__ void k_emu_reduce(EmuRed r) {
     if (r.beta != 0.0) out += r.beta * *c;
     *c = out;
   }
+}
+
+// magic number and shift of the division by d (1 <= d < 2^31) for dividends below 2^31
+void div_inv_consts(int64_t d, uint32_t* magic, uint32_t* shift) {
+  uint32_t l = 0;
+  while ((uint64_t(1) << l) < uint64_t(d)) ++l;
+  *magic = uint32_t(((uint64_t(1) << 32) * ((uint64_t(1) << l) - uint64_t(d))) / uint64_t(d) + 1);
+  *shift = l;
 }
 
 int grid_for(int64_t total, int threads) {
@@ -376,7 +404,15 @@ bool gemm_emu(const Gemm& g, Arena& ws, cudaStream_t s, int sm_count, int* err) 
     r.n0 = n0;
     r.nb = P.nb;
     r.sCb = P.sCb;
-    k_emu_reduce<<<grid_for(M * nw, 256), 256, 0, s>>>(r);
+    // 32-bit index arithmetic when every element index, grid stride and batched column fits
+    const int64_t blocks = grid_for(M * nw, 256);
+    r.small = (M * nw + blocks * 256 < (int64_t(1) << 31) && n0 + nw < (int64_t(1) << 31)) ? 1 : 0;
+    r.nw_magic = r.nw_shift = r.nb_magic = r.nb_shift = 0;
+    if (r.small) {
+      div_inv_consts(nw, &r.nw_magic, &r.nw_shift);
+      if (P.nb > 0) div_inv_consts(P.nb, &r.nb_magic, &r.nb_shift);
+    }
+    k_emu_reduce<<<unsigned(blocks), 256, 0, s>>>(r);
     MLCC_CHECK_LAUNCH();
   }
   return true;
